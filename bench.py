@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled LBM + Stokeslet-fit Langevin step on GB300.
+
+One step = one full pass of the hot path: particle gather / Stokeslet fit /
+Philox random force / Langevin update / reaction-force accumulation, VACF
+accumulation (lag 5000), fused pull-stream + BGK collision over the whole
+lattice, and the body-force term at the particle nodes.
+
+Default workload: 256^3 periodic box (FP32 deviation storage), tau = 0.8,
+16384 Brownian particles (M = 10, gamma = 0.5, kT = 1e-4, uniformly random
+positions, Maxwellian velocities), VACF to lag 5000.  value = lattice
+updates per second (MLUPS) over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbp|reference]
+
+Under torchrun (N > 1) every rank runs its own replica box (replicas only, no
+collective in the step) and the timing is the max over ranks.
+--impl reference times the FP64 CPU oracle on this host's cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1909_13412_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "MLUPS and % HBM roofline per GB300 at fixed accuracy vs FP64 oracle; plain vs BF16/batched"
+BYTES_PER_NODE = 2 * 15 * 4  # FP32 deviation storage: 15 loads + 15 stores per node update
+K3_SOURCE = os.path.join(ROOT, "paper_1909_13412_gb300", "csrc", "lbm_kernels.cu")
+K3_PROFILE = os.path.join(ROOT, "profiles", "stream_collide_256.md")
+VACF_LAG = 5000
+LAUNCHES_PER_STEP = 5  # particles, vacf corr, vacf reduce, stream-collide, apply
+
+
+def workload(name):
+    return {"brownian_256": wl.BROWNIAN_256, "brownian_128": wl.BROWNIAN_128,
+            "brownian_64": wl.BROWNIAN_64}[name]
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per stream-collide launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    if not os.path.exists(K3_PROFILE):
+        return None
+    text = open(K3_PROFILE).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_launch_256:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_b):
+        return None
+    sha = hashlib.sha256(open(K3_SOURCE, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def oracle_setup(w, ps):
+    import oracle
+    nz, ny, nx = w.shape_zyx
+    o = oracle.Sim(nx, ny, nz, w.tau)
+    o.add_particles(ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    o.set_params(kT=w.kT, seed=w.seed_noise)
+    return o
+
+
+def cpu_baseline(w, ps, target_s=10.0):
+    import oracle
+    o = oracle_setup(w, ps)
+    t0 = time.perf_counter()
+    o.step(1)  # warm-up (first touch of the arrays)
+    t1 = time.perf_counter() - t0
+    steps = int(min(50, max(1, target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": w.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps (after 1 warm-up step) of the {w.name} workload "
+                      f"({w.nodes} nodes, {w.n_particles} particles; VACF accumulation not included)"}
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    ps = w.particles()
+    o = oracle_setup(w, ps)
+    t0 = time.perf_counter()
+    o.step(max(1, args.warmup))
+    t_warm = (time.perf_counter() - t0) / max(1, args.warmup)
+    # bound the timed CPU work to ~2 minutes whatever --steps asks for
+    steps = int(max(1, min(args.steps, 120.0 / max(t_warm, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    value = w.nodes * steps / dt / 1e6
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w, world),
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} timed FP64 oracle steps of the full {w.name} workload "
+                                   f"(after {max(1, args.warmup)} warm-up steps)"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, world):
+    nz, ny, nx = w.shape_zyx
+    return {"workload": w.name, "lattice": [nx, ny, nz], "nodes_per_rank": w.nodes,
+            "particles_per_rank": w.n_particles, "tau": w.tau, "kT": w.kT, "M": w.M,
+            "gamma": w.gamma, "coupling": "stokeslet", "storage": "f32 deviation",
+            "vacf_max_lag": VACF_LAG, "parallelism": f"replicas{world}",
+            "l2": "no flush: 2 x 1.0 GB population buffers per step exceed the 129 MB L2"}
+
+
+# ---------------------------------------------------------------------------- GPU run
+def run_gpu(args, w):
+    import torch
+    from paper_1909_13412_gb300 import lbp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ps = w.particles()
+    nz, ny, nx = w.shape_zyx
+    h = lbp.lbp_create(nx, ny, nz, w.tau)
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise + rank)
+    lbp.lbp_vacf_configure(h, VACF_LAG)
+
+    # warm-up, then the timed region with per-launch events around the stream-collide kernel
+    lbp.lbp_step(h, args.warmup)
+    lbp.lbp_check(h)
+    lbp.lbp_timing_enable(h, True)
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        lbp.lbp_step(h, args.steps)
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end)
+    k3_ms, k3_n = lbp.lbp_timing_read(h)
+    lbp.lbp_timing_enable(h, False)
+    lbp.lbp_check(h)
+    t = torch.tensor([ms, k3_ms / max(k3_n, 1)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, k3_avg_ms = float(t[0]), float(t[1])
+    value = world * w.nodes * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: per step the external
+    # forces go host->device and positions + velocities come back
+    n = ps.n
+    fext = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
+    r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    v_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 20))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lbp.lbp_particles_set_external_force(h, fext)
+        lbp.lbp_step(h, 1)
+        lbp.lbp_particles_read(h, r=r_h, v=v_h)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * w.nodes * e2e_steps / float(te[0]) / 1e6
+    lbp.lbp_check(h)
+    lbp.lbp_destroy(h)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_NODE * w.nodes / (k3_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(w, world),
+        "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": achieved,
+                     "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE * w.nodes,
+                     "avg_launch_ms": k3_avg_ms, "launches": k3_n},
+        "particle_updates_per_s": world * n * args.steps / (ms_max * 1e-3),
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": fext.nbytes,
+                "d2h_bytes_per_step": r_h.nbytes + v_h.nbytes, "steps": e2e_steps},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, ps)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["lbp", "reference"], default="lbp")
+    ap.add_argument("--workload", default="brownian_256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "lbp":
+        args.warmup = 3
+    w = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

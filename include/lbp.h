@@ -1,0 +1,197 @@
+/*
+ * lbp.h -- C ABI of liblbp: a D3Q15 lattice-Boltzmann fluid two-way coupled to
+ * Langevin point particles by the Stokeslet-fit friction estimate of
+ * Yoshida, Kinjo & Washizu, "Numerical simulation method for Brownian particles
+ * dispersed in incompressible fluids" (arXiv:1909.13412).
+ *
+ * Units: lattice units throughout, dx = dt = C = rho0 = dV = 1.
+ *
+ * One call of lbp_step advances the system by one time step n -> n+1, which is
+ * (Section 2 of the paper, with the step order stated below):
+ *   1. streaming, Eq. 20, as a pull f_a(x) = fhat_a(x - e_a) on a periodic box;
+ *   2. moments rho~ = sum_a f_a (Eq. 12), u = sum_a e_a f_a (Eq. 13);
+ *   3. for every particle, the friction force F_H from the least-squares fit of
+ *      the Stokeslet flow of Eq. 8 to u - V at the eight corners of the cell
+ *      holding r_i, F_H = gamma U_inf e^N (Section 2.1 with Eq. 7);
+ *   4. the random force F_R = sqrt(2 gamma kT) xi (Eqs. 4-5), xi from a
+ *      Philox-4x64-10 stream keyed by (seed) and counted by (step, particle);
+ *   5. the reaction force -F_H spread onto the eight corners with trilinear
+ *      weights of r_i^n (Eq. 9);
+ *   6. the Langevin update V += F_H + F_R + F_ext over M, r += V (Eqs. 1-2,
+ *      semi-implicit Euler, periodic wrap);
+ *   7. the BGK collision with body force (Eqs. 14, 15, 17, 18, 19):
+ *      fhat_a = f_a + (f^eq_a - f_a)/tau + 3 w_a F.e_a.
+ * The state kept between steps is the post-collision fhat.
+ *
+ * Populations: D3Q15 in this order (e_x, e_y, e_z), weights w:
+ *   0 ( 0, 0, 0) 2/9;  1 ( 1, 0, 0)  2 (-1, 0, 0)  3 ( 0, 1, 0)  4 ( 0,-1, 0)
+ *   5 ( 0, 0, 1)  6 ( 0, 0,-1) 1/9;  7 ( 1, 1, 1)  8 (-1,-1,-1)  9 ( 1, 1,-1)
+ *   10 (-1,-1, 1) 11 ( 1,-1, 1) 12 (-1, 1,-1) 13 (-1, 1, 1) 14 ( 1,-1,-1) 1/72.
+ * Field arrays exchanged through this ABI are FP64, structure of arrays with x
+ * fastest: f[a][z][y][x] (15 * N values, N = nx*ny*nz), rho[z][y][x],
+ * u[k][z][y][x] (k = x, y, z component; 3 * N values).  Particle arrays are
+ * FP64, array of structures: r[i][k], v[i][k] (3 * n values), in insertion
+ * order (particle ids are 0, 1, ... in the order of lbp_particles_add calls).
+ *
+ * Memory and streams: the library owns its device state (allocated at create
+ * and at particles_add).  Every pointer passed in is owned by the caller; it is
+ * a host pointer if the call's on_device argument is 0, else a device pointer
+ * on the current device.  All work is ordered after the work already queued on
+ * the stream given to lbp_create, and later work on that stream is ordered
+ * after it.  Calls that take host pointers return after their copies finish;
+ * calls that take device pointers are asynchronous with respect to the host.
+ * A handle must not be used from two host threads at once.
+ *
+ * Errors: every call returns an lbp_status; nothing is thrown across the ABI.
+ * lbp_last_error() returns a message for the last failing call of the calling
+ * thread.  Arguments are validated before any work is queued: an invalid call
+ * changes nothing.
+ */
+#ifndef LBP_H
+#define LBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBP_OK = 0,
+    LBP_EINVAL = 1,   /* bad argument (size, tau <= 1/2, radius, null pointer, ...) */
+    LBP_ENOMEM = 2,   /* device allocation failed */
+    LBP_ECUDA = 3,    /* a CUDA call failed; the message names it */
+    LBP_ETIMEOUT = 4, /* a bounded device wait ran out */
+    LBP_ENAN = 5,     /* a particle velocity or position became non-finite */
+    LBP_ESTATE = 6,   /* call not valid in the current state */
+    LBP_ERANGE = 7    /* a reaction force exceeded the fixed-point range (|F| >= 64) */
+} lbp_status;
+
+/* Storage of the populations on the device.  Arithmetic is FP32 in every case;
+ * the stored quantity is the deviation f_a - w_a from the rest state.          */
+typedef enum {
+    LBP_F32 = 0
+} lbp_precision;
+
+/* Friction model. STOKESLET is the paper's method (Eq. 8); POINTWISE is Eq. 7
+ * with u(r_i) interpolated trilinearly from the same eight corners; BROWNIAN is
+ * Eq. 6 (F_H = -gamma V, fluid not coupled).                                    */
+typedef enum {
+    LBP_STOKESLET = 0,
+    LBP_POINTWISE = 1,
+    LBP_BROWNIAN = 2
+} lbp_coupling;
+
+typedef struct {
+    int nx, ny, nz;  /* periodic box, each >= 1; nx*ny*nz <= 2^31 - 1          */
+    double tau;      /* BGK relaxation time (Eq. 15), > 1/2: nu = (tau-1/2)/3   */
+    int precision;   /* lbp_precision                                           */
+} lbp_lattice_desc;
+
+typedef struct {
+    double kT;              /* thermal energy; sigma^2 = 2 gamma kT (Eq. 5); >= 0    */
+    uint64_t seed;          /* Philox key word 0                                     */
+    int mode;               /* lbp_coupling                                          */
+    int fit_exclude_inside; /* 1: corners with r_p < R are left out of the fit       */
+} lbp_particle_params;
+
+typedef struct lbp_sim lbp_sim;
+
+/* Create a periodic box with the fluid at rest (f_a = w_a, rho~ = 1) and no
+ * particles.  stream: a cudaStream_t (NULL = the legacy default stream).
+ * Section 2.2 (Eqs. 12-20).                                                    */
+lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out);
+
+/* Free every device resource of the handle.  NULL is accepted.               */
+lbp_status lbp_destroy(lbp_sim *sim);
+
+/* Replace the stored post-collision populations fhat with f ([15][nz][ny][nx]
+ * FP64).  Eq. 19 output state.                                                 */
+lbp_status lbp_set_populations(lbp_sim *sim, const double *f, int on_device);
+
+/* Read the stored post-collision populations fhat into f ([15][nz][ny][nx]).  */
+lbp_status lbp_read_populations(lbp_sim *sim, double *f, int on_device);
+
+/* Moments of the streamed populations f^{n+1}(x) = fhat(x - e_a), i.e. the
+ * fields the particles see at the next step: rho~ (Eq. 12), u (Eq. 13) and
+ * p = rho~/3 (pressure, Section 2.2).  Any of rho, u, p may be NULL.            */
+lbp_status lbp_read_fields(lbp_sim *sim, double *rho, double *u, double *p, int on_device);
+
+/* Append n particles (ids continue from the current count).  r in [0, L) per
+ * component; mass > 0; gamma >= 0; radius > 0 (radius may be NULL: then
+ * R = gamma / (6 pi nu), Stokes' law with nu = (tau - 1/2)/3).  Section 2.1.  */
+lbp_status lbp_particles_add(lbp_sim *sim, int n, const double *r, const double *v,
+                             const double *mass, const double *gamma, const double *radius,
+                             int on_device);
+
+/* Coupling parameters for all particles (Sections 2.1; Eqs. 4-8).            */
+lbp_status lbp_particles_set_params(lbp_sim *sim, const lbp_particle_params *params);
+
+/* External force per particle (adds to Eq. 1; NULL = zero) and pinned flags
+ * (1 = V and r are held fixed, the particle still exerts its reaction force;
+ * NULL = none pinned).                                                          */
+lbp_status lbp_particles_set_external_force(lbp_sim *sim, const double *f_ext,
+                                            const uint8_t *pinned, int on_device);
+
+/* Overwrite positions and/or velocities (either may be NULL).                */
+lbp_status lbp_particles_set_state(lbp_sim *sim, const double *r, const double *v, int on_device);
+
+/* Read positions, velocities and the last step's F_H and F_R (any may be NULL). */
+lbp_status lbp_particles_read(lbp_sim *sim, double *r, double *v, double *f_h, double *f_r,
+                              int on_device);
+
+/* Cell of each particle and the trilinear weights of its eight corners as the
+ * device computes them (Eq. 9 spreading): base[i][k] = floor(r_i,k) (int32,
+ * [n][3]); weights[i][p] for corner p = cx + 2 cy + 4 cz ([n][8] FP64).       */
+lbp_status lbp_particles_read_cells(lbp_sim *sim, int32_t *base, double *weights, int on_device);
+
+/* Number of particles.                                                       */
+lbp_status lbp_particles_count(lbp_sim *sim, int *n);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the handle's stream).       */
+lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
+
+/* The step index n that the next step uses as its Philox counter.            */
+lbp_status lbp_set_step_index(lbp_sim *sim, int64_t step);
+lbp_status lbp_get_step_index(lbp_sim *sim, int64_t *step);
+
+/* Velocity autocorrelation (Section 3, Fig. 2): from the next step on, every
+ * step's post-update velocities are samples t = 0, 1, ...; lbp_vacf_read gives
+ * csum[k] = sum over particles i and origins t0 with t0 + k <= last sample of
+ * V_i(t0).V_i(t0+k), and counts[k] = the number of (i, t0) pairs, k = 0..max_lag.
+ * Products are formed in FP32, sums accumulated in FP64.  max_lag = -1 turns
+ * it off.                                                                       */
+lbp_status lbp_vacf_configure(lbp_sim *sim, int max_lag);
+lbp_status lbp_vacf_read(lbp_sim *sim, double *csum, int64_t *counts, int on_device);
+
+/* Wait for the handle's queued work and report device-side errors: LBP_ENAN if
+ * a particle state became non-finite, LBP_ERANGE on fixed-point overflow.     */
+lbp_status lbp_check(lbp_sim *sim);
+
+/* Use CUDA graphs for lbp_step (default 1).                                  */
+lbp_status lbp_set_use_graphs(lbp_sim *sim, int enable);
+
+/* Kernel timing: while enabled, lbp_step records CUDA events around every
+ * launch of the stream-collide kernel; lbp_timing_read waits for them and
+ * returns the summed duration (ms) and the number of launches since enable.   */
+lbp_status lbp_timing_enable(lbp_sim *sim, int enable);
+lbp_status lbp_timing_read(lbp_sim *sim, double *ms_total, int64_t *launches);
+
+/* Philox-4x64-10 block function on the device (Salmon et al., SC'11), for
+ * bit-exact checks: out[4 i + j] = word j of Philox(ctr[4 i .. 4 i + 3],
+ * key[0..1]) for i < n.  All three pointers are device pointers.              */
+lbp_status lbp_philox4x64_10(const uint64_t *ctr, const uint64_t *key, uint64_t *out,
+                             int64_t n, void *stream);
+
+/* Message of the calling thread's last failing call ("" if none).            */
+const char *lbp_last_error(void);
+
+/* ABI version: 10000 * major + 100 * minor + patch.                          */
+int lbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBP_H */

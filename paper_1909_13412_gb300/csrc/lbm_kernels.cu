@@ -1,0 +1,187 @@
+// lbm_kernels.cu -- D3Q15 lattice kernels of liblbp (sm_103a).
+//
+// Storage: 15 planes (structure of arrays, x fastest), plane stride P >= N,
+// holding the deviation g_a = fhat_a - w_a of the post-collision populations
+// from the rest state.  With sum_a w_a = 1 and sum_a w_a e_a = 0 the moments
+// of Eqs. 12-13 are rho~ - 1 = sum_a g_a and u = sum_a e_a g_a, and the
+// collision of Eqs. 15, 17 and 19 becomes, exactly,
+//     g'_a = g_a + (geq_a - g_a)/tau,
+//     geq_a = w_a [(rho~ - 1) + 3 e_a.u + 9/2 (e_a.u)^2 - 3/2 u.u],
+// so FP32 arithmetic acts on the small deviations instead of on O(0.1)
+// populations.
+#include <cuda_runtime.h>
+
+#include "lbp_internal.cuh"
+
+namespace lbp {
+
+// ---------------------------------------------------------------------------
+// Fused pull-stream + moments + BGK collision (Eqs. 20, 12, 13, 15, 17, 19).
+// One thread per node; a block walks whole x-rows (grid-stride over rows so
+// the grid is a multiple of the SM count).  The 15 loads of a node are
+// independent, so every thread keeps 60 bytes in flight.  The body force of
+// Eq. 19 is added afterwards at the few nodes next to particles
+// (particle_kernels.cu), which is the same sum because the force term does
+// not depend on f.
+// ---------------------------------------------------------------------------
+template <int BX>
+__global__ void __launch_bounds__(BX) k_stream_collide(const float *__restrict__ src,
+                                                       float *__restrict__ dst, int nx, int ny,
+                                                       int nz, long long P, float omega,
+                                                       int nchunks, long long *bump) {
+    const long long nitems = (long long)ny * nz * nchunks;
+    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const long long row = item / nchunks;
+        const int chunk = (int)(item - row * nchunks);
+        const int x = chunk * BX + threadIdx.x;
+        if (x >= nx) continue;
+        const int z = (int)(row / ny);
+        const int y = (int)(row - (long long)z * ny);
+        // source coordinate x - e for e = -1, 0, +1 (index e + 1), periodic
+        const int X[3] = {x == nx - 1 ? 0 : x + 1, x, x == 0 ? nx - 1 : x - 1};
+        const int Y[3] = {y == ny - 1 ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
+        const int Z[3] = {z == nz - 1 ? 0 : z + 1, z, z == 0 ? nz - 1 : z - 1};
+        float g[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const long long s = (long long)a * P +
+                                ((long long)Z[ez(a) + 1] * ny + Y[ey(a) + 1]) * nx + X[ex(a) + 1];
+            g[a] = __ldg(src + s);
+        }
+        float drho = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            drho += g[a];
+            if (ex(a)) ux += ex(a) > 0 ? g[a] : -g[a];
+            if (ey(a)) uy += ey(a) > 0 ? g[a] : -g[a];
+            if (ez(a)) uz += ez(a) > 0 ? g[a] : -g[a];
+        }
+        const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+        const long long d = ((long long)z * ny + y) * nx + x;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float eu = (float)ex(a) * ux + (float)ey(a) * uy + (float)ez(a) * uz;
+            const float geq = wgtf(a) * (drho + 3.f * eu + 4.5f * eu * eu - usq15);
+            dst[(long long)a * P + d] = g[a] + omega * (geq - g[a]);
+        }
+    }
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+}
+
+constexpr int SC_BX = 128;
+static int g_sc_blocks_per_sm = 0;
+
+// Occupancy of the stream-collide kernel; called once at lbp_create (outside
+// any stream capture).
+cudaError_t prepare_lbm_kernels() {
+    if (g_sc_blocks_per_sm) return cudaSuccess;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sc_blocks_per_sm,
+                                                                  k_stream_collide<SC_BX>, SC_BX, 0);
+    if (g_sc_blocks_per_sm < 1) g_sc_blocks_per_sm = 1;
+    return e;
+}
+
+cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, bool bump_step,
+                                  cudaStream_t st) {
+    constexpr int BX = SC_BX;
+    const int nchunks = (s.nx + BX - 1) / BX;
+    const long long items = (long long)s.ny * s.nz * nchunks;
+    long long grid = (long long)s.num_sms * g_sc_blocks_per_sm;
+    if (grid > items) grid = items;
+    if (grid < 1) grid = 1;
+    k_stream_collide<BX><<<(unsigned)grid, BX, 0, st>>>(src, dst, s.nx, s.ny, s.nz, s.P,
+                                                         (float)(1.0 / s.tau), nchunks,
+                                                         bump_step ? s.d_step : nullptr);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 <-> deviation storage.  f is [15][N] FP64 (the ABI layout).
+// ---------------------------------------------------------------------------
+__global__ void k_from_f64(const double *__restrict__ f, float *__restrict__ g, long long N,
+                           long long P) {
+    const long long total = (long long)Q * N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / N);
+        const long long i = t - (long long)a * N;
+        g[(long long)a * P + i] = (float)(f[t] - wgt(a));
+    }
+}
+
+__global__ void k_to_f64(const float *__restrict__ g, double *__restrict__ f, long long N,
+                         long long P) {
+    const long long total = (long long)Q * N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / N);
+        const long long i = t - (long long)a * N;
+        f[t] = wgt(a) + (double)g[(long long)a * P + i];
+    }
+}
+
+static unsigned grid_for(long long work, int threads, int num_sms) {
+    long long g = (work + threads - 1) / threads;
+    const long long cap = (long long)num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+cudaError_t launch_fill_rest(Sim &s, float *dst, cudaStream_t st) {
+    return cudaMemsetAsync(dst, 0, sizeof(float) * Q * s.P, st);
+}
+
+cudaError_t launch_from_f64(Sim &s, const double *f, float *dst, cudaStream_t st) {
+    k_from_f64<<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(f, dst, s.N, s.P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f64(Sim &s, const float *src, double *f, cudaStream_t st) {
+    k_to_f64<<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(src, f, s.N, s.P);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Moments of the streamed populations (Eqs. 12-13) and p = rho~/3, in FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_fields(const float *__restrict__ src, double *rho, double *u, double *p, int nx,
+                         int ny, int nz, long long P) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long yz = i / nx;
+        const int y = (int)(yz % ny);
+        const int z = (int)(yz / ny);
+        double drho = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            int xs = x - ex(a), ys = y - ey(a), zs = z - ez(a);
+            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+            const double g = (double)src[(long long)a * P + ((long long)zs * ny + ys) * nx + xs];
+            drho += g;
+            ux += ex(a) * g;
+            uy += ey(a) * g;
+            uz += ez(a) * g;
+        }
+        if (rho) rho[i] = 1.0 + drho;
+        if (u) {
+            u[i] = ux;
+            u[N + i] = uy;
+            u[2 * N + i] = uz;
+        }
+        if (p) p[i] = (1.0 + drho) / 3.0;
+    }
+}
+
+cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, double *p,
+                          cudaStream_t st) {
+    k_fields<<<grid_for(s.N, 256, s.num_sms), 256, 0, st>>>(src, rho, u, p, s.nx, s.ny, s.nz,
+                                                            s.P);
+    return cudaGetLastError();
+}
+
+}  // namespace lbp

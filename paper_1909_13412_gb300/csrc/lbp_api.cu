@@ -1,0 +1,737 @@
+// lbp_api.cu -- the C ABI of liblbp (declared in include/lbp.h).
+//
+// Host side of the library: argument validation, device allocation, layout
+// conversion for the ABI arrays, and the per-step launch sequence
+//
+//      s1:  k_particles (reads fhat^{n-1}) -> VACF block --------.
+//      s0:  k_stream_collide (fhat^{n-1} -> fhat^n) ----- join -> k_apply
+//
+// The particle kernel only reads the old populations and the stream-collide
+// kernel does not need the particles' forces (the body-force term is added by
+// k_apply afterwards), so the two run concurrently.  A step is captured once
+// per buffer parity into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbp_internal.cuh"
+
+namespace lbp {
+int vacf_block_samples();
+int vacf_chunk_components();
+}  // namespace lbp
+
+using namespace lbp;
+
+struct lbp_sim : public lbp::Sim {
+    std::vector<double> h_gamma, h_radius;  // host copies for parameter updates
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+lbp_status fail(lbp_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            if (e_ == cudaErrorMemoryAllocation) {                                       \
+                (void)cudaGetLastError();                                                \
+                return fail(LBP_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_));       \
+            }                                                                            \
+            return fail(LBP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));            \
+        }                                                                                \
+    } while (0)
+
+#define CHECK_SIM(s)                                                   \
+    do {                                                               \
+        if (!(s)) return fail(LBP_EINVAL, "null lbp_sim handle");      \
+    } while (0)
+
+const double kSqrt3Bound = 1.7320508075688772;  // R must stay below sqrt(3) dx (Section 2.2)
+
+lbp_status enter(lbp_sim *s) {
+    CK(cudaEventRecord(s->ev_in, s->user));
+    CK(cudaStreamWaitEvent(s->s0, s->ev_in, 0));
+    return LBP_OK;
+}
+
+lbp_status leave(lbp_sim *s) {
+    CK(cudaEventRecord(s->ev_out, s->s0));
+    CK(cudaStreamWaitEvent(s->user, s->ev_out, 0));
+    return LBP_OK;
+}
+
+void drop_graphs(lbp_sim *s) {
+    for (int i = 0; i < 2; ++i)
+        if (s->graph[i]) {
+            cudaGraphExecDestroy(s->graph[i]);
+            s->graph[i] = nullptr;
+        }
+}
+
+lbp_status stage(lbp_sim *s, size_t bytes) {
+    if (s->stage_bytes >= bytes) return LBP_OK;
+    if (s->stage) {
+        CK(cudaStreamSynchronize(s->s0));
+        cudaFree(s->stage);
+        s->stage = nullptr;
+        s->stage_bytes = 0;
+    }
+    CK(cudaMalloc(&s->stage, bytes));
+    s->stage_bytes = bytes;
+    return LBP_OK;
+}
+
+template <typename T>
+lbp_status dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    CK(cudaMalloc((void **)p, sizeof(T) * count));
+    return LBP_OK;
+}
+
+#define TRY(x)                              \
+    do {                                    \
+        lbp_status st_ = (x);               \
+        if (st_ != LBP_OK) return st_;      \
+    } while (0)
+
+bool radius_ok(double R, int exclude) {
+    if (!(R > 0.0) || !std::isfinite(R)) return false;
+    return exclude ? R < 0.5 * kSqrt3Bound : R < kSqrt3Bound;
+}
+
+double nu_of(double tau) { return (tau - 0.5) / 3.0; }
+
+// one time step on (st0, st1); st1 is forked from / joined into st0
+lbp_status enqueue_step(lbp_sim *s, bool timed) {
+    const float *src = s->f[s->cur];
+    float *dst = s->f[s->cur ^ 1];
+    if (s->np > 0) {
+        CK(cudaEventRecord(s->ev_fork, s->s0));
+        CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
+        CK(launch_particles(*s, src, s->s1));
+        CK(launch_vacf_block(*s, false, s->s1));
+        CK(cudaEventRecord(s->ev_join, s->s1));
+    }
+    if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
+    CK(launch_stream_collide(*s, src, dst, s->np == 0, s->s0));
+    if (timed) {
+        CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
+        s->ntimed += 1;
+    }
+    if (s->np > 0) {
+        CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
+        CK(launch_apply_forces(*s, dst, s->s0));
+    }
+    return LBP_OK;
+}
+
+lbp_status fold_timing(lbp_sim *s) {
+    if (s->ntimed == 0) return LBP_OK;
+    CK(cudaEventSynchronize(s->tev[2 * s->ntimed - 1]));
+    for (int i = 0; i < s->ntimed; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, s->tev[2 * i], s->tev[2 * i + 1]));
+        s->timed_ms += ms;
+    }
+    s->timed_launches += s->ntimed;
+    s->ntimed = 0;
+    return LBP_OK;
+}
+
+lbp_status capture(lbp_sim *s, int parity) {
+    cudaGraph_t g = nullptr;
+    const int saved = s->cur;
+    s->cur = parity;
+    CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
+    lbp_status st = enqueue_step(s, false);
+    cudaError_t e = cudaStreamEndCapture(s->s0, &g);
+    s->cur = saved;
+    if (st != LBP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&s->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return LBP_OK;
+}
+
+lbp_status host_to_device(lbp_sim *s, void *dst, const void *src, size_t bytes, int on_device) {
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       s->s0));
+    return LBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbp_version(void) { return 100; }
+
+const char *lbp_last_error(void) { return g_err.c_str(); }
+
+lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out) {
+    if (!desc || !out) return fail(LBP_EINVAL, "lbp_create: null argument");
+    *out = nullptr;
+    if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
+        return fail(LBP_EINVAL, "lbp_create: box sizes must be >= 1 (got %d %d %d)", desc->nx,
+                    desc->ny, desc->nz);
+    const long long N = (long long)desc->nx * desc->ny * desc->nz;
+    if (N > 2147483647ll) return fail(LBP_EINVAL, "lbp_create: nx*ny*nz = %lld exceeds 2^31-1", N);
+    if (!(desc->tau > 0.5) || !std::isfinite(desc->tau))
+        return fail(LBP_EINVAL, "lbp_create: tau must be finite and > 1/2 (nu = (tau-1/2)/3 > 0)");
+    if (desc->precision != LBP_F32)
+        return fail(LBP_EINVAL, "lbp_create: unsupported precision %d", desc->precision);
+
+    lbp_sim *s = new lbp_sim();
+    s->nx = desc->nx;
+    s->ny = desc->ny;
+    s->nz = desc->nz;
+    s->N = N;
+    s->P = (N + 63) / 64 * 64;
+    s->tau = desc->tau;
+    s->precision = desc->precision;
+    s->user = (cudaStream_t)stream;
+    s->sqrt3 = std::sqrt(3.0);
+    auto bail = [&](lbp_status st) {
+        std::string keep = g_err;
+        lbp_destroy(s);
+        g_err = keep;
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&s->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->dev);
+    if (e == cudaSuccess) e = prepare_lbm_kernels();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s0, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s1, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        fail(LBP_ECUDA, "lbp_create: %s", cudaGetErrorString(e));
+        return bail(LBP_ECUDA);
+    }
+    lbp_status st = LBP_OK;
+    for (int i = 0; i < 2 && st == LBP_OK; ++i) st = dalloc(&s->f[i], (size_t)Q * s->P);
+    if (st == LBP_OK) st = dalloc(&s->d_step, 1);
+    if (st == LBP_OK) st = dalloc(&s->d_err, 1);
+    if (st == LBP_OK) st = dalloc(&s->d_vacf, 4);
+    if (st != LBP_OK) return bail(st);
+    e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch_fill_rest(*s, s->f[i], s->s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_vacf, 0, 4 * sizeof(long long), s->s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->s0);
+    if (e != cudaSuccess) {
+        fail(LBP_ECUDA, "lbp_create: %s", cudaGetErrorString(e));
+        return bail(LBP_ECUDA);
+    }
+    *out = s;
+    return LBP_OK;
+}
+
+lbp_status lbp_destroy(lbp_sim *s) {
+    if (!s) return LBP_OK;
+    if (s->s0) cudaStreamSynchronize(s->s0);
+    if (s->s1) cudaStreamSynchronize(s->s1);
+    drop_graphs(s);
+    void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
+                    s->mass, s->gamma, s->radius, s->sig, s->pinned, s->hkey, s->hacc, s->hlist,
+                    s->hcount, s->ring, s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part,
+                    s->stage};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
+        if (s->tev[i]) cudaEventDestroy(s->tev[i]);
+    cudaEvent_t evs[] = {s->ev_in, s->ev_out, s->ev_fork, s->ev_join};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (s->s0) cudaStreamDestroy(s->s0);
+    if (s->s1) cudaStreamDestroy(s->s1);
+    delete s;
+    return LBP_OK;
+}
+
+lbp_status lbp_set_populations(lbp_sim *s, const double *f, int on_device) {
+    CHECK_SIM(s);
+    if (!f) return fail(LBP_EINVAL, "lbp_set_populations: null f");
+    TRY(enter(s));
+    float *dst = s->f[s->cur];
+    if (on_device) {
+        CK(launch_from_f64(*s, f, dst, s->s0));
+    } else {
+        TRY(stage(s, sizeof(double) * Q * s->N));
+        CK(cudaMemcpyAsync(s->stage, f, sizeof(double) * Q * s->N, cudaMemcpyHostToDevice, s->s0));
+        CK(launch_from_f64(*s, s->stage, dst, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    }
+    return leave(s);
+}
+
+lbp_status lbp_read_populations(lbp_sim *s, double *f, int on_device) {
+    CHECK_SIM(s);
+    if (!f) return fail(LBP_EINVAL, "lbp_read_populations: null f");
+    TRY(enter(s));
+    const float *src = s->f[s->cur];
+    if (on_device) {
+        CK(launch_to_f64(*s, src, f, s->s0));
+    } else {
+        TRY(stage(s, sizeof(double) * Q * s->N));
+        CK(launch_to_f64(*s, src, s->stage, s->s0));
+        CK(cudaMemcpyAsync(f, s->stage, sizeof(double) * Q * s->N, cudaMemcpyDeviceToHost, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    }
+    return leave(s);
+}
+
+lbp_status lbp_read_fields(lbp_sim *s, double *rho, double *u, double *p, int on_device) {
+    CHECK_SIM(s);
+    if (!rho && !u && !p) return LBP_OK;
+    TRY(enter(s));
+    const float *src = s->f[s->cur];
+    if (on_device) {
+        CK(launch_fields(*s, src, rho, u, p, s->s0));
+    } else {
+        TRY(stage(s, sizeof(double) * 5 * s->N));
+        double *drho = s->stage, *du = s->stage + s->N, *dp = s->stage + 4 * s->N;
+        CK(launch_fields(*s, src, rho ? drho : nullptr, u ? du : nullptr, p ? dp : nullptr, s->s0));
+        if (rho) CK(cudaMemcpyAsync(rho, drho, sizeof(double) * s->N, cudaMemcpyDeviceToHost, s->s0));
+        if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * s->N, cudaMemcpyDeviceToHost, s->s0));
+        if (p) CK(cudaMemcpyAsync(p, dp, sizeof(double) * s->N, cudaMemcpyDeviceToHost, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    }
+    return leave(s);
+}
+
+static lbp_status fetch_host(lbp_sim *s, std::vector<double> &dst, const double *src, size_t count,
+                             int on_device) {
+    dst.resize(count);
+    if (count == 0) return LBP_OK;
+    if (on_device) {
+        CK(cudaMemcpyAsync(dst.data(), src, sizeof(double) * count, cudaMemcpyDeviceToHost, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    } else {
+        std::memcpy(dst.data(), src, sizeof(double) * count);
+    }
+    return LBP_OK;
+}
+
+lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v,
+                             const double *mass, const double *gamma, const double *radius,
+                             int on_device) {
+    CHECK_SIM(s);
+    if (n < 0) return fail(LBP_EINVAL, "lbp_particles_add: n < 0");
+    if (n == 0) return LBP_OK;
+    if (!r || !v || !mass || !gamma)
+        return fail(LBP_EINVAL, "lbp_particles_add: r, v, mass and gamma are required");
+    if ((long long)s->np + n > (1 << 26))
+        return fail(LBP_EINVAL, "lbp_particles_add: more than 2^26 particles");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    CK(cudaStreamSynchronize(s->s1));
+    std::vector<double> hr, hv, hm, hg, hR;
+    TRY(fetch_host(s, hr, r, 3 * (size_t)n, on_device));
+    TRY(fetch_host(s, hv, v, 3 * (size_t)n, on_device));
+    TRY(fetch_host(s, hm, mass, n, on_device));
+    TRY(fetch_host(s, hg, gamma, n, on_device));
+    if (radius) TRY(fetch_host(s, hR, radius, n, on_device));
+    const int L[3] = {s->nx, s->ny, s->nz};
+    const double nu = nu_of(s->tau);
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            const double x = hr[3 * i + k];
+            if (!(x >= 0.0) || !(x < (double)L[k]))
+                return fail(LBP_EINVAL, "lbp_particles_add: r[%d][%d] = %g outside [0, %d)", i, k, x, L[k]);
+            if (!std::isfinite(hv[3 * i + k]))
+                return fail(LBP_EINVAL, "lbp_particles_add: v[%d][%d] is not finite", i, k);
+        }
+        if (!(hm[i] > 0.0) || !std::isfinite(hm[i]))
+            return fail(LBP_EINVAL, "lbp_particles_add: mass[%d] must be > 0", i);
+        if (!(hg[i] >= 0.0) || !std::isfinite(hg[i]))
+            return fail(LBP_EINVAL, "lbp_particles_add: gamma[%d] must be >= 0", i);
+        if (!radius) hR.push_back(hg[i] / (6.0 * M_PI * nu));
+        if (!radius_ok(hR[i], s->exclude_inside))
+            return fail(LBP_EINVAL,
+                        "lbp_particles_add: radius[%d] = %g must be > 0 and < %s dx (Section 2.2)",
+                        i, hR[i], s->exclude_inside ? "sqrt(3)/2" : "sqrt(3)");
+    }
+
+    // grow the device arrays
+    const int np_new = s->np + n;
+    if (np_new > s->cap) {
+        int cap = s->cap ? s->cap : 64;
+        while (cap < np_new) cap *= 2;
+        CK(cudaStreamSynchronize(s->s0));
+        CK(cudaStreamSynchronize(s->s1));
+        double **vec[] = {&s->r, &s->v, &s->fh, &s->fr, &s->fext};
+        for (double **pp : vec) {
+            double *nb = nullptr;
+            TRY(dalloc(&nb, 3 * (size_t)cap));
+            CK(cudaMemset(nb, 0, sizeof(double) * 3 * cap));
+            if (*pp) {
+                for (int k = 0; k < 3; ++k)
+                    CK(cudaMemcpy(nb + (size_t)k * cap, *pp + (size_t)k * s->cap,
+                                  sizeof(double) * s->np, cudaMemcpyDeviceToDevice));
+                cudaFree(*pp);
+            }
+            *pp = nb;
+        }
+        double **sca[] = {&s->mass, &s->gamma, &s->radius, &s->sig};
+        for (double **pp : sca) {
+            double *nb = nullptr;
+            TRY(dalloc(&nb, (size_t)cap));
+            CK(cudaMemset(nb, 0, sizeof(double) * cap));
+            if (*pp) {
+                CK(cudaMemcpy(nb, *pp, sizeof(double) * s->np, cudaMemcpyDeviceToDevice));
+                cudaFree(*pp);
+            }
+            *pp = nb;
+        }
+        unsigned char *np8 = nullptr;
+        TRY(dalloc(&np8, (size_t)cap));
+        CK(cudaMemset(np8, 0, cap));
+        if (s->pinned) {
+            CK(cudaMemcpy(np8, s->pinned, s->np, cudaMemcpyDeviceToDevice));
+            cudaFree(s->pinned);
+        }
+        s->pinned = np8;
+        // reaction-force hash: at least 16 slots per particle (8 corners, load <= 1/2)
+        int bits = 6;
+        while ((1ll << bits) < 16ll * cap) ++bits;
+        if (s->hkey) cudaFree(s->hkey);
+        if (s->hacc) cudaFree(s->hacc);
+        if (s->hlist) cudaFree(s->hlist);
+        if (s->hcount) cudaFree(s->hcount);
+        s->hkey = nullptr;
+        s->hacc = nullptr;
+        s->hlist = nullptr;
+        s->hcount = nullptr;
+        s->hash_bits = bits;
+        TRY(dalloc(&s->hkey, (size_t)1 << bits));
+        TRY(dalloc(&s->hacc, (size_t)3 << bits));
+        TRY(dalloc(&s->hlist, (size_t)1 << bits));
+        TRY(dalloc(&s->hcount, 2));
+        CK(launch_hash_clear(*s, s->s0));
+        s->cap = cap;
+    }
+    // upload the new particles into the SoA planes
+    std::vector<double> plane(n);
+    for (int k = 0; k < 3; ++k) {
+        for (int i = 0; i < n; ++i) plane[i] = hr[3 * i + k];
+        CK(cudaMemcpy(s->r + (size_t)k * s->cap + s->np, plane.data(), sizeof(double) * n,
+                      cudaMemcpyHostToDevice));
+        for (int i = 0; i < n; ++i) plane[i] = hv[3 * i + k];
+        CK(cudaMemcpy(s->v + (size_t)k * s->cap + s->np, plane.data(), sizeof(double) * n,
+                      cudaMemcpyHostToDevice));
+    }
+    std::vector<double> sg(n);
+    for (int i = 0; i < n; ++i) sg[i] = std::sqrt(2.0 * hg[i] * s->kT);
+    CK(cudaMemcpy(s->mass + s->np, hm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->gamma + s->np, hg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->radius + s->np, hR.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->sig + s->np, sg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    s->h_gamma.insert(s->h_gamma.end(), hg.begin(), hg.end());
+    s->h_radius.insert(s->h_radius.end(), hR.begin(), hR.end());
+    s->np = np_new;
+    // the VACF ring is laid out per particle count: adding particles turns it off
+    s->vacf_lag = -1;
+    drop_graphs(s);
+    return leave(s);
+}
+
+lbp_status lbp_particles_count(lbp_sim *s, int *n) {
+    CHECK_SIM(s);
+    if (!n) return fail(LBP_EINVAL, "lbp_particles_count: null n");
+    *n = s->np;
+    return LBP_OK;
+}
+
+lbp_status lbp_particles_set_params(lbp_sim *s, const lbp_particle_params *prm) {
+    CHECK_SIM(s);
+    if (!prm) return fail(LBP_EINVAL, "lbp_particles_set_params: null params");
+    if (!(prm->kT >= 0.0) || !std::isfinite(prm->kT))
+        return fail(LBP_EINVAL, "lbp_particles_set_params: kT must be finite and >= 0");
+    if (prm->mode < LBP_STOKESLET || prm->mode > LBP_BROWNIAN)
+        return fail(LBP_EINVAL, "lbp_particles_set_params: unknown coupling mode %d", prm->mode);
+    for (int i = 0; i < s->np; ++i)
+        if (!radius_ok(s->h_radius[i], prm->fit_exclude_inside))
+            return fail(LBP_EINVAL,
+                        "lbp_particles_set_params: radius[%d] = %g too large for fit_exclude_inside=%d",
+                        i, s->h_radius[i], prm->fit_exclude_inside);
+    TRY(enter(s));
+    s->kT = prm->kT;
+    s->seed = prm->seed;
+    s->mode = prm->mode;
+    s->exclude_inside = prm->fit_exclude_inside ? 1 : 0;
+    if (s->np) {
+        std::vector<double> sg(s->np);
+        for (int i = 0; i < s->np; ++i) sg[i] = std::sqrt(2.0 * s->h_gamma[i] * s->kT);
+        CK(cudaMemcpyAsync(s->sig, sg.data(), sizeof(double) * s->np, cudaMemcpyHostToDevice, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    }
+    drop_graphs(s);
+    return leave(s);
+}
+
+static lbp_status upload_vec3(lbp_sim *s, double *dst_soa, const double *src_aos, int on_device) {
+    const int n = s->np;
+    if (on_device) {
+        CK(launch_aos_to_soa(src_aos, dst_soa, n, s->cap, 0, s->s0));
+        return LBP_OK;
+    }
+    std::vector<double> plane(3 * (size_t)n);
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < n; ++i) plane[(size_t)k * n + i] = src_aos[3 * i + k];
+    for (int k = 0; k < 3; ++k)
+        CK(cudaMemcpyAsync(dst_soa + (size_t)k * s->cap, plane.data() + (size_t)k * n,
+                           sizeof(double) * n, cudaMemcpyHostToDevice, s->s0));
+    CK(cudaStreamSynchronize(s->s0));
+    return LBP_OK;
+}
+
+lbp_status lbp_particles_set_external_force(lbp_sim *s, const double *f_ext, const uint8_t *pinned,
+                                            int on_device) {
+    CHECK_SIM(s);
+    if (s->np == 0) return LBP_OK;
+    TRY(enter(s));
+    if (f_ext) {
+        TRY(upload_vec3(s, s->fext, f_ext, on_device));
+    } else {
+        CK(cudaMemsetAsync(s->fext, 0, sizeof(double) * 3 * s->cap, s->s0));
+    }
+    if (pinned) {
+        TRY(host_to_device(s, s->pinned, pinned, s->np, on_device));
+        if (!on_device) CK(cudaStreamSynchronize(s->s0));
+    } else {
+        CK(cudaMemsetAsync(s->pinned, 0, s->cap, s->s0));
+    }
+    return leave(s);
+}
+
+lbp_status lbp_particles_set_state(lbp_sim *s, const double *r, const double *v, int on_device) {
+    CHECK_SIM(s);
+    if (s->np == 0) return LBP_OK;
+    if (r) {
+        std::vector<double> hr;
+        TRY(fetch_host(s, hr, r, 3 * (size_t)s->np, on_device));
+        const int L[3] = {s->nx, s->ny, s->nz};
+        for (int i = 0; i < s->np; ++i)
+            for (int k = 0; k < 3; ++k)
+                if (!(hr[3 * i + k] >= 0.0) || !(hr[3 * i + k] < (double)L[k]))
+                    return fail(LBP_EINVAL, "lbp_particles_set_state: r[%d][%d] outside the box", i, k);
+    }
+    if (v) {
+        std::vector<double> hv;
+        TRY(fetch_host(s, hv, v, 3 * (size_t)s->np, on_device));
+        for (double x : hv)
+            if (!std::isfinite(x)) return fail(LBP_EINVAL, "lbp_particles_set_state: non-finite v");
+    }
+    TRY(enter(s));
+    if (r) TRY(upload_vec3(s, s->r, r, on_device));
+    if (v) TRY(upload_vec3(s, s->v, v, on_device));
+    return leave(s);
+}
+
+lbp_status lbp_particles_read(lbp_sim *s, double *r, double *v, double *f_h, double *f_r,
+                              int on_device) {
+    CHECK_SIM(s);
+    if (s->np == 0) return LBP_OK;
+    TRY(enter(s));
+    const double *srcs[4] = {s->r, s->v, s->fh, s->fr};
+    double *dsts[4] = {r, v, f_h, f_r};
+    if (!on_device) TRY(stage(s, sizeof(double) * 12 * (size_t)s->np));
+    for (int q = 0; q < 4; ++q) {
+        if (!dsts[q]) continue;
+        double *tgt = on_device ? dsts[q] : s->stage + (size_t)q * 3 * s->np;
+        CK(launch_soa_to_aos(srcs[q], tgt, s->np, s->cap, s->s0));
+        if (!on_device)
+            CK(cudaMemcpyAsync(dsts[q], tgt, sizeof(double) * 3 * s->np, cudaMemcpyDeviceToHost,
+                               s->s0));
+    }
+    if (!on_device) CK(cudaStreamSynchronize(s->s0));
+    return leave(s);
+}
+
+lbp_status lbp_particles_read_cells(lbp_sim *s, int32_t *base, double *weights, int on_device) {
+    CHECK_SIM(s);
+    if (!base || !weights) return fail(LBP_EINVAL, "lbp_particles_read_cells: null output");
+    if (s->np == 0) return LBP_OK;
+    TRY(enter(s));
+    if (on_device) {
+        CK(launch_cells(*s, base, weights, s->s0));
+    } else {
+        TRY(stage(s, sizeof(double) * 11 * (size_t)s->np));
+        int *db = reinterpret_cast<int *>(s->stage);
+        double *dw = s->stage + 2 * (size_t)s->np;
+        CK(launch_cells(*s, db, dw, s->s0));
+        CK(cudaMemcpyAsync(base, db, sizeof(int) * 3 * s->np, cudaMemcpyDeviceToHost, s->s0));
+        CK(cudaMemcpyAsync(weights, dw, sizeof(double) * 8 * s->np, cudaMemcpyDeviceToHost, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    }
+    return leave(s);
+}
+
+lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
+    CHECK_SIM(s);
+    if (nsteps < 0) return fail(LBP_EINVAL, "lbp_step: nsteps < 0");
+    if (nsteps == 0) return LBP_OK;
+    TRY(enter(s));
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (s->timing) {
+            if (s->ntimed == lbp::Sim::MAX_TIMED) TRY(fold_timing(s));
+            TRY(enqueue_step(s, true));
+        } else if (s->use_graphs) {
+            if (!s->graph[s->cur]) TRY(capture(s, s->cur));
+            CK(cudaGraphLaunch(s->graph[s->cur], s->s0));
+        } else {
+            TRY(enqueue_step(s, false));
+        }
+        s->cur ^= 1;
+        s->step += 1;
+    }
+    return leave(s);
+}
+
+lbp_status lbp_set_step_index(lbp_sim *s, int64_t step) {
+    CHECK_SIM(s);
+    if (step < 0) return fail(LBP_EINVAL, "lbp_set_step_index: step < 0");
+    TRY(enter(s));
+    long long v = step;
+    CK(cudaMemcpyAsync(s->d_step, &v, sizeof(long long), cudaMemcpyHostToDevice, s->s0));
+    CK(cudaStreamSynchronize(s->s0));
+    s->step = step;
+    s->vacf_lag = -1;
+    drop_graphs(s);
+    return leave(s);
+}
+
+lbp_status lbp_get_step_index(lbp_sim *s, int64_t *step) {
+    CHECK_SIM(s);
+    if (!step) return fail(LBP_EINVAL, "lbp_get_step_index: null step");
+    *step = s->step;
+    return LBP_OK;
+}
+
+lbp_status lbp_vacf_configure(lbp_sim *s, int max_lag) {
+    CHECK_SIM(s);
+    if (max_lag < -1) return fail(LBP_EINVAL, "lbp_vacf_configure: max_lag < -1");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    drop_graphs(s);
+    s->vacf_lag = -1;
+    void **bufs[] = {(void **)&s->ring, (void **)&s->vacf_sum, (void **)&s->vacf_cnt,
+                     (void **)&s->vacf_part};
+    for (void **b : bufs)
+        if (*b) {
+            cudaFree(*b);
+            *b = nullptr;
+        }
+    if (max_lag < 0) return leave(s);
+    if (s->np == 0) return fail(LBP_ESTATE, "lbp_vacf_configure: add particles first");
+    const int B = vacf_block_samples();
+    const long long ncomp = 3ll * s->np;
+    const size_t ring_bytes = sizeof(float) * (size_t)(max_lag + B) * (size_t)ncomp;
+    if (ring_bytes > ((size_t)64 << 30))
+        return fail(LBP_EINVAL, "lbp_vacf_configure: ring of %zu bytes exceeds 64 GiB", ring_bytes);
+    s->vacf_cap = max_lag + B;
+    s->vacf_nchunks = (int)((ncomp + vacf_chunk_components() - 1) / vacf_chunk_components());
+    TRY(dalloc(&s->ring, (size_t)s->vacf_cap * ncomp));
+    TRY(dalloc(&s->vacf_sum, (size_t)max_lag + 1));
+    TRY(dalloc(&s->vacf_cnt, (size_t)max_lag + 1));
+    TRY(dalloc(&s->vacf_part, (size_t)s->vacf_nchunks * (max_lag + 1)));
+    CK(cudaMemsetAsync(s->vacf_sum, 0, sizeof(double) * (max_lag + 1), s->s0));
+    CK(cudaMemsetAsync(s->vacf_cnt, 0, sizeof(long long) * (max_lag + 1), s->s0));
+    long long hv[4] = {s->step, 0, 0, 0};
+    CK(cudaMemcpyAsync(s->d_vacf, hv, sizeof(hv), cudaMemcpyHostToDevice, s->s0));
+    CK(cudaStreamSynchronize(s->s0));
+    s->vacf_lag = max_lag;
+    return leave(s);
+}
+
+lbp_status lbp_vacf_read(lbp_sim *s, double *csum, int64_t *counts, int on_device) {
+    CHECK_SIM(s);
+    if (s->vacf_lag < 0) return fail(LBP_ESTATE, "lbp_vacf_read: VACF not configured");
+    TRY(enter(s));
+    CK(launch_vacf_block(*s, true, s->s0));
+    const size_t K1 = (size_t)s->vacf_lag + 1;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (csum) CK(cudaMemcpyAsync(csum, s->vacf_sum, sizeof(double) * K1, kind, s->s0));
+    if (counts) CK(cudaMemcpyAsync(counts, s->vacf_cnt, sizeof(long long) * K1, kind, s->s0));
+    if (!on_device) CK(cudaStreamSynchronize(s->s0));
+    return leave(s);
+}
+
+lbp_status lbp_check(lbp_sim *s) {
+    CHECK_SIM(s);
+    CK(cudaStreamSynchronize(s->s0));
+    CK(cudaStreamSynchronize(s->s1));
+    int err = 0;
+    CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CK(cudaMemset(s->d_err, 0, sizeof(int)));
+        if (err & ERR_NAN) return fail(LBP_ENAN, "lbp_check: a particle velocity or position became non-finite or left the box");
+        if (err & ERR_RANGE) return fail(LBP_ERANGE, "lbp_check: a reaction force exceeded the fixed-point range");
+        return fail(LBP_ESTATE, "lbp_check: reaction-force table overflow");
+    }
+    return LBP_OK;
+}
+
+lbp_status lbp_set_use_graphs(lbp_sim *s, int enable) {
+    CHECK_SIM(s);
+    s->use_graphs = enable ? 1 : 0;
+    if (!enable) drop_graphs(s);
+    return LBP_OK;
+}
+
+lbp_status lbp_timing_enable(lbp_sim *s, int enable) {
+    CHECK_SIM(s);
+    if (enable && !s->tev[0]) {
+        for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i) CK(cudaEventCreate(&s->tev[i]));
+    }
+    if (!enable) TRY(fold_timing(s));
+    s->timing = enable ? 1 : 0;
+    s->timed_ms = 0.0;
+    s->timed_launches = 0;
+    s->ntimed = 0;
+    return LBP_OK;
+}
+
+lbp_status lbp_timing_read(lbp_sim *s, double *ms_total, int64_t *launches) {
+    CHECK_SIM(s);
+    TRY(fold_timing(s));
+    if (ms_total) *ms_total = s->timed_ms;
+    if (launches) *launches = s->timed_launches;
+    return LBP_OK;
+}
+
+lbp_status lbp_philox4x64_10(const uint64_t *ctr, const uint64_t *key, uint64_t *out, int64_t n,
+                             void *stream) {
+    if (n < 0) return fail(LBP_EINVAL, "lbp_philox4x64_10: n < 0");
+    if (n > 0 && (!ctr || !key || !out)) return fail(LBP_EINVAL, "lbp_philox4x64_10: null pointer");
+    CK(launch_philox((const unsigned long long *)ctr, (const unsigned long long *)key,
+                     (unsigned long long *)out, n, (cudaStream_t)stream));
+    return LBP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// lbp_internal.cuh -- device-side definitions shared by the liblbp translation
+// units: the D3Q15 table, the Philox-4x64-10 block function, the handle layout
+// and the kernel launchers.  Written for sm_103a (GB300).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbp.h"
+
+namespace lbp {
+
+constexpr int Q = 15;
+
+// D3Q15 velocity set in the order the ABI documents (Section 2.2, Succi's
+// fifteen-velocity set): rest, 6 faces, 8 corners; opposite pairs adjacent.
+__host__ __device__ constexpr int ex(int a) {
+    return a == 1 ? 1 : a == 2 ? -1 : (a == 7 || a == 9 || a == 11 || a == 14) ? 1
+         : (a == 8 || a == 10 || a == 12 || a == 13) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int a) {
+    return a == 3 ? 1 : a == 4 ? -1 : (a == 7 || a == 9 || a == 12 || a == 13) ? 1
+         : (a == 8 || a == 10 || a == 11 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez(int a) {
+    return a == 5 ? 1 : a == 6 ? -1 : (a == 7 || a == 10 || a == 11 || a == 13) ? 1
+         : (a == 8 || a == 9 || a == 12 || a == 14) ? -1 : 0;
+}
+// weights: 2/9 rest, 1/9 faces, 1/72 corners
+__host__ __device__ constexpr double wgt(int a) {
+    return a == 0 ? 2.0 / 9.0 : a <= 6 ? 1.0 / 9.0 : 1.0 / 72.0;
+}
+__host__ __device__ constexpr float wgtf(int a) {
+    return a == 0 ? 2.0f / 9.0f : a <= 6 ? 1.0f / 9.0f : 1.0f / 72.0f;
+}
+
+// Reaction forces are summed per node in 64-bit fixed point so that the sum
+// is exact and independent of the order in which particles add to it.
+constexpr double FIX_SCALE = 72057594037927936.0;      // 2^56
+constexpr double FIX_INV = 1.0 / 72057594037927936.0;  // 2^-56
+constexpr double FIX_LIMIT = 64.0;                     // |contribution| < 2^6
+constexpr unsigned long long HASH_EMPTY = ~0ull;
+
+// error bits in Sim::d_err
+constexpr int ERR_NAN = 1;
+constexpr int ERR_RANGE = 2;
+constexpr int ERR_HASH = 4;
+
+// ------------------------------------------------------------------ Philox
+// Philox-4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 64x64->128 multiplications with the published multipliers; the key is
+// bumped by the published Weyl constants between rounds.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const unsigned long long lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+        const unsigned long long lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+        const unsigned long long n0 = hi1 ^ c[1] ^ k0;
+        const unsigned long long n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// --------------------------------------------------------------- handle
+struct Sim {
+    int nx = 0, ny = 0, nz = 0;
+    int64_t N = 0;  // nodes
+    int64_t P = 0;  // plane stride (elements), N rounded up to 64
+    double tau = 1.0;
+    int precision = LBP_F32;
+    int dev = 0;
+    int num_sms = 0;
+
+    cudaStream_t user = nullptr;  // caller's stream
+    cudaStream_t s0 = nullptr;    // library main stream (non-blocking)
+    cudaStream_t s1 = nullptr;    // library side stream (particles, VACF)
+    cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+
+    float *f[2] = {nullptr, nullptr};  // deviation populations, 15 planes of P
+    int cur = 0;                       // f[cur] holds fhat^n
+    int64_t step = 0;                  // host mirror of the step index
+    long long *d_step = nullptr;       // device step index (Philox counter)
+    int *d_err = nullptr;
+
+    // particles, FP64 structure of arrays, 3 planes of cap for vectors
+    int np = 0, cap = 0;
+    double *r = nullptr, *v = nullptr, *fh = nullptr, *fr = nullptr, *fext = nullptr;
+    double *mass = nullptr, *gamma = nullptr, *radius = nullptr, *sig = nullptr;
+    unsigned char *pinned = nullptr;
+    double kT = 0.0;
+    unsigned long long seed = 0;
+    int mode = LBP_STOKESLET;
+    int exclude_inside = 0;
+    double sqrt3 = 0.0;
+
+    // reaction-force accumulator: open-addressing hash of node -> fixed-point force
+    int hash_bits = 0;
+    unsigned long long *hkey = nullptr;  // [H]
+    unsigned long long *hacc = nullptr;  // [3][H]
+    unsigned int *hlist = nullptr;       // [H] slots in use
+    unsigned int *hcount = nullptr;      // [2]: used slots, finished blocks
+
+    // VACF
+    int vacf_lag = -1;
+    int vacf_cap = 0;             // ring length in samples
+    float *ring = nullptr;        // [vacf_cap][3 * cap]
+    long long *d_vacf = nullptr;  // [0] t0 step, [1] samples correlated
+    double *vacf_sum = nullptr;   // [K + 1]
+    long long *vacf_cnt = nullptr;
+    double *vacf_part = nullptr;  // [nchunks][K + 1]
+    int vacf_nchunks = 0;
+
+    // scratch for host <-> device conversions
+    double *stage = nullptr;
+    size_t stage_bytes = 0;
+
+    // graphs
+    int use_graphs = 1;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    // kernel timing
+    int timing = 0;
+    int ntimed = 0;
+    static constexpr int MAX_TIMED = 4096;
+    cudaEvent_t tev[2 * MAX_TIMED] = {};
+    double timed_ms = 0.0;
+    int64_t timed_launches = 0;
+};
+
+// ------------------------------------------------------------ launchers
+// lbm_kernels.cu
+cudaError_t prepare_lbm_kernels();
+cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, bool bump_step,
+                                  cudaStream_t st);
+cudaError_t launch_fill_rest(Sim &s, float *dst, cudaStream_t st);
+cudaError_t launch_from_f64(Sim &s, const double *f, float *dst, cudaStream_t st);
+cudaError_t launch_to_f64(Sim &s, const float *src, double *f, cudaStream_t st);
+cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, double *p,
+                          cudaStream_t st);
+// particle_kernels.cu
+cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st);
+cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st);
+cudaError_t launch_hash_clear(Sim &s, cudaStream_t st);
+cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
+                              cudaStream_t st);
+cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);
+cudaError_t launch_cells(Sim &s, int *base, double *weights, cudaStream_t st);
+cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long long *key,
+                          unsigned long long *out, int64_t n, cudaStream_t st);
+// vacf_kernels.cu
+cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st);
+
+}  // namespace lbp

@@ -1,0 +1,311 @@
+"""Thin ctypes binding of liblbp (include/lbp.h), with the C function names.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of liblbp.so.  Arrays may be numpy arrays (host memory, ``on_device=0``) or
+CUDA torch tensors (device memory, ``on_device=1``); the binding checks dtype,
+size and contiguity, passes the raw pointer and raises ``LbpError`` on any
+non-zero status.  If liblbp.so has not been built the import of a function
+raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbp.so")
+
+LBP_OK, LBP_EINVAL, LBP_ENOMEM, LBP_ECUDA, LBP_ETIMEOUT, LBP_ENAN, LBP_ESTATE, LBP_ERANGE = range(8)
+LBP_F32 = 0
+LBP_STOKESLET, LBP_POINTWISE, LBP_BROWNIAN = 0, 1, 2
+Q = 15
+
+_STATUS_NAMES = {0: "LBP_OK", 1: "LBP_EINVAL", 2: "LBP_ENOMEM", 3: "LBP_ECUDA", 4: "LBP_ETIMEOUT",
+                 5: "LBP_ENAN", 6: "LBP_ESTATE", 7: "LBP_ERANGE"}
+
+
+class LbpError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        super().__init__(f"{func}: {_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lbp_lattice_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("tau", C.c_double),
+                ("precision", C.c_int)]
+
+
+class lbp_particle_params(C.Structure):
+    _fields_ = [("kT", C.c_double), ("seed", C.c_uint64), ("mode", C.c_int),
+                ("fit_exclude_inside", C.c_int)]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "lbp_create": [C.POINTER(lbp_lattice_desc), _vp, C.POINTER(_vp)],
+    "lbp_destroy": [_vp],
+    "lbp_set_populations": [_vp, _vp, C.c_int],
+    "lbp_read_populations": [_vp, _vp, C.c_int],
+    "lbp_read_fields": [_vp, _vp, _vp, _vp, C.c_int],
+    "lbp_particles_add": [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int],
+    "lbp_particles_set_params": [_vp, C.POINTER(lbp_particle_params)],
+    "lbp_particles_set_external_force": [_vp, _vp, _vp, C.c_int],
+    "lbp_particles_set_state": [_vp, _vp, _vp, C.c_int],
+    "lbp_particles_read": [_vp, _vp, _vp, _vp, _vp, C.c_int],
+    "lbp_particles_read_cells": [_vp, _vp, _vp, C.c_int],
+    "lbp_particles_count": [_vp, C.POINTER(C.c_int)],
+    "lbp_step": [_vp, C.c_int64],
+    "lbp_set_step_index": [_vp, C.c_int64],
+    "lbp_get_step_index": [_vp, C.POINTER(C.c_int64)],
+    "lbp_vacf_configure": [_vp, C.c_int],
+    "lbp_vacf_read": [_vp, _vp, _vp, C.c_int],
+    "lbp_check": [_vp],
+    "lbp_set_use_graphs": [_vp, C.c_int],
+    "lbp_timing_enable": [_vp, C.c_int],
+    "lbp_timing_read": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
+    "lbp_philox4x64_10": [_vp, _vp, _vp, C.c_int64, _vp],
+}
+
+_lib = None
+
+
+def load():
+    """Load liblbp.so; raise if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = C.CDLL(LIB_PATH)
+        for name, argtypes in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = argtypes
+            fn.restype = C.c_int
+        lib.lbp_last_error.argtypes = []
+        lib.lbp_last_error.restype = C.c_char_p
+        lib.lbp_version.argtypes = []
+        lib.lbp_version.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS) + ["lbp_last_error", "lbp_version"]
+
+
+def _call(name, *args):
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != LBP_OK:
+        raise LbpError(st, name, lib.lbp_last_error().decode())
+    return st
+
+
+# ------------------------------------------------------------------ marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype, count, name, writable=False):
+    """(pointer, on_device) of a numpy array or torch tensor of `count` elements."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        tmap = {np.float64: (torch.float64,), np.int64: (torch.int64,),
+                np.uint64: (torch.int64, getattr(torch, "uint64", torch.int64)),
+                np.uint8: (torch.uint8,), np.int32: (torch.int32,)}
+        if x.dtype not in tmap[dtype]:
+            raise TypeError(f"{name}: expected {tmap[dtype][0]}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if count is not None and x.numel() != count:
+            raise ValueError(f"{name}: expected {count} elements, got {x.numel()}")
+        return C.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    a = x
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"{name}: expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    if writable and not a.flags.writeable:
+        raise ValueError(f"{name}: array is read-only")
+    if count is not None and a.size != count:
+        raise ValueError(f"{name}: expected {count} elements, got {a.size}")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+def _same_side(*pairs):
+    sides = {d for _, d in pairs if d is not None}
+    if len(sides) > 1:
+        raise ValueError("all arrays of one call must be on the same side (host or device)")
+    return sides.pop() if sides else 0
+
+
+class Handle:
+    """Owning wrapper of an lbp_sim* with its sizes (the C calls stay the API)."""
+
+    def __init__(self, ptr, nx, ny, nz):
+        self.ptr = ptr
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.N = nx * ny * nz
+
+    @property
+    def np(self):
+        n = C.c_int()
+        _call("lbp_particles_count", self.ptr, C.byref(n))
+        return n.value
+
+    def close(self):
+        if self.ptr:
+            lbp_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ the C calls
+def lbp_version() -> int:
+    return load().lbp_version()
+
+
+def lbp_last_error() -> str:
+    return load().lbp_last_error().decode()
+
+
+def lbp_create(nx, ny, nz, tau, precision=LBP_F32, stream=None) -> Handle:
+    desc = lbp_lattice_desc(int(nx), int(ny), int(nz), float(tau), int(precision))
+    out = C.c_void_p()
+    s = C.c_void_p(stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else 0))
+    _call("lbp_create", C.byref(desc), s, C.byref(out))
+    return Handle(out, int(nx), int(ny), int(nz))
+
+
+def lbp_destroy(h: Handle):
+    if h.ptr:
+        _call("lbp_destroy", h.ptr)
+        h.ptr = None
+
+
+def lbp_set_populations(h: Handle, f):
+    p, d = _ptr(f, np.float64, Q * h.N, "f")
+    _call("lbp_set_populations", h.ptr, p, d)
+
+
+def lbp_read_populations(h: Handle, f):
+    p, d = _ptr(f, np.float64, Q * h.N, "f", writable=True)
+    _call("lbp_read_populations", h.ptr, p, d)
+    return f
+
+
+def lbp_read_fields(h: Handle, rho=None, u=None, p=None):
+    a = _ptr(rho, np.float64, h.N, "rho", True)
+    b = _ptr(u, np.float64, 3 * h.N, "u", True)
+    c = _ptr(p, np.float64, h.N, "p", True)
+    d = _same_side(a, b, c)
+    _call("lbp_read_fields", h.ptr, a[0], b[0], c[0], d)
+
+
+def lbp_particles_add(h: Handle, r, v, mass, gamma, radius=None):
+    n = (r.numel() if _is_torch(r) else r.size) // 3
+    args = [_ptr(r, np.float64, 3 * n, "r"), _ptr(v, np.float64, 3 * n, "v"),
+            _ptr(mass, np.float64, n, "mass"), _ptr(gamma, np.float64, n, "gamma"),
+            _ptr(radius, np.float64, n, "radius")]
+    d = _same_side(*args)
+    _call("lbp_particles_add", h.ptr, n, *[a[0] for a in args], d)
+
+
+def lbp_particles_set_params(h: Handle, kT=0.0, seed=0, mode=LBP_STOKESLET, fit_exclude_inside=0):
+    prm = lbp_particle_params(float(kT), int(seed), int(mode), int(fit_exclude_inside))
+    _call("lbp_particles_set_params", h.ptr, C.byref(prm))
+
+
+def lbp_particles_set_external_force(h: Handle, f_ext=None, pinned=None):
+    n = h.np
+    a = _ptr(f_ext, np.float64, 3 * n, "f_ext")
+    b = _ptr(pinned, np.uint8, n, "pinned")
+    d = _same_side(a, b)
+    _call("lbp_particles_set_external_force", h.ptr, a[0], b[0], d)
+
+
+def lbp_particles_set_state(h: Handle, r=None, v=None):
+    n = h.np
+    a = _ptr(r, np.float64, 3 * n, "r")
+    b = _ptr(v, np.float64, 3 * n, "v")
+    d = _same_side(a, b)
+    _call("lbp_particles_set_state", h.ptr, a[0], b[0], d)
+
+
+def lbp_particles_read(h: Handle, r=None, v=None, f_h=None, f_r=None):
+    n = h.np
+    args = [_ptr(x, np.float64, 3 * n, nm, True) for x, nm in ((r, "r"), (v, "v"), (f_h, "f_h"), (f_r, "f_r"))]
+    d = _same_side(*args)
+    _call("lbp_particles_read", h.ptr, *[a[0] for a in args], d)
+
+
+def lbp_particles_read_cells(h: Handle, base, weights):
+    n = h.np
+    a = _ptr(base, np.int32, 3 * n, "base", True)
+    b = _ptr(weights, np.float64, 8 * n, "weights", True)
+    d = _same_side(a, b)
+    _call("lbp_particles_read_cells", h.ptr, a[0], b[0], d)
+
+
+def lbp_particles_count(h: Handle) -> int:
+    return h.np
+
+
+def lbp_step(h: Handle, nsteps=1):
+    _call("lbp_step", h.ptr, int(nsteps))
+
+
+def lbp_set_step_index(h: Handle, step):
+    _call("lbp_set_step_index", h.ptr, int(step))
+
+
+def lbp_get_step_index(h: Handle) -> int:
+    v = C.c_int64()
+    _call("lbp_get_step_index", h.ptr, C.byref(v))
+    return v.value
+
+
+def lbp_vacf_configure(h: Handle, max_lag):
+    _call("lbp_vacf_configure", h.ptr, int(max_lag))
+
+
+def lbp_vacf_read(h: Handle, csum, counts):
+    a = _ptr(csum, np.float64, None, "csum", True)
+    b = _ptr(counts, np.int64, None, "counts", True)
+    d = _same_side(a, b)
+    _call("lbp_vacf_read", h.ptr, a[0], b[0], d)
+
+
+def lbp_check(h: Handle):
+    _call("lbp_check", h.ptr)
+
+
+def lbp_set_use_graphs(h: Handle, enable):
+    _call("lbp_set_use_graphs", h.ptr, int(bool(enable)))
+
+
+def lbp_timing_enable(h: Handle, enable):
+    _call("lbp_timing_enable", h.ptr, int(bool(enable)))
+
+
+def lbp_timing_read(h: Handle):
+    ms = C.c_double()
+    n = C.c_int64()
+    _call("lbp_timing_read", h.ptr, C.byref(ms), C.byref(n))
+    return ms.value, n.value
+
+
+def lbp_philox4x64_10(ctr, key, out, n, stream=None):
+    """ctr [n,4], key [2], out [n,4]: 64-bit CUDA tensors (int64 holding the uint64 bits)."""
+    a = _ptr(ctr, np.uint64, 4 * n, "ctr")
+    b = _ptr(key, np.uint64, 2, "key")
+    c = _ptr(out, np.uint64, 4 * n, "out", True)
+    if {a[1], b[1], c[1]} != {1}:
+        raise ValueError("lbp_philox4x64_10 takes device tensors")
+    s = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _call("lbp_philox4x64_10", a[0], b[0], c[0], int(n), s)

@@ -1,0 +1,64 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/lbp.h declares, and rejects invalid arguments before any CUDA work."""
+import os
+import re
+
+import pytest
+
+from paper_1909_13412_gb300 import build as lbp_build
+from paper_1909_13412_gb300 import lbp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lbp_build.build()
+    return lbp.load()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "lbp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("lbp_create", "lbp_step", "lbp_read_fields", "lbp_particles_add",
+                     "lbp_particles_read", "lbp_destroy", "lbp_vacf_read"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(header_functions()) == set(lbp.exported_symbols())
+
+
+def test_version(lib):
+    assert lbp.lbp_version() >= 100
+
+
+@pytest.mark.parametrize("args", [
+    (0, 4, 4, 0.8), (4, -1, 4, 0.8), (4, 4, 4, 0.5), (4, 4, 4, 0.3), (4, 4, 4, float("nan")),
+    (2048, 2048, 1024, 0.8),
+])
+def test_create_rejects_invalid_boxes_before_touching_the_gpu(lib, args):
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_create(*args)
+    assert ei.value.status == lbp.LBP_EINVAL
+    assert lbp.lbp_last_error()
+
+
+def test_create_rejects_unknown_precision(lib):
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_create(4, 4, 4, 0.8, precision=9)
+    assert ei.value.status == lbp.LBP_EINVAL
+
+
+def test_null_handle_is_rejected(lib):
+    import ctypes as C
+    st = lib.lbp_step(C.c_void_p(0), 1)
+    assert st == lbp.LBP_EINVAL
+    assert lib.lbp_destroy(C.c_void_p(0)) == lbp.LBP_OK

@@ -1,0 +1,372 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written in each test):
+  * bit-exact: Philox blocks, the random force F_R, cell indices and trilinear
+    weights (integer/bit-level work, same IEEE expressions on both sides);
+  * populations after one step: |g_gpu - g_oracle| <= 1e-6 max|f_oracle - w|
+    (FP32 storage of the deviation g = f - w carries ~6e-8 relative rounding);
+  * particle velocity after 10^3 steps (single kicked particle): 1e-4 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_13412_gb300 import lbp
+from paper_1909_13412_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E, W = oracle.d3q15()
+W4 = W[:, None, None, None]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1909_13412_gb300 import build as lbp_build
+    lbp_build.build()
+    lbp.load()
+    torch.cuda.set_device(0)
+
+
+def gpu_sim(shape_zyx, tau, ps=None, kT=0.0, seed=0, mode=lbp.LBP_STOKESLET, exclude=0, graphs=True):
+    nz, ny, nx = shape_zyx
+    h = lbp.lbp_create(nx, ny, nz, tau)
+    lbp.lbp_set_use_graphs(h, graphs)
+    if ps is not None:
+        lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        lbp.lbp_particles_set_params(h, kT=kT, seed=seed, mode=mode, fit_exclude_inside=exclude)
+    return h
+
+
+def oracle_sim(shape_zyx, tau, ps=None, kT=0.0, seed=0, mode=0, exclude=0):
+    nz, ny, nx = shape_zyx
+    o = oracle.Sim(nx, ny, nz, tau)
+    if ps is not None:
+        o.add_particles(ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        o.set_params(kT=kT, seed=seed, mode=mode, exclude_inside=exclude)
+    return o
+
+
+def gpu_pops(h):
+    f = np.empty((15, h.nz, h.ny, h.nx))
+    lbp.lbp_read_populations(h, f)
+    return f
+
+
+def gpu_particles(h):
+    n = h.np
+    out = [np.empty((n, 3)) for _ in range(4)]
+    lbp.lbp_particles_read(h, *out)
+    return out
+
+
+def dev_scale(fo):
+    return np.max(np.abs(fo - W4))
+
+
+# ---------------------------------------------------------------- bit-exact pieces
+def test_philox_bit_exact():
+    g = np.random.default_rng(0)
+    n = 4096
+    ctr = g.integers(0, 2 ** 63, (n, 4), dtype=np.int64).astype(np.uint64) * np.uint64(2) + np.uint64(1)
+    ctr[:16] = np.arange(64, dtype=np.uint64).reshape(16, 4)
+    key = np.array([0x0123456789ABCDEF, 0xFEDCBA9876543210], np.uint64)
+    out = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+    lbp.lbp_philox4x64_10(torch.from_numpy(ctr.view(np.int64)).cuda(),
+                          torch.from_numpy(key.view(np.int64)).cuda(), out, n)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint64)
+    for i in list(range(64)) + list(range(n - 64, n)):
+        assert np.array_equal(got[i], oracle.philox4x64_10(ctr[i], key)), i
+
+
+def test_random_force_bit_exact():
+    shape = (6, 7, 9)
+    ps = wl.uniform_particles(50, shape, 10.0, 0.5, 0.26, 1e-4, 3, 4)
+    h = gpu_sim(shape, 0.8, ps, kT=2.5e-4, seed=1234)
+    o = oracle_sim(shape, 0.8, ps, kT=2.5e-4, seed=1234)
+    for n in range(3):
+        lbp.lbp_step(h, 1)
+        o.step(1)
+        _, _, _, FR = gpu_particles(h)
+        _, _, _, FRo = o.particles()
+        assert np.array_equal(FR.view(np.uint64), FRo.view(np.uint64)), n
+    lbp.lbp_set_step_index(h, 10 ** 12)
+    o.set_step(10 ** 12)
+    lbp.lbp_step(h, 1)
+    o.step(1)
+    assert np.array_equal(gpu_particles(h)[3], o.particles()[3])
+
+
+def test_cell_indexing_and_weights_bit_exact():
+    shape = (12, 11, 10)
+    g = np.random.default_rng(5)
+    r = g.random((300, 3)) * np.array([10, 11, 12.0])
+    r[:6] = [[0, 0, 0], [9.999999999999998, 10.999999999999998, 11.999999999999998],
+             [3.0, 4.0, 5.0], [0.5, 0.5, 0.5], [1e-300, 2.0, 7.25], [9.5, 0.1, 11.0]]
+    ps = wl.ParticleSet(r, np.zeros_like(r), np.full(300, 10.0), np.full(300, 0.5), np.full(300, 0.2))
+    h = gpu_sim(shape, 0.8, ps)
+    base = np.empty((300, 3), np.int32)
+    wts = np.empty((300, 8))
+    lbp.lbp_particles_read_cells(h, base, wts)
+    for i in range(300):
+        b, _, Wp = oracle.corners(r[i])
+        assert np.array_equal(base[i], b)
+        assert np.array_equal(wts[i], Wp), i
+
+
+# ---------------------------------------------------------------- lattice step
+@pytest.mark.parametrize("shape,tau", [((13, 21, 300), 0.8), ((5, 3, 37), 0.6), ((1, 1, 1), 1.3),
+                                       ((2, 130, 7), 0.55)])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_stream_collide_one_step(shape, tau, graphs):
+    """Random non-equilibrium state, no particles: several 128-node x-chunks and
+    a ragged tail (nx = 300), odd sizes and 1-node boxes."""
+    f0 = wl.perturbed_populations(W, shape, 0.05, 17)
+    h = gpu_sim(shape, tau, graphs=graphs)
+    lbp.lbp_set_populations(h, f0)
+    lbp.lbp_step(h, 1)
+    o = oracle_sim(shape, tau)
+    o.set_fhat(f0)
+    o.step(1)
+    fo = o.fhat()
+    err = np.max(np.abs(gpu_pops(h) - fo))
+    assert err <= 1e-6 * dev_scale(fo), err / dev_scale(fo)
+
+
+def test_set_read_populations_roundtrip_and_rest_state():
+    shape = (4, 5, 6)
+    h = gpu_sim(shape, 0.8)
+    assert np.array_equal(gpu_pops(h), np.broadcast_to(W4, (15,) + shape))
+    f0 = wl.perturbed_populations(W, shape, 0.1, 1)
+    lbp.lbp_set_populations(h, f0)
+    got = gpu_pops(h)
+    # stored as FP32 deviations: |error| <= 2^-24 |f - w|
+    assert np.all(np.abs(got - f0) <= 2.0 ** -24 * np.abs(f0 - W4) + 1e-300)
+
+
+def test_fields_parity_and_device_pointers():
+    shape = (9, 10, 11)
+    f0 = wl.perturbed_populations(W, shape, 0.05, 4)
+    h = gpu_sim(shape, 0.7)
+    lbp.lbp_set_populations(h, torch.from_numpy(f0.reshape(-1)).cuda())
+    o = oracle_sim(shape, 0.7)
+    o.set_fhat(f0)
+    rho, u, p = (torch.empty(n * 990, dtype=torch.float64, device="cuda") for n in (1, 3, 1))
+    lbp.lbp_read_fields(h, rho, u, p)
+    torch.cuda.synchronize()
+    ro, uo, po = o.fields()
+    scale = dev_scale(f0)
+    assert np.max(np.abs(rho.cpu().numpy().reshape(shape) - ro)) <= 1e-6 * scale
+    assert np.max(np.abs(u.cpu().numpy().reshape((3,) + shape) - uo)) <= 1e-6 * scale
+    assert np.max(np.abs(p.cpu().numpy().reshape(shape) - po)) <= 1e-6 * scale
+
+
+def test_many_steps_conserve_mass_and_stay_close():
+    shape = (16, 16, 16)
+    f0 = wl.perturbed_populations(W, shape, 0.02, 9)
+    h = gpu_sim(shape, 0.9)
+    lbp.lbp_set_populations(h, f0)
+    lbp.lbp_step(h, 100)
+    o = oracle_sim(shape, 0.9)
+    o.set_fhat(f0)
+    o.step(100)
+    fo = o.fhat()
+    f = gpu_pops(h)
+    assert abs(f.sum() - f0.sum()) <= 1e-6 * dev_scale(f0) * 15 * 4096
+    assert np.max(np.abs(f - fo)) <= 1e-5 * dev_scale(f0)
+
+
+# ---------------------------------------------------------------- coupled step
+def test_kicked_particle_relaxation_1000_steps():
+    """The 32^3 single-particle relaxation run: V after 10^3 steps to 1e-4."""
+    w = wl.RELAXATION_32
+    ps = wl.relaxation_particle(w)
+    h = gpu_sim(w.shape_zyx, w.tau, ps)
+    o = oracle_sim(w.shape_zyx, w.tau, ps)
+    lbp.lbp_step(h, 1)
+    o.step(1)
+    _, V1, FH1, _ = gpu_particles(h)
+    _, V1o, FH1o, _ = o.particles()
+    assert FH1[0, 0] / (-0.5 * 0.01) == pytest.approx(1.40724, rel=1e-5)
+    assert np.allclose(FH1, FH1o, rtol=1e-9, atol=1e-18)
+    lbp.lbp_step(h, 999)
+    o.step(999)
+    r, V, _, _ = gpu_particles(h)
+    ro, Vo, _, _ = o.particles()
+    assert np.max(np.abs(V - Vo)) <= 1e-4 * np.max(np.abs(Vo))
+    assert np.max(np.abs(r - ro)) <= 1e-6
+    lbp.lbp_check(h)
+
+
+@pytest.mark.parametrize("mode", [lbp.LBP_STOKESLET, lbp.LBP_POINTWISE, lbp.LBP_BROWNIAN])
+@pytest.mark.parametrize("exclude", [0, 1])
+def test_coupled_brownian_particles(mode, exclude):
+    """40 particles, some sharing cells and nodes, with noise: 60 steps."""
+    shape = (14, 17, 19)
+    ps = wl.uniform_particles(40, shape, 10.0, 0.5, wl.stokes_radius(0.5, 0.7), 1e-4, 21, 22)
+    Lxyz = np.array([19.0, 17.0, 14.0])
+    ps.r[1] = np.floor(ps.r[0]) + [0.1, 0.8, 0.45]               # same cell as particle 0
+    ps.r[3] = (np.floor(ps.r[2]) + [1.2, 0.3, 0.6]) % Lxyz       # shares four nodes with particle 2
+    ps.r[4] = [18.9, 16.95, 13.99]   # touches the periodic seams in x, y and z
+    h = gpu_sim(shape, 0.7, ps, kT=1e-4, seed=77, mode=mode, exclude=exclude)
+    o = oracle_sim(shape, 0.7, ps, kT=1e-4, seed=77, mode=mode, exclude=exclude)
+    lbp.lbp_step(h, 60)
+    o.step(60)
+    r, V, FH, FR = gpu_particles(h)
+    ro, Vo, FHo, FRo = o.particles()
+    assert np.array_equal(FR, FRo)
+    vs = np.max(np.abs(Vo))
+    assert np.max(np.abs(V - Vo)) <= 1e-5 * vs
+    assert np.max(np.abs(FH - FHo)) <= 1e-5 * np.max(np.abs(FHo))
+    d = np.abs(r - ro)
+    d = np.minimum(d, np.array([19, 17, 14.0]) - d)
+    assert np.max(d) <= 1e-6
+    fo = o.fhat()
+    assert np.max(np.abs(gpu_pops(h) - fo)) <= 1e-5 * dev_scale(fo)
+    lbp.lbp_check(h)
+
+
+def test_pinned_particle_and_external_force():
+    shape = (10, 10, 10)
+    r = np.array([[5.5, 5.5, 5.5], [2.3, 7.1, 4.4]])
+    ps = wl.ParticleSet(r, np.array([[0.0, 0, 0], [0.001, 0, 0.002]]), np.array([10.0, 5.0]),
+                        np.array([0.5, 0.3]), np.array([0.26, 0.2]))
+    f0 = np.broadcast_to(np.stack([oracle.feq(1.0, np.array([1e-3, 0, 0]))], 1)[:, :, None, None],
+                         (15,) + shape).copy()
+    fext = np.array([[0.0, 0, 0], [1e-5, -2e-5, 0]])
+    pin = np.array([1, 0], np.uint8)
+    h = gpu_sim(shape, 0.8, ps)
+    lbp.lbp_set_populations(h, f0)
+    lbp.lbp_particles_set_external_force(h, fext, pin)
+    o = oracle_sim(shape, 0.8, ps)
+    o.set_fhat(f0)
+    o.set_external(fext, pin)
+    lbp.lbp_step(h, 40)
+    o.step(40)
+    rg, Vg, FHg, _ = gpu_particles(h)
+    ro, Vo, FHo, _ = o.particles()
+    assert np.array_equal(rg[0], r[0]) and np.array_equal(Vg[0], [0, 0, 0])
+    assert np.allclose(FHg, FHo, rtol=1e-5, atol=1e-12)
+    assert np.allclose(Vg, Vo, rtol=1e-5, atol=1e-12)
+
+
+def test_momentum_budget_on_gpu():
+    shape = (12, 12, 12)
+    ps = wl.uniform_particles(20, shape, 8.0, 0.4, 0.2, 1e-4, 5, 6)
+    h = gpu_sim(shape, 0.75, ps, kT=1e-4, seed=3)
+
+    def P():
+        f = gpu_pops(h)
+        _, V, _, _ = gpu_particles(h)
+        return E.T.astype(float) @ f.reshape(15, -1).sum(1) + (ps.M[:, None] * V).sum(0)
+
+    P0 = P()
+    inj = np.zeros(3)
+    for _ in range(20):
+        lbp.lbp_step(h, 1)
+        inj += gpu_particles(h)[3].sum(0)
+    # fluid momentum carries FP32 rounding of ~1e-8 per node population
+    assert np.allclose(P() - P0, inj, atol=1e-9)
+
+
+def test_deterministic_and_graph_invariant():
+    shape = (10, 12, 14)
+    ps = wl.uniform_particles(60, shape, 10.0, 0.5, 0.26, 1e-4, 8, 9)
+    outs = []
+    for graphs in (True, False, True):
+        h = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=5, graphs=graphs)
+        lbp.lbp_step(h, 30)
+        outs.append((gpu_pops(h), gpu_particles(h)[1]))
+        lbp.lbp_destroy(h)
+    for f, V in outs[1:]:
+        assert np.array_equal(f, outs[0][0])
+        assert np.array_equal(V, outs[0][1])
+
+
+# ---------------------------------------------------------------- VACF
+def test_vacf_matches_oracle_on_the_same_trajectory():
+    shape = (8, 8, 8)
+    ps = wl.uniform_particles(37, shape, 6.0, 0.5, 0.2, 1e-4, 1, 2)
+    h = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=2)
+    K = 90
+    lbp.lbp_vacf_configure(h, K)
+    traj = []
+    T = 150  # two full 64-sample blocks and a partial one
+    for _ in range(T):
+        lbp.lbp_step(h, 1)
+        traj.append(gpu_particles(h)[1])
+    cs = np.empty(K + 1)
+    cnt = np.empty(K + 1, np.int64)
+    lbp.lbp_vacf_read(h, cs, cnt)
+    ref, refc = oracle.vacf(np.array(traj, np.float32).astype(np.float64), K)
+    assert np.array_equal(cnt, refc)
+    assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
+    # reading again after more steps continues the same sums
+    for _ in range(70):
+        lbp.lbp_step(h, 1)
+        traj.append(gpu_particles(h)[1])
+    lbp.lbp_vacf_read(h, cs, cnt)
+    ref, refc = oracle.vacf(np.array(traj, np.float32).astype(np.float64), K)
+    assert np.array_equal(cnt, refc)
+    assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
+
+
+def test_vacf_requires_particles():
+    h = gpu_sim((4, 4, 4), 0.8)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_vacf_configure(h, 10)
+    assert ei.value.status == lbp.LBP_ESTATE
+
+
+# ---------------------------------------------------------------- validation on device
+def test_particle_validation():
+    h = gpu_sim((8, 8, 8), 0.8)
+    bad = [
+        (np.array([[8.0, 1, 1]]), np.zeros((1, 3)), [1.0], [0.5], [0.2]),   # outside the box
+        (np.array([[1.0, 1, 1]]), np.full((1, 3), np.nan), [1.0], [0.5], [0.2]),
+        (np.array([[1.0, 1, 1]]), np.zeros((1, 3)), [0.0], [0.5], [0.2]),   # mass
+        (np.array([[1.0, 1, 1]]), np.zeros((1, 3)), [1.0], [0.5], [2.0]),   # R > sqrt(3)
+    ]
+    for r, v, m, g, R in bad:
+        with pytest.raises(lbp.LbpError) as ei:
+            lbp.lbp_particles_add(h, r, v, np.array(m), np.array(g), np.array(R))
+        assert ei.value.status == lbp.LBP_EINVAL
+    assert h.np == 0
+    lbp.lbp_particles_add(h, np.array([[1.0, 1, 1]]), np.zeros((1, 3)), np.array([1.0]),
+                          np.array([0.5]), np.array([1.0]))
+    with pytest.raises(lbp.LbpError):
+        lbp.lbp_particles_set_params(h, fit_exclude_inside=1)  # R = 1 > sqrt(3)/2
+    with pytest.raises(lbp.LbpError):
+        lbp.lbp_particles_set_params(h, kT=-1.0)
+
+
+def test_stokes_radius_default():
+    h = gpu_sim((8, 8, 8), 0.8)
+    r = np.array([[4.5, 4.5, 4.5]])
+    lbp.lbp_particles_add(h, r, np.array([[0.01, 0, 0]]), np.array([10.0]), np.array([0.5]))
+    lbp.lbp_step(h, 1)
+    _, _, FH, _ = gpu_particles(h)
+    R = 0.5 / (6 * math.pi * 0.1)
+    U, _ = oracle.stokeslet_fit(oracle.corners(r[0])[1], np.zeros((8, 3)), np.array([0.01, 0, 0]), R)
+    assert FH[0, 0] == pytest.approx(-0.5 * U, rel=1e-9)
+
+
+def test_nan_watchdog():
+    h = gpu_sim((8, 8, 8), 0.8)
+    lbp.lbp_particles_add(h, np.array([[4.5, 4.5, 4.5]]), np.zeros((1, 3)), np.array([1.0]),
+                          np.array([0.5]), np.array([0.2]))
+    lbp.lbp_particles_set_external_force(h, np.array([[np.inf, 0.0, 0.0]]))
+    lbp.lbp_step(h, 1)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_check(h)
+    assert ei.value.status == lbp.LBP_ENAN
+    r = np.empty((1, 3))
+    lbp.lbp_particles_read(h, r=r)
+    assert np.all((r >= 0) & (r < 8))
+    lbp.lbp_check(h)  # the flag is cleared once reported
