@@ -16,24 +16,39 @@
 namespace lbp {
 
 // ---------------------------------------------------------------------------
-// Fused pull-stream + moments + BGK collision (Eqs. 20, 12, 13, 15, 17, 19).
-// One thread per node; a block walks whole x-rows (grid-stride over rows so
-// the grid is a multiple of the SM count).  The 15 loads of a node are
-// independent, so every thread keeps 60 bytes in flight.  The body force of
-// Eq. 19 is added afterwards at the few nodes next to particles
-// (particle_kernels.cu), which is the same sum because the force term does
-// not depend on f.
+// Fused pull-stream + moments + forced BGK collision (Eqs. 20, 12, 13, 15, 17,
+// 18, 19).  One thread per node; a block walks whole x-rows with a grid-stride
+// loop (the grid is a multiple of the SM count).  The 15 loads of a node are
+// independent, so every thread keeps 60 bytes in flight.
+//
+// Body force: the particle kernel has summed each particle's reaction force
+// -F_H W_p into fq (64-bit fixed point) and set the node's bit in `mask`.  A
+// warp covers 32 consecutive x of one row, i.e. exactly one mask word: lane 0
+// reads it and clears it, and the lanes whose bit is set add 3 w_a F.e_a to
+// their post-collision populations and zero their fq entries.
 // ---------------------------------------------------------------------------
 template <int BX>
 __global__ void __launch_bounds__(BX) k_stream_collide(const float *__restrict__ src,
                                                        float *__restrict__ dst, int nx, int ny,
                                                        int nz, long long P, float omega,
-                                                       int nchunks, long long *bump) {
+                                                       int nchunks, unsigned int *mask, int mwords,
+                                                       unsigned long long *fq, long long N,
+                                                       long long *bump) {
     const long long nitems = (long long)ny * nz * nchunks;
+    const int lane = threadIdx.x & 31;
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
         const long long row = item / nchunks;
         const int chunk = (int)(item - row * nchunks);
-        const int x = chunk * BX + threadIdx.x;
+        const int xw = chunk * BX + (threadIdx.x & ~31);  // first x of this warp
+        if (xw >= nx) continue;                           // uniform per warp
+        unsigned int word = 0u;
+        if (mask) {
+            const long long widx = row * mwords + (xw >> 5);
+            if (lane == 0) word = mask[widx];
+            word = __shfl_sync(0xffffffffu, word, 0);
+            if (lane == 0 && word) mask[widx] = 0u;
+        }
+        const int x = xw + lane;
         if (x >= nx) continue;
         const int z = (int)(row / ny);
         const int y = (int)(row - (long long)z * ny);
@@ -57,12 +72,24 @@ __global__ void __launch_bounds__(BX) k_stream_collide(const float *__restrict__
             if (ez(a)) uz += ez(a) > 0 ? g[a] : -g[a];
         }
         const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-        const long long d = ((long long)z * ny + y) * nx + x;
+        const long long d = row * nx + x;
+        float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+        if ((word >> lane) & 1u) {
+            const unsigned long long a0 = fq[d], a1 = fq[N + d], a2 = fq[2 * N + d];
+            fq[d] = 0ull;
+            fq[N + d] = 0ull;
+            fq[2 * N + d] = 0ull;
+            const float inv = 1.3877787807814457e-17f;  // 2^-56
+            F0 = 3.f * inv * __ll2float_rn((long long)a0);
+            F1 = 3.f * inv * __ll2float_rn((long long)a1);
+            F2 = 3.f * inv * __ll2float_rn((long long)a2);
+        }
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const float eu = (float)ex(a) * ux + (float)ey(a) * uy + (float)ez(a) * uz;
             const float geq = wgtf(a) * (drho + 3.f * eu + 4.5f * eu * eu - usq15);
-            dst[(long long)a * P + d] = g[a] + omega * (geq - g[a]);
+            const float G = wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
+            dst[(long long)a * P + d] = g[a] + omega * (geq - g[a]) + G;
         }
     }
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
@@ -81,17 +108,17 @@ cudaError_t prepare_lbm_kernels() {
     return e;
 }
 
-cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, bool bump_step,
-                                  cudaStream_t st) {
+cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, cudaStream_t st) {
     constexpr int BX = SC_BX;
     const int nchunks = (s.nx + BX - 1) / BX;
     const long long items = (long long)s.ny * s.nz * nchunks;
     long long grid = (long long)s.num_sms * g_sc_blocks_per_sm;
     if (grid > items) grid = items;
     if (grid < 1) grid = 1;
-    k_stream_collide<BX><<<(unsigned)grid, BX, 0, st>>>(src, dst, s.nx, s.ny, s.nz, s.P,
-                                                         (float)(1.0 / s.tau), nchunks,
-                                                         bump_step ? s.d_step : nullptr);
+    const bool forces = s.np > 0 && s.fq != nullptr;
+    k_stream_collide<BX><<<(unsigned)grid, BX, 0, st>>>(
+        src, dst, s.nx, s.ny, s.nz, s.P, (float)(1.0 / s.tau), nchunks,
+        forces ? s.mask : nullptr, s.mwords, s.fq, s.N, s.d_step);
     return cudaGetLastError();
 }
 

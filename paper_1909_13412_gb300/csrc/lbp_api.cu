@@ -3,13 +3,13 @@
 // Host side of the library: argument validation, device allocation, layout
 // conversion for the ABI arrays, and the per-step launch sequence
 //
-//      s1:  k_particles (reads fhat^{n-1}) -> VACF block --------.
-//      s0:  k_stream_collide (fhat^{n-1} -> fhat^n) ----- join -> k_apply
+//      s0:  k_particles (fhat^{n-1} -> F_H, V, r, reaction forces)
+//           -> k_stream_collide (fhat^{n-1} + forces -> fhat^n)
+//      s1:  every 64th step, the VACF block, forked after k_particles and
+//           joined after k_stream_collide, so it overlaps the lattice pass.
 //
-// The particle kernel only reads the old populations and the stream-collide
-// kernel does not need the particles' forces (the body-force term is added by
-// k_apply afterwards), so the two run concurrently.  A step is captured once
-// per buffer parity into a CUDA graph and replayed.
+// A step is captured into a CUDA graph per (buffer parity, VACF block due)
+// and replayed.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -20,11 +20,6 @@
 #include <vector>
 
 #include "lbp_internal.cuh"
-
-namespace lbp {
-int vacf_block_samples();
-int vacf_chunk_components();
-}  // namespace lbp
 
 using namespace lbp;
 
@@ -79,10 +74,11 @@ lbp_status leave(lbp_sim *s) {
 
 void drop_graphs(lbp_sim *s) {
     for (int i = 0; i < 2; ++i)
-        if (s->graph[i]) {
-            cudaGraphExecDestroy(s->graph[i]);
-            s->graph[i] = nullptr;
-        }
+        for (int j = 0; j < 2; ++j)
+            if (s->graph[i][j]) {
+                cudaGraphExecDestroy(s->graph[i][j]);
+                s->graph[i][j] = nullptr;
+            }
 }
 
 lbp_status stage(lbp_sim *s, size_t bytes) {
@@ -119,27 +115,24 @@ bool radius_ok(double R, int exclude) {
 
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
-// one time step on (st0, st1); st1 is forked from / joined into st0
-lbp_status enqueue_step(lbp_sim *s, bool timed) {
+// one time step; the VACF block (if due) runs on s1 beside the lattice pass
+lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
     const float *src = s->f[s->cur];
     float *dst = s->f[s->cur ^ 1];
-    if (s->np > 0) {
+    if (s->np > 0) CK(launch_particles(*s, src, s->s0));
+    if (vacf_due) {
         CK(cudaEventRecord(s->ev_fork, s->s0));
         CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
-        CK(launch_particles(*s, src, s->s1));
         CK(launch_vacf_block(*s, false, s->s1));
         CK(cudaEventRecord(s->ev_join, s->s1));
     }
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
-    CK(launch_stream_collide(*s, src, dst, s->np == 0, s->s0));
+    CK(launch_stream_collide(*s, src, dst, s->s0));
     if (timed) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
     }
-    if (s->np > 0) {
-        CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
-        CK(launch_apply_forces(*s, dst, s->s0));
-    }
+    if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
     return LBP_OK;
 }
 
@@ -156,12 +149,12 @@ lbp_status fold_timing(lbp_sim *s) {
     return LBP_OK;
 }
 
-lbp_status capture(lbp_sim *s, int parity) {
+lbp_status capture(lbp_sim *s, int parity, int due) {
     cudaGraph_t g = nullptr;
     const int saved = s->cur;
     s->cur = parity;
     CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
-    lbp_status st = enqueue_step(s, false);
+    lbp_status st = enqueue_step(s, false, due != 0);
     cudaError_t e = cudaStreamEndCapture(s->s0, &g);
     s->cur = saved;
     if (st != LBP_OK) {
@@ -169,7 +162,7 @@ lbp_status capture(lbp_sim *s, int parity) {
         return st;
     }
     CK(e);
-    e = cudaGraphInstantiate(&s->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&s->graph[parity][due], g, 0);
     cudaGraphDestroy(g);
     CK(e);
     return LBP_OK;
@@ -236,12 +229,16 @@ lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out)
     if (st == LBP_OK) st = dalloc(&s->d_step, 1);
     if (st == LBP_OK) st = dalloc(&s->d_err, 1);
     if (st == LBP_OK) st = dalloc(&s->d_vacf, 4);
+    s->mwords = (s->nx + 31) / 32;
+    const size_t mask_words = (size_t)s->ny * s->nz * s->mwords;
+    if (st == LBP_OK) st = dalloc(&s->mask, mask_words);
     if (st != LBP_OK) return bail(st);
     e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch_fill_rest(*s, s->f[i], s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_vacf, 0, 4 * sizeof(long long), s->s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->mask, 0, sizeof(unsigned int) * mask_words, s->s0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->s0);
     if (e != cudaSuccess) {
         fail(LBP_ECUDA, "lbp_create: %s", cudaGetErrorString(e));
@@ -257,9 +254,8 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
-                    s->mass, s->gamma, s->radius, s->sig, s->pinned, s->hkey, s->hacc, s->hlist,
-                    s->hcount, s->ring, s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part,
-                    s->stage};
+                    s->mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->ring,
+                    s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
@@ -416,23 +412,11 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
             cudaFree(s->pinned);
         }
         s->pinned = np8;
-        // reaction-force hash: at least 16 slots per particle (8 corners, load <= 1/2)
-        int bits = 6;
-        while ((1ll << bits) < 16ll * cap) ++bits;
-        if (s->hkey) cudaFree(s->hkey);
-        if (s->hacc) cudaFree(s->hacc);
-        if (s->hlist) cudaFree(s->hlist);
-        if (s->hcount) cudaFree(s->hcount);
-        s->hkey = nullptr;
-        s->hacc = nullptr;
-        s->hlist = nullptr;
-        s->hcount = nullptr;
-        s->hash_bits = bits;
-        TRY(dalloc(&s->hkey, (size_t)1 << bits));
-        TRY(dalloc(&s->hacc, (size_t)3 << bits));
-        TRY(dalloc(&s->hlist, (size_t)1 << bits));
-        TRY(dalloc(&s->hcount, 2));
-        CK(launch_hash_clear(*s, s->s0));
+        // reaction-force accumulator: 3 x 64-bit per node, allocated once
+        if (!s->fq) {
+            TRY(dalloc(&s->fq, 3 * (size_t)s->N));
+            CK(cudaMemset(s->fq, 0, sizeof(unsigned long long) * 3 * (size_t)s->N));
+        }
         s->cap = cap;
     }
     // upload the new particles into the SoA planes
@@ -597,15 +581,25 @@ lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
     if (nsteps < 0) return fail(LBP_EINVAL, "lbp_step: nsteps < 0");
     if (nsteps == 0) return LBP_OK;
     TRY(enter(s));
+    const int B = vacf_block_samples();
     for (int64_t n = 0; n < nsteps; ++n) {
+        // the VACF correlator runs when the step completes a block of B samples
+        bool due = false;
+        if (s->vacf_lag >= 0 && s->np > 0) {
+            const long long written = s->step - s->vacf_t0 + 1;
+            if (written - s->vacf_done_host >= B) {
+                due = true;
+                s->vacf_done_host += B;
+            }
+        }
         if (s->timing) {
             if (s->ntimed == lbp::Sim::MAX_TIMED) TRY(fold_timing(s));
-            TRY(enqueue_step(s, true));
+            TRY(enqueue_step(s, true, due));
         } else if (s->use_graphs) {
-            if (!s->graph[s->cur]) TRY(capture(s, s->cur));
-            CK(cudaGraphLaunch(s->graph[s->cur], s->s0));
+            if (!s->graph[s->cur][due]) TRY(capture(s, s->cur, due));
+            CK(cudaGraphLaunch(s->graph[s->cur][due], s->s0));
         } else {
-            TRY(enqueue_step(s, false));
+            TRY(enqueue_step(s, false, due));
         }
         s->cur ^= 1;
         s->step += 1;
@@ -666,6 +660,8 @@ lbp_status lbp_vacf_configure(lbp_sim *s, int max_lag) {
     CK(cudaMemcpyAsync(s->d_vacf, hv, sizeof(hv), cudaMemcpyHostToDevice, s->s0));
     CK(cudaStreamSynchronize(s->s0));
     s->vacf_lag = max_lag;
+    s->vacf_t0 = s->step;
+    s->vacf_done_host = 0;
     return leave(s);
 }
 
@@ -674,6 +670,7 @@ lbp_status lbp_vacf_read(lbp_sim *s, double *csum, int64_t *counts, int on_devic
     if (s->vacf_lag < 0) return fail(LBP_ESTATE, "lbp_vacf_read: VACF not configured");
     TRY(enter(s));
     CK(launch_vacf_block(*s, true, s->s0));
+    s->vacf_done_host = s->step - s->vacf_t0;
     const size_t K1 = (size_t)s->vacf_lag + 1;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (csum) CK(cudaMemcpyAsync(csum, s->vacf_sum, sizeof(double) * K1, kind, s->s0));
@@ -691,8 +688,7 @@ lbp_status lbp_check(lbp_sim *s) {
     if (err) {
         CK(cudaMemset(s->d_err, 0, sizeof(int)));
         if (err & ERR_NAN) return fail(LBP_ENAN, "lbp_check: a particle velocity or position became non-finite or left the box");
-        if (err & ERR_RANGE) return fail(LBP_ERANGE, "lbp_check: a reaction force exceeded the fixed-point range");
-        return fail(LBP_ESTATE, "lbp_check: reaction-force table overflow");
+        return fail(LBP_ERANGE, "lbp_check: a friction force exceeded the fixed-point range (|F_H| >= 64)");
     }
     return LBP_OK;
 }

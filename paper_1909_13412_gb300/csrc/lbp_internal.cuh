@@ -36,15 +36,12 @@ __host__ __device__ constexpr float wgtf(int a) {
 
 // Reaction forces are summed per node in 64-bit fixed point so that the sum
 // is exact and independent of the order in which particles add to it.
-constexpr double FIX_SCALE = 72057594037927936.0;      // 2^56
-constexpr double FIX_INV = 1.0 / 72057594037927936.0;  // 2^-56
-constexpr double FIX_LIMIT = 64.0;                     // |contribution| < 2^6
-constexpr unsigned long long HASH_EMPTY = ~0ull;
+constexpr double FIX_SCALE = 72057594037927936.0;  // 2^56
+constexpr double FIX_LIMIT = 64.0;                 // |F_H| < 2^6 per particle
 
 // error bits in Sim::d_err
 constexpr int ERR_NAN = 1;
 constexpr int ERR_RANGE = 2;
-constexpr int ERR_HASH = 4;
 
 // ------------------------------------------------------------------ Philox
 // Philox-4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -103,18 +100,20 @@ struct Sim {
     int exclude_inside = 0;
     double sqrt3 = 0.0;
 
-    // reaction-force accumulator: open-addressing hash of node -> fixed-point force
-    int hash_bits = 0;
-    unsigned long long *hkey = nullptr;  // [H]
-    unsigned long long *hacc = nullptr;  // [3][H]
-    unsigned int *hlist = nullptr;       // [H] slots in use
-    unsigned int *hcount = nullptr;      // [2]: used slots, finished blocks
+    // reaction force: fixed-point accumulator per node and a bit per node
+    // marking the nodes that hold one (both cleared by the stream-collide kernel)
+    unsigned long long *fq = nullptr;  // [3][N], allocated with the first particle
+    unsigned int *mask = nullptr;      // [ny * nz][mwords]
+    int mwords = 0;                    // ceil(nx / 32)
 
     // VACF
     int vacf_lag = -1;
     int vacf_cap = 0;             // ring length in samples
     float *ring = nullptr;        // [vacf_cap][3 * cap]
-    long long *d_vacf = nullptr;  // [0] t0 step, [1] samples correlated
+    long long *d_vacf = nullptr;  // [0] t0 step, [1] samples correlated, [2] samples written,
+                                  // [3] block counter of the reduce kernel
+    long long vacf_done_host = 0; // host mirror of d_vacf[1]
+    long long vacf_t0 = 0;        // step index of sample 0
     double *vacf_sum = nullptr;   // [K + 1]
     long long *vacf_cnt = nullptr;
     double *vacf_part = nullptr;  // [nchunks][K + 1]
@@ -126,7 +125,7 @@ struct Sim {
 
     // graphs
     int use_graphs = 1;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][vacf block due]
 
     // kernel timing
     int timing = 0;
@@ -140,8 +139,7 @@ struct Sim {
 // ------------------------------------------------------------ launchers
 // lbm_kernels.cu
 cudaError_t prepare_lbm_kernels();
-cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, bool bump_step,
-                                  cudaStream_t st);
+cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, cudaStream_t st);
 cudaError_t launch_fill_rest(Sim &s, float *dst, cudaStream_t st);
 cudaError_t launch_from_f64(Sim &s, const double *f, float *dst, cudaStream_t st);
 cudaError_t launch_to_f64(Sim &s, const float *src, double *f, cudaStream_t st);
@@ -149,8 +147,6 @@ cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, doub
                           cudaStream_t st);
 // particle_kernels.cu
 cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st);
-cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st);
-cudaError_t launch_hash_clear(Sim &s, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);
@@ -158,6 +154,8 @@ cudaError_t launch_cells(Sim &s, int *base, double *weights, cudaStream_t st);
 cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long long *key,
                           unsigned long long *out, int64_t n, cudaStream_t st);
 // vacf_kernels.cu
+int vacf_block_samples();
+int vacf_chunk_components();
 cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st);
 
 }  // namespace lbp

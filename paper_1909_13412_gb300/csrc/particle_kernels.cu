@@ -1,21 +1,27 @@
-// particle_kernels.cu -- two-way coupling kernels of liblbp (sm_103a).
+// particle_kernels.cu -- two-way coupling kernel of liblbp (sm_103a).
 //
-//  k_particles : one warp per particle.  Gathers u^N at the eight corners of
-//                the particle's cell from the stored populations (pull, i.e.
-//                the streamed f^n of Eq. 20), fits the Stokeslet flow of Eq. 8
-//                with warp-shuffle reductions, draws the Philox random force
-//                (Eqs. 4-5), advances V and r (Eqs. 1-2) in FP64 and adds the
-//                reaction force -F_H W_p (Eq. 9) to a per-node accumulator.
-//  k_apply     : adds the body-force term 3 w_a F.e_a of Eqs. 18-19 to the
-//                post-collision populations at every node that received a
-//                reaction force, then clears the accumulator.
+// k_particles: one thread per particle.  It gathers u^N at the eight corners
+// of the particle's cell from the stored populations (a pull, i.e. the
+// streamed f^n of Eq. 20), fits the Stokeslet flow of Eq. 8, draws the Philox
+// random force (Eqs. 4-5), advances V and r (Eqs. 1-2) and adds the reaction
+// force -F_H W_p (Eq. 9) to the nodes of its cell.
 //
-// Determinism: per-node reaction forces are summed as 64-bit fixed-point
-// integers (scale 2^56) with integer atomics, so the sum is exact and does not
-// depend on the order in which particles add to it; no floating-point atomics
-// are used.  The accumulator is an open-addressing hash of node index ->
-// (Fx, Fy, Fz) sized to at least twice the 8 n_p nodes particles can touch,
-// with a list of the slots in use, so no dense force field is read or cleared.
+// Why a thread, not a warp, per particle: GB300 issues FP64 at 1/64 of the
+// FP32 rate, so a warp-wide FP64 instruction costs the same whether one lane
+// or 32 lanes need it.  Packing 32 particles into a warp divides the FP64
+// instruction count per particle by 32; with one particle per warp the FP64
+// work of the fit dominated the whole time step.  Precision split: corner
+// geometry (d_p, 1/r_p, the Stokeslet basis a_p and the unit vector e^N) in
+// FP32; relative velocities w_p, the normal-equation sums sum w.a and
+// sum |a|^2, U_inf, F_H, the random force, the trilinear weights and the
+// Langevin update in FP64.
+//
+// Reaction forces go to a dense per-node accumulator of 64-bit fixed-point
+// integers (scale 2^56), added with integer atomics: the per-node sum is exact
+// and independent of the order in which particles add to it (no
+// floating-point atomics).  A bit per node in `mask` marks the nodes that
+// received a force; the stream-collide kernel reads the mask, applies the
+// body-force term of Eqs. 18-19 at those nodes and clears both.
 #include <cuda_runtime.h>
 
 #include "lbp_internal.cuh"
@@ -26,6 +32,7 @@ struct ParticleArgs {
     const float *g;  // deviation populations fhat^{n-1}
     int nx, ny, nz;
     long long P;
+    long long N;
     double *r, *v, *fh, *fr;
     const double *fext, *mass, *gamma, *radius, *sig;
     const unsigned char *pinned;
@@ -34,136 +41,122 @@ struct ParticleArgs {
     unsigned long long seed;
     double sqrt3;
     int mode, exclude_inside;
-    unsigned long long *hkey, *hacc;
-    unsigned int *hlist, *hcount;
-    int hash_bits;
+    unsigned long long *fq;  // [3][N] fixed-point reaction force
+    unsigned int *mask;      // [rows][mwords]
+    int mwords;
     float *ring;
     int ring_cap;
-    const long long *d_vacf;  // [0] = first sampled step, or null
+    long long *d_vacf;  // [0] first sampled step, [2] samples written
     int *err;
 };
 
-__device__ __forceinline__ double wsum8(double x) {
-    // sum over the eight corners (lane bits 2..4); every lane ends with the sum
-    x += __shfl_xor_sync(0xffffffffu, x, 4);
-    x += __shfl_xor_sync(0xffffffffu, x, 8);
-    x += __shfl_xor_sync(0xffffffffu, x, 16);
-    return x;
-}
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-__device__ __forceinline__ void hash_add(const ParticleArgs &A, unsigned long long node,
-                                         long long q0, long long q1, long long q2) {
-    const unsigned int H = 1u << A.hash_bits;
-    const unsigned int mask = H - 1u;
-    unsigned int h = (unsigned int)((node * 0x9E3779B97F4A7C15ull) >> (64 - A.hash_bits));
-    for (unsigned int probe = 0; probe < H; ++probe) {
-        const unsigned long long prev = atomicCAS(&A.hkey[h], HASH_EMPTY, node);
-        if (prev == HASH_EMPTY) {
-            const unsigned int idx = atomicAdd(&A.hcount[0], 1u);
-            A.hlist[idx] = h;
-        }
-        if (prev == HASH_EMPTY || prev == node) {
-            atomicAdd(&A.hacc[h], (unsigned long long)q0);
-            atomicAdd(&A.hacc[H + h], (unsigned long long)q1);
-            atomicAdd(&A.hacc[2 * (size_t)H + h], (unsigned long long)q2);
-            return;
-        }
-        h = (h + 1u) & mask;
+__global__ void __launch_bounds__(128) k_particles(const ParticleArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long step = *A.d_step;
+    if (A.ring && i == 0) {
+        const long long m = step - A.d_vacf[0];
+        if (m >= 0) A.d_vacf[2] = m + 1;
     }
-    atomicOr(A.err, ERR_HASH);
-}
-
-__device__ __forceinline__ long long to_fixed(double x, int *err) {
-    if (!(fabs(x) < FIX_LIMIT)) {
-        atomicOr(err, ERR_RANGE);
-        return 0;
-    }
-    return __double2ll_rn(x * FIX_SCALE);
-}
-
-__global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
-    const int lane = threadIdx.x & 31;
-    const int i = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    if (i >= A.np) return;  // uniform per warp
+    if (i >= A.np) return;
     const int cap = A.cap;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
     const double r0 = A.r[i], r1 = A.r[cap + i], r2 = A.r[2 * cap + i];
     const double V0 = A.v[i], V1 = A.v[cap + i], V2 = A.v[2 * cap + i];
-    const long long step = *A.d_step;
 
-    // cell of the particle: base = floor(r), frac = r - base (exact)
+    // cell: base = floor(r), q = r - base (exact), corners base + {0,1}
     const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
     const double q0 = r0 - b0, q1 = r1 - b1, q2 = r2 - b2;
-    const int p = lane >> 2, j = lane & 3;
-    const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
-    int X = (int)b0 + c0, Y = (int)b1 + c1, Z = (int)b2 + c2;
-    if (X >= A.nx) X -= A.nx;
-    if (Y >= A.ny) Y -= A.ny;
-    if (Z >= A.nz) Z -= A.nz;
+    const int ib0 = (int)b0, ib1 = (int)b1, ib2 = (int)b2;
+    // source coordinates base + o for o = -1, 0, 1, 2 (index o + 1), periodic
+    const int xs[4] = {wrapi(ib0 - 1, nx), ib0, wrapi(ib0 + 1, nx), wrapi(ib0 + 2, nx)};
+    const int ys[4] = {wrapi(ib1 - 1, ny), ib1, wrapi(ib1 + 1, ny), wrapi(ib1 + 2, ny)};
+    const int zs[4] = {wrapi(ib2 - 1, nz), ib2, wrapi(ib2 + 1, nz), wrapi(ib2 + 2, nz)};
 
-    // u^N at corner p: sum_a e_a g_a(x_p - e_a); lane j of the corner takes a = j mod 4
-    double ux = 0.0, uy = 0.0, uz = 0.0;
+    // pass 1: u at the eight corners, u = sum_a e_a g_a(x_p - e_a) (FP32)
+    float ux[8], uy[8], uz[8];
 #pragma unroll
-    for (int a = 1; a < Q; ++a) {
-        if ((a & 3) == j) {
-            int xs = X - ex(a), ys = Y - ey(a), zs = Z - ez(a);
-            xs = xs < 0 ? xs + A.nx : (xs >= A.nx ? xs - A.nx : xs);
-            ys = ys < 0 ? ys + A.ny : (ys >= A.ny ? ys - A.ny : ys);
-            zs = zs < 0 ? zs + A.nz : (zs >= A.nz ? zs - A.nz : zs);
-            const double gv =
-                (double)__ldg(A.g + (long long)a * A.P + ((long long)zs * A.ny + ys) * A.nx + xs);
-            if (ex(a)) ux += ex(a) > 0 ? gv : -gv;
-            if (ey(a)) uy += ey(a) > 0 ? gv : -gv;
-            if (ez(a)) uz += ez(a) > 0 ? gv : -gv;
+    for (int p = 0; p < 8; ++p) {
+        const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            const long long src = (long long)a * A.P +
+                                  ((long long)zs[c2 - ez(a) + 1] * ny + ys[c1 - ey(a) + 1]) * nx +
+                                  xs[c0 - ex(a) + 1];
+            const float gv = __ldg(A.g + src);
+            if (ex(a)) sx += ex(a) > 0 ? gv : -gv;
+            if (ey(a)) sy += ey(a) > 0 ? gv : -gv;
+            if (ez(a)) sz += ez(a) > 0 ? gv : -gv;
         }
-    }
-#pragma unroll
-    for (int m = 1; m <= 2; m <<= 1) {
-        ux += __shfl_xor_sync(0xffffffffu, ux, m);
-        uy += __shfl_xor_sync(0xffffffffu, uy, m);
-        uz += __shfl_xor_sync(0xffffffffu, uz, m);
+        ux[p] = sx;
+        uy[p] = sy;
+        uz[p] = sz;
     }
 
-    // corner offset d_p = x_p - r and trilinear weight W_p (same expressions as Eq. 9 reading)
-    const double d0 = c0 ? 1.0 - q0 : -q0;
-    const double d1 = c1 ? 1.0 - q1 : -q1;
-    const double d2 = c2 ? 1.0 - q2 : -q2;
-    const double Wp = __dmul_rn(__dmul_rn(__dmul_rn(1.0, c0 ? q0 : 1.0 - q0), c1 ? q1 : 1.0 - q1),
-                                c2 ? q2 : 1.0 - q2);
+    // trilinear weights of the corners (Eq. 9 reading), FP64, same expression as the oracle
+    const double wx[2] = {1.0 - q0, q0}, wy[2] = {1.0 - q1, q1}, wz[2] = {1.0 - q2, q2};
+
     const double gam = A.gamma[i];
-    const double w0 = ux - V0, w1 = uy - V1, w2 = uz - V2;
-
-    double F0, F1, F2;
+    double F0 = 0.0, F1 = 0.0, F2 = 0.0;
     bool spread = true;
     if (A.mode == LBP_STOKESLET) {
-        // Eq. 8: e^N from the mean relative velocity, then one-parameter least squares
-        const double m0 = wsum8(w0) / 8.0, m1 = wsum8(w1) / 8.0, m2 = wsum8(w2) / 8.0;
-        const double nw = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
-        double U = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
-        if (nw != 0.0) {
-            e0 = m0 / nw;
-            e1 = m1 / nw;
-            e2 = m2 / nw;
-            const double R = A.radius[i];
-            const double rp = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-            double num = 0.0, den = 0.0;
-            if (!(rp < 1e-12) && !(A.exclude_inside && rp < R)) {
-                const double xx = e0 * d0 + e1 * d1 + e2 * d2;
-                const double k1 = 1.0 - 3.0 * R / (4.0 * rp);
-                const double k2 = 3.0 * R * xx / (4.0 * rp * rp * rp);
-                const double a0 = k1 * e0 - k2 * d0, a1 = k1 * e1 - k2 * d1, a2 = k1 * e2 - k2 * d2;
-                num = w0 * a0 + w1 * a1 + w2 * a2;
-                den = a0 * a0 + a1 * a1 + a2 * a2;
-            }
-            num = wsum8(num);
-            den = wsum8(den);
-            U = den == 0.0 ? 0.0 : num / den;
+        // e^N: direction of the mean relative velocity w-bar = mean(u_p) - V
+        float su0 = 0.f, su1 = 0.f, su2 = 0.f;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            su0 += ux[p];
+            su1 += uy[p];
+            su2 += uz[p];
         }
-        F0 = gam * U * e0;
-        F1 = gam * U * e1;
-        F2 = gam * U * e2;
+        const double m0 = (double)(su0 * 0.125f) - V0;
+        const double m1 = (double)(su1 * 0.125f) - V1;
+        const double m2 = (double)(su2 * 0.125f) - V2;
+        const double n2 = m0 * m0 + m1 * m1 + m2 * m2;
+        if (n2 > 0.0) {
+            const double inv = 1.0 / sqrt(n2);
+            const float e0 = (float)(m0 * inv), e1 = (float)(m1 * inv), e2 = (float)(m2 * inv);
+            const float R = (float)A.radius[i];
+            const float R2 = R * R, R34 = 0.75f * R;
+            // corner offsets d_p = c - q
+            const float dx[2] = {(float)(-q0), (float)(1.0 - q0)};
+            const float dy[2] = {(float)(-q1), (float)(1.0 - q1)};
+            const float dz[2] = {(float)(-q2), (float)(1.0 - q2)};
+            double num = 0.0, den = 0.0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const float d0 = dx[p & 1], d1 = dy[(p >> 1) & 1], d2 = dz[(p >> 2) & 1];
+                const float rr = d0 * d0 + d1 * d1 + d2 * d2;
+                if (rr < 1e-24f) continue;
+                if (A.exclude_inside && rr < R2) continue;
+                const float ir = rsqrtf(rr);
+                const float x = e0 * d0 + e1 * d1 + e2 * d2;
+                const float k1 = 1.f - R34 * ir;
+                const float k2 = R34 * x * ir * ir * ir;
+                const double a0 = (double)(k1 * e0 - k2 * d0);
+                const double a1 = (double)(k1 * e1 - k2 * d1);
+                const double a2 = (double)(k1 * e2 - k2 * d2);
+                // normal equations of the one-parameter least-squares fit, FP64
+                num += ((double)ux[p] - V0) * a0 + ((double)uy[p] - V1) * a1 + ((double)uz[p] - V2) * a2;
+                den += a0 * a0 + a1 * a1 + a2 * a2;
+            }
+            const double U = den > 0.0 ? num / den : 0.0;
+            const double gU = gam * U;
+            F0 = gU * (double)e0;
+            F1 = gU * (double)e1;
+            F2 = gU * (double)e2;
+        }
     } else if (A.mode == LBP_POINTWISE) {
         // Eq. 7 with u(r_i) = sum_p W_p u^N_p
-        const double ur0 = wsum8(Wp * ux), ur1 = wsum8(Wp * uy), ur2 = wsum8(Wp * uz);
+        double ur0 = 0.0, ur1 = 0.0, ur2 = 0.0;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const double Wp = __dmul_rn(__dmul_rn(wx[p & 1], wy[(p >> 1) & 1]), wz[(p >> 2) & 1]);
+            ur0 += Wp * (double)ux[p];
+            ur1 += Wp * (double)uy[p];
+            ur2 += Wp * (double)uz[p];
+        }
         F0 = -gam * (V0 - ur0);
         F1 = -gam * (V1 - ur1);
         F2 = -gam * (V2 - ur2);
@@ -175,63 +168,74 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         spread = false;
     }
 
-    // Eq. 9: reaction force -F_H W_p at corner p (one lane per corner)
-    if (spread && j == 0) {
-        const unsigned long long node =
-            (unsigned long long)(((long long)Z * A.ny + Y) * A.nx + X);
-        const long long a0 = to_fixed(-F0 * Wp, A.err);
-        const long long a1 = to_fixed(-F1 * Wp, A.err);
-        const long long a2 = to_fixed(-F2 * Wp, A.err);
-        hash_add(A, node, a0, a1, a2);
+    // Eq. 9: reaction force -F_H W_p at the eight corners, fixed point, exact sums
+    if (spread) {
+        const double s0 = -F0 * FIX_SCALE, s1 = -F1 * FIX_SCALE, s2 = -F2 * FIX_SCALE;
+        const bool ok = fabs(F0) < FIX_LIMIT && fabs(F1) < FIX_LIMIT && fabs(F2) < FIX_LIMIT;
+        if (!ok) atomicOr(A.err, ERR_RANGE);
+        if (ok) {
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
+                const double Wp = __dmul_rn(__dmul_rn(wx[c0], wy[c1]), wz[c2]);
+                const int X = xs[c0 + 1], Y = ys[c1 + 1], Z = zs[c2 + 1];
+                const long long row = (long long)Z * ny + Y;
+                const long long node = row * nx + X;
+                atomicAdd(A.fq + node, (unsigned long long)__double2ll_rn(s0 * Wp));
+                atomicAdd(A.fq + A.N + node, (unsigned long long)__double2ll_rn(s1 * Wp));
+                atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)__double2ll_rn(s2 * Wp));
+                atomicOr(A.mask + row * A.mwords + (X >> 5), 1u << (X & 31));
+            }
+        }
     }
 
-    if (lane == 0) {
-        // Eqs. 4-5: F_R = sqrt(2 gamma kT) xi, xi = sqrt3 (2u - 1), u from 53 Philox bits
-        unsigned long long c[4] = {(unsigned long long)step, (unsigned long long)i, 0ull, 0ull};
-        philox4x64_10(c, A.seed, 0ull);
-        const double sg = A.sig[i];
-        double R3[3];
+    // Eqs. 4-5: F_R = sqrt(2 gamma kT) xi, xi = sqrt3 (2u - 1) with
+    // u = ((x >> 11) + 1/2) 2^-53 from Philox(counter = (step, i, 0, 0), key = (seed, 0)).
+    // 2u - 1 is formed as fma((double)(2k + 1), 2^-53, -1): the same correctly
+    // rounded value as 2 ((double)k + 1/2) 2^-53 - 1, so F_R is bit-identical
+    // to the oracle's.
+    unsigned long long c[4] = {(unsigned long long)step, (unsigned long long)i, 0ull, 0ull};
+    philox4x64_10(c, A.seed, 0ull);
+    const double sg = A.sig[i];
+    double R3[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double u = __dmul_rn(__dadd_rn(__ull2double_rn(c[k] >> 11), 0.5), 0x1.0p-53);
-            const double xi = __dmul_rn(A.sqrt3, __dsub_rn(__dmul_rn(2.0, u), 1.0));
-            R3[k] = __dmul_rn(sg, xi);
-        }
-        const double FH3[3] = {F0, F1, F2};
-        double Vn[3] = {V0, V1, V2};
-        const double Vo[3] = {V0, V1, V2};
-        const double ro[3] = {r0, r1, r2};
-        const int L[3] = {A.nx, A.ny, A.nz};
-        const bool pin = A.pinned[i] != 0;
-        bool bad = false;
+    for (int k = 0; k < 3; ++k) {
+        const double t = __fma_rn(__ull2double_rn(2ull * (c[k] >> 11) + 1ull), 0x1.0p-53, -1.0);
+        R3[k] = __dmul_rn(sg, __dmul_rn(A.sqrt3, t));
+    }
+    const double FH3[3] = {F0, F1, F2};
+    const double Vo[3] = {V0, V1, V2};
+    const double ro[3] = {r0, r1, r2};
+    const int L[3] = {nx, ny, nz};
+    double Vn[3] = {V0, V1, V2};
+    const bool pin = A.pinned[i] != 0;
+    const double invM = 1.0 / A.mass[i];
+    bool bad = false;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            A.fh[k * cap + i] = FH3[k];
-            A.fr[k * cap + i] = R3[k];
-            if (!pin) {
-                // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
-                const double acc = __ddiv_rn(__dadd_rn(__dadd_rn(FH3[k], R3[k]), A.fext[k * cap + i]),
-                                             A.mass[i]);
-                Vn[k] = __dadd_rn(Vo[k], acc);
-                double rn = __dadd_rn(ro[k], Vn[k]);
-                if (rn < 0.0) rn = __dadd_rn(rn, (double)L[k]);
-                if (rn >= (double)L[k]) rn = __dsub_rn(rn, (double)L[k]);
-                bad |= !isfinite(Vn[k]) || !isfinite(rn) || !(rn >= 0.0) || !(rn < (double)L[k]);
-                if (bad) rn = 0.0;  // keep the next gather inside the box
-                A.v[k * cap + i] = Vn[k];
-                A.r[k * cap + i] = rn;
-            }
+    for (int k = 0; k < 3; ++k) {
+        A.fh[k * cap + i] = FH3[k];
+        A.fr[k * cap + i] = R3[k];
+        if (!pin) {
+            // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
+            Vn[k] = Vo[k] + (FH3[k] + R3[k] + A.fext[k * cap + i]) * invM;
+            double rn = ro[k] + Vn[k];
+            if (rn < 0.0) rn += (double)L[k];
+            if (rn >= (double)L[k]) rn -= (double)L[k];
+            const bool b = !isfinite(Vn[k]) || !(rn >= 0.0) || !(rn < (double)L[k]);
+            if (b) rn = 0.0;  // keep the next gather inside the box; reported as LBP_ENAN
+            bad |= b;
+            A.v[k * cap + i] = Vn[k];
+            A.r[k * cap + i] = rn;
         }
-        if (bad) atomicOr(A.err, ERR_NAN);
-        if (A.ring) {
-            const long long m = step - A.d_vacf[0];
-            if (m >= 0) {
-                const long long slot = m % A.ring_cap;
-                float *dst = A.ring + slot * 3 * (long long)A.np;
-                dst[i] = (float)Vn[0];
-                dst[A.np + i] = (float)Vn[1];
-                dst[2 * A.np + i] = (float)Vn[2];
-            }
+    }
+    if (bad) atomicOr(A.err, ERR_NAN);
+    if (A.ring) {
+        const long long m = step - A.d_vacf[0];
+        if (m >= 0) {
+            float *dst = A.ring + (m % A.ring_cap) * 3 * (long long)A.np;
+            dst[i] = (float)Vn[0];
+            dst[A.np + i] = (float)Vn[1];
+            dst[2 * A.np + i] = (float)Vn[2];
         }
     }
 }
@@ -244,6 +248,7 @@ cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
     A.ny = s.ny;
     A.nz = s.nz;
     A.P = s.P;
+    A.N = s.N;
     A.r = s.r;
     A.v = s.v;
     A.fh = s.fh;
@@ -261,87 +266,17 @@ cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
     A.sqrt3 = s.sqrt3;
     A.mode = s.mode;
     A.exclude_inside = s.exclude_inside;
-    A.hkey = s.hkey;
-    A.hacc = s.hacc;
-    A.hlist = s.hlist;
-    A.hcount = s.hcount;
-    A.hash_bits = s.hash_bits;
+    A.fq = s.fq;
+    A.mask = s.mask;
+    A.mwords = s.mwords;
     A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
-    const int warps_per_block = 8;
-    const unsigned grid = (unsigned)((s.np + warps_per_block - 1) / warps_per_block);
-    k_particles<<<grid, 32 * warps_per_block, 0, st>>>(A);
+    const int threads = 128;
+    const unsigned grid = (unsigned)((s.np + threads - 1) / threads);
+    k_particles<<<grid, threads, 0, st>>>(A);
     return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Body-force term at the nodes that received reaction forces, then clear.
-// The last block to finish resets the slot counter and advances the step.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_apply(float *g, long long P, unsigned long long *hkey,
-                                               unsigned long long *hacc, const unsigned int *hlist,
-                                               unsigned int *hcount, int hash_bits,
-                                               long long *d_step) {
-    const unsigned int H = 1u << hash_bits;
-    const unsigned int count = hcount[0];
-    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < count;
-         t += gridDim.x * blockDim.x) {
-        const unsigned int h = hlist[t];
-        const long long node = (long long)hkey[h];
-        const double F0 = (double)(long long)hacc[h] * FIX_INV;
-        const double F1 = (double)(long long)hacc[H + h] * FIX_INV;
-        const double F2 = (double)(long long)hacc[2 * (size_t)H + h] * FIX_INV;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const double G = wgt(a) * (3.0 * (ex(a) * F0 + ey(a) * F1 + ez(a) * F2));
-            float *q = g + (long long)a * P + node;
-            *q = (float)((double)*q + G);
-        }
-        hkey[h] = HASH_EMPTY;
-        hacc[h] = 0ull;
-        hacc[H + h] = 0ull;
-        hacc[2 * (size_t)H + h] = 0ull;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int done = atomicAdd(&hcount[1], 1u);
-        if (done == gridDim.x - 1) {
-            hcount[0] = 0u;
-            hcount[1] = 0u;
-            *d_step += 1;
-            __threadfence();
-        }
-    }
-}
-
-cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st) {
-    long long work = 8ll * s.np;
-    long long grid = (work + 255) / 256;
-    if (grid > 4ll * s.num_sms) grid = 4ll * s.num_sms;
-    if (grid < 1) grid = 1;
-    k_apply<<<(unsigned)grid, 256, 0, st>>>(dst, s.P, s.hkey, s.hacc, s.hlist, s.hcount,
-                                            s.hash_bits, s.d_step);
-    return cudaGetLastError();
-}
-
-__global__ void k_hash_clear(unsigned long long *hkey, unsigned long long *hacc, unsigned int H) {
-    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < H; t += gridDim.x * blockDim.x) {
-        hkey[t] = HASH_EMPTY;
-        hacc[t] = 0ull;
-        hacc[H + t] = 0ull;
-        hacc[2 * (size_t)H + t] = 0ull;
-    }
-}
-
-cudaError_t launch_hash_clear(Sim &s, cudaStream_t st) {
-    const unsigned int H = 1u << s.hash_bits;
-    k_hash_clear<<<(H + 255) / 256, 256, 0, st>>>(s.hkey, s.hacc, H);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return cudaMemsetAsync(s.hcount, 0, 2 * sizeof(unsigned int), st);
 }
 
 // ---------------------------------------------------------------------------
@@ -385,12 +320,9 @@ __global__ void k_cells(const double *r, int cap, int np, int *base, double *wei
     base[3 * i] = (int)b0;
     base[3 * i + 1] = (int)b1;
     base[3 * i + 2] = (int)b2;
-    for (int p = 0; p < 8; ++p) {
-        const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
-        weights[8 * i + p] =
-            __dmul_rn(__dmul_rn(__dmul_rn(1.0, c0 ? q0 : 1.0 - q0), c1 ? q1 : 1.0 - q1),
-                      c2 ? q2 : 1.0 - q2);
-    }
+    const double wx[2] = {1.0 - q0, q0}, wy[2] = {1.0 - q1, q1}, wz[2] = {1.0 - q2, q2};
+    for (int p = 0; p < 8; ++p)
+        weights[8 * i + p] = __dmul_rn(__dmul_rn(wx[p & 1], wy[(p >> 1) & 1]), wz[(p >> 2) & 1]);
 }
 
 cudaError_t launch_cells(Sim &s, int *base, double *weights, cudaStream_t st) {

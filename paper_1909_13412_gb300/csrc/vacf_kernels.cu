@@ -36,9 +36,7 @@ struct VacfArgs {
     int cap;     // ring samples
     int ncomp;   // 3 n_p
     int K;
-    const long long *d_step;
-    long long *d_vacf;  // [0] t0, [1] samples done
-    int step_offset;    // samples available = d_step - t0 + step_offset
+    long long *d_vacf;  // [0] t0, [1] samples done, [2] samples written, [3] block counter
     int flush;
     double *part;       // [nchunks][K+1]
     double *sum;        // [K+1]
@@ -49,7 +47,7 @@ struct VacfArgs {
 
 __device__ __forceinline__ bool vacf_range(const VacfArgs &A, long long &tb, long long &te) {
     tb = A.d_vacf[1];
-    te = *A.d_step - A.d_vacf[0] + A.step_offset;
+    te = A.d_vacf[2];
     if (te - tb > VB) te = tb + VB;
     if (A.flush) return te > tb;
     return te - tb == VB;
@@ -148,15 +146,13 @@ cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st) {
     A.cap = s.vacf_cap;
     A.ncomp = 3 * s.np;
     A.K = s.vacf_lag;
-    A.d_step = s.d_step;
     A.d_vacf = s.d_vacf;
-    A.step_offset = flush ? 0 : 1;
     A.flush = flush ? 1 : 0;
     A.part = s.vacf_part;
     A.sum = s.vacf_sum;
     A.cnt = s.vacf_cnt;
     A.np = s.np;
-    A.done = reinterpret_cast<unsigned int *>(s.d_vacf + 2);
+    A.done = reinterpret_cast<unsigned int *>(s.d_vacf + 3);
     dim3 g1((s.vacf_lag + VKT) / VKT, s.vacf_nchunks);
     k_vacf_corr<<<g1, 256, 0, st>>>(A);
     cudaError_t e = cudaGetLastError();

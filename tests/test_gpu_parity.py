@@ -69,6 +69,11 @@ def dev_scale(fo):
     return np.max(np.abs(fo - W4))
 
 
+# The oracle's own FP64 rounding leaves ~1e-16 absolute noise even in a state
+# at rest; comparisons of populations carry this floor.
+F64_FLOOR = 1e-14
+
+
 # ---------------------------------------------------------------- bit-exact pieces
 def test_philox_bit_exact():
     g = np.random.default_rng(0)
@@ -136,7 +141,7 @@ def test_stream_collide_one_step(shape, tau, graphs):
     o.step(1)
     fo = o.fhat()
     err = np.max(np.abs(gpu_pops(h) - fo))
-    assert err <= 1e-6 * dev_scale(fo), err / dev_scale(fo)
+    assert err <= 1e-6 * dev_scale(fo) + F64_FLOOR, err / dev_scale(fo)
 
 
 def test_set_read_populations_roundtrip_and_rest_state():
@@ -179,7 +184,7 @@ def test_many_steps_conserve_mass_and_stay_close():
     fo = o.fhat()
     f = gpu_pops(h)
     assert abs(f.sum() - f0.sum()) <= 1e-6 * dev_scale(f0) * 15 * 4096
-    assert np.max(np.abs(f - fo)) <= 1e-5 * dev_scale(f0)
+    assert np.max(np.abs(f - fo)) <= 1e-5 * dev_scale(f0) + F64_FLOOR
 
 
 # ---------------------------------------------------------------- coupled step
@@ -228,7 +233,7 @@ def test_coupled_brownian_particles(mode, exclude):
     d = np.minimum(d, np.array([19, 17, 14.0]) - d)
     assert np.max(d) <= 1e-6
     fo = o.fhat()
-    assert np.max(np.abs(gpu_pops(h) - fo)) <= 1e-5 * dev_scale(fo)
+    assert np.max(np.abs(gpu_pops(h) - fo)) <= 1e-5 * dev_scale(fo) + F64_FLOOR
     lbp.lbp_check(h)
 
 
