@@ -48,7 +48,7 @@ LAUNCHES_PER_STEP = 2  # particles, stream-collide (+2 VACF kernels every 64 ste
 
 def workload(name):
     return {"brownian_256": wl.BROWNIAN_256, "brownian_128": wl.BROWNIAN_128,
-            "brownian_64": wl.BROWNIAN_64}[name]
+            "brownian_64": wl.BROWNIAN_64, "profile_128": wl.PROFILE_128}[name]
 
 
 def dist_env():
@@ -194,12 +194,12 @@ def run_reference(args, w):
     return 0
 
 
-def config_of(w, world):
+def config_of(w, world, vacf_lag=VACF_LAG):
     nz, ny, nx = w.shape_zyx
     return {"workload": w.name, "lattice": [nx, ny, nz], "nodes_per_rank": w.nodes,
             "particles_per_rank": w.n_particles, "tau": w.tau, "kT": w.kT, "M": w.M,
             "gamma": w.gamma, "coupling": "stokeslet", "storage": "f32 deviation",
-            "vacf_max_lag": VACF_LAG, "parallelism": f"replicas{world}",
+            "vacf_max_lag": vacf_lag, "parallelism": f"replicas{world}",
             "l2": "no flush: 2 x 1.0 GB population buffers per step exceed the 129 MB L2"}
 
 
@@ -225,7 +225,7 @@ def run_gpu(args, w):
     h = lbp.lbp_create(nx, ny, nz, w.tau)
     lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
     lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise + rank)
-    lbp.lbp_vacf_configure(h, VACF_LAG)
+    lbp.lbp_vacf_configure(h, args.vacf_lag)
 
     # warm-up, then the timed region with per-launch events around the stream-collide kernel
     lbp.lbp_step(h, args.warmup)
@@ -282,7 +282,7 @@ def run_gpu(args, w):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(w, world),
+        "config": config_of(w, world, args.vacf_lag),
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide", "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -311,6 +311,7 @@ def main():
     ap.add_argument("--impl", choices=["lbp", "reference"], default="lbp")
     ap.add_argument("--workload", default="brownian_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--vacf-lag", type=int, default=VACF_LAG)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "lbp":
         args.warmup = 3

@@ -65,7 +65,7 @@ typedef enum {
     LBP_ETIMEOUT = 4, /* a bounded device wait ran out */
     LBP_ENAN = 5,     /* a particle velocity or position became non-finite */
     LBP_ESTATE = 6,   /* call not valid in the current state */
-    LBP_ERANGE = 7    /* a reaction force exceeded the fixed-point range (|F| >= 64) */
+    LBP_ERANGE = 7    /* a friction force exceeded the fixed-point range (|F_H| >= 32) */
 } lbp_status;
 
 /* Storage of the populations on the device.  Arithmetic is FP32 in every case;
@@ -141,10 +141,12 @@ lbp_status lbp_particles_set_state(lbp_sim *sim, const double *r, const double *
 lbp_status lbp_particles_read(lbp_sim *sim, double *r, double *v, double *f_h, double *f_r,
                               int on_device);
 
-/* Cell of each particle and the trilinear weights of its eight corners as the
- * device computes them (Eq. 9 spreading): base[i][k] = floor(r_i,k) (int32,
- * [n][3]); weights[i][p] for corner p = cx + 2 cy + 4 cz ([n][8] FP64).       */
-lbp_status lbp_particles_read_cells(lbp_sim *sim, int32_t *base, double *weights, int on_device);
+/* Cell of each particle as the device computes it: base[i][k] = floor(r_i,k)
+ * (int32, [n][3]) and the cell fraction q[i][k] = r_i,k - base[i][k] (FP64,
+ * exact, [n][3]).  The reaction force of Eq. 9 is shared over the corners
+ * base + {0,1}^3 with the trilinear weights of q (31-bit fixed-point
+ * fractions; the eight shares sum to -F_H exactly).                          */
+lbp_status lbp_particles_read_cells(lbp_sim *sim, int32_t *base, double *frac, int on_device);
 
 /* Number of particles.                                                       */
 lbp_status lbp_particles_count(lbp_sim *sim, int *n);

@@ -16,109 +16,70 @@
 namespace lbp {
 
 // ---------------------------------------------------------------------------
-// Fused pull-stream + moments + forced BGK collision (Eqs. 20, 12, 13, 15, 17,
-// 18, 19).  One thread per node; a block walks whole x-rows with a grid-stride
-// loop (the grid is a multiple of the SM count).  The 15 loads of a node are
-// independent, so every thread keeps 60 bytes in flight.
-//
-// Body force: the particle kernel has summed each particle's reaction force
-// -F_H W_p into fq (64-bit fixed point) and set the node's bit in `mask`.  A
-// warp covers 32 consecutive x of one row, i.e. exactly one mask word: lane 0
-// reads it and clears it, and the lanes whose bit is set add 3 w_a F.e_a to
-// their post-collision populations and zero their fq entries.
+// Fused pull-stream + moments + BGK collision (Eqs. 20, 12, 13, 15, 17, 19).
+// One thread per node and one block per 128-node segment of an x-row (a full
+// grid, not a persistent loop: the hardware block scheduler keeps the blocks
+// in flight on a narrow window of consecutive rows, which keeps the 15 read
+// and 15 write streams local in DRAM, and balances the tail).  The 15 loads
+// of a node are independent, so every thread has 60 bytes in flight.  The
+// body-force term of Eqs. 18-19 is added afterwards at the nodes next to
+// particles (k_apply_forces in particle_kernels.cu); the force term does not
+// depend on f, so the sum is the same.
 // ---------------------------------------------------------------------------
 template <int BX>
 __global__ void __launch_bounds__(BX) k_stream_collide(const float *__restrict__ src,
                                                        float *__restrict__ dst, int nx, int ny,
                                                        int nz, long long P, float omega,
-                                                       int nchunks, unsigned int *mask, int mwords,
-                                                       unsigned long long *fq, long long N,
-                                                       long long *bump) {
-    const long long nitems = (long long)ny * nz * nchunks;
-    const int lane = threadIdx.x & 31;
-    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const long long row = item / nchunks;
-        const int chunk = (int)(item - row * nchunks);
-        const int xw = chunk * BX + (threadIdx.x & ~31);  // first x of this warp
-        if (xw >= nx) continue;                           // uniform per warp
-        unsigned int word = 0u;
-        if (mask) {
-            const long long widx = row * mwords + (xw >> 5);
-            if (lane == 0) word = mask[widx];
-            word = __shfl_sync(0xffffffffu, word, 0);
-            if (lane == 0 && word) mask[widx] = 0u;
-        }
-        const int x = xw + lane;
-        if (x >= nx) continue;
-        const int z = (int)(row / ny);
-        const int y = (int)(row - (long long)z * ny);
-        // source coordinate x - e for e = -1, 0, +1 (index e + 1), periodic
-        const int X[3] = {x == nx - 1 ? 0 : x + 1, x, x == 0 ? nx - 1 : x - 1};
-        const int Y[3] = {y == ny - 1 ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
-        const int Z[3] = {z == nz - 1 ? 0 : z + 1, z, z == 0 ? nz - 1 : z - 1};
-        float g[Q];
+                                                       int nchunks, long long *bump) {
+    const unsigned item = blockIdx.x;
+    const unsigned row = item / (unsigned)nchunks;
+    const int chunk = (int)(item - row * (unsigned)nchunks);
+    const int x = chunk * BX + threadIdx.x;
+    if (bump && item == 0 && threadIdx.x == 0) *bump += 1;
+    if (x >= nx) return;
+    const int z = (int)(row / (unsigned)ny);
+    const int y = (int)(row - (unsigned)z * ny);
+    // source coordinate x - e for e = -1, 0, +1 (index e + 1), periodic
+    const int X[3] = {x == nx - 1 ? 0 : x + 1, x, x == 0 ? nx - 1 : x - 1};
+    const int Y[3] = {y == ny - 1 ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
+    const int Z[3] = {z == nz - 1 ? 0 : z + 1, z, z == 0 ? nz - 1 : z - 1};
+    float g[Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const long long s = (long long)a * P +
-                                ((long long)Z[ez(a) + 1] * ny + Y[ey(a) + 1]) * nx + X[ex(a) + 1];
-            g[a] = __ldg(src + s);
-        }
-        float drho = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            drho += g[a];
-            if (ex(a)) ux += ex(a) > 0 ? g[a] : -g[a];
-            if (ey(a)) uy += ey(a) > 0 ? g[a] : -g[a];
-            if (ez(a)) uz += ez(a) > 0 ? g[a] : -g[a];
-        }
-        const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-        const long long d = row * nx + x;
-        float F0 = 0.f, F1 = 0.f, F2 = 0.f;
-        if ((word >> lane) & 1u) {
-            const unsigned long long a0 = fq[d], a1 = fq[N + d], a2 = fq[2 * N + d];
-            fq[d] = 0ull;
-            fq[N + d] = 0ull;
-            fq[2 * N + d] = 0ull;
-            const float inv = 1.3877787807814457e-17f;  // 2^-56
-            F0 = 3.f * inv * __ll2float_rn((long long)a0);
-            F1 = 3.f * inv * __ll2float_rn((long long)a1);
-            F2 = 3.f * inv * __ll2float_rn((long long)a2);
-        }
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float eu = (float)ex(a) * ux + (float)ey(a) * uy + (float)ez(a) * uz;
-            const float geq = wgtf(a) * (drho + 3.f * eu + 4.5f * eu * eu - usq15);
-            const float G = wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
-            dst[(long long)a * P + d] = g[a] + omega * (geq - g[a]) + G;
-        }
+    for (int a = 0; a < Q; ++a) {
+        const long long s = (long long)a * P +
+                            ((long long)Z[ez(a) + 1] * ny + Y[ey(a) + 1]) * nx + X[ex(a) + 1];
+        g[a] = __ldg(src + s);
     }
-    if (bump && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+    float drho = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        drho += g[a];
+        if (ex(a)) ux += ex(a) > 0 ? g[a] : -g[a];
+        if (ey(a)) uy += ey(a) > 0 ? g[a] : -g[a];
+        if (ez(a)) uz += ez(a) > 0 ? g[a] : -g[a];
+    }
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const long long d = (long long)row * nx + x;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const float eu = (float)ex(a) * ux + (float)ey(a) * uy + (float)ez(a) * uz;
+        const float geq = wgtf(a) * (drho + 3.f * eu + 4.5f * eu * eu - usq15);
+        dst[(long long)a * P + d] = g[a] + omega * (geq - g[a]);
+    }
 }
 
 constexpr int SC_BX = 128;
-static int g_sc_blocks_per_sm = 0;
 
-// Occupancy of the stream-collide kernel; called once at lbp_create (outside
-// any stream capture).
-cudaError_t prepare_lbm_kernels() {
-    if (g_sc_blocks_per_sm) return cudaSuccess;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sc_blocks_per_sm,
-                                                                  k_stream_collide<SC_BX>, SC_BX, 0);
-    if (g_sc_blocks_per_sm < 1) g_sc_blocks_per_sm = 1;
-    return e;
-}
+cudaError_t prepare_lbm_kernels() { return cudaSuccess; }
 
 cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, cudaStream_t st) {
     constexpr int BX = SC_BX;
     const int nchunks = (s.nx + BX - 1) / BX;
     const long long items = (long long)s.ny * s.nz * nchunks;
-    long long grid = (long long)s.num_sms * g_sc_blocks_per_sm;
-    if (grid > items) grid = items;
-    if (grid < 1) grid = 1;
-    const bool forces = s.np > 0 && s.fq != nullptr;
-    k_stream_collide<BX><<<(unsigned)grid, BX, 0, st>>>(
-        src, dst, s.nx, s.ny, s.nz, s.P, (float)(1.0 / s.tau), nchunks,
-        forces ? s.mask : nullptr, s.mwords, s.fq, s.N, s.d_step);
+    // the step index advances here when no particle kernel runs this step
+    k_stream_collide<BX><<<(unsigned)items, BX, 0, st>>>(src, dst, s.nx, s.ny, s.nz, s.P,
+                                                          (float)(1.0 / s.tau), nchunks,
+                                                          s.np > 0 ? nullptr : s.d_step);
     return cudaGetLastError();
 }
 

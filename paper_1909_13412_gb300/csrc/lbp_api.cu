@@ -4,9 +4,10 @@
 // conversion for the ABI arrays, and the per-step launch sequence
 //
 //      s0:  k_particles (fhat^{n-1} -> F_H, V, r, reaction forces)
-//           -> k_stream_collide (fhat^{n-1} + forces -> fhat^n)
+//           -> k_stream_collide (fhat^{n-1} -> fhat^n without the body force)
+//           -> k_apply_forces (body force at the particles' corner nodes)
 //      s1:  every 64th step, the VACF block, forked after k_particles and
-//           joined after k_stream_collide, so it overlaps the lattice pass.
+//           joined at the end of the step, so it overlaps the lattice pass.
 //
 // A step is captured into a CUDA graph per (buffer parity, VACF block due)
 // and replayed.
@@ -132,6 +133,7 @@ lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
     }
+    if (s->np > 0) CK(launch_apply_forces(*s, dst, s->s0));
     if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
     return LBP_OK;
 }
@@ -254,7 +256,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
-                    s->mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->ring,
+                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->nodes, s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -393,7 +395,7 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
             }
             *pp = nb;
         }
-        double **sca[] = {&s->mass, &s->gamma, &s->radius, &s->sig};
+        double **sca[] = {&s->mass, &s->inv_mass, &s->gamma, &s->radius, &s->sig};
         for (double **pp : sca) {
             double *nb = nullptr;
             TRY(dalloc(&nb, (size_t)cap));
@@ -412,6 +414,11 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
             cudaFree(s->pinned);
         }
         s->pinned = np8;
+        int *nn = nullptr;
+        TRY(dalloc(&nn, 8 * (size_t)cap));
+        CK(cudaMemset(nn, 0xff, sizeof(int) * 8 * (size_t)cap));
+        if (s->nodes) cudaFree(s->nodes);
+        s->nodes = nn;
         // reaction-force accumulator: 3 x 64-bit per node, allocated once
         if (!s->fq) {
             TRY(dalloc(&s->fq, 3 * (size_t)s->N));
@@ -432,6 +439,9 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
     std::vector<double> sg(n);
     for (int i = 0; i < n; ++i) sg[i] = std::sqrt(2.0 * hg[i] * s->kT);
     CK(cudaMemcpy(s->mass + s->np, hm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    std::vector<double> him(n);
+    for (int i = 0; i < n; ++i) him[i] = 1.0 / hm[i];
+    CK(cudaMemcpy(s->inv_mass + s->np, him.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->gamma + s->np, hg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->radius + s->np, hR.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->sig + s->np, sg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
@@ -557,20 +567,20 @@ lbp_status lbp_particles_read(lbp_sim *s, double *r, double *v, double *f_h, dou
     return leave(s);
 }
 
-lbp_status lbp_particles_read_cells(lbp_sim *s, int32_t *base, double *weights, int on_device) {
+lbp_status lbp_particles_read_cells(lbp_sim *s, int32_t *base, double *frac, int on_device) {
     CHECK_SIM(s);
-    if (!base || !weights) return fail(LBP_EINVAL, "lbp_particles_read_cells: null output");
+    if (!base || !frac) return fail(LBP_EINVAL, "lbp_particles_read_cells: null output");
     if (s->np == 0) return LBP_OK;
     TRY(enter(s));
     if (on_device) {
-        CK(launch_cells(*s, base, weights, s->s0));
+        CK(launch_cells(*s, base, frac, s->s0));
     } else {
-        TRY(stage(s, sizeof(double) * 11 * (size_t)s->np));
-        int *db = reinterpret_cast<int *>(s->stage);
-        double *dw = s->stage + 2 * (size_t)s->np;
-        CK(launch_cells(*s, db, dw, s->s0));
+        TRY(stage(s, sizeof(double) * 6 * (size_t)s->np));
+        double *df = s->stage;
+        int *db = reinterpret_cast<int *>(s->stage + 3 * (size_t)s->np);
+        CK(launch_cells(*s, db, df, s->s0));
         CK(cudaMemcpyAsync(base, db, sizeof(int) * 3 * s->np, cudaMemcpyDeviceToHost, s->s0));
-        CK(cudaMemcpyAsync(weights, dw, sizeof(double) * 8 * s->np, cudaMemcpyDeviceToHost, s->s0));
+        CK(cudaMemcpyAsync(frac, df, sizeof(double) * 3 * s->np, cudaMemcpyDeviceToHost, s->s0));
         CK(cudaStreamSynchronize(s->s0));
     }
     return leave(s);
@@ -688,7 +698,7 @@ lbp_status lbp_check(lbp_sim *s) {
     if (err) {
         CK(cudaMemset(s->d_err, 0, sizeof(int)));
         if (err & ERR_NAN) return fail(LBP_ENAN, "lbp_check: a particle velocity or position became non-finite or left the box");
-        return fail(LBP_ERANGE, "lbp_check: a friction force exceeded the fixed-point range (|F_H| >= 64)");
+        return fail(LBP_ERANGE, "lbp_check: a friction force exceeded the fixed-point range (|F_H| >= 32)");
     }
     return LBP_OK;
 }

@@ -37,7 +37,7 @@ __host__ __device__ constexpr float wgtf(int a) {
 // Reaction forces are summed per node in 64-bit fixed point so that the sum
 // is exact and independent of the order in which particles add to it.
 constexpr double FIX_SCALE = 72057594037927936.0;  // 2^56
-constexpr double FIX_LIMIT = 64.0;                 // |F_H| < 2^6 per particle
+constexpr double FIX_LIMIT = 32.0;                 // |F_H| < 2^5 per particle
 
 // error bits in Sim::d_err
 constexpr int ERR_NAN = 1;
@@ -92,7 +92,7 @@ struct Sim {
     // particles, FP64 structure of arrays, 3 planes of cap for vectors
     int np = 0, cap = 0;
     double *r = nullptr, *v = nullptr, *fh = nullptr, *fr = nullptr, *fext = nullptr;
-    double *mass = nullptr, *gamma = nullptr, *radius = nullptr, *sig = nullptr;
+    double *mass = nullptr, *inv_mass = nullptr, *gamma = nullptr, *radius = nullptr, *sig = nullptr;
     unsigned char *pinned = nullptr;
     double kT = 0.0;
     unsigned long long seed = 0;
@@ -101,10 +101,11 @@ struct Sim {
     double sqrt3 = 0.0;
 
     // reaction force: fixed-point accumulator per node and a bit per node
-    // marking the nodes that hold one (both cleared by the stream-collide kernel)
+    // marking the nodes that hold one (both cleared by the apply pass)
     unsigned long long *fq = nullptr;  // [3][N], allocated with the first particle
     unsigned int *mask = nullptr;      // [ny * nz][mwords]
     int mwords = 0;                    // ceil(nx / 32)
+    int *nodes = nullptr;              // [8 cap] corner nodes of this step's shares
 
     // VACF
     int vacf_lag = -1;
@@ -147,10 +148,11 @@ cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, doub
                           cudaStream_t st);
 // particle_kernels.cu
 cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st);
+cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);
-cudaError_t launch_cells(Sim &s, int *base, double *weights, cudaStream_t st);
+cudaError_t launch_cells(Sim &s, int *base, double *frac, cudaStream_t st);
 cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long long *key,
                           unsigned long long *out, int64_t n, cudaStream_t st);
 // vacf_kernels.cu

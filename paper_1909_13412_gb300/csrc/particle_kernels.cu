@@ -1,27 +1,41 @@
 // particle_kernels.cu -- two-way coupling kernel of liblbp (sm_103a).
 //
-// k_particles: one thread per particle.  It gathers u^N at the eight corners
-// of the particle's cell from the stored populations (a pull, i.e. the
-// streamed f^n of Eq. 20), fits the Stokeslet flow of Eq. 8, draws the Philox
-// random force (Eqs. 4-5), advances V and r (Eqs. 1-2) and adds the reaction
-// force -F_H W_p (Eq. 9) to the nodes of its cell.
+// k_particles: a block of 256 threads serves 32 particles in three phases.
+//   A. eight threads per particle (one per corner) gather u^N at the corners
+//      of the particle's cell from the stored populations (a pull, i.e. the
+//      streamed f^n of Eq. 20): 14 independent loads per thread;
+//   B. one thread per particle fits the Stokeslet flow of Eq. 8, draws the
+//      Philox random force (Eqs. 4-5) and advances V and r (Eqs. 1-2);
+//   C. eight threads per particle add the shares of the reaction force -F_H
+//      (Eq. 9) to the corner nodes.
+// k_apply_forces: adds the body-force term 3 w_a F.e_a of Eqs. 18-19 to the
+//   post-collision populations at the nodes that received reaction forces.
 //
-// Why a thread, not a warp, per particle: GB300 issues FP64 at 1/64 of the
+// Why one thread per particle in phase B: GB300 issues FP64 at 1/64 of the
 // FP32 rate, so a warp-wide FP64 instruction costs the same whether one lane
-// or 32 lanes need it.  Packing 32 particles into a warp divides the FP64
-// instruction count per particle by 32; with one particle per warp the FP64
-// work of the fit dominated the whole time step.  Precision split: corner
-// geometry (d_p, 1/r_p, the Stokeslet basis a_p and the unit vector e^N) in
-// FP32; relative velocities w_p, the normal-equation sums sum w.a and
-// sum |a|^2, U_inf, F_H, the random force, the trilinear weights and the
-// Langevin update in FP64.
+// or 32 lanes need it.  Packing 32 particles into the warp that does the FP64
+// work divides its FP64 instruction count per particle by 32; with one
+// particle per warp the FP64 work of the fit dominated the whole time step.
+//
+// Precision split.  FP64: positions, velocities, the cell/fraction of r, the
+// least-squares solve U_inf = (sum w.a)/(sum |a|^2), F_H, the random force
+// and the Langevin update.  FP32: the gathered u^N (the lattice is FP32), the
+// corner geometry (d_p, 1/r_p, the basis a_p, e^N) and the eight-point sums of
+// the normal equations.  The relative velocity w_p = u_p - V is formed as
+// (u_p - V_hi) - V_lo with V = V_hi + V_lo split into two floats, so it keeps
+// FP32 relative accuracy even when the particle moves with the fluid and u_p
+// and V nearly cancel.
 //
 // Reaction forces go to a dense per-node accumulator of 64-bit fixed-point
 // integers (scale 2^56), added with integer atomics: the per-node sum is exact
 // and independent of the order in which particles add to it (no
-// floating-point atomics).  A bit per node in `mask` marks the nodes that
-// received a force; the stream-collide kernel reads the mask, applies the
-// body-force term of Eqs. 18-19 at those nodes and clears both.
+// floating-point atomics).  -F_H is converted to fixed point once and split
+// over the eight corners by the trilinear fractions with integer arithmetic
+// (the 1 - q share is the remainder), so the eight shares sum to -F_H exactly
+// and the momentum the fluid receives is exactly what the particle lost.  A
+// bit per node in `mask` marks the nodes that received a force; the apply
+// pass claims each node once by clearing its bit, applies the body-force
+// term there and zeroes its accumulator.
 #include <cuda_runtime.h>
 
 #include "lbp_internal.cuh"
@@ -34,7 +48,7 @@ struct ParticleArgs {
     long long P;
     long long N;
     double *r, *v, *fh, *fr;
-    const double *fext, *mass, *gamma, *radius, *sig;
+    const double *fext, *inv_mass, *gamma, *radius, *sig;
     const unsigned char *pinned;
     int cap, np;
     const long long *d_step;
@@ -44,6 +58,7 @@ struct ParticleArgs {
     unsigned long long *fq;  // [3][N] fixed-point reaction force
     unsigned int *mask;      // [rows][mwords]
     int mwords;
+    int *nodes;              // [8 cap] corner nodes that received a share, or -1
     float *ring;
     int ring_cap;
     long long *d_vacf;  // [0] first sampled step, [2] samples written
@@ -52,191 +67,247 @@ struct ParticleArgs {
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-__global__ void __launch_bounds__(128) k_particles(const ParticleArgs A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int PB = 32;  // particles per block of k_particles
+
+__global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
+    __shared__ int s_base[PB][3];
+    __shared__ float s_u[PB][8][3];
+    __shared__ long long s_fix[PB][3];
+    __shared__ long long s_frac[PB][3];
+    __shared__ int s_spread[PB];
+    const int t = threadIdx.x, lane = t & 31;
+    const int i0 = blockIdx.x * PB;
     const long long step = *A.d_step;
-    if (A.ring && i == 0) {
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int cap = A.cap;
+    if (A.ring && blockIdx.x == 0 && t == 0) {
         const long long m = step - A.d_vacf[0];
         if (m >= 0) A.d_vacf[2] = m + 1;
     }
-    if (i >= A.np) return;
-    const int cap = A.cap;
-    const int nx = A.nx, ny = A.ny, nz = A.nz;
-    const double r0 = A.r[i], r1 = A.r[cap + i], r2 = A.r[2 * cap + i];
-    const double V0 = A.v[i], V1 = A.v[cap + i], V2 = A.v[2 * cap + i];
 
-    // cell: base = floor(r), q = r - base (exact), corners base + {0,1}
-    const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
-    const double q0 = r0 - b0, q1 = r1 - b1, q2 = r2 - b2;
-    const int ib0 = (int)b0, ib1 = (int)b1, ib2 = (int)b2;
-    // source coordinates base + o for o = -1, 0, 1, 2 (index o + 1), periodic
-    const int xs[4] = {wrapi(ib0 - 1, nx), ib0, wrapi(ib0 + 1, nx), wrapi(ib0 + 2, nx)};
-    const int ys[4] = {wrapi(ib1 - 1, ny), ib1, wrapi(ib1 + 1, ny), wrapi(ib1 + 2, ny)};
-    const int zs[4] = {wrapi(ib2 - 1, nz), ib2, wrapi(ib2 + 1, nz), wrapi(ib2 + 2, nz)};
+    // ---- cell of each particle (warp 0): base = floor(r), q = r - base (exact)
+    const int ip = i0 + lane;
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    if (t < 32 && ip < A.np) {
+        r0 = A.r[ip];
+        r1 = A.r[cap + ip];
+        r2 = A.r[2 * cap + ip];
+        const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
+        q0 = r0 - b0;
+        q1 = r1 - b1;
+        q2 = r2 - b2;
+        s_base[lane][0] = (int)b0;
+        s_base[lane][1] = (int)b1;
+        s_base[lane][2] = (int)b2;
+    }
+    __syncthreads();
 
-    // pass 1: u at the eight corners, u = sum_a e_a g_a(x_p - e_a) (FP32)
-    float ux[8], uy[8], uz[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
+    // ---- phase A: u at corner p, u = sum_a e_a g_a(x_p - e_a) (FP32)
+    const int j = t >> 3, p = t & 7;
+    const int ij = i0 + j;
+    const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
+    int X = 0, Y = 0, Z = 0;
+    if (ij < A.np) {
+        X = wrapi(s_base[j][0] + c0, nx);
+        Y = wrapi(s_base[j][1] + c1, ny);
+        Z = wrapi(s_base[j][2] + c2, nz);
+        const int xs[3] = {wrapi(X + 1, nx), X, wrapi(X - 1, nx)};  // x - e for e = -1, 0, 1
+        const int ys[3] = {wrapi(Y + 1, ny), Y, wrapi(Y - 1, ny)};
+        const int zs[3] = {wrapi(Z + 1, nz), Z, wrapi(Z - 1, nz)};
         float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
         for (int a = 1; a < Q; ++a) {
             const long long src = (long long)a * A.P +
-                                  ((long long)zs[c2 - ez(a) + 1] * ny + ys[c1 - ey(a) + 1]) * nx +
-                                  xs[c0 - ex(a) + 1];
+                                  ((long long)zs[ez(a) + 1] * ny + ys[ey(a) + 1]) * nx + xs[ex(a) + 1];
             const float gv = __ldg(A.g + src);
             if (ex(a)) sx += ex(a) > 0 ? gv : -gv;
             if (ey(a)) sy += ey(a) > 0 ? gv : -gv;
             if (ez(a)) sz += ez(a) > 0 ? gv : -gv;
         }
-        ux[p] = sx;
-        uy[p] = sy;
-        uz[p] = sz;
+        s_u[j][p][0] = sx;
+        s_u[j][p][1] = sy;
+        s_u[j][p][2] = sz;
     }
+    __syncthreads();
 
-    // trilinear weights of the corners (Eq. 9 reading), FP64, same expression as the oracle
-    const double wx[2] = {1.0 - q0, q0}, wy[2] = {1.0 - q1, q1}, wz[2] = {1.0 - q2, q2};
-
-    const double gam = A.gamma[i];
-    double F0 = 0.0, F1 = 0.0, F2 = 0.0;
-    bool spread = true;
-    if (A.mode == LBP_STOKESLET) {
-        // e^N: direction of the mean relative velocity w-bar = mean(u_p) - V
-        float su0 = 0.f, su1 = 0.f, su2 = 0.f;
+    // ---- phase B (warp 0): fit, random force, Langevin update
+    if (t < 32 && ip < A.np) {
+        const int i = ip;
+        const double V0 = A.v[i], V1 = A.v[cap + i], V2 = A.v[2 * cap + i];
+        const double gam = A.gamma[i];
+        double F0 = 0.0, F1 = 0.0, F2 = 0.0;
+        bool spread = true;
+        if (A.mode == LBP_STOKESLET) {
+            // w_p = u_p - V in FP32 with V split as V_hi + V_lo
+            const float Vh0 = (float)V0, Vh1 = (float)V1, Vh2 = (float)V2;
+            const float Vl0 = (float)(V0 - (double)Vh0), Vl1 = (float)(V1 - (double)Vh1),
+                        Vl2 = (float)(V2 - (double)Vh2);
+            float w0[8], w1[8], w2[8];
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            su0 += ux[p];
-            su1 += uy[p];
-            su2 += uz[p];
-        }
-        const double m0 = (double)(su0 * 0.125f) - V0;
-        const double m1 = (double)(su1 * 0.125f) - V1;
-        const double m2 = (double)(su2 * 0.125f) - V2;
-        const double n2 = m0 * m0 + m1 * m1 + m2 * m2;
-        if (n2 > 0.0) {
-            const double inv = 1.0 / sqrt(n2);
-            const float e0 = (float)(m0 * inv), e1 = (float)(m1 * inv), e2 = (float)(m2 * inv);
-            const float R = (float)A.radius[i];
-            const float R2 = R * R, R34 = 0.75f * R;
-            // corner offsets d_p = c - q
-            const float dx[2] = {(float)(-q0), (float)(1.0 - q0)};
-            const float dy[2] = {(float)(-q1), (float)(1.0 - q1)};
-            const float dz[2] = {(float)(-q2), (float)(1.0 - q2)};
-            double num = 0.0, den = 0.0;
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const float d0 = dx[p & 1], d1 = dy[(p >> 1) & 1], d2 = dz[(p >> 2) & 1];
-                const float rr = d0 * d0 + d1 * d1 + d2 * d2;
-                if (rr < 1e-24f) continue;
-                if (A.exclude_inside && rr < R2) continue;
-                const float ir = rsqrtf(rr);
-                const float x = e0 * d0 + e1 * d1 + e2 * d2;
-                const float k1 = 1.f - R34 * ir;
-                const float k2 = R34 * x * ir * ir * ir;
-                const double a0 = (double)(k1 * e0 - k2 * d0);
-                const double a1 = (double)(k1 * e1 - k2 * d1);
-                const double a2 = (double)(k1 * e2 - k2 * d2);
-                // normal equations of the one-parameter least-squares fit, FP64
-                num += ((double)ux[p] - V0) * a0 + ((double)uy[p] - V1) * a1 + ((double)uz[p] - V2) * a2;
-                den += a0 * a0 + a1 * a1 + a2 * a2;
+            for (int c = 0; c < 8; ++c) {
+                w0[c] = (s_u[lane][c][0] - Vh0) - Vl0;
+                w1[c] = (s_u[lane][c][1] - Vh1) - Vl1;
+                w2[c] = (s_u[lane][c][2] - Vh2) - Vl2;
+                m0 += w0[c];
+                m1 += w1[c];
+                m2 += w2[c];
             }
-            const double U = den > 0.0 ? num / den : 0.0;
-            const double gU = gam * U;
-            F0 = gU * (double)e0;
-            F1 = gU * (double)e1;
-            F2 = gU * (double)e2;
-        }
-    } else if (A.mode == LBP_POINTWISE) {
-        // Eq. 7 with u(r_i) = sum_p W_p u^N_p
-        double ur0 = 0.0, ur1 = 0.0, ur2 = 0.0;
+            // e^N: direction of the mean relative velocity (scaled before the
+            // norm so that tiny velocities do not underflow)
+            const float sc = fmaxf(fabsf(m0), fmaxf(fabsf(m1), fabsf(m2)));
+            if (sc > 0.f) {
+                const float is = 1.f / sc;
+                const float n0 = m0 * is, n1 = m1 * is, n2 = m2 * is;
+                const float inrm = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+                const float e0 = n0 * inrm, e1 = n1 * inrm, e2 = n2 * inrm;
+                const float R = (float)A.radius[i];
+                const float R2 = R * R, R34 = 0.75f * R;
+                // corner offsets d_p = c - q
+                const float dx[2] = {(float)(-q0), (float)(1.0 - q0)};
+                const float dy[2] = {(float)(-q1), (float)(1.0 - q1)};
+                const float dz[2] = {(float)(-q2), (float)(1.0 - q2)};
+                float num = 0.f, den = 0.f;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            const double Wp = __dmul_rn(__dmul_rn(wx[p & 1], wy[(p >> 1) & 1]), wz[(p >> 2) & 1]);
-            ur0 += Wp * (double)ux[p];
-            ur1 += Wp * (double)uy[p];
-            ur2 += Wp * (double)uz[p];
+                for (int c = 0; c < 8; ++c) {
+                    const float d0 = dx[c & 1], d1 = dy[(c >> 1) & 1], d2 = dz[(c >> 2) & 1];
+                    const float rr = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (rr < 1e-24f) continue;
+                    if (A.exclude_inside && rr < R2) continue;
+                    const float ir = rsqrtf(rr);
+                    const float x = e0 * d0 + e1 * d1 + e2 * d2;
+                    const float k1 = 1.f - R34 * ir;
+                    const float k2 = R34 * x * ir * ir * ir;
+                    const float a0 = k1 * e0 - k2 * d0, a1 = k1 * e1 - k2 * d1, a2 = k1 * e2 - k2 * d2;
+                    num += w0[c] * a0 + w1[c] * a1 + w2[c] * a2;
+                    den += a0 * a0 + a1 * a1 + a2 * a2;
+                }
+                // one-parameter normal equation U sum|a|^2 = sum w.a, solved in FP64
+                const double U = den > 0.f ? (double)num / (double)den : 0.0;
+                const double gU = gam * U;
+                F0 = gU * (double)e0;
+                F1 = gU * (double)e1;
+                F2 = gU * (double)e2;
+            }
+        } else if (A.mode == LBP_POINTWISE) {
+            // Eq. 7 with u(r_i) = sum_p W_p u^N_p (trilinear)
+            const float fx = (float)q0, fy = (float)q1, fz = (float)q2;
+            const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
+            float ur0 = 0.f, ur1 = 0.f, ur2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float Wp = wx[c & 1] * wy[(c >> 1) & 1] * wz[(c >> 2) & 1];
+                ur0 += Wp * s_u[lane][c][0];
+                ur1 += Wp * s_u[lane][c][1];
+                ur2 += Wp * s_u[lane][c][2];
+            }
+            F0 = -gam * (V0 - (double)ur0);
+            F1 = -gam * (V1 - (double)ur1);
+            F2 = -gam * (V2 - (double)ur2);
+        } else {
+            // Eq. 6: friction against a fluid at rest; nothing is returned to the fluid
+            F0 = -gam * V0;
+            F1 = -gam * V1;
+            F2 = -gam * V2;
+            spread = false;
         }
-        F0 = -gam * (V0 - ur0);
-        F1 = -gam * (V1 - ur1);
-        F2 = -gam * (V2 - ur2);
-    } else {
-        // Eq. 6: friction against a fluid at rest; nothing is returned to the fluid
-        F0 = -gam * V0;
-        F1 = -gam * V1;
-        F2 = -gam * V2;
-        spread = false;
-    }
+        if (spread) {
+            const bool ok = fabs(F0) < FIX_LIMIT && fabs(F1) < FIX_LIMIT && fabs(F2) < FIX_LIMIT;
+            if (!ok) {
+                atomicOr(A.err, ERR_RANGE);
+                spread = false;
+            } else {
+                s_fix[lane][0] = __double2ll_rn(-F0 * FIX_SCALE);
+                s_fix[lane][1] = __double2ll_rn(-F1 * FIX_SCALE);
+                s_fix[lane][2] = __double2ll_rn(-F2 * FIX_SCALE);
+                // q as 31-bit fractions q31 = floor(q 2^31) in bits 32..62
+                s_frac[lane][0] = (long long)((unsigned long long)__double2uint_rz(q0 * 2147483648.0) << 32);
+                s_frac[lane][1] = (long long)((unsigned long long)__double2uint_rz(q1 * 2147483648.0) << 32);
+                s_frac[lane][2] = (long long)((unsigned long long)__double2uint_rz(q2 * 2147483648.0) << 32);
+            }
+        }
+        s_spread[lane] = spread ? 1 : 0;
 
-    // Eq. 9: reaction force -F_H W_p at the eight corners, fixed point, exact sums
-    if (spread) {
-        const double s0 = -F0 * FIX_SCALE, s1 = -F1 * FIX_SCALE, s2 = -F2 * FIX_SCALE;
-        const bool ok = fabs(F0) < FIX_LIMIT && fabs(F1) < FIX_LIMIT && fabs(F2) < FIX_LIMIT;
-        if (!ok) atomicOr(A.err, ERR_RANGE);
-        if (ok) {
+        // Eqs. 4-5: F_R = sqrt(2 gamma kT) xi, xi = sqrt3 (2u - 1) with
+        // u = ((x >> 11) + 1/2) 2^-53 from Philox(counter = (step, i, 0, 0), key = (seed, 0)).
+        // 2u - 1 is formed as fma((double)(2k + 1), 2^-53, -1): the same correctly
+        // rounded value as 2 ((double)k + 1/2) 2^-53 - 1, so F_R is bit-identical
+        // to the oracle's.
+        unsigned long long ctr[4] = {(unsigned long long)step, (unsigned long long)i, 0ull, 0ull};
+        philox4x64_10(ctr, A.seed, 0ull);
+        const double sg = A.sig[i];
+        double R3[3];
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
-                const double Wp = __dmul_rn(__dmul_rn(wx[c0], wy[c1]), wz[c2]);
-                const int X = xs[c0 + 1], Y = ys[c1 + 1], Z = zs[c2 + 1];
-                const long long row = (long long)Z * ny + Y;
-                const long long node = row * nx + X;
-                atomicAdd(A.fq + node, (unsigned long long)__double2ll_rn(s0 * Wp));
-                atomicAdd(A.fq + A.N + node, (unsigned long long)__double2ll_rn(s1 * Wp));
-                atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)__double2ll_rn(s2 * Wp));
-                atomicOr(A.mask + row * A.mwords + (X >> 5), 1u << (X & 31));
+        for (int k = 0; k < 3; ++k) {
+            const double tt = __fma_rn(__ull2double_rn(2ull * (ctr[k] >> 11) + 1ull), 0x1.0p-53, -1.0);
+            R3[k] = __dmul_rn(sg, __dmul_rn(A.sqrt3, tt));
+        }
+        const double FH3[3] = {F0, F1, F2};
+        const double Vo[3] = {V0, V1, V2};
+        const double ro[3] = {r0, r1, r2};
+        const int L[3] = {nx, ny, nz};
+        double Vn[3] = {V0, V1, V2};
+        const bool pin = A.pinned[i] != 0;
+        const double invM = A.inv_mass[i];
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            A.fh[k * cap + i] = FH3[k];
+            A.fr[k * cap + i] = R3[k];
+            if (!pin) {
+                // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
+                Vn[k] = Vo[k] + (FH3[k] + R3[k] + A.fext[k * cap + i]) * invM;
+                double rn = ro[k] + Vn[k];
+                if (rn < 0.0) rn += (double)L[k];
+                if (rn >= (double)L[k]) rn -= (double)L[k];
+                const bool b = !isfinite(Vn[k]) || !(rn >= 0.0) || !(rn < (double)L[k]);
+                if (b) rn = 0.0;  // keep the next gather inside the box; reported as LBP_ENAN
+                bad |= b;
+                A.v[k * cap + i] = Vn[k];
+                A.r[k * cap + i] = rn;
+            }
+        }
+        if (bad) atomicOr(A.err, ERR_NAN);
+        if (A.ring) {
+            const long long m = step - A.d_vacf[0];
+            if (m >= 0) {
+                float *dst = A.ring + (m % A.ring_cap) * 3 * (long long)A.np;
+                dst[i] = (float)Vn[0];
+                dst[A.np + i] = (float)Vn[1];
+                dst[2 * A.np + i] = (float)Vn[2];
             }
         }
     }
+    __syncthreads();
 
-    // Eqs. 4-5: F_R = sqrt(2 gamma kT) xi, xi = sqrt3 (2u - 1) with
-    // u = ((x >> 11) + 1/2) 2^-53 from Philox(counter = (step, i, 0, 0), key = (seed, 0)).
-    // 2u - 1 is formed as fma((double)(2k + 1), 2^-53, -1): the same correctly
-    // rounded value as 2 ((double)k + 1/2) 2^-53 - 1, so F_R is bit-identical
-    // to the oracle's.
-    unsigned long long c[4] = {(unsigned long long)step, (unsigned long long)i, 0ull, 0ull};
-    philox4x64_10(c, A.seed, 0ull);
-    const double sg = A.sig[i];
-    double R3[3];
+    // ---- phase C: share of corner p of the fixed-point reaction force -F_H.
+    // Per axis the far corner (c = 1) takes floor(v q) -- the signed high half
+    // of (2 v) (q31 2^32) -- and the near corner the rest, so the eight shares
+    // add up to v exactly.  |v| < 2^61 (|F_H| < 32), so 2 v stays within int64.
+    if (ij < A.np) {
+        int node_out = -1;
+        if (s_spread[j]) {
+            const int cc[3] = {c0, c1, c2};
+            long long sh[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double t = __fma_rn(__ull2double_rn(2ull * (c[k] >> 11) + 1ull), 0x1.0p-53, -1.0);
-        R3[k] = __dmul_rn(sg, __dmul_rn(A.sqrt3, t));
-    }
-    const double FH3[3] = {F0, F1, F2};
-    const double Vo[3] = {V0, V1, V2};
-    const double ro[3] = {r0, r1, r2};
-    const int L[3] = {nx, ny, nz};
-    double Vn[3] = {V0, V1, V2};
-    const bool pin = A.pinned[i] != 0;
-    const double invM = 1.0 / A.mass[i];
-    bool bad = false;
+            for (int k = 0; k < 3; ++k) {
+                long long v = s_fix[j][k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        A.fh[k * cap + i] = FH3[k];
-        A.fr[k * cap + i] = R3[k];
-        if (!pin) {
-            // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
-            Vn[k] = Vo[k] + (FH3[k] + R3[k] + A.fext[k * cap + i]) * invM;
-            double rn = ro[k] + Vn[k];
-            if (rn < 0.0) rn += (double)L[k];
-            if (rn >= (double)L[k]) rn -= (double)L[k];
-            const bool b = !isfinite(Vn[k]) || !(rn >= 0.0) || !(rn < (double)L[k]);
-            if (b) rn = 0.0;  // keep the next gather inside the box; reported as LBP_ENAN
-            bad |= b;
-            A.v[k * cap + i] = Vn[k];
-            A.r[k * cap + i] = rn;
+                for (int ax = 0; ax < 3; ++ax) {
+                    const long long far = __mul64hi(2 * v, s_frac[j][ax]);
+                    v = cc[ax] ? far : v - far;
+                }
+                sh[k] = v;
+            }
+            const long long row = (long long)Z * ny + Y;
+            const long long node = row * nx + X;
+            atomicAdd(A.fq + node, (unsigned long long)sh[0]);
+            atomicAdd(A.fq + A.N + node, (unsigned long long)sh[1]);
+            atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)sh[2]);
+            atomicOr(A.mask + row * A.mwords + (X >> 5), 1u << (X & 31));
+            node_out = (int)node;
         }
-    }
-    if (bad) atomicOr(A.err, ERR_NAN);
-    if (A.ring) {
-        const long long m = step - A.d_vacf[0];
-        if (m >= 0) {
-            float *dst = A.ring + (m % A.ring_cap) * 3 * (long long)A.np;
-            dst[i] = (float)Vn[0];
-            dst[A.np + i] = (float)Vn[1];
-            dst[2 * A.np + i] = (float)Vn[2];
-        }
+        A.nodes[8 * (long long)ij + p] = node_out;
     }
 }
 
@@ -254,7 +325,7 @@ cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
     A.fh = s.fh;
     A.fr = s.fr;
     A.fext = s.fext;
-    A.mass = s.mass;
+    A.inv_mass = s.inv_mass;
     A.gamma = s.gamma;
     A.radius = s.radius;
     A.sig = s.sig;
@@ -269,13 +340,56 @@ cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
     A.fq = s.fq;
     A.mask = s.mask;
     A.mwords = s.mwords;
+    A.nodes = s.nodes;
     A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
-    const int threads = 128;
-    const unsigned grid = (unsigned)((s.np + threads - 1) / threads);
-    k_particles<<<grid, threads, 0, st>>>(A);
+    const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
+    k_particles<<<grid, 8 * PB, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Body-force term of Eqs. 18-19 at the nodes that received reaction forces.
+// One thread per (particle, corner) entry; the first entry of a node to clear
+// the node's mask bit owns it, so each node is updated exactly once.  The
+// per-node force is the exact fixed-point sum of all particles' shares.  The
+// step index advances here (this is the last kernel of a step).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_apply_forces(float *g, long long P, long long N, int nx,
+                                                      int mwords, const int *nodes, int nentries,
+                                                      unsigned int *mask, unsigned long long *fq,
+                                                      long long *d_step) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) *d_step += 1;
+    if (e >= nentries) return;
+    const int node = nodes[e];
+    if (node < 0) return;
+    const int row = node / nx;
+    const int X = node - row * nx;
+    const unsigned int bit = 1u << (X & 31);
+    const unsigned int old = atomicAnd(mask + (long long)row * mwords + (X >> 5), ~bit);
+    if (!(old & bit)) return;
+    const float inv = 1.3877787807814457e-17f;  // 2^-56
+    const float F0 = 3.f * inv * __ll2float_rn((long long)fq[node]);
+    const float F1 = 3.f * inv * __ll2float_rn((long long)fq[N + node]);
+    const float F2 = 3.f * inv * __ll2float_rn((long long)fq[2 * N + node]);
+    fq[node] = 0ull;
+    fq[N + node] = 0ull;
+    fq[2 * N + node] = 0ull;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        float *q = g + (long long)a * P + node;
+        *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
+    }
+}
+
+cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st) {
+    const int n = 8 * s.np;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    k_apply_forces<<<grid > 0 ? grid : 1, 256, 0, st>>>(dst, s.P, s.N, s.nx, s.mwords, s.nodes, n,
+                                                        s.mask, s.fq, s.d_step);
     return cudaGetLastError();
 }
 
@@ -309,25 +423,22 @@ cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cud
     return cudaGetLastError();
 }
 
-// Cell base index and trilinear weights of the current positions, with the
-// same expressions k_particles uses (for bit-exact checks of the indexing).
-__global__ void k_cells(const double *r, int cap, int np, int *base, double *weights) {
+// Cell base index and cell fraction of the current positions, with the same
+// expressions k_particles uses (for bit-exact checks of the indexing).
+__global__ void k_cells(const double *r, int cap, int np, int *base, double *frac) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    const double r0 = r[i], r1 = r[cap + i], r2 = r[2 * cap + i];
-    const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
-    const double q0 = r0 - b0, q1 = r1 - b1, q2 = r2 - b2;
-    base[3 * i] = (int)b0;
-    base[3 * i + 1] = (int)b1;
-    base[3 * i + 2] = (int)b2;
-    const double wx[2] = {1.0 - q0, q0}, wy[2] = {1.0 - q1, q1}, wz[2] = {1.0 - q2, q2};
-    for (int p = 0; p < 8; ++p)
-        weights[8 * i + p] = __dmul_rn(__dmul_rn(wx[p & 1], wy[(p >> 1) & 1]), wz[(p >> 2) & 1]);
+    for (int k = 0; k < 3; ++k) {
+        const double rk = r[(long long)k * cap + i];
+        const double b = floor(rk);
+        base[3 * i + k] = (int)b;
+        frac[3 * i + k] = rk - b;
+    }
 }
 
-cudaError_t launch_cells(Sim &s, int *base, double *weights, cudaStream_t st) {
+cudaError_t launch_cells(Sim &s, int *base, double *frac, cudaStream_t st) {
     if (s.np == 0) return cudaSuccess;
-    k_cells<<<(s.np + 127) / 128, 128, 0, st>>>(s.r, s.cap, s.np, base, weights);
+    k_cells<<<(s.np + 127) / 128, 128, 0, st>>>(s.r, s.cap, s.np, base, frac);
     return cudaGetLastError();
 }
 

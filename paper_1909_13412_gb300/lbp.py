@@ -244,10 +244,10 @@ def lbp_particles_read(h: Handle, r=None, v=None, f_h=None, f_r=None):
     _call("lbp_particles_read", h.ptr, *[a[0] for a in args], d)
 
 
-def lbp_particles_read_cells(h: Handle, base, weights):
+def lbp_particles_read_cells(h: Handle, base, frac):
     n = h.np
     a = _ptr(base, np.int32, 3 * n, "base", True)
-    b = _ptr(weights, np.float64, 8 * n, "weights", True)
+    b = _ptr(frac, np.float64, 3 * n, "frac", True)
     d = _same_side(a, b)
     _call("lbp_particles_read_cells", h.ptr, a[0], b[0], d)
 
