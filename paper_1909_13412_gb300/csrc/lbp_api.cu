@@ -3,11 +3,14 @@
 // Host side of the library: argument validation, device allocation, layout
 // conversion for the ABI arrays, and the per-step launch sequence
 //
-//      s0:  k_particles (fhat^{n-1} -> F_H, V, r, reaction forces)
-//           -> k_stream_collide (fhat^{n-1} -> fhat^n without the body force)
+//      s1:  k_particles (fhat^{n-1} -> F_H, V, r, reaction forces)
+//           [-> VACF block every 64th step]  ------------------------.
+//      s0:  k_stream_collide (fhat^{n-1} -> fhat^n, no body force) -- join
 //           -> k_apply_forces (body force at the particles' corner nodes)
-//      s1:  every 64th step, the VACF block, forked after k_particles and
-//           joined at the end of the step, so it overlaps the lattice pass.
+//
+// The particle kernel only reads fhat^{n-1} and the lattice pass does not
+// need this step's forces (the force term of Eq. 19 does not depend on f), so
+// the two run concurrently and only the body-force pass is serial.
 //
 // A step is captured into a CUDA graph per (buffer parity, VACF block due)
 // and replayed.
@@ -116,15 +119,16 @@ bool radius_ok(double R, int exclude) {
 
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
-// one time step; the VACF block (if due) runs on s1 beside the lattice pass
+// one time step: the particle kernel (and the VACF block, if due) run on s1
+// beside the lattice pass on s0; the body-force pass joins them
 lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
     const float *src = s->f[s->cur];
     float *dst = s->f[s->cur ^ 1];
-    if (s->np > 0) CK(launch_particles(*s, src, s->s0));
-    if (vacf_due) {
+    if (s->np > 0) {
         CK(cudaEventRecord(s->ev_fork, s->s0));
         CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
-        CK(launch_vacf_block(*s, false, s->s1));
+        CK(launch_particles(*s, src, s->s1));
+        if (vacf_due) CK(launch_vacf_block(*s, false, s->s1));
         CK(cudaEventRecord(s->ev_join, s->s1));
     }
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
@@ -133,8 +137,10 @@ lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
     }
-    if (s->np > 0) CK(launch_apply_forces(*s, dst, s->s0));
-    if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
+    if (s->np > 0) {
+        CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
+        CK(launch_apply_forces(*s, dst, s->s0));
+    }
     return LBP_OK;
 }
 

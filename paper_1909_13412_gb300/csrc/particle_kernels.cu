@@ -378,8 +378,9 @@ __global__ void __launch_bounds__(256) k_apply_forces(float *g, long long P, lon
     fq[node] = 0ull;
     fq[N + node] = 0ull;
     fq[2 * N + node] = 0ull;
+    // the rest population (e_0 = 0) receives no force
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
+    for (int a = 1; a < Q; ++a) {
         float *q = g + (long long)a * P + node;
         *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
     }
