@@ -3,14 +3,11 @@
 // Host side of the library: argument validation, device allocation, layout
 // conversion for the ABI arrays, and the per-step launch sequence
 //
-//      s1:  k_particles (fhat^{n-1} -> F_H, V, r, reaction forces)
-//           [-> VACF block every 64th step]  ------------------------.
-//      s0:  k_stream_collide (fhat^{n-1} -> fhat^n, no body force) -- join
-//           -> k_apply_forces (body force at the particles' corner nodes)
-//
-// The particle kernel only reads fhat^{n-1} and the lattice pass does not
-// need this step's forces (the force term of Eq. 19 does not depend on f), so
-// the two run concurrently and only the body-force pass is serial.
+//      s0:  k_particles (fhat^{n-1} -> F_H, V, r, force records)
+//           -> k_stream_collide_forced (fhat^{n-1} + records -> fhat^n)
+//           -> k_apply_overflow (shares that did not fit a record; usually none)
+//      s1:  every 64th step the VACF block, forked after k_particles and
+//           joined at the end of the step, so it overlaps the lattice pass.
 //
 // A step is captured into a CUDA graph per (buffer parity, VACF block due)
 // and replayed.
@@ -119,27 +116,32 @@ bool radius_ok(double R, int exclude) {
 
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
-// one time step: the particle kernel (and the VACF block, if due) run on s1
-// beside the lattice pass on s0; the body-force pass joins them
+// one time step (see the sequence at the top of this file)
 lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
     const float *src = s->f[s->cur];
     float *dst = s->f[s->cur ^ 1];
+    const int parity = s->cur;
     if (s->np > 0) {
-        CK(cudaEventRecord(s->ev_fork, s->s0));
-        CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
-        CK(launch_particles(*s, src, s->s1));
-        if (vacf_due) CK(launch_vacf_block(*s, false, s->s1));
-        CK(cudaEventRecord(s->ev_join, s->s1));
+        CK(launch_particles(*s, src, parity, s->s0));
+        if (vacf_due) {
+            CK(cudaEventRecord(s->ev_fork, s->s0));
+            CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
+            CK(launch_vacf_block(*s, false, s->s1));
+            CK(cudaEventRecord(s->ev_join, s->s1));
+        }
     }
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
-    CK(launch_stream_collide(*s, src, dst, s->s0));
+    if (s->np > 0)
+        CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
+    else
+        CK(launch_stream_collide(*s, src, dst, s->s0));
     if (timed) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
     }
     if (s->np > 0) {
-        CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
-        CK(launch_apply_forces(*s, dst, s->s0));
+        CK(launch_apply_overflow(*s, dst, parity, s->s0));
+        if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
     }
     return LBP_OK;
 }
@@ -262,7 +264,8 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
-                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->nodes, s->ring,
+                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->rec[0],
+                    s->rec[1], s->d_oflow, s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -420,15 +423,19 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
             cudaFree(s->pinned);
         }
         s->pinned = np8;
-        int *nn = nullptr;
-        TRY(dalloc(&nn, 8 * (size_t)cap));
-        CK(cudaMemset(nn, 0xff, sizeof(int) * 8 * (size_t)cap));
-        if (s->nodes) cudaFree(s->nodes);
-        s->nodes = nn;
-        // reaction-force accumulator: 3 x 64-bit per node, allocated once
+
+        // force records (two step parities) and the dense overflow
+        // accumulator (3 x 64-bit per node), allocated with the first particle
         if (!s->fq) {
+            s->nseg = (long long)s->ny * s->nz * ((s->nx + SEG - 1) / SEG);
             TRY(dalloc(&s->fq, 3 * (size_t)s->N));
             CK(cudaMemset(s->fq, 0, sizeof(unsigned long long) * 3 * (size_t)s->N));
+            for (int q = 0; q < 2; ++q) {
+                TRY(dalloc(&s->rec[q], (size_t)s->nseg * REC_WORDS));
+                CK(cudaMemset(s->rec[q], 0, sizeof(unsigned long long) * (size_t)s->nseg * REC_WORDS));
+            }
+            TRY(dalloc(&s->d_oflow, 2));
+            CK(cudaMemset(s->d_oflow, 0, 2 * sizeof(int)));
         }
         s->cap = cap;
     }

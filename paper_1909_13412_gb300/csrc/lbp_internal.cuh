@@ -39,6 +39,20 @@ __host__ __device__ constexpr float wgtf(int a) {
 constexpr double FIX_SCALE = 72057594037927936.0;  // 2^56
 constexpr double FIX_LIMIT = 32.0;                 // |F_H| < 2^5 per particle
 
+// Per-segment force records.  Every 128-node segment of an x-row (the block
+// of the stream-collide kernel) owns a 256-byte record: a count and up to
+// REC_SLOTS (x, fixed-point force share) entries appended by the particle
+// kernel.  The stream-collide kernel loads its record together with the
+// populations and adds the force term in registers.  Entries beyond the
+// capacity go to the dense per-node accumulator instead (see the kernels).
+constexpr int SEG = 128;                 // nodes per segment (stream-collide block)
+constexpr int REC_SLOTS = 8;
+constexpr int REC_WORDS = 32;            // 8-byte words per record (256 bytes)
+// layout (8-byte words): [0] count | pad, [1..4] x of slots 0..7 (two int32
+// per word), [5 + 3 s + k] fixed-point share k of slot s.
+constexpr int REC_X0 = 1;
+constexpr int REC_F0 = 5;
+
 // error bits in Sim::d_err
 constexpr int ERR_NAN = 1;
 constexpr int ERR_RANGE = 2;
@@ -100,12 +114,14 @@ struct Sim {
     int exclude_inside = 0;
     double sqrt3 = 0.0;
 
-    // reaction force: fixed-point accumulator per node and a bit per node
-    // marking the nodes that hold one (both cleared by the apply pass)
+    // overflow of the force records: fixed-point accumulator per node and a bit
+    // per node marking the nodes that hold one (both cleared by the overflow pass)
     unsigned long long *fq = nullptr;  // [3][N], allocated with the first particle
     unsigned int *mask = nullptr;      // [ny * nz][mwords]
     int mwords = 0;                    // ceil(nx / 32)
-    int *nodes = nullptr;              // [8 cap] corner nodes of this step's shares
+    unsigned long long *rec[2] = {nullptr, nullptr};  // [segments][REC_WORDS], by step parity
+    long long nseg = 0;                                // ny * nz * ceil(nx / SEG)
+    int *d_oflow = nullptr;                            // [2] overflow flags by step parity
 
     // VACF
     int vacf_lag = -1;
@@ -141,14 +157,16 @@ struct Sim {
 // lbm_kernels.cu
 cudaError_t prepare_lbm_kernels();
 cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, cudaStream_t st);
+cudaError_t launch_stream_collide_forced(Sim &s, const float *src, float *dst, int parity,
+                                         cudaStream_t st);
 cudaError_t launch_fill_rest(Sim &s, float *dst, cudaStream_t st);
 cudaError_t launch_from_f64(Sim &s, const double *f, float *dst, cudaStream_t st);
 cudaError_t launch_to_f64(Sim &s, const float *src, double *f, cudaStream_t st);
 cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, double *p,
                           cudaStream_t st);
 // particle_kernels.cu
-cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st);
-cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st);
+cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t st);
+cudaError_t launch_apply_overflow(Sim &s, float *dst, int parity, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);

@@ -6,10 +6,10 @@
 //      streamed f^n of Eq. 20): 14 independent loads per thread;
 //   B. one thread per particle fits the Stokeslet flow of Eq. 8, draws the
 //      Philox random force (Eqs. 4-5) and advances V and r (Eqs. 1-2);
-//   C. eight threads per particle add the shares of the reaction force -F_H
-//      (Eq. 9) to the corner nodes.
-// k_apply_forces: adds the body-force term 3 w_a F.e_a of Eqs. 18-19 to the
-//   post-collision populations at the nodes that received reaction forces.
+//   C. eight threads per particle append the shares of the reaction force
+//      -F_H (Eq. 9) at the corner nodes to the force records of the row
+//      segments holding those nodes; the stream-collide kernel applies them.
+// k_apply_overflow: applies the shares that did not fit in a record.
 //
 // Why one thread per particle in phase B: GB300 issues FP64 at 1/64 of the
 // FP32 rate, so a warp-wide FP64 instruction costs the same whether one lane
@@ -26,16 +26,18 @@
 // FP32 relative accuracy even when the particle moves with the fluid and u_p
 // and V nearly cancel.
 //
-// Reaction forces go to a dense per-node accumulator of 64-bit fixed-point
-// integers (scale 2^56), added with integer atomics: the per-node sum is exact
-// and independent of the order in which particles add to it (no
-// floating-point atomics).  -F_H is converted to fixed point once and split
-// over the eight corners by the trilinear fractions with integer arithmetic
-// (the 1 - q share is the remainder), so the eight shares sum to -F_H exactly
-// and the momentum the fluid receives is exactly what the particle lost.  A
-// bit per node in `mask` marks the nodes that received a force; the apply
-// pass claims each node once by clearing its bit, applies the body-force
-// term there and zeroes its accumulator.
+// Reaction forces are 64-bit fixed-point integers (scale 2^56).  -F_H is
+// converted once and split over the eight corners by the trilinear fractions
+// with integer arithmetic (the 1 - q share is the remainder), so the eight
+// shares sum to -F_H exactly and the momentum the fluid receives is exactly
+// what the particle lost.  Each share is appended to the record of its row
+// segment (slot index from an integer atomic on the record's count).  The
+// per-node force is the integer sum of the matching entries, so it is exact
+// and independent of the order in which particles appended them (no
+// floating-point atomics).  When a record is full the share goes to a dense
+// per-node accumulator (integer atomics) and the node's bit is set in
+// `mask`; whether a record overflows depends only on how many shares it
+// receives, so the split between the two paths is deterministic too.
 #include <cuda_runtime.h>
 
 #include "lbp_internal.cuh"
@@ -55,10 +57,12 @@ struct ParticleArgs {
     unsigned long long seed;
     double sqrt3;
     int mode, exclude_inside;
-    unsigned long long *fq;  // [3][N] fixed-point reaction force
+    unsigned long long *rec; // force records of this step's parity
+    int nchunks;             // segments per row
+    int *oflow;              // overflow flag of this step's parity
+    unsigned long long *fq;  // [3][N] fixed-point overflow accumulator
     unsigned int *mask;      // [rows][mwords]
     int mwords;
-    int *nodes;              // [8 cap] corner nodes that received a share, or -1
     float *ring;
     int ring_cap;
     long long *d_vacf;  // [0] first sampled step, [2] samples written
@@ -284,34 +288,39 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
     // Per axis the far corner (c = 1) takes floor(v q) -- the signed high half
     // of (2 v) (q31 2^32) -- and the near corner the rest, so the eight shares
     // add up to v exactly.  |v| < 2^61 (|F_H| < 32), so 2 v stays within int64.
-    if (ij < A.np) {
-        int node_out = -1;
-        if (s_spread[j]) {
-            const int cc[3] = {c0, c1, c2};
-            long long sh[3];
+    if (ij < A.np && s_spread[j]) {
+        const int cc[3] = {c0, c1, c2};
+        long long sh[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                long long v = s_fix[j][k];
+        for (int k = 0; k < 3; ++k) {
+            long long v = s_fix[j][k];
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    const long long far = __mul64hi(2 * v, s_frac[j][ax]);
-                    v = cc[ax] ? far : v - far;
-                }
-                sh[k] = v;
+            for (int ax = 0; ax < 3; ++ax) {
+                const long long far = __mul64hi(2 * v, s_frac[j][ax]);
+                v = cc[ax] ? far : v - far;
             }
-            const long long row = (long long)Z * ny + Y;
+            sh[k] = v;
+        }
+        const long long row = (long long)Z * ny + Y;
+        unsigned long long *rec = A.rec + (size_t)(row * A.nchunks + X / SEG) * REC_WORDS;
+        const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
+        if (slot < (unsigned)REC_SLOTS) {
+            reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
+            rec[REC_F0 + 3 * slot] = (unsigned long long)sh[0];
+            rec[REC_F0 + 3 * slot + 1] = (unsigned long long)sh[1];
+            rec[REC_F0 + 3 * slot + 2] = (unsigned long long)sh[2];
+        } else {
             const long long node = row * nx + X;
             atomicAdd(A.fq + node, (unsigned long long)sh[0]);
             atomicAdd(A.fq + A.N + node, (unsigned long long)sh[1]);
             atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)sh[2]);
             atomicOr(A.mask + row * A.mwords + (X >> 5), 1u << (X & 31));
-            node_out = (int)node;
+            *A.oflow = 1;
         }
-        A.nodes[8 * (long long)ij + p] = node_out;
     }
 }
 
-cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
+cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t st) {
     if (s.np == 0) return cudaSuccess;
     ParticleArgs A;
     A.g = src;
@@ -340,7 +349,9 @@ cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
     A.fq = s.fq;
     A.mask = s.mask;
     A.mwords = s.mwords;
-    A.nodes = s.nodes;
+    A.rec = s.rec[parity];
+    A.nchunks = (s.nx + SEG - 1) / SEG;
+    A.oflow = s.d_oflow + parity;
     A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
@@ -351,46 +362,51 @@ cudaError_t launch_particles(Sim &s, const float *src, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Body-force term of Eqs. 18-19 at the nodes that received reaction forces.
-// One thread per (particle, corner) entry; the first entry of a node to clear
-// the node's mask bit owns it, so each node is updated exactly once.  The
-// per-node force is the exact fixed-point sum of all particles' shares.  The
-// step index advances here (this is the last kernel of a step).
+// Body-force term of Eqs. 18-19 at the nodes whose shares overflowed their
+// record.  Only runs (past its first check) when an overflow happened this
+// step.  One thread per mask word: it owns the 32 nodes of the word, applies
+// each flagged node's exact fixed-point sum to the post-collision populations
+// and clears the word and the accumulators.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_apply_forces(float *g, long long P, long long N, int nx,
-                                                      int mwords, const int *nodes, int nentries,
-                                                      unsigned int *mask, unsigned long long *fq,
-                                                      long long *d_step) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e == 0) *d_step += 1;
-    if (e >= nentries) return;
-    const int node = nodes[e];
-    if (node < 0) return;
-    const int row = node / nx;
-    const int X = node - row * nx;
-    const unsigned int bit = 1u << (X & 31);
-    const unsigned int old = atomicAnd(mask + (long long)row * mwords + (X >> 5), ~bit);
-    if (!(old & bit)) return;
-    const float inv = 1.3877787807814457e-17f;  // 2^-56
-    const float F0 = 3.f * inv * __ll2float_rn((long long)fq[node]);
-    const float F1 = 3.f * inv * __ll2float_rn((long long)fq[N + node]);
-    const float F2 = 3.f * inv * __ll2float_rn((long long)fq[2 * N + node]);
-    fq[node] = 0ull;
-    fq[N + node] = 0ull;
-    fq[2 * N + node] = 0ull;
-    // the rest population (e_0 = 0) receives no force
+__global__ void __launch_bounds__(256) k_apply_overflow(float *g, long long P, long long N, int nx,
+                                                        int mwords, long long nwords,
+                                                        unsigned int *mask, unsigned long long *fq,
+                                                        const int *oflow) {
+    if (*oflow == 0) return;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < nwords;
+         w += (long long)gridDim.x * blockDim.x) {
+        unsigned int word = mask[w];
+        if (!word) continue;
+        mask[w] = 0u;
+        const long long row = w / mwords;
+        const int xb = (int)(w - row * mwords) * 32;
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1u;
+            const long long node = row * nx + xb + b;
+            const float inv = 1.3877787807814457e-17f;  // 2^-56
+            const float F0 = 3.f * inv * __ll2float_rn((long long)fq[node]);
+            const float F1 = 3.f * inv * __ll2float_rn((long long)fq[N + node]);
+            const float F2 = 3.f * inv * __ll2float_rn((long long)fq[2 * N + node]);
+            fq[node] = 0ull;
+            fq[N + node] = 0ull;
+            fq[2 * N + node] = 0ull;
+            // the rest population (e_0 = 0) receives no force
 #pragma unroll
-    for (int a = 1; a < Q; ++a) {
-        float *q = g + (long long)a * P + node;
-        *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
+            for (int a = 1; a < Q; ++a) {
+                float *q = g + (long long)a * P + node;
+                *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
+            }
+        }
     }
 }
 
-cudaError_t launch_apply_forces(Sim &s, float *dst, cudaStream_t st) {
-    const int n = 8 * s.np;
-    const unsigned grid = (unsigned)((n + 255) / 256);
-    k_apply_forces<<<grid > 0 ? grid : 1, 256, 0, st>>>(dst, s.P, s.N, s.nx, s.mwords, s.nodes, n,
-                                                        s.mask, s.fq, s.d_step);
+cudaError_t launch_apply_overflow(Sim &s, float *dst, int parity, cudaStream_t st) {
+    const long long nwords = (long long)s.ny * s.nz * s.mwords;
+    long long grid = (nwords + 255) / 256;
+    if (grid > 8ll * s.num_sms) grid = 8ll * s.num_sms;
+    k_apply_overflow<<<(unsigned)grid, 256, 0, st>>>(dst, s.P, s.N, s.nx, s.mwords, nwords, s.mask,
+                                                     s.fq, s.d_oflow + parity);
     return cudaGetLastError();
 }
 

@@ -262,6 +262,29 @@ def test_coupled_brownian_particles(mode, exclude):
     lbp.lbp_check(h)
 
 
+@pytest.mark.parametrize("shape,n", [((3, 4, 5), 60), ((6, 5, 130), 400)])
+def test_dense_particles_overflow_the_force_records(shape, n):
+    """Many particles per 128-node row segment: shares beyond a segment's 8
+    record slots take the overflow path; the result must still match the
+    oracle and be bit-reproducible."""
+    ps = wl.uniform_particles(n, shape, 10.0, 0.5, 0.2, 1e-4, 31, 32)
+    outs = []
+    for graphs in (True, False):
+        h = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=4, graphs=graphs)
+        lbp.lbp_step(h, 25)
+        outs.append((gpu_pops(h), gpu_particles(h)))
+        lbp.lbp_check(h)
+        lbp.lbp_destroy(h)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1][1], outs[1][1][1])
+    o = oracle_sim(shape, 0.8, ps, kT=1e-4, seed=4)
+    o.step(25)
+    fo = o.fhat()
+    _, Vo, _, _ = o.particles()
+    assert np.max(np.abs(outs[0][0] - fo)) <= 1e-5 * dev_scale(fo) + F64_FLOOR
+    assert np.max(np.abs(outs[0][1][1] - Vo)) <= 1e-5 * np.max(np.abs(Vo))
+
+
 def test_pinned_particle_and_external_force():
     shape = (10, 10, 10)
     r = np.array([[5.5, 5.5, 5.5], [2.3, 7.1, 4.4]])
