@@ -265,7 +265,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     drop_graphs(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->rec[0],
-                    s->rec[1], s->d_oflow, s->ring,
+                    s->rec[1], s->d_ocount, s->olist[0], s->olist[1], s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -434,9 +434,17 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
                 TRY(dalloc(&s->rec[q], (size_t)s->nseg * REC_WORDS));
                 CK(cudaMemset(s->rec[q], 0, sizeof(unsigned long long) * (size_t)s->nseg * REC_WORDS));
             }
-            TRY(dalloc(&s->d_oflow, 2));
-            CK(cudaMemset(s->d_oflow, 0, 2 * sizeof(int)));
+            TRY(dalloc(&s->d_ocount, 2));
+            CK(cudaMemset(s->d_ocount, 0, 2 * sizeof(unsigned int)));
         }
+        // overflow lists: at most 8 shares per particle from the particle
+        // kernel plus 8 per overflowed record (< 8 per particle)
+        for (int q = 0; q < 2; ++q) {
+            if (s->olist[q]) cudaFree(s->olist[q]);
+            s->olist[q] = nullptr;
+            TRY(dalloc(&s->olist[q], 16 * (size_t)cap + 64));
+        }
+        s->ocap = (unsigned int)(16 * (size_t)cap + 64);
         s->cap = cap;
     }
     // upload the new particles into the SoA planes

@@ -121,7 +121,9 @@ struct Sim {
     int mwords = 0;                    // ceil(nx / 32)
     unsigned long long *rec[2] = {nullptr, nullptr};  // [segments][REC_WORDS], by step parity
     long long nseg = 0;                                // ny * nz * ceil(nx / SEG)
-    int *d_oflow = nullptr;                            // [2] overflow flags by step parity
+    unsigned int *d_ocount = nullptr;                  // [2] overflow list lengths by step parity
+    unsigned int *olist[2] = {nullptr, nullptr};       // mask words holding overflowed shares
+    unsigned int ocap = 0;                             // capacity of each overflow list
 
     // VACF
     int vacf_lag = -1;

@@ -59,7 +59,9 @@ struct ParticleArgs {
     int mode, exclude_inside;
     unsigned long long *rec; // force records of this step's parity
     int nchunks;             // segments per row
-    int *oflow;              // overflow flag of this step's parity
+    unsigned int *ocount;    // overflow list of this step's parity
+    unsigned int *olist;
+    unsigned int ocap;
     unsigned long long *fq;  // [3][N] fixed-point overflow accumulator
     unsigned int *mask;      // [rows][mwords]
     int mwords;
@@ -314,8 +316,10 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
             atomicAdd(A.fq + node, (unsigned long long)sh[0]);
             atomicAdd(A.fq + A.N + node, (unsigned long long)sh[1]);
             atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)sh[2]);
-            atomicOr(A.mask + row * A.mwords + (X >> 5), 1u << (X & 31));
-            *A.oflow = 1;
+            const unsigned int w = (unsigned)row * (unsigned)A.mwords + (unsigned)(X >> 5);
+            atomicOr(A.mask + w, 1u << (X & 31));
+            const unsigned int e = atomicAdd(A.ocount, 1u);
+            if (e < A.ocap) A.olist[e] = w;
         }
     }
 }
@@ -351,7 +355,9 @@ cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t 
     A.mwords = s.mwords;
     A.rec = s.rec[parity];
     A.nchunks = (s.nx + SEG - 1) / SEG;
-    A.oflow = s.d_oflow + parity;
+    A.ocount = s.d_ocount + parity;
+    A.olist = s.olist[parity];
+    A.ocap = s.ocap;
     A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
@@ -363,23 +369,24 @@ cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t 
 
 // ---------------------------------------------------------------------------
 // Body-force term of Eqs. 18-19 at the nodes whose shares overflowed their
-// record.  Only runs (past its first check) when an overflow happened this
-// step.  One thread per mask word: it owns the 32 nodes of the word, applies
-// each flagged node's exact fixed-point sum to the post-collision populations
-// and clears the word and the accumulators.
+// record.  The overflow list holds the mask words of those nodes (a word may
+// be listed more than once); the thread that swaps a word to zero owns its
+// flagged nodes, applies each node's exact fixed-point sum to the
+// post-collision populations and clears the accumulators.  With no overflow
+// (the usual case) the kernel only reads the list length.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_apply_overflow(float *g, long long P, long long N, int nx,
-                                                        int mwords, long long nwords,
-                                                        unsigned int *mask, unsigned long long *fq,
-                                                        const int *oflow) {
-    if (*oflow == 0) return;
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < nwords;
-         w += (long long)gridDim.x * blockDim.x) {
-        unsigned int word = mask[w];
-        if (!word) continue;
-        mask[w] = 0u;
-        const long long row = w / mwords;
-        const int xb = (int)(w - row * mwords) * 32;
+                                                        int mwords, unsigned int *mask,
+                                                        unsigned long long *fq,
+                                                        const unsigned int *ocount,
+                                                        const unsigned int *olist, unsigned int ocap) {
+    unsigned int n = *ocount;
+    if (n > ocap) n = ocap;
+    for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const unsigned int w = olist[e];
+        unsigned int word = atomicExch(mask + w, 0u);
+        const long long row = w / (unsigned)mwords;
+        const int xb = (int)(w - (unsigned)row * (unsigned)mwords) * 32;
         while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1u;
@@ -402,11 +409,8 @@ __global__ void __launch_bounds__(256) k_apply_overflow(float *g, long long P, l
 }
 
 cudaError_t launch_apply_overflow(Sim &s, float *dst, int parity, cudaStream_t st) {
-    const long long nwords = (long long)s.ny * s.nz * s.mwords;
-    long long grid = (nwords + 255) / 256;
-    if (grid > 8ll * s.num_sms) grid = 8ll * s.num_sms;
-    k_apply_overflow<<<(unsigned)grid, 256, 0, st>>>(dst, s.P, s.N, s.nx, s.mwords, nwords, s.mask,
-                                                     s.fq, s.d_oflow + parity);
+    k_apply_overflow<<<2 * s.num_sms, 256, 0, st>>>(dst, s.P, s.N, s.nx, s.mwords, s.mask, s.fq,
+                                                    s.d_ocount + parity, s.olist[parity], s.ocap);
     return cudaGetLastError();
 }
 
