@@ -305,8 +305,11 @@ def test_pinned_particle_and_external_force():
     rg, Vg, FHg, _ = gpu_particles(h)
     ro, Vo, FHo, _ = o.particles()
     assert np.array_equal(rg[0], r[0]) and np.array_equal(Vg[0], [0, 0, 0])
-    assert np.allclose(FHg, FHo, rtol=1e-5, atol=1e-12)
-    assert np.allclose(Vg, Vo, rtol=1e-5, atol=1e-12)
+    # FP32 rounding of the 1e-3 background flow sets the error scale: compare
+    # each particle's force and velocity against its own magnitude
+    for i in range(2):
+        assert np.max(np.abs(FHg[i] - FHo[i])) <= 1e-5 * np.max(np.abs(FHo[i]))
+        assert np.max(np.abs(Vg[i] - Vo[i])) <= 1e-5 * max(np.max(np.abs(Vo[i])), 1e-30)
 
 
 def test_momentum_budget_on_gpu():
