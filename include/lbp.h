@@ -171,6 +171,13 @@ lbp_status lbp_vacf_read(lbp_sim *sim, double *csum, int64_t *counts, int on_dev
  * a particle state became non-finite, LBP_ERANGE on fixed-point overflow.     */
 lbp_status lbp_check(lbp_sim *sim);
 
+/* Diagnostics of the last completed step (waits for the handle's work):
+ * out[0] = reaction-force shares that did not fit their row segment's record
+ * and took the overflow path (both counts are implementation details of the
+ * force accumulation; the results do not depend on them), out[1] = capacity of
+ * a record in shares, out[2] = number of row segments.  n = entries of out.   */
+lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
+
 /* Use CUDA graphs for lbp_step (default 1).                                  */
 lbp_status lbp_set_use_graphs(lbp_sim *sim, int enable);
 

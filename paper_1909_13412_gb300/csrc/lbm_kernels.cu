@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(BX) k_stream_collide(Planes pl, int nx, int ny
 // entries whose x is its own and adds 3 w_a F.e_a to its post-collision
 // populations.  A record that overflowed (count > REC_SLOTS) is not applied
 // here: warp 0 moves its entries to the dense accumulator, where the
-// particle kernel already put the rest, lists their mask words, and
+// particle kernel already put the rest, lists the nodes, and
 // k_apply_overflow applies the whole sums.  The block also clears the count
 // of its record of the previous step (which the next step's particle kernel
 // refills) and block 0 the previous step's overflow count.
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
                     const unsigned int w = (unsigned)row * (unsigned)mwords + (unsigned)(xs >> 5);
                     atomicOr(mask + w, 1u << (xs & 31));
                     const unsigned int e = atomicAdd(ocount_cur, 1u);
-                    if (e < ocap) olist[e] = w;
+                    if (e < ocap) olist[e] = (unsigned int)node;
                 }
             }
         }

@@ -724,6 +724,20 @@ lbp_status lbp_check(lbp_sim *s) {
     return LBP_OK;
 }
 
+lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
+    CHECK_SIM(s);
+    if (n < 0 || (n > 0 && !out)) return fail(LBP_EINVAL, "lbp_diagnostics: bad output");
+    CK(cudaStreamSynchronize(s->s0));
+    int64_t v[3] = {0, REC_SLOTS, s->nseg};
+    if (s->d_ocount) {
+        unsigned int c[2] = {0u, 0u};
+        CK(cudaMemcpy(c, s->d_ocount, sizeof(c), cudaMemcpyDeviceToHost));
+        v[0] = c[s->cur ^ 1];  // parity of the last completed step
+    }
+    for (int i = 0; i < n && i < 3; ++i) out[i] = v[i];
+    return LBP_OK;
+}
+
 lbp_status lbp_set_use_graphs(lbp_sim *s, int enable) {
     CHECK_SIM(s);
     s->use_graphs = enable ? 1 : 0;

@@ -122,7 +122,7 @@ struct Sim {
     unsigned long long *rec[2] = {nullptr, nullptr};  // [segments][REC_WORDS], by step parity
     long long nseg = 0;                                // ny * nz * ceil(nx / SEG)
     unsigned int *d_ocount = nullptr;                  // [2] overflow list lengths by step parity
-    unsigned int *olist[2] = {nullptr, nullptr};       // mask words holding overflowed shares
+    unsigned int *olist[2] = {nullptr, nullptr};       // nodes holding overflowed shares
     unsigned int ocap = 0;                             // capacity of each overflow list
 
     // VACF

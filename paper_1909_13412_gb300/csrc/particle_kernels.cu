@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
             const unsigned int w = (unsigned)row * (unsigned)A.mwords + (unsigned)(X >> 5);
             atomicOr(A.mask + w, 1u << (X & 31));
             const unsigned int e = atomicAdd(A.ocount, 1u);
-            if (e < A.ocap) A.olist[e] = w;
+            if (e < A.ocap) A.olist[e] = (unsigned int)node;
         }
     }
 }
@@ -369,11 +369,11 @@ cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t 
 
 // ---------------------------------------------------------------------------
 // Body-force term of Eqs. 18-19 at the nodes whose shares overflowed their
-// record.  The overflow list holds the mask words of those nodes (a word may
-// be listed more than once); the thread that swaps a word to zero owns its
-// flagged nodes, applies each node's exact fixed-point sum to the
+// record.  The overflow list holds those nodes (a node may be listed more than
+// once); one thread per entry, and the thread that clears the node's mask bit
+// owns the node: it applies the node's exact fixed-point sum to the
 // post-collision populations and clears the accumulators.  With no overflow
-// (the usual case) the kernel only reads the list length.
+// the kernel only reads the list length.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_apply_overflow(float *g, long long P, long long N, int nx,
                                                         int mwords, unsigned int *mask,
@@ -383,27 +383,24 @@ __global__ void __launch_bounds__(256) k_apply_overflow(float *g, long long P, l
     unsigned int n = *ocount;
     if (n > ocap) n = ocap;
     for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const unsigned int w = olist[e];
-        unsigned int word = atomicExch(mask + w, 0u);
-        const long long row = w / (unsigned)mwords;
-        const int xb = (int)(w - (unsigned)row * (unsigned)mwords) * 32;
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1u;
-            const long long node = row * nx + xb + b;
-            const float inv = 1.3877787807814457e-17f;  // 2^-56
-            const float F0 = 3.f * inv * __ll2float_rn((long long)fq[node]);
-            const float F1 = 3.f * inv * __ll2float_rn((long long)fq[N + node]);
-            const float F2 = 3.f * inv * __ll2float_rn((long long)fq[2 * N + node]);
-            fq[node] = 0ull;
-            fq[N + node] = 0ull;
-            fq[2 * N + node] = 0ull;
-            // the rest population (e_0 = 0) receives no force
+        const unsigned int node = olist[e];
+        const unsigned int row = node / (unsigned)nx;
+        const unsigned int X = node - row * (unsigned)nx;
+        const unsigned int bit = 1u << (X & 31);
+        const unsigned int old = atomicAnd(mask + (size_t)row * mwords + (X >> 5), ~bit);
+        if (!(old & bit)) continue;
+        const float inv = 1.3877787807814457e-17f;  // 2^-56
+        const float F0 = 3.f * inv * __ll2float_rn((long long)fq[node]);
+        const float F1 = 3.f * inv * __ll2float_rn((long long)fq[N + node]);
+        const float F2 = 3.f * inv * __ll2float_rn((long long)fq[2 * N + node]);
+        fq[node] = 0ull;
+        fq[N + node] = 0ull;
+        fq[2 * N + node] = 0ull;
+        // the rest population (e_0 = 0) receives no force
 #pragma unroll
-            for (int a = 1; a < Q; ++a) {
-                float *q = g + (long long)a * P + node;
-                *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
-            }
+        for (int a = 1; a < Q; ++a) {
+            float *q = g + (long long)a * P + node;
+            *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
         }
     }
 }

@@ -63,6 +63,7 @@ _SIGS = {
     "lbp_vacf_read": [_vp, _vp, _vp, C.c_int],
     "lbp_check": [_vp],
     "lbp_set_use_graphs": [_vp, C.c_int],
+    "lbp_diagnostics": [_vp, _vp, C.c_int],
     "lbp_timing_enable": [_vp, C.c_int],
     "lbp_timing_read": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
     "lbp_philox4x64_10": [_vp, _vp, _vp, C.c_int64, _vp],
@@ -283,6 +284,12 @@ def lbp_vacf_read(h: Handle, csum, counts):
 
 def lbp_check(h: Handle):
     _call("lbp_check", h.ptr)
+
+
+def lbp_diagnostics(h: Handle):
+    out = np.zeros(3, np.int64)
+    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 3)
+    return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2])}
 
 
 def lbp_set_use_graphs(h: Handle, enable):
