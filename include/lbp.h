@@ -193,6 +193,24 @@ lbp_status lbp_timing_read(lbp_sim *sim, double *ms_total, int64_t *launches);
 lbp_status lbp_philox4x64_10(const uint64_t *ctr, const uint64_t *key, uint64_t *out,
                              int64_t n, void *stream);
 
+/* VACF of a caller-supplied trajectory without any device allocation (the
+ * paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc where they need the result, e.g. inside an allocator or memory
+ * pool they do not control).  samples: device array [T][ncomp] of FP32
+ * velocity components (any component order within a sample); outputs on the
+ * device: csum[k] = sum over t0 <= T-1-k and all components of
+ * samples[t0] * samples[t0 + k], counts[k] = npairs * (T - k) (0 if k >= T),
+ * k = 0..max_lag -- the same estimator as lbp_vacf_read (products FP32, sums
+ * FP64).  Scratch is a fixed 4 MiB array inside the library, so
+ * ceil(ncomp / 1024) * (max_lag + 1) must not exceed 524288 (LBP_EINVAL
+ * otherwise).  The first call on a device looks up that array's address; make
+ * it before capturing this routine into a CUDA graph.  All calls on a device
+ * share the array: calls that overlap on the GPU (different streams, host
+ * threads) race and must be serialised by the caller.  Asynchronous on
+ * `stream`; outputs are zeroed by the call.                                   */
+lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp, int max_lag,
+                                      int npairs, double *csum, int64_t *counts, void *stream);
+
 /* Message of the calling thread's last failing call ("" if none).            */
 const char *lbp_last_error(void);
 

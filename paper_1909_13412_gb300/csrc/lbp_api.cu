@@ -186,6 +186,9 @@ lbp_status host_to_device(lbp_sim *s, void *dst, const void *src, size_t bytes, 
 
 }  // namespace
 
+// Error hook for entry points defined in other translation units.
+lbp_status lbp_set_error_for_noalloc(lbp_status st, const char *msg) { return fail(st, "%s", msg); }
+
 extern "C" {
 
 int lbp_version(void) { return 100; }

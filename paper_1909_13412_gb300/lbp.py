@@ -67,6 +67,7 @@ _SIGS = {
     "lbp_timing_enable": [_vp, C.c_int],
     "lbp_timing_read": [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
     "lbp_philox4x64_10": [_vp, _vp, _vp, C.c_int64, _vp],
+    "lbp_vacf_correlate_noalloc": [_vp, C.c_int64, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
 }
 
 _lib = None
@@ -114,7 +115,7 @@ def _ptr(x, dtype, count, name, writable=False):
         return None, None
     if _is_torch(x):
         import torch
-        tmap = {np.float64: (torch.float64,), np.int64: (torch.int64,),
+        tmap = {np.float64: (torch.float64,), np.int64: (torch.int64,), np.float32: (torch.float32,),
                 np.uint64: (torch.int64, getattr(torch, "uint64", torch.int64)),
                 np.uint8: (torch.uint8,), np.int32: (torch.int32,)}
         if x.dtype not in tmap[dtype]:
@@ -316,3 +317,15 @@ def lbp_philox4x64_10(ctr, key, out, n, stream=None):
         raise ValueError("lbp_philox4x64_10 takes device tensors")
     s = C.c_void_p(stream.cuda_stream if stream is not None else 0)
     _call("lbp_philox4x64_10", a[0], b[0], c[0], int(n), s)
+
+
+def lbp_vacf_correlate_noalloc(samples, T, ncomp, max_lag, npairs, csum, counts, stream=None):
+    """VACF of a device trajectory [T][ncomp] (FP32) without device allocation."""
+    a = _ptr(samples, np.float32, T * ncomp, "samples") if T > 0 else (C.c_void_p(0), 1)
+    b = _ptr(csum, np.float64, max_lag + 1, "csum", True)
+    c = _ptr(counts, np.int64, max_lag + 1, "counts", True)
+    if {a[1], b[1], c[1]} != {1}:
+        raise ValueError("lbp_vacf_correlate_noalloc takes device tensors")
+    s = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _call("lbp_vacf_correlate_noalloc", a[0], int(T), int(ncomp), int(max_lag), int(npairs), b[0],
+          c[0], s)
