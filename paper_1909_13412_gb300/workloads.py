@@ -110,9 +110,9 @@ BROWNIAN_128 = Workload("brownian_128^3_2000p", (128, 128, 128), 0.8, 2000, kT=1
 BROWNIAN_256 = Workload("brownian_256^3_16384p", (256, 256, 256), 0.8, 16384, kT=1e-4,
                         steps=5000)
 
-# 128^3 with 16384 particles: a small case (0.25 GB of populations, still
-# larger than L2) for detailed profiles of the two kernels.
-PROFILE_128 = Workload("profile_128^3_16384p", (128, 128, 128), 0.8, 16384, kT=1e-4, steps=100)
+# 128^3 with 2048 particles (the particle density of the 256^3 case): a small
+# case (0.25 GB of populations, still larger than L2) for detailed profiles.
+PROFILE_128 = Workload("profile_128^3_2048p", (128, 128, 128), 0.8, 2048, kT=1e-4, steps=100)
 
 # 64^3 subrun of the 256^3 case at the same number density.
 BROWNIAN_64 = Workload("brownian_64^3_256p", (64, 64, 64), 0.8, 256, kT=1e-4, steps=5000)
