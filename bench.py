@@ -43,7 +43,7 @@ BYTES_PER_NODE = 2 * 15 * 4  # FP32 deviation storage: 15 loads + 15 stores per 
 K3_SOURCE = os.path.join(ROOT, "paper_1909_13412_gb300", "csrc", "lbm_kernels.cu")
 K3_PROFILE = os.path.join(ROOT, "profiles", "stream_collide_forced_256.md")
 VACF_LAG = 5000
-LAUNCHES_PER_STEP = 3  # particles, stream-collide, overflow pass (+2 VACF kernels every 64 steps)
+LAUNCHES_PER_STEP = 2  # particles, stream-collide (+2 VACF kernels every 64 steps)
 
 
 def workload(name):

@@ -120,31 +120,27 @@ __global__ void __launch_bounds__(BX) k_stream_collide(Planes pl, int nx, int ny
 // population loads (its address depends only on the block index, so no load
 // waits on another), then each lane sums, exactly in 64-bit fixed point, the
 // entries whose x is its own and adds 3 w_a F.e_a to its post-collision
-// populations.  A record that overflowed (count > REC_SLOTS) is not applied
-// here: warp 0 moves its entries to the dense accumulator, where the
-// particle kernel already put the rest, lists the nodes, and
-// k_apply_overflow applies the whole sums.  The block also clears the count
-// of its record of the previous step (which the next step's particle kernel
-// refills) and block 0 the previous step's overflow count.
+// populations.  If the record overflowed (count > REC_SLOTS) the particle
+// kernel put the shares that did not fit into the dense per-node
+// accumulator: the lanes of that (rare) segment also read and clear their
+// node's accumulator and add it to the record sum -- still an exact integer
+// sum of all the node's shares.  The block clears the count of its record of
+// the previous step, which the next step's particle kernel refills.
 // ---------------------------------------------------------------------------
 template <int BX>
 __global__ void __launch_bounds__(BX) k_stream_collide_forced(
     Planes pl, int nx, int ny, int nz, float omega, int nchunks,
     const unsigned long long *__restrict__ rec_cur, unsigned long long *rec_prev,
-    unsigned int *ocount_cur, unsigned int *ocount_prev, unsigned int *olist, unsigned int ocap,
-    unsigned long long *fq, unsigned int *mask, int mwords, long long *bump) {
+    unsigned long long *fq, long long *bump) {
     static_assert(BX == SEG, "one block per force-record segment");
     const unsigned item = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned row = item / (unsigned)nchunks;
     const int chunk = (int)(item - row * (unsigned)nchunks);
-    if (item == 0 && threadIdx.x == 0) {
-        *bump += 1;
-        *ocount_prev = 0u;
-    }
+    if (item == 0 && threadIdx.x == 0) *bump += 1;
     if (threadIdx.x == 0) rec_prev[(size_t)item * REC_WORDS] = 0ull;
     const int xw = chunk * BX + (threadIdx.x & ~31);
-    if (xw >= nx) return;  // whole warp past the end of the row (never warp 0)
+    if (xw >= nx) return;  // whole warp past the end of the row
     const int x0 = xw + lane;
     const bool act = x0 < nx;
     const int x = act ? x0 : nx - 1;
@@ -157,45 +153,33 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
     const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw, 0) & 0xffffffffull);
     float F0 = 0.f, F1 = 0.f, F2 = 0.f;
     if (cnt > 0) {
-        if (cnt <= REC_SLOTS) {
-            long long a0 = 0, a1 = 0, a2 = 0;
-            for (int sl = 0; sl < cnt; ++sl) {
-                const unsigned long long xw2 = __shfl_sync(0xffffffffu, rw, REC_X0 + (sl >> 1));
-                const int xs = (int)(unsigned)(xw2 >> (32 * (sl & 1)));
-                const long long v0 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl);
-                const long long v1 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 1);
-                const long long v2 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 2);
-                if (xs == x) {
-                    a0 += v0;
-                    a1 += v1;
-                    a2 += v2;
-                }
-            }
-            const float inv = 1.3877787807814457e-17f;  // 2^-56
-            F0 = inv * __ll2float_rn(a0);
-            F1 = inv * __ll2float_rn(a1);
-            F2 = inv * __ll2float_rn(a2);
-        } else if (threadIdx.x < 32) {
-            const long long N = (long long)nx * ny * nz;
-#pragma unroll
-            for (int sl = 0; sl < REC_SLOTS; ++sl) {
-                const unsigned long long xw2 = __shfl_sync(0xffffffffu, rw, REC_X0 + (sl >> 1));
-                const int xs = (int)(unsigned)(xw2 >> (32 * (sl & 1)));
-                const unsigned long long v0 = __shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl);
-                const unsigned long long v1 = __shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 1);
-                const unsigned long long v2 = __shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 2);
-                if (lane == sl) {
-                    const long long node = (long long)row * nx + xs;
-                    atomicAdd(fq + node, v0);
-                    atomicAdd(fq + N + node, v1);
-                    atomicAdd(fq + 2 * N + node, v2);
-                    const unsigned int w = (unsigned)row * (unsigned)mwords + (unsigned)(xs >> 5);
-                    atomicOr(mask + w, 1u << (xs & 31));
-                    const unsigned int e = atomicAdd(ocount_cur, 1u);
-                    if (e < ocap) olist[e] = (unsigned int)node;
-                }
+        const int used = cnt < REC_SLOTS ? cnt : REC_SLOTS;
+        long long a0 = 0, a1 = 0, a2 = 0;
+        for (int sl = 0; sl < used; ++sl) {
+            const unsigned long long xw2 = __shfl_sync(0xffffffffu, rw, REC_X0 + (sl >> 1));
+            const int xs = (int)(unsigned)(xw2 >> (32 * (sl & 1)));
+            const long long v0 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl);
+            const long long v1 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 1);
+            const long long v2 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 2);
+            if (xs == x) {
+                a0 += v0;
+                a1 += v1;
+                a2 += v2;
             }
         }
+        if (cnt > REC_SLOTS && act) {
+            const long long N = (long long)nx * ny * nz;
+            a0 += (long long)fq[n.d];
+            a1 += (long long)fq[N + n.d];
+            a2 += (long long)fq[2 * N + n.d];
+            fq[n.d] = 0ull;
+            fq[N + n.d] = 0ull;
+            fq[2 * N + n.d] = 0ull;
+        }
+        const float inv = 1.3877787807814457e-17f;  // 2^-56
+        F0 = inv * __ll2float_rn(a0);
+        F1 = inv * __ll2float_rn(a1);
+        F2 = inv * __ll2float_rn(a2);
     }
     if (!act) return;
     collide_store(g, pl, n.d, omega, F0, F1, F2);
@@ -230,8 +214,7 @@ cudaError_t launch_stream_collide_forced(Sim &s, const float *src, float *dst, i
     const long long items = (long long)s.ny * s.nz * nchunks;
     k_stream_collide_forced<BX><<<(unsigned)items, BX, 0, st>>>(
         planes_of(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks, s.rec[parity],
-        s.rec[parity ^ 1], s.d_ocount + parity, s.d_ocount + (parity ^ 1), s.olist[parity],
-        s.ocap, s.fq, s.mask, s.mwords, s.d_step);
+        s.rec[parity ^ 1], s.fq, s.d_step);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,6 @@
 //
 //      s0:  k_particles (fhat^{n-1} -> F_H, V, r, force records)
 //           -> k_stream_collide_forced (fhat^{n-1} + records -> fhat^n)
-//           -> k_apply_overflow (shares that did not fit a record; usually none)
 //      s1:  every 64th step the VACF block, forked after k_particles and
 //           joined at the end of the step, so it overlaps the lattice pass.
 //
@@ -139,10 +138,7 @@ lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
     }
-    if (s->np > 0) {
-        CK(launch_apply_overflow(*s, dst, parity, s->s0));
-        if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
-    }
+    if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
     return LBP_OK;
 }
 
@@ -242,16 +238,14 @@ lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out)
     if (st == LBP_OK) st = dalloc(&s->d_step, 1);
     if (st == LBP_OK) st = dalloc(&s->d_err, 1);
     if (st == LBP_OK) st = dalloc(&s->d_vacf, 4);
-    s->mwords = (s->nx + 31) / 32;
-    const size_t mask_words = (size_t)s->ny * s->nz * s->mwords;
-    if (st == LBP_OK) st = dalloc(&s->mask, mask_words);
+
     if (st != LBP_OK) return bail(st);
     e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch_fill_rest(*s, s->f[i], s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_vacf, 0, 4 * sizeof(long long), s->s0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->mask, 0, sizeof(unsigned int) * mask_words, s->s0);
+
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->s0);
     if (e != cudaSuccess) {
         fail(LBP_ECUDA, "lbp_create: %s", cudaGetErrorString(e));
@@ -267,8 +261,8 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
-                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->mask, s->rec[0],
-                    s->rec[1], s->d_ocount, s->olist[0], s->olist[1], s->ring,
+                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->rec[0],
+                    s->rec[1], s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -437,17 +431,7 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
                 TRY(dalloc(&s->rec[q], (size_t)s->nseg * REC_WORDS));
                 CK(cudaMemset(s->rec[q], 0, sizeof(unsigned long long) * (size_t)s->nseg * REC_WORDS));
             }
-            TRY(dalloc(&s->d_ocount, 2));
-            CK(cudaMemset(s->d_ocount, 0, 2 * sizeof(unsigned int)));
         }
-        // overflow lists: at most 8 shares per particle from the particle
-        // kernel plus 8 per overflowed record (< 8 per particle)
-        for (int q = 0; q < 2; ++q) {
-            if (s->olist[q]) cudaFree(s->olist[q]);
-            s->olist[q] = nullptr;
-            TRY(dalloc(&s->olist[q], 16 * (size_t)cap + 64));
-        }
-        s->ocap = (unsigned int)(16 * (size_t)cap + 64);
         s->cap = cap;
     }
     // upload the new particles into the SoA planes
@@ -732,10 +716,15 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
     if (n < 0 || (n > 0 && !out)) return fail(LBP_EINVAL, "lbp_diagnostics: bad output");
     CK(cudaStreamSynchronize(s->s0));
     int64_t v[3] = {0, REC_SLOTS, s->nseg};
-    if (s->d_ocount) {
-        unsigned int c[2] = {0u, 0u};
-        CK(cudaMemcpy(c, s->d_ocount, sizeof(c), cudaMemcpyDeviceToHost));
-        v[0] = c[s->cur ^ 1];  // parity of the last completed step
+    if (s->rec[0]) {
+        // shares beyond the slots of the records of the last completed step
+        std::vector<unsigned long long> words((size_t)s->nseg * REC_WORDS);
+        CK(cudaMemcpy(words.data(), s->rec[s->cur ^ 1], sizeof(unsigned long long) * words.size(),
+                      cudaMemcpyDeviceToHost));
+        for (long long q = 0; q < s->nseg; ++q) {
+            const long long c = (long long)(words[(size_t)q * REC_WORDS] & 0xffffffffull);
+            if (c > REC_SLOTS) v[0] += c - REC_SLOTS;
+        }
     }
     for (int i = 0; i < n && i < 3; ++i) out[i] = v[i];
     return LBP_OK;

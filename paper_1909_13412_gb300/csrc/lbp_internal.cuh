@@ -44,7 +44,7 @@ constexpr double FIX_LIMIT = 32.0;                 // |F_H| < 2^5 per particle
 // REC_SLOTS (x, fixed-point force share) entries appended by the particle
 // kernel.  The stream-collide kernel loads its record together with the
 // populations and adds the force term in registers.  Entries beyond the
-// capacity go to the dense per-node accumulator instead (see the kernels).
+// capacity go to a dense per-node accumulator instead (see the kernels).
 constexpr int SEG = 128;                 // nodes per segment (stream-collide block)
 constexpr int REC_SLOTS = 8;
 constexpr int REC_WORDS = 32;            // 8-byte words per record (256 bytes)
@@ -114,16 +114,11 @@ struct Sim {
     int exclude_inside = 0;
     double sqrt3 = 0.0;
 
-    // overflow of the force records: fixed-point accumulator per node and a bit
-    // per node marking the nodes that hold one (both cleared by the overflow pass)
+    // force records and their overflow: a fixed-point accumulator per node that
+    // the stream-collide block of an overflowed segment reads and clears
     unsigned long long *fq = nullptr;  // [3][N], allocated with the first particle
-    unsigned int *mask = nullptr;      // [ny * nz][mwords]
-    int mwords = 0;                    // ceil(nx / 32)
     unsigned long long *rec[2] = {nullptr, nullptr};  // [segments][REC_WORDS], by step parity
     long long nseg = 0;                                // ny * nz * ceil(nx / SEG)
-    unsigned int *d_ocount = nullptr;                  // [2] overflow list lengths by step parity
-    unsigned int *olist[2] = {nullptr, nullptr};       // nodes holding overflowed shares
-    unsigned int ocap = 0;                             // capacity of each overflow list
 
     // VACF
     int vacf_lag = -1;
@@ -168,7 +163,6 @@ cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, doub
                           cudaStream_t st);
 // particle_kernels.cu
 cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t st);
-cudaError_t launch_apply_overflow(Sim &s, float *dst, int parity, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);

@@ -9,7 +9,6 @@
 //   C. eight threads per particle append the shares of the reaction force
 //      -F_H (Eq. 9) at the corner nodes to the force records of the row
 //      segments holding those nodes; the stream-collide kernel applies them.
-// k_apply_overflow: applies the shares that did not fit in a record.
 //
 // Why one thread per particle in phase B: GB300 issues FP64 at 1/64 of the
 // FP32 rate, so a warp-wide FP64 instruction costs the same whether one lane
@@ -35,9 +34,9 @@
 // per-node force is the integer sum of the matching entries, so it is exact
 // and independent of the order in which particles appended them (no
 // floating-point atomics).  When a record is full the share goes to a dense
-// per-node accumulator (integer atomics) and the node's bit is set in
-// `mask`; whether a record overflows depends only on how many shares it
-// receives, so the split between the two paths is deterministic too.
+// per-node accumulator (integer atomics), which the stream-collide block of
+// an overflowed segment adds to the record sum; the total is the same exact
+// integer sum whichever shares found a slot.
 #include <cuda_runtime.h>
 
 #include "lbp_internal.cuh"
@@ -59,12 +58,7 @@ struct ParticleArgs {
     int mode, exclude_inside;
     unsigned long long *rec; // force records of this step's parity
     int nchunks;             // segments per row
-    unsigned int *ocount;    // overflow list of this step's parity
-    unsigned int *olist;
-    unsigned int ocap;
     unsigned long long *fq;  // [3][N] fixed-point overflow accumulator
-    unsigned int *mask;      // [rows][mwords]
-    int mwords;
     float *ring;
     int ring_cap;
     long long *d_vacf;  // [0] first sampled step, [2] samples written
@@ -316,10 +310,6 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
             atomicAdd(A.fq + node, (unsigned long long)sh[0]);
             atomicAdd(A.fq + A.N + node, (unsigned long long)sh[1]);
             atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)sh[2]);
-            const unsigned int w = (unsigned)row * (unsigned)A.mwords + (unsigned)(X >> 5);
-            atomicOr(A.mask + w, 1u << (X & 31));
-            const unsigned int e = atomicAdd(A.ocount, 1u);
-            if (e < A.ocap) A.olist[e] = (unsigned int)node;
         }
     }
 }
@@ -351,63 +341,14 @@ cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t 
     A.mode = s.mode;
     A.exclude_inside = s.exclude_inside;
     A.fq = s.fq;
-    A.mask = s.mask;
-    A.mwords = s.mwords;
     A.rec = s.rec[parity];
     A.nchunks = (s.nx + SEG - 1) / SEG;
-    A.ocount = s.d_ocount + parity;
-    A.olist = s.olist[parity];
-    A.ocap = s.ocap;
     A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
     const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
     k_particles<<<grid, 8 * PB, 0, st>>>(A);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Body-force term of Eqs. 18-19 at the nodes whose shares overflowed their
-// record.  The overflow list holds those nodes (a node may be listed more than
-// once); one thread per entry, and the thread that clears the node's mask bit
-// owns the node: it applies the node's exact fixed-point sum to the
-// post-collision populations and clears the accumulators.  With no overflow
-// the kernel only reads the list length.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_apply_overflow(float *g, long long P, long long N, int nx,
-                                                        int mwords, unsigned int *mask,
-                                                        unsigned long long *fq,
-                                                        const unsigned int *ocount,
-                                                        const unsigned int *olist, unsigned int ocap) {
-    unsigned int n = *ocount;
-    if (n > ocap) n = ocap;
-    for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const unsigned int node = olist[e];
-        const unsigned int row = node / (unsigned)nx;
-        const unsigned int X = node - row * (unsigned)nx;
-        const unsigned int bit = 1u << (X & 31);
-        const unsigned int old = atomicAnd(mask + (size_t)row * mwords + (X >> 5), ~bit);
-        if (!(old & bit)) continue;
-        const float inv = 1.3877787807814457e-17f;  // 2^-56
-        const float F0 = 3.f * inv * __ll2float_rn((long long)fq[node]);
-        const float F1 = 3.f * inv * __ll2float_rn((long long)fq[N + node]);
-        const float F2 = 3.f * inv * __ll2float_rn((long long)fq[2 * N + node]);
-        fq[node] = 0ull;
-        fq[N + node] = 0ull;
-        fq[2 * N + node] = 0ull;
-        // the rest population (e_0 = 0) receives no force
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            float *q = g + (long long)a * P + node;
-            *q += wgtf(a) * ((float)ex(a) * F0 + (float)ey(a) * F1 + (float)ez(a) * F2);
-        }
-    }
-}
-
-cudaError_t launch_apply_overflow(Sim &s, float *dst, int parity, cudaStream_t st) {
-    k_apply_overflow<<<2 * s.num_sms, 256, 0, st>>>(dst, s.P, s.N, s.nx, s.mwords, s.mask, s.fq,
-                                                    s.d_ocount + parity, s.olist[parity], s.ocap);
     return cudaGetLastError();
 }
 

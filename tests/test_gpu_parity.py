@@ -273,6 +273,7 @@ def test_dense_particles_overflow_the_force_records(shape, n):
         h = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=4, graphs=graphs)
         lbp.lbp_step(h, 25)
         outs.append((gpu_pops(h), gpu_particles(h)))
+        assert lbp.lbp_diagnostics(h)["overflow_shares"] > 0  # the overflow path ran
         lbp.lbp_check(h)
         lbp.lbp_destroy(h)
     assert np.array_equal(outs[0][0], outs[1][0])
