@@ -85,13 +85,29 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         if (m >= 0) A.d_vacf[2] = m + 1;
     }
 
-    // ---- cell of each particle (warp 0): base = floor(r), q = r - base (exact)
+    // ---- cell of each particle (warp 0): base = floor(r), q = r - base (exact).
+    // Warp 0 also loads all the particle state phase B needs now, so that its
+    // loads overlap this step's other memory round trips.
     const int ip = i0 + lane;
     double r0 = 0.0, r1 = 0.0, r2 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    double V0 = 0.0, V1 = 0.0, V2 = 0.0, gam = 0.0, Rd = 0.0, sg = 0.0, invM = 0.0;
+    double fe0 = 0.0, fe1 = 0.0, fe2 = 0.0;
+    bool pin = false;
     if (t < 32 && ip < A.np) {
         r0 = A.r[ip];
         r1 = A.r[cap + ip];
         r2 = A.r[2 * cap + ip];
+        V0 = A.v[ip];
+        V1 = A.v[cap + ip];
+        V2 = A.v[2 * cap + ip];
+        gam = A.gamma[ip];
+        Rd = A.radius[ip];
+        sg = A.sig[ip];
+        invM = A.inv_mass[ip];
+        fe0 = A.fext[ip];
+        fe1 = A.fext[cap + ip];
+        fe2 = A.fext[2 * cap + ip];
+        pin = A.pinned[ip] != 0;
         const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
         q0 = r0 - b0;
         q1 = r1 - b1;
@@ -133,8 +149,6 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
     // ---- phase B (warp 0): fit, random force, Langevin update
     if (t < 32 && ip < A.np) {
         const int i = ip;
-        const double V0 = A.v[i], V1 = A.v[cap + i], V2 = A.v[2 * cap + i];
-        const double gam = A.gamma[i];
         double F0 = 0.0, F1 = 0.0, F2 = 0.0;
         bool spread = true;
         if (A.mode == LBP_STOKESLET) {
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
                 const float n0 = m0 * is, n1 = m1 * is, n2 = m2 * is;
                 const float inrm = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
                 const float e0 = n0 * inrm, e1 = n1 * inrm, e2 = n2 * inrm;
-                const float R = (float)A.radius[i];
+                const float R = (float)Rd;
                 const float R2 = R * R, R34 = 0.75f * R;
                 // corner offsets d_p = c - q
                 const float dx[2] = {(float)(-q0), (float)(1.0 - q0)};
@@ -235,7 +249,6 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         // to the oracle's.
         unsigned long long ctr[4] = {(unsigned long long)step, (unsigned long long)i, 0ull, 0ull};
         philox4x64_10(ctr, A.seed, 0ull);
-        const double sg = A.sig[i];
         double R3[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -245,10 +258,9 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         const double FH3[3] = {F0, F1, F2};
         const double Vo[3] = {V0, V1, V2};
         const double ro[3] = {r0, r1, r2};
+        const double fe[3] = {fe0, fe1, fe2};
         const int L[3] = {nx, ny, nz};
         double Vn[3] = {V0, V1, V2};
-        const bool pin = A.pinned[i] != 0;
-        const double invM = A.inv_mass[i];
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -256,7 +268,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
             A.fr[k * cap + i] = R3[k];
             if (!pin) {
                 // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
-                Vn[k] = Vo[k] + (FH3[k] + R3[k] + A.fext[k * cap + i]) * invM;
+                Vn[k] = Vo[k] + (FH3[k] + R3[k] + fe[k]) * invM;
                 double rn = ro[k] + Vn[k];
                 if (rn < 0.0) rn += (double)L[k];
                 if (rn >= (double)L[k]) rn -= (double)L[k];
