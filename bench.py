@@ -56,6 +56,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(values, device, dist=None):
+    """Element-wise max of per-rank timings over all ranks (identity when alone)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def aggregate_mlups(world, nodes_per_rank, steps, max_ms):
+    """Whole-job lattice updates per second (MLUPS) over `world` replica boxes."""
+    return world * nodes_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -243,11 +257,8 @@ def run_gpu(args, w):
     k3_ms, k3_n = lbp.lbp_timing_read(h)
     lbp.lbp_timing_enable(h, False)
     lbp.lbp_check(h)
-    t = torch.tensor([ms, k3_ms / max(k3_n, 1)], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, k3_avg_ms = float(t[0]), float(t[1])
-    value = world * w.nodes * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max, k3_avg_ms = max_over_ranks([ms, k3_ms / max(k3_n, 1)], "cuda", dist)
+    value = aggregate_mlups(world, w.nodes, args.steps, ms_max)
 
     # end to end through the C ABI with host buffers: per step the external
     # forces go host->device and positions + velocities come back
@@ -264,10 +275,8 @@ def run_gpu(args, w):
         lbp.lbp_particles_read(h, r=r_h, v=v_h)
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * w.nodes * e2e_steps / float(te[0]) / 1e6
+    e2e_max_s, = max_over_ranks([e2e_s], "cuda", dist)
+    e2e_value = aggregate_mlups(world, w.nodes, e2e_steps, e2e_max_s * 1e3)
     lbp.lbp_check(h)
     lbp.lbp_destroy(h)
 
