@@ -20,6 +20,7 @@ collective in the step) and the timing is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import math
@@ -39,7 +40,9 @@ sys.path.insert(0, ROOT)
 from paper_1909_13412_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "MLUPS and % HBM roofline per GB300 at fixed accuracy vs FP64 oracle; plain vs BF16/batched"
-BYTES_PER_NODE = 2 * 15 * 4  # FP32 deviation storage: 15 loads + 15 stores per node update
+# algorithmic bytes per node update: 15 loads + 15 stores of the stored deviation
+BYTES_PER_NODE = {"f32": 2 * 15 * 4, "bf16": 2 * 15 * 2, "f16": 2 * 15 * 2}
+PRECISION_CODE = {"f32": 0, "bf16": 1, "f16": 2}
 K3_SOURCE = os.path.join(ROOT, "paper_1909_13412_gb300", "csrc", "lbm_kernels.cu")
 K3_PROFILE = os.path.join(ROOT, "profiles", "stream_collide_forced_256.md")
 VACF_LAG = 5000
@@ -208,11 +211,11 @@ def run_reference(args, w):
     return 0
 
 
-def config_of(w, world, vacf_lag=VACF_LAG):
+def config_of(w, world, vacf_lag=VACF_LAG, precision="f32"):
     nz, ny, nx = w.shape_zyx
     return {"workload": w.name, "lattice": [nx, ny, nz], "nodes_per_rank": w.nodes,
             "particles_per_rank": w.n_particles, "tau": w.tau, "kT": w.kT, "M": w.M,
-            "gamma": w.gamma, "coupling": "stokeslet", "storage": "f32 deviation",
+            "gamma": w.gamma, "coupling": "stokeslet", "storage": f"{precision} deviation",
             "vacf_max_lag": vacf_lag, "parallelism": f"replicas{world}",
             "l2": "no flush: 2 x 1.0 GB population buffers per step exceed the 129 MB L2"}
 
@@ -236,28 +239,38 @@ def run_gpu(args, w):
 
     ps = w.particles()
     nz, ny, nx = w.shape_zyx
-    h = lbp.lbp_create(nx, ny, nz, w.tau)
-    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
-    lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise + rank)
-    lbp.lbp_vacf_configure(h, args.vacf_lag)
 
-    # warm-up, then the timed region with per-launch events around the stream-collide kernel
-    lbp.lbp_step(h, args.warmup)
-    lbp.lbp_check(h)
-    lbp.lbp_timing_enable(h, True)
-    stream = torch.cuda.current_stream()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    with ClockSampler(local) as clk:
-        start.record(stream)
-        lbp.lbp_step(h, args.steps)
-        end.record(stream)
+    def make(precision):
+        h = lbp.lbp_create(nx, ny, nz, w.tau, precision=PRECISION_CODE[precision])
+        lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise + rank)
+        lbp.lbp_vacf_configure(h, args.vacf_lag)
+        return h
+
+    def timed(h, steps, warmup, clocks=None):
+        """K steps between CUDA events on the caller's stream; the library's own
+        events around every stream-collide launch give that kernel's duration."""
+        lbp.lbp_step(h, warmup)
+        lbp.lbp_check(h)
+        lbp.lbp_timing_enable(h, True)
+        stream = torch.cuda.current_stream()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
-    ms = start.elapsed_time(end)
-    k3_ms, k3_n = lbp.lbp_timing_read(h)
-    lbp.lbp_timing_enable(h, False)
-    lbp.lbp_check(h)
-    ms_max, k3_avg_ms = max_over_ranks([ms, k3_ms / max(k3_n, 1)], "cuda", dist)
+        with (clocks if clocks is not None else contextlib.nullcontext()):
+            start.record(stream)
+            lbp.lbp_step(h, steps)
+            end.record(stream)
+            barrier()
+        ms = start.elapsed_time(end)
+        k3_ms, k3_n = lbp.lbp_timing_read(h)
+        lbp.lbp_timing_enable(h, False)
+        lbp.lbp_check(h)
+        return ms, k3_ms / max(k3_n, 1), k3_n
+
+    h = make(args.precision)
+    clk = ClockSampler(local)
+    ms, k3_one, k3_n = timed(h, args.steps, args.warmup, clk)
+    ms_max, k3_avg_ms = max_over_ranks([ms, k3_one], "cuda", dist)
     value = aggregate_mlups(world, w.nodes, args.steps, ms_max)
 
     # end to end through the C ABI with host buffers: per step the external
@@ -280,26 +293,45 @@ def run_gpu(args, w):
     lbp.lbp_check(h)
     lbp.lbp_destroy(h)
 
+    # the other storage types on the same workload (shorter runs)
+    variants = {}
+    if not args.no_variants:
+        for prec in ("f32", "bf16", "f16"):
+            if prec == args.precision:
+                continue
+            hv = make(prec)
+            vsteps = max(1, min(args.steps, 500))
+            vms, vk3, _ = timed(hv, vsteps, args.warmup)
+            vms, vk3 = max_over_ranks([vms, vk3], "cuda", dist)
+            lbp.lbp_destroy(hv)
+            vach = BYTES_PER_NODE[prec] * w.nodes / (vk3 * 1e-3) / 1e9
+            variants[prec] = {"value": aggregate_mlups(world, w.nodes, vsteps, vms), "unit": "MLUPS",
+                              "steps": vsteps, "ms_per_step": vms / vsteps,
+                              "stream_collide_ms": vk3, "achieved_gbs": vach,
+                              "frac": vach / measured_peaks()[0],
+                              "bytes_per_node": BYTES_PER_NODE[prec]}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_NODE * w.nodes / (k3_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic()
+    achieved = BYTES_PER_NODE[args.precision] * w.nodes / (k3_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic() if args.precision == "f32" else None
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(w, world, args.vacf_lag),
+        "config": config_of(w, world, args.vacf_lag, args.precision),
         "roofline": {"bound": "hbm", "kernel": "k_stream_collide_forced", "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": BYTES_PER_NODE * w.nodes,
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.precision] * w.nodes,
                      "avg_launch_ms": k3_avg_ms, "launches": k3_n},
         "particle_updates_per_s": world * n * args.steps / (ms_max * 1e-3),
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": fext.nbytes,
                 "d2h_bytes_per_step": r_h.nbytes + v_h.nbytes, "steps": e2e_steps},
+        "variants": variants,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps
                         + 2 * sum(1 for n in range(args.warmup, args.warmup + args.steps) if (n + 1) % 64 == 0),
         "clocks": clk.summary(),
@@ -321,6 +353,8 @@ def main():
     ap.add_argument("--workload", default="brownian_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vacf-lag", type=int, default=VACF_LAG)
+    ap.add_argument("--precision", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "lbp":
         args.warmup = 3

@@ -69,9 +69,16 @@ typedef enum {
 } lbp_status;
 
 /* Storage of the populations on the device.  Arithmetic is FP32 in every case;
- * the stored quantity is the deviation f_a - w_a from the rest state.          */
+ * the stored quantity is the deviation g_a = f_a - w_a from the rest state:
+ *   LBP_F32  g_a as float (120 bytes moved per node update);
+ *   LBP_BF16 g_a rounded to bfloat16 (60 bytes);
+ *   LBP_F16  g_a * 1024 / w_a rounded to binary16 (60 bytes; the per-population
+ *            scale keeps slow-flow deviations in binary16's normal range).
+ * Particle state, the fit's solve and the VACF sums stay FP64.                */
 typedef enum {
-    LBP_F32 = 0
+    LBP_F32 = 0,
+    LBP_BF16 = 1,
+    LBP_F16 = 2
 } lbp_precision;
 
 /* Friction model. STOKESLET is the paper's method (Eq. 8); POINTWISE is Eq. 7

@@ -2,7 +2,8 @@
 //
 // Storage: 15 planes (structure of arrays, x fastest), plane stride P >= N,
 // holding the deviation g_a = fhat_a - w_a of the post-collision populations
-// from the rest state.  With sum_a w_a = 1 and sum_a w_a e_a = 0 the moments
+// from the rest state, as FP32, BF16 or scaled FP16 (the Store* types of
+// lbp_internal.cuh); every kernel is a template on the storage type.  With sum_a w_a = 1 and sum_a w_a e_a = 0 the moments
 // of Eqs. 12-13 are rho~ - 1 = sum_a g_a and u = sum_a e_a g_a, and the
 // collision of Eqs. 15, 17 and 19 becomes, exactly,
 //     g'_a = g_a + (geq_a - g_a)/tau,
@@ -30,14 +31,16 @@ namespace lbp {
 // which keeps the instruction count low enough that the kernel stays bound
 // by DRAM bandwidth.  Measured on GB300 at 256^3: within 2% of a plain copy.
 // ---------------------------------------------------------------------------
+template <typename St>
 struct Planes {
-    const float *s[Q];
-    float *d[Q];
+    const typename St::T *s[Q];
+    typename St::T *d[Q];
 };
 
 // collision of one node and the store of its 15 post-collision deviations;
 // (F0, F1, F2) is the body force of Eq. 18 at the node (zero if none)
-__device__ __forceinline__ void collide_store(const float g[Q], const Planes &pl, int d,
+template <typename St>
+__device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
                                               float omega, float F0, float F1, float F2) {
     float drho = 0.f;
 #pragma unroll
@@ -49,7 +52,7 @@ __device__ __forceinline__ void collide_store(const float g[Q], const Planes &pl
     const float uz = (g[5] - g[6]) + c78 - c910 + c1112 + c1314;
     const float base = drho - 1.5f * (ux * ux + uy * uy + uz * uz);
     const float om1 = 1.f - omega;
-    pl.d[0][d] = om1 * g[0] + omega * ((2.f / 9.f) * base);
+    St::store(pl.d[0] + d, 0, om1 * g[0] + omega * ((2.f / 9.f) * base));
     // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, weight W
 #define LBP_PAIR(A, W, EU, FE)                                         \
     {                                                                  \
@@ -57,8 +60,8 @@ __device__ __forceinline__ void collide_store(const float g[Q], const Planes &pl
         const float sym = (W) * (base + 4.5f * eu * eu);               \
         const float anti = (3.f * (W)) * eu;                           \
         const float fe = (3.f * (W)) * (FE);                           \
-        pl.d[A][d] = om1 * g[A] + omega * (sym + anti) + fe;           \
-        pl.d[A + 1][d] = om1 * g[A + 1] + omega * (sym - anti) - fe;   \
+        St::store(pl.d[A] + d, A, om1 * g[A] + omega * (sym + anti) + fe);         \
+        St::store(pl.d[A + 1] + d, A + 1, om1 * g[A + 1] + omega * (sym - anti) - fe); \
     }
     LBP_PAIR(1, 1.f / 9.f, ux, F0)
     LBP_PAIR(3, 1.f / 9.f, uy, F1)
@@ -95,8 +98,8 @@ __device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int n
     return n;
 }
 
-template <int BX>
-__global__ void __launch_bounds__(BX) k_stream_collide(Planes pl, int nx, int ny, int nz,
+template <int BX, typename St>
+__global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, int nx, int ny, int nz,
                                                        float omega, int nchunks, long long *bump) {
     const unsigned item = blockIdx.x;
     const unsigned row = item / (unsigned)nchunks;
@@ -108,8 +111,8 @@ __global__ void __launch_bounds__(BX) k_stream_collide(Planes pl, int nx, int ny
     float g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a)
-        g[a] = __ldg(pl.s[a] + (n.d + n.ox[ex(a) + 1] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]));
-    collide_store(g, pl, n.d, omega, 0.f, 0.f, 0.f);
+        g[a] = St::load(pl.s[a] + (n.d + n.ox[ex(a) + 1] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]), a);
+    collide_store<St>(g, pl, n.d, omega, 0.f, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -127,9 +130,9 @@ __global__ void __launch_bounds__(BX) k_stream_collide(Planes pl, int nx, int ny
 // sum of all the node's shares.  The block clears the count of its record of
 // the previous step, which the next step's particle kernel refills.
 // ---------------------------------------------------------------------------
-template <int BX>
+template <int BX, typename St>
 __global__ void __launch_bounds__(BX) k_stream_collide_forced(
-    Planes pl, int nx, int ny, int nz, float omega, int nchunks,
+    Planes<St> pl, int nx, int ny, int nz, float omega, int nchunks,
     const unsigned long long *__restrict__ rec_cur, unsigned long long *rec_prev,
     unsigned long long *fq, long long *bump) {
     static_assert(BX == SEG, "one block per force-record segment");
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
     float g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a)
-        g[a] = __ldg(pl.s[a] + (n.d + n.ox[ex(a) + 1] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]));
+        g[a] = St::load(pl.s[a] + (n.d + n.ox[ex(a) + 1] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]), a);
     const unsigned long long rw = __ldg(rec_cur + (size_t)item * REC_WORDS + lane);
     const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw, 0) & 0xffffffffull);
     float F0 = 0.f, F1 = 0.f, F2 = 0.f;
@@ -182,64 +185,85 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
         F2 = inv * __ll2float_rn(a2);
     }
     if (!act) return;
-    collide_store(g, pl, n.d, omega, F0, F1, F2);
+    collide_store<St>(g, pl, n.d, omega, F0, F1, F2);
 }
 
 constexpr int SC_BX = SEG;
 
 cudaError_t prepare_lbm_kernels() { return cudaSuccess; }
 
-static Planes planes_of(const Sim &s, const float *src, float *dst) {
-    Planes pl;
+template <typename St>
+static Planes<St> planes_of(const Sim &s, const void *src, void *dst) {
+    Planes<St> pl;
+    const typename St::T *a0 = static_cast<const typename St::T *>(src);
+    typename St::T *b0 = static_cast<typename St::T *>(dst);
     for (int a = 0; a < Q; ++a) {
-        pl.s[a] = src + (long long)a * s.P;
-        pl.d[a] = dst + (long long)a * s.P;
+        pl.s[a] = a0 + (long long)a * s.P;
+        pl.d[a] = b0 + (long long)a * s.P;
     }
     return pl;
 }
 
-cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, cudaStream_t st) {
+// Run F<StoreX>() for the handle's storage type.
+template <typename F>
+static cudaError_t by_storage(const Sim &s, F &&f) {
+    switch (s.precision) {
+        case LBP_BF16: return f(StoreBF16{});
+        case LBP_F16: return f(StoreF16{});
+        default: return f(StoreF32{});
+    }
+}
+
+cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st) {
     constexpr int BX = SC_BX;
     const int nchunks = (s.nx + BX - 1) / BX;
     const long long items = (long long)s.ny * s.nz * nchunks;
-    k_stream_collide<BX><<<(unsigned)items, BX, 0, st>>>(planes_of(s, src, dst), s.nx, s.ny, s.nz,
-                                                          (float)(1.0 / s.tau), nchunks, s.d_step);
-    return cudaGetLastError();
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_stream_collide<BX, St><<<(unsigned)items, BX, 0, st>>>(
+            planes_of<St>(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks, s.d_step);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_stream_collide_forced(Sim &s, const float *src, float *dst, int parity,
+cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st) {
     constexpr int BX = SC_BX;
     const int nchunks = (s.nx + BX - 1) / BX;
     const long long items = (long long)s.ny * s.nz * nchunks;
-    k_stream_collide_forced<BX><<<(unsigned)items, BX, 0, st>>>(
-        planes_of(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks, s.rec[parity],
-        s.rec[parity ^ 1], s.fq, s.d_step);
-    return cudaGetLastError();
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_stream_collide_forced<BX, St><<<(unsigned)items, BX, 0, st>>>(
+            planes_of<St>(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks,
+            s.rec[parity], s.rec[parity ^ 1], s.fq, s.d_step);
+        return cudaGetLastError();
+    });
 }
 
 // ---------------------------------------------------------------------------
 // FP64 <-> deviation storage.  f is [15][N] FP64 (the ABI layout).
 // ---------------------------------------------------------------------------
-__global__ void k_from_f64(const double *__restrict__ f, float *__restrict__ g, long long N,
-                           long long P) {
+template <typename St>
+__global__ void k_from_f64(const double *__restrict__ f, typename St::T *__restrict__ g,
+                           long long N, long long P) {
     const long long total = (long long)Q * N;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int a = (int)(t / N);
         const long long i = t - (long long)a * N;
-        g[(long long)a * P + i] = (float)(f[t] - wgt(a));
+        St::store(g + (long long)a * P + i, a, (float)(f[t] - wgt(a)));
     }
 }
 
-__global__ void k_to_f64(const float *__restrict__ g, double *__restrict__ f, long long N,
+template <typename St>
+__global__ void k_to_f64(const typename St::T *__restrict__ g, double *__restrict__ f, long long N,
                          long long P) {
     const long long total = (long long)Q * N;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int a = (int)(t / N);
         const long long i = t - (long long)a * N;
-        f[t] = wgt(a) + (double)g[(long long)a * P + i];
+        f[t] = wgt(a) + (double)St::load(g + (long long)a * P + i, a);
     }
 }
 
@@ -251,25 +275,35 @@ static unsigned grid_for(long long work, int threads, int num_sms) {
     return (unsigned)g;
 }
 
-cudaError_t launch_fill_rest(Sim &s, float *dst, cudaStream_t st) {
-    return cudaMemsetAsync(dst, 0, sizeof(float) * Q * s.P, st);
+cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st) {
+    // all three storage types encode 0 as all-zero bits
+    return cudaMemsetAsync(dst, 0, (size_t)storage_bytes(s.precision) * Q * s.P, st);
 }
 
-cudaError_t launch_from_f64(Sim &s, const double *f, float *dst, cudaStream_t st) {
-    k_from_f64<<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(f, dst, s.N, s.P);
-    return cudaGetLastError();
+cudaError_t launch_from_f64(Sim &s, const double *f, void *dst, cudaStream_t st) {
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_from_f64<St><<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(
+            f, static_cast<typename St::T *>(dst), s.N, s.P);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_to_f64(Sim &s, const float *src, double *f, cudaStream_t st) {
-    k_to_f64<<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(src, f, s.N, s.P);
-    return cudaGetLastError();
+cudaError_t launch_to_f64(Sim &s, const void *src, double *f, cudaStream_t st) {
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_to_f64<St><<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(
+            static_cast<const typename St::T *>(src), f, s.N, s.P);
+        return cudaGetLastError();
+    });
 }
 
 // ---------------------------------------------------------------------------
 // Moments of the streamed populations (Eqs. 12-13) and p = rho~/3, in FP64.
 // ---------------------------------------------------------------------------
-__global__ void k_fields(const float *__restrict__ src, double *rho, double *u, double *p, int nx,
-                         int ny, int nz, long long P) {
+template <typename St>
+__global__ void k_fields(const typename St::T *__restrict__ src, double *rho, double *u, double *p,
+                         int nx, int ny, int nz, long long P) {
     const long long N = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -284,7 +318,8 @@ __global__ void k_fields(const float *__restrict__ src, double *rho, double *u, 
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
             zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-            const double g = (double)src[(long long)a * P + ((long long)zs * ny + ys) * nx + xs];
+            const double g =
+                (double)St::load(src + (long long)a * P + ((long long)zs * ny + ys) * nx + xs, a);
             drho += g;
             ux += ex(a) * g;
             uy += ey(a) * g;
@@ -300,11 +335,14 @@ __global__ void k_fields(const float *__restrict__ src, double *rho, double *u, 
     }
 }
 
-cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, double *p,
+cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, double *p,
                           cudaStream_t st) {
-    k_fields<<<grid_for(s.N, 256, s.num_sms), 256, 0, st>>>(src, rho, u, p, s.nx, s.ny, s.nz,
-                                                            s.P);
-    return cudaGetLastError();
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_fields<St><<<grid_for(s.N, 256, s.num_sms), 256, 0, st>>>(
+            static_cast<const typename St::T *>(src), rho, u, p, s.nx, s.ny, s.nz, s.P);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace lbp

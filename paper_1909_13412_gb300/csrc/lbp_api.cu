@@ -117,8 +117,8 @@ double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
 // one time step (see the sequence at the top of this file)
 lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
-    const float *src = s->f[s->cur];
-    float *dst = s->f[s->cur ^ 1];
+    const void *src = s->f[s->cur];
+    void *dst = s->f[s->cur ^ 1];
     const int parity = s->cur;
     if (s->np > 0) {
         CK(launch_particles(*s, src, parity, s->s0));
@@ -201,7 +201,7 @@ lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out)
     if (N > 2147483647ll) return fail(LBP_EINVAL, "lbp_create: nx*ny*nz = %lld exceeds 2^31-1", N);
     if (!(desc->tau > 0.5) || !std::isfinite(desc->tau))
         return fail(LBP_EINVAL, "lbp_create: tau must be finite and > 1/2 (nu = (tau-1/2)/3 > 0)");
-    if (desc->precision != LBP_F32)
+    if (desc->precision != LBP_F32 && desc->precision != LBP_BF16 && desc->precision != LBP_F16)
         return fail(LBP_EINVAL, "lbp_create: unsupported precision %d", desc->precision);
 
     lbp_sim *s = new lbp_sim();
@@ -234,7 +234,11 @@ lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out)
         return bail(LBP_ECUDA);
     }
     lbp_status st = LBP_OK;
-    for (int i = 0; i < 2 && st == LBP_OK; ++i) st = dalloc(&s->f[i], (size_t)Q * s->P);
+    for (int i = 0; i < 2 && st == LBP_OK; ++i) {
+        char *buf = nullptr;
+        st = dalloc(&buf, (size_t)storage_bytes(s->precision) * Q * s->P);
+        s->f[i] = buf;
+    }
     if (st == LBP_OK) st = dalloc(&s->d_step, 1);
     if (st == LBP_OK) st = dalloc(&s->d_err, 1);
     if (st == LBP_OK) st = dalloc(&s->d_vacf, 4);
@@ -281,7 +285,7 @@ lbp_status lbp_set_populations(lbp_sim *s, const double *f, int on_device) {
     CHECK_SIM(s);
     if (!f) return fail(LBP_EINVAL, "lbp_set_populations: null f");
     TRY(enter(s));
-    float *dst = s->f[s->cur];
+    void *dst = s->f[s->cur];
     if (on_device) {
         CK(launch_from_f64(*s, f, dst, s->s0));
     } else {
@@ -297,7 +301,7 @@ lbp_status lbp_read_populations(lbp_sim *s, double *f, int on_device) {
     CHECK_SIM(s);
     if (!f) return fail(LBP_EINVAL, "lbp_read_populations: null f");
     TRY(enter(s));
-    const float *src = s->f[s->cur];
+    const void *src = s->f[s->cur];
     if (on_device) {
         CK(launch_to_f64(*s, src, f, s->s0));
     } else {
@@ -313,7 +317,7 @@ lbp_status lbp_read_fields(lbp_sim *s, double *rho, double *u, double *p, int on
     CHECK_SIM(s);
     if (!rho && !u && !p) return LBP_OK;
     TRY(enter(s));
-    const float *src = s->f[s->cur];
+    const void *src = s->f[s->cur];
     if (on_device) {
         CK(launch_fields(*s, src, rho, u, p, s->s0));
     } else {

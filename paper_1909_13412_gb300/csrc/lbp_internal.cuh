@@ -3,6 +3,8 @@
 // and the kernel launchers.  Written for sm_103a (GB300).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,6 +35,39 @@ __host__ __device__ constexpr double wgt(int a) {
 __host__ __device__ constexpr float wgtf(int a) {
     return a == 0 ? 2.0f / 9.0f : a <= 6 ? 1.0f / 9.0f : 1.0f / 72.0f;
 }
+
+// ------------------------------------------------------------ storage
+// The populations are stored as deviations g_a = f_a - w_a from the rest
+// state; arithmetic is always FP32.  Three storage types:
+//   F32  : g_a as float (120 bytes per node update);
+//   BF16 : g_a rounded to bfloat16 (60 bytes);
+//   F16  : g_a * (F16_SCALE / w_a) rounded to binary16 (60 bytes).  The
+//          per-population scale keeps the deviations of slow flows inside
+//          binary16's normal range (|g/w| down to ~6e-8 stays normal) while
+//          |g/w| up to 64 still fits.
+constexpr float F16_SCALE = 1024.f;
+
+struct StoreF32 {
+    using T = float;
+    static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
+    static __device__ __forceinline__ void store(T *p, int, float v) { *p = v; }
+};
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float load(const T *p, int) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void store(T *p, int, float v) { *p = __float2bfloat16_rn(v); }
+};
+struct StoreF16 {
+    using T = __half;
+    static __device__ __forceinline__ float load(const T *p, int a) {
+        return __half2float(__ldg(p)) * (wgtf(a) * (1.f / F16_SCALE));
+    }
+    static __device__ __forceinline__ void store(T *p, int a, float v) {
+        *p = __float2half_rn(v * (F16_SCALE / wgtf(a)));
+    }
+};
+
+__host__ __device__ constexpr int storage_bytes(int precision) { return precision == LBP_F32 ? 4 : 2; }
 
 // Reaction forces are summed per node in 64-bit fixed point so that the sum
 // is exact and independent of the order in which particles add to it.
@@ -97,7 +132,7 @@ struct Sim {
     cudaStream_t s1 = nullptr;    // library side stream (particles, VACF)
     cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
 
-    float *f[2] = {nullptr, nullptr};  // deviation populations, 15 planes of P
+    void *f[2] = {nullptr, nullptr};   // deviation populations, 15 planes of P (storage type)
     int cur = 0;                       // f[cur] holds fhat^n
     int64_t step = 0;                  // host mirror of the step index
     long long *d_step = nullptr;       // device step index (Philox counter)
@@ -153,16 +188,16 @@ struct Sim {
 // ------------------------------------------------------------ launchers
 // lbm_kernels.cu
 cudaError_t prepare_lbm_kernels();
-cudaError_t launch_stream_collide(Sim &s, const float *src, float *dst, cudaStream_t st);
-cudaError_t launch_stream_collide_forced(Sim &s, const float *src, float *dst, int parity,
+cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st);
+cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st);
-cudaError_t launch_fill_rest(Sim &s, float *dst, cudaStream_t st);
-cudaError_t launch_from_f64(Sim &s, const double *f, float *dst, cudaStream_t st);
-cudaError_t launch_to_f64(Sim &s, const float *src, double *f, cudaStream_t st);
-cudaError_t launch_fields(Sim &s, const float *src, double *rho, double *u, double *p,
+cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st);
+cudaError_t launch_from_f64(Sim &s, const double *f, void *dst, cudaStream_t st);
+cudaError_t launch_to_f64(Sim &s, const void *src, double *f, cudaStream_t st);
+cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, double *p,
                           cudaStream_t st);
 // particle_kernels.cu
-cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t st);
+cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);

@@ -44,7 +44,7 @@
 namespace lbp {
 
 struct ParticleArgs {
-    const float *g;  // deviation populations fhat^{n-1}
+    const void *g;   // deviation populations fhat^{n-1} (storage type of the handle)
     int nx, ny, nz;
     long long P;
     long long N;
@@ -69,7 +69,9 @@ __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >
 
 constexpr int PB = 32;  // particles per block of k_particles
 
+template <typename St>
 __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
+    const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[PB][3];
     __shared__ float s_u[PB][8][3];
     __shared__ long long s_fix[PB][3];
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         for (int a = 1; a < Q; ++a) {
             const long long src = (long long)a * A.P +
                                   ((long long)zs[ez(a) + 1] * ny + ys[ey(a) + 1]) * nx + xs[ex(a) + 1];
-            const float gv = __ldg(A.g + src);
+            const float gv = St::load(G + src, a);
             if (ex(a)) sx += ex(a) > 0 ? gv : -gv;
             if (ey(a)) sy += ey(a) > 0 ? gv : -gv;
             if (ez(a)) sz += ez(a) > 0 ? gv : -gv;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
     }
 }
 
-cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t st) {
+cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st) {
     if (s.np == 0) return cudaSuccess;
     ParticleArgs A;
     A.g = src;
@@ -360,7 +362,11 @@ cudaError_t launch_particles(Sim &s, const float *src, int parity, cudaStream_t 
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
     const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
-    k_particles<<<grid, 8 * PB, 0, st>>>(A);
+    switch (s.precision) {
+        case LBP_BF16: k_particles<StoreBF16><<<grid, 8 * PB, 0, st>>>(A); break;
+        case LBP_F16: k_particles<StoreF16><<<grid, 8 * PB, 0, st>>>(A); break;
+        default: k_particles<StoreF32><<<grid, 8 * PB, 0, st>>>(A); break;
+    }
     return cudaGetLastError();
 }
 

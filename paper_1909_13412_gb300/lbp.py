@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbp.so")
 
 LBP_OK, LBP_EINVAL, LBP_ENOMEM, LBP_ECUDA, LBP_ETIMEOUT, LBP_ENAN, LBP_ESTATE, LBP_ERANGE = range(8)
-LBP_F32 = 0
+LBP_F32, LBP_BF16, LBP_F16 = 0, 1, 2
 LBP_STOKESLET, LBP_POINTWISE, LBP_BROWNIAN = 0, 1, 2
 Q = 15
 
