@@ -98,94 +98,124 @@ __device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int n
     return n;
 }
 
-template <int BX, typename St>
+// Each block serves R rows (consecutive in y) of one SEG-node x-segment: a
+// thread issues the 15 R loads of its R nodes before any arithmetic.  R = 2
+// for the 2-byte storage types, whose 15 loads per node alone keep too few
+// bytes in flight to saturate HBM; R = 1 for FP32.
+template <int BX, typename St, int R>
 __global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, int nx, int ny, int nz,
                                                        float omega, int nchunks, long long *bump) {
-    const unsigned item = blockIdx.x;
-    const unsigned row = item / (unsigned)nchunks;
-    const int chunk = (int)(item - row * (unsigned)nchunks);
+    const unsigned nrows = (unsigned)ny * (unsigned)nz;
+    const unsigned grp = blockIdx.x / (unsigned)nchunks;
+    const int chunk = (int)(blockIdx.x - grp * (unsigned)nchunks);
     const int x = chunk * BX + threadIdx.x;
-    if (item == 0 && threadIdx.x == 0) *bump += 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     if (x >= nx) return;
-    const NodeIdx n = node_index(x, row, nx, ny, nz);
-    float g[Q];
+    NodeIdx n[R];
+    float g[R][Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a)
-        g[a] = St::load(pl.s[a] + (n.d + n.ox[ex(a) + 1] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]), a);
-    collide_store<St>(g, pl, n.d, omega, 0.f, 0.f, 0.f);
+    for (int h = 0; h < R; ++h) {
+        const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
+        n[h] = node_index(x, row, nx, ny, nz);
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
+                                          n[h].oz[ez(a) + 1]), a);
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, omega, 0.f, 0.f, 0.f);
+}
+
+// Sum, exactly in 64-bit fixed point, the record entries whose x is this
+// lane's x; rw is this lane's word of the 256-byte record (see lbp_internal.cuh).
+__device__ __forceinline__ void record_sum(unsigned long long rw, int cnt, int x, long long &a0,
+                                           long long &a1, long long &a2) {
+    const int used = cnt < REC_SLOTS ? cnt : REC_SLOTS;
+    for (int sl = 0; sl < used; ++sl) {
+        const unsigned long long xw2 = __shfl_sync(0xffffffffu, rw, REC_X0 + (sl >> 1));
+        const int xs = (int)(unsigned)(xw2 >> (32 * (sl & 1)));
+        const long long v0 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl);
+        const long long v1 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 1);
+        const long long v2 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 2);
+        if (xs == x) {
+            a0 += v0;
+            a1 += v1;
+            a2 += v2;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // The same pass with the body force of Eqs. 18-19 (particles present).
-// Each block is one SEG-node segment of a row and owns one force record
-// (lbp_internal.cuh) filled by this step's particle kernel.  Every warp loads
-// the 256-byte record -- one 8-byte word per lane -- together with its
-// population loads (its address depends only on the block index, so no load
+// Every SEG-node segment of a row owns one force record (lbp_internal.cuh)
+// filled by this step's particle kernel.  Every warp loads the 256-byte
+// record of each of its rows -- one 8-byte word per lane -- together with its
+// population loads (the address depends only on the block index, so no load
 // waits on another), then each lane sums, exactly in 64-bit fixed point, the
 // entries whose x is its own and adds 3 w_a F.e_a to its post-collision
-// populations.  If the record overflowed (count > REC_SLOTS) the particle
-// kernel put the shares that did not fit into the dense per-node
-// accumulator: the lanes of that (rare) segment also read and clear their
-// node's accumulator and add it to the record sum -- still an exact integer
-// sum of all the node's shares.  The block clears the count of its record of
-// the previous step, which the next step's particle kernel refills.
+// populations.  If a record overflowed (count > REC_SLOTS) the particle kernel
+// put the shares that did not fit into the dense per-node accumulator: the
+// lanes of that (rare) segment also read and clear their node's accumulator
+// and add it to the record sum -- still an exact integer sum of all the node's
+// shares.  The block clears the counts of its rows' records of the previous
+// step, which the next step's particle kernel refills.
 // ---------------------------------------------------------------------------
-template <int BX, typename St>
+template <int BX, typename St, int R>
 __global__ void __launch_bounds__(BX) k_stream_collide_forced(
     Planes<St> pl, int nx, int ny, int nz, float omega, int nchunks,
     const unsigned long long *__restrict__ rec_cur, unsigned long long *rec_prev,
     unsigned long long *fq, long long *bump) {
     static_assert(BX == SEG, "one block per force-record segment");
-    const unsigned item = blockIdx.x;
+    const unsigned nrows = (unsigned)ny * (unsigned)nz;
     const int lane = threadIdx.x & 31;
-    const unsigned row = item / (unsigned)nchunks;
-    const int chunk = (int)(item - row * (unsigned)nchunks);
-    if (item == 0 && threadIdx.x == 0) *bump += 1;
-    if (threadIdx.x == 0) rec_prev[(size_t)item * REC_WORDS] = 0ull;
+    const unsigned grp = blockIdx.x / (unsigned)nchunks;
+    const int chunk = (int)(blockIdx.x - grp * (unsigned)nchunks);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+    if (threadIdx.x < R && grp * R + threadIdx.x < nrows)
+        rec_prev[((size_t)(grp * R + threadIdx.x) * nchunks + chunk) * REC_WORDS] = 0ull;
     const int xw = chunk * BX + (threadIdx.x & ~31);
     if (xw >= nx) return;  // whole warp past the end of the row
     const int x0 = xw + lane;
     const bool act = x0 < nx;
     const int x = act ? x0 : nx - 1;
-    const NodeIdx n = node_index(x, row, nx, ny, nz);
-    float g[Q];
+    NodeIdx n[R];
+    float g[R][Q];
+    unsigned long long rw[R];
 #pragma unroll
-    for (int a = 0; a < Q; ++a)
-        g[a] = St::load(pl.s[a] + (n.d + n.ox[ex(a) + 1] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]), a);
-    const unsigned long long rw = __ldg(rec_cur + (size_t)item * REC_WORDS + lane);
-    const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw, 0) & 0xffffffffull);
-    float F0 = 0.f, F1 = 0.f, F2 = 0.f;
-    if (cnt > 0) {
-        const int used = cnt < REC_SLOTS ? cnt : REC_SLOTS;
-        long long a0 = 0, a1 = 0, a2 = 0;
-        for (int sl = 0; sl < used; ++sl) {
-            const unsigned long long xw2 = __shfl_sync(0xffffffffu, rw, REC_X0 + (sl >> 1));
-            const int xs = (int)(unsigned)(xw2 >> (32 * (sl & 1)));
-            const long long v0 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl);
-            const long long v1 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 1);
-            const long long v2 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 2);
-            if (xs == x) {
-                a0 += v0;
-                a1 += v1;
-                a2 += v2;
-            }
-        }
-        if (cnt > REC_SLOTS && act) {
-            const long long N = (long long)nx * ny * nz;
-            a0 += (long long)fq[n.d];
-            a1 += (long long)fq[N + n.d];
-            a2 += (long long)fq[2 * N + n.d];
-            fq[n.d] = 0ull;
-            fq[N + n.d] = 0ull;
-            fq[2 * N + n.d] = 0ull;
-        }
-        const float inv = 1.3877787807814457e-17f;  // 2^-56
-        F0 = inv * __ll2float_rn(a0);
-        F1 = inv * __ll2float_rn(a1);
-        F2 = inv * __ll2float_rn(a2);
+    for (int h = 0; h < R; ++h) {
+        const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
+        n[h] = node_index(x, row, nx, ny, nz);
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
+                                          n[h].oz[ez(a) + 1]), a);
+        rw[h] = __ldg(rec_cur + ((size_t)row * nchunks + chunk) * REC_WORDS + lane);
     }
-    if (!act) return;
-    collide_store<St>(g, pl, n.d, omega, F0, F1, F2);
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw[h], 0) & 0xffffffffull);
+        float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+        if (cnt > 0 && grp * R + h < nrows) {
+            long long a0 = 0, a1 = 0, a2 = 0;
+            record_sum(rw[h], cnt, x, a0, a1, a2);
+            if (cnt > REC_SLOTS && act) {
+                const long long N = (long long)nx * ny * nz;
+                const int d = n[h].d;
+                a0 += (long long)fq[d];
+                a1 += (long long)fq[N + d];
+                a2 += (long long)fq[2 * N + d];
+                fq[d] = 0ull;
+                fq[N + d] = 0ull;
+                fq[2 * N + d] = 0ull;
+            }
+            const float inv = 1.3877787807814457e-17f;  // 2^-56
+            F0 = inv * __ll2float_rn(a0);
+            F1 = inv * __ll2float_rn(a1);
+            F2 = inv * __ll2float_rn(a2);
+        }
+        if (act && grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, omega, F0, F1, F2);
+    }
 }
 
 constexpr int SC_BX = SEG;
@@ -214,13 +244,18 @@ static cudaError_t by_storage(const Sim &s, F &&f) {
     }
 }
 
+// rows per block: 1 for FP32 storage, 2 for the 2-byte types
+template <typename St>
+constexpr int rows_per_block() { return sizeof(typename St::T) == 4 ? 1 : 2; }
+
 cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st) {
     constexpr int BX = SC_BX;
     const int nchunks = (s.nx + BX - 1) / BX;
-    const long long items = (long long)s.ny * s.nz * nchunks;
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
-        k_stream_collide<BX, St><<<(unsigned)items, BX, 0, st>>>(
+        constexpr int R = rows_per_block<St>();
+        const long long items = ((long long)s.ny * s.nz + R - 1) / R * nchunks;
+        k_stream_collide<BX, St, R><<<(unsigned)items, BX, 0, st>>>(
             planes_of<St>(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks, s.d_step);
         return cudaGetLastError();
     });
@@ -230,10 +265,11 @@ cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int
                                          cudaStream_t st) {
     constexpr int BX = SC_BX;
     const int nchunks = (s.nx + BX - 1) / BX;
-    const long long items = (long long)s.ny * s.nz * nchunks;
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
-        k_stream_collide_forced<BX, St><<<(unsigned)items, BX, 0, st>>>(
+        constexpr int R = rows_per_block<St>();
+        const long long items = ((long long)s.ny * s.nz + R - 1) / R * nchunks;
+        k_stream_collide_forced<BX, St, R><<<(unsigned)items, BX, 0, st>>>(
             planes_of<St>(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks,
             s.rec[parity], s.rec[parity ^ 1], s.fq, s.d_step);
         return cudaGetLastError();
