@@ -51,7 +51,28 @@ LAUNCHES_PER_STEP = 2  # particles, stream-collide (+2 VACF kernels every 64 ste
 
 def workload(name):
     return {"brownian_256": wl.BROWNIAN_256, "brownian_128": wl.BROWNIAN_128,
-            "brownian_64": wl.BROWNIAN_64, "profile_128": wl.PROFILE_128}[name]
+            "brownian_64": wl.BROWNIAN_64, "profile_128": wl.PROFILE_128,
+            "ensemble_68": wl.ENSEMBLE_68}[name]
+
+
+def make_handle(lbp, w, precision, seed, vacf_lag):
+    """A handle holding workload w: one box, or a batch of boxes for an ensemble
+    (per-particle VACF, one particle per replica)."""
+    if isinstance(w, wl.Ensemble):
+        h = lbp.lbp_create_batch(w.boxes, precision=PRECISION_CODE[precision])
+        for b in range(len(w.boxes)):
+            pb = w.particles(b)
+            lbp.lbp_particles_add_to(h, b, pb.r, pb.V, pb.M, pb.gamma, pb.R)
+        lbp.lbp_particles_set_params(h, kT=w.kT, seed=seed)
+        lbp.lbp_vacf_configure_ex(h, vacf_lag, 1)
+        return h
+    nz, ny, nx = w.shape_zyx
+    ps = w.particles()
+    h = lbp.lbp_create(nx, ny, nz, w.tau, precision=PRECISION_CODE[precision])
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=w.kT, seed=seed)
+    lbp.lbp_vacf_configure(h, vacf_lag)
+    return h
 
 
 def dist_env():
@@ -183,6 +204,9 @@ def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if isinstance(w, wl.Ensemble):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single-box workloads"}))
+        return 0
     import oracle
     ps = w.particles()
     o = oracle_setup(w, ps)
@@ -212,6 +236,13 @@ def run_reference(args, w):
 
 
 def config_of(w, world, vacf_lag=VACF_LAG, precision="f32"):
+    if isinstance(w, wl.Ensemble):
+        return {"workload": w.name, "boxes": [list(b) for b in w.boxes], "nodes_per_rank": w.nodes,
+                "particles_per_rank": w.n_particles, "kT": w.kT, "M": w.M, "gamma": w.gamma,
+                "coupling": "stokeslet", "storage": f"{precision} deviation",
+                "vacf_max_lag": vacf_lag, "vacf": "per particle (= per replica)",
+                "parallelism": f"replicas{world}",
+                "l2": "no flush: 2 x 2.6 GB population buffers per step exceed the 129 MB L2"}
     nz, ny, nx = w.shape_zyx
     return {"workload": w.name, "lattice": [nx, ny, nz], "nodes_per_rank": w.nodes,
             "particles_per_rank": w.n_particles, "tau": w.tau, "kT": w.kT, "M": w.M,
@@ -237,14 +268,11 @@ def run_gpu(args, w):
             dist.barrier()
         torch.cuda.synchronize()
 
-    ps = w.particles()
-    nz, ny, nx = w.shape_zyx
-
-    def make(precision):
-        h = lbp.lbp_create(nx, ny, nz, w.tau, precision=PRECISION_CODE[precision])
-        lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
-        lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise + rank)
-        lbp.lbp_vacf_configure(h, args.vacf_lag)
+    def make(precision, wk=w):
+        h = make_handle(lbp, wk, precision, wk.seed_noise + rank, args.vacf_lag)
+        # block shape of the lattice kernel, picked by timing (outside the timed region)
+        rows, tms = lbp.lbp_autotune(h, 10)
+        h.tuned = {"rows_per_block": rows, "ms_by_rows": dict(zip((1, 2, 4), tms))}
         return h
 
     def timed(h, steps, warmup, clocks=None):
@@ -268,6 +296,7 @@ def run_gpu(args, w):
         return ms, k3_ms / max(k3_n, 1), k3_n
 
     h = make(args.precision)
+    tuned = h.tuned
     clk = ClockSampler(local)
     ms, k3_one, k3_n = timed(h, args.steps, args.warmup, clk)
     ms_max, k3_avg_ms = max_over_ranks([ms, k3_one], "cuda", dist)
@@ -275,7 +304,7 @@ def run_gpu(args, w):
 
     # end to end through the C ABI with host buffers: per step the external
     # forces go host->device and positions + velocities come back
-    n = ps.n
+    n = w.n_particles
     fext = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
     r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     v_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
@@ -295,7 +324,7 @@ def run_gpu(args, w):
 
     # the other storage types on the same workload (shorter runs)
     variants = {}
-    if not args.no_variants:
+    if not args.no_variants and not isinstance(w, wl.Ensemble):
         for prec in ("f32", "bf16", "f16"):
             if prec == args.precision:
                 continue
@@ -309,7 +338,25 @@ def run_gpu(args, w):
                               "steps": vsteps, "ms_per_step": vms / vsteps,
                               "stream_collide_ms": vk3, "achieved_gbs": vach,
                               "frac": vach / measured_peaks()[0],
-                              "bytes_per_node": BYTES_PER_NODE[prec]}
+                              "bytes_per_node": BYTES_PER_NODE[prec], "autotune": hv.tuned}
+        # the batched uneven ensemble: one handle, one lattice launch per step
+        e = wl.ENSEMBLE_68
+        hb = make(args.precision, e)
+        bsteps = max(1, min(args.steps, 1000))
+        btuned = hb.tuned
+        bms, bk3, _ = timed(hb, bsteps, args.warmup)
+        bms, bk3 = max_over_ranks([bms, bk3], "cuda", dist)
+        lbp.lbp_destroy(hb)
+        bach = BYTES_PER_NODE[args.precision] * e.nodes / (bk3 * 1e-3) / 1e9
+        variants["batched"] = {"workload": e.name, "value": aggregate_mlups(world, e.nodes, bsteps, bms),
+                               "unit": "MLUPS", "boxes": len(e.boxes), "nodes": e.nodes,
+                               "particles": e.n_particles, "storage": f"{args.precision} deviation",
+                               "vacf": f"per particle (= per replica) to lag {args.vacf_lag}",
+                               "steps": bsteps, "ms_per_step": bms / bsteps,
+                               "stream_collide_ms": bk3, "achieved_gbs": bach,
+                               "frac": bach / measured_peaks()[0],
+                               "particle_updates_per_s": world * e.n_particles * bsteps / (bms * 1e-3),
+                               "autotune": btuned}
 
     if rank != 0:
         if dist:
@@ -317,7 +364,7 @@ def run_gpu(args, w):
         return 0
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_NODE[args.precision] * w.nodes / (k3_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic() if args.precision == "f32" else None
+    traffic = recorded_traffic() if (args.precision == "f32" and w is wl.BROWNIAN_256) else None
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -331,13 +378,14 @@ def run_gpu(args, w):
         "particle_updates_per_s": world * n * args.steps / (ms_max * 1e-3),
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": fext.nbytes,
                 "d2h_bytes_per_step": r_h.nbytes + v_h.nbytes, "steps": e2e_steps},
+        "autotune": tuned,
         "variants": variants,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps
-                        + 2 * sum(1 for n in range(args.warmup, args.warmup + args.steps) if (n + 1) % 64 == 0),
+                        + (1 if isinstance(w, wl.Ensemble) else 2) * sum(1 for n in range(args.warmup, args.warmup + args.steps) if (n + 1) % 64 == 0),
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, ps)
+    if not args.no_cpu_baseline and not isinstance(w, wl.Ensemble):
+        line["cpu_baseline"] = cpu_baseline(w, w.particles())
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -110,6 +110,20 @@ typedef struct lbp_sim lbp_sim;
  * Section 2.2 (Eqs. 12-20).                                                    */
 lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out);
 
+/* Batched ensemble: nrep independent periodic boxes of possibly different
+ * sizes and tau (one precision for all), stepped together by the same kernel
+ * launches (each launch covers every box).  Populations and fields of all
+ * boxes are concatenated node-wise: box r occupies global nodes
+ * [node_offset_r, node_offset_r + nx_r ny_r nz_r) of every array exchanged
+ * through this ABI (see lbp_replica_info).  1 <= nrep <= 256; lbp_create is
+ * the case nrep = 1.  Section 3 averages the VACF over independent particles;
+ * the boxes are how such an ensemble is run at once.                           */
+lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *stream, lbp_sim **out);
+
+/* Box `replica` of a batch: dims = (nx, ny, nz), tau, first global node.     */
+lbp_status lbp_replica_info(lbp_sim *sim, int replica, int *dims, double *tau, int64_t *node_offset);
+lbp_status lbp_replica_count(lbp_sim *sim, int *nrep);
+
 /* Free every device resource of the handle.  NULL is accepted.               */
 lbp_status lbp_destroy(lbp_sim *sim);
 
@@ -131,6 +145,13 @@ lbp_status lbp_read_fields(lbp_sim *sim, double *rho, double *u, double *p, int 
 lbp_status lbp_particles_add(lbp_sim *sim, int n, const double *r, const double *v,
                              const double *mass, const double *gamma, const double *radius,
                              int on_device);
+
+/* lbp_particles_add for the box `replica` of a batch (positions in that box's
+ * own coordinates); lbp_particles_add adds to box 0.  Particle ids stay global
+ * (insertion order over all boxes).                                          */
+lbp_status lbp_particles_add_to(lbp_sim *sim, int replica, int n, const double *r, const double *v,
+                                const double *mass, const double *gamma, const double *radius,
+                                int on_device);
 
 /* Coupling parameters for all particles (Sections 2.1; Eqs. 4-8).            */
 lbp_status lbp_particles_set_params(lbp_sim *sim, const lbp_particle_params *params);
@@ -174,6 +195,18 @@ lbp_status lbp_get_step_index(lbp_sim *sim, int64_t *step);
 lbp_status lbp_vacf_configure(lbp_sim *sim, int max_lag);
 lbp_status lbp_vacf_read(lbp_sim *sim, double *csum, int64_t *counts, int on_device);
 
+/* The same estimator kept per particle, for ensembles whose particles are not
+ * alike (a batch of boxes of different sizes or viscosities, Section 3's
+ * dependence of the VACF on L and nu): per_particle = 0 is lbp_vacf_configure;
+ * per_particle = 1 keeps csum[i][k] = sum over origins t0 of V_i(t0).V_i(t0+k)
+ * for each particle i (row-major [n_particles][max_lag + 1], FP64, products
+ * FP32), read with lbp_vacf_read_per_particle; counts[k] is then the number of
+ * origins t0, the same for every particle.  LBP_EINVAL if n_particles > 65535
+ * or n_particles * (max_lag + 1) > 2^28.  Adding particles or setting the step index turns the
+ * VACF off, as for lbp_vacf_configure.                                        */
+lbp_status lbp_vacf_configure_ex(lbp_sim *sim, int max_lag, int per_particle);
+lbp_status lbp_vacf_read_per_particle(lbp_sim *sim, double *csum, int64_t *counts, int on_device);
+
 /* Wait for the handle's queued work and report device-side errors: LBP_ENAN if
  * a particle state became non-finite, LBP_ERANGE on fixed-point overflow.     */
 lbp_status lbp_check(lbp_sim *sim);
@@ -182,8 +215,26 @@ lbp_status lbp_check(lbp_sim *sim);
  * out[0] = reaction-force shares that did not fit their row segment's record
  * and took the overflow path (both counts are implementation details of the
  * force accumulation; the results do not depend on them), out[1] = capacity of
- * a record in shares, out[2] = number of row segments.  n = entries of out.   */
+ * a record in shares, out[2] = number of row segments, out[3] = rows of 128
+ * nodes per lattice-kernel block (see lbp_autotune).  n = entries of out.    */
 lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
+
+/* Block-shape autotuner of the fused stream-collide kernel.  Times the kernel
+ * this handle's steps launch (with the particle coupling if it has particles)
+ * on its own lattice for each candidate shape -- 1, 2 or 4 rows of 128 nodes
+ * per block of 128 threads -- as `launches` back-to-back launches (1..1000)
+ * after two warm-up launches, twice, and keeps the shape with the smallest
+ * mean launch time for all later steps.  rows (optional) receives the chosen
+ * rows per block; ms (optional, 3 doubles) the mean launch times in ms for
+ * 1, 2 and 4 rows.  The simulation state is unchanged: the launches read the
+ * current populations, write only the buffer the next step overwrites, see an
+ * all-zero copy of the force records and bump a scratch step counter.
+ * Synchronous.  The default before any call: 1 row for LBP_F32, 2 otherwise. */
+lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, double *ms);
+
+/* Fix the rows per block by hand (1, 2 or 4; else LBP_EINVAL).  Results do
+ * not depend on it: each node's arithmetic is the same for every shape.     */
+lbp_status lbp_set_block_rows(lbp_sim *sim, int rows);
 
 /* Use CUDA graphs for lbp_step (default 1).                                  */
 lbp_status lbp_set_use_graphs(lbp_sim *sim, int enable);

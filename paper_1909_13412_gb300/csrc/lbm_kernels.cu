@@ -12,6 +12,10 @@
 // populations.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include <cstring>
+
 #include "lbp_internal.cuh"
 
 namespace lbp {
@@ -98,25 +102,32 @@ __device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int n
     return n;
 }
 
-// Each block serves R rows (consecutive in y) of one SEG-node x-segment: a
-// thread issues the 15 R loads of its R nodes before any arithmetic.  R = 2
-// for the 2-byte storage types, whose 15 loads per node alone keep too few
-// bytes in flight to saturate HBM; R = 1 for FP32.
-template <int BX, typename St, int R>
-__global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, int nx, int ny, int nz,
-                                                       float omega, int nchunks, long long *bump) {
+// Each block serves R rows (consecutive in y) of one SEG-node x-segment of one
+// replica box: a thread issues the 15 R loads of its R nodes before any
+// arithmetic.  R = 2 for the 2-byte storage types, whose 15 loads per node
+// alone keep too few bytes in flight; R = 1 for FP32.  The block finds its box
+// in the replica table (a kernel parameter; one entry for a single box).
+template <int BX, typename St, int R, int MAXR>
+__global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, const RepTable<MAXR> rt,
+                                                       long long *bump) {
+    const int r = find_block_rep(rt, blockIdx.x);
+    const Rep &rp = rt.rep[r];
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
     const unsigned nrows = (unsigned)ny * (unsigned)nz;
-    const unsigned grp = blockIdx.x / (unsigned)nchunks;
-    const int chunk = (int)(blockIdx.x - grp * (unsigned)nchunks);
+    const unsigned item = blockIdx.x - rt.item_off[r];
+    const unsigned grp = item / (unsigned)nchunks;
+    const int chunk = (int)(item - grp * (unsigned)nchunks);
     const int x = chunk * BX + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     if (x >= nx) return;
+    const int base = (int)rp.node_off;
     NodeIdx n[R];
     float g[R][Q];
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
         n[h] = node_index(x, row, nx, ny, nz);
+        n[h].d += base;
 #pragma unroll
         for (int a = 0; a < Q; ++a)
             g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
@@ -124,7 +135,7 @@ __global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, int nx, in
     }
 #pragma unroll
     for (int h = 0; h < R; ++h)
-        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, omega, 0.f, 0.f, 0.f);
+        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, 0.f, 0.f, 0.f);
 }
 
 // Sum, exactly in 64-bit fixed point, the record entries whose x is this
@@ -161,24 +172,29 @@ __device__ __forceinline__ void record_sum(unsigned long long rw, int cnt, int x
 // shares.  The block clears the counts of its rows' records of the previous
 // step, which the next step's particle kernel refills.
 // ---------------------------------------------------------------------------
-template <int BX, typename St, int R>
+template <int BX, typename St, int R, int MAXR>
 __global__ void __launch_bounds__(BX) k_stream_collide_forced(
-    Planes<St> pl, int nx, int ny, int nz, float omega, int nchunks,
-    const unsigned long long *__restrict__ rec_cur, unsigned long long *rec_prev,
-    unsigned long long *fq, long long *bump) {
+    Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
     static_assert(BX == SEG, "one block per force-record segment");
+    const int r = find_block_rep(rt, blockIdx.x);
+    const Rep &rp = rt.rep[r];
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
     const unsigned nrows = (unsigned)ny * (unsigned)nz;
     const int lane = threadIdx.x & 31;
-    const unsigned grp = blockIdx.x / (unsigned)nchunks;
-    const int chunk = (int)(blockIdx.x - grp * (unsigned)nchunks);
+    const unsigned item = blockIdx.x - rt.item_off[r];
+    const unsigned grp = item / (unsigned)nchunks;
+    const int chunk = (int)(item - grp * (unsigned)nchunks);
+    const size_t seg0 = (size_t)rp.seg_off;
     if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     if (threadIdx.x < R && grp * R + threadIdx.x < nrows)
-        rec_prev[((size_t)(grp * R + threadIdx.x) * nchunks + chunk) * REC_WORDS] = 0ull;
+        rec_prev[(seg0 + (size_t)(grp * R + threadIdx.x) * nchunks + chunk) * REC_WORDS] = 0ull;
     const int xw = chunk * BX + (threadIdx.x & ~31);
     if (xw >= nx) return;  // whole warp past the end of the row
     const int x0 = xw + lane;
     const bool act = x0 < nx;
     const int x = act ? x0 : nx - 1;
+    const int base = (int)rp.node_off;
     NodeIdx n[R];
     float g[R][Q];
     unsigned long long rw[R];
@@ -186,11 +202,12 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
         n[h] = node_index(x, row, nx, ny, nz);
+        n[h].d += base;
 #pragma unroll
         for (int a = 0; a < Q; ++a)
             g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
                                           n[h].oz[ez(a) + 1]), a);
-        rw[h] = __ldg(rec_cur + ((size_t)row * nchunks + chunk) * REC_WORDS + lane);
+        rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
     }
 #pragma unroll
     for (int h = 0; h < R; ++h) {
@@ -200,21 +217,20 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
             long long a0 = 0, a1 = 0, a2 = 0;
             record_sum(rw[h], cnt, x, a0, a1, a2);
             if (cnt > REC_SLOTS && act) {
-                const long long N = (long long)nx * ny * nz;
                 const int d = n[h].d;
                 a0 += (long long)fq[d];
-                a1 += (long long)fq[N + d];
-                a2 += (long long)fq[2 * N + d];
+                a1 += (long long)fq[Ntot + d];
+                a2 += (long long)fq[2 * Ntot + d];
                 fq[d] = 0ull;
-                fq[N + d] = 0ull;
-                fq[2 * N + d] = 0ull;
+                fq[Ntot + d] = 0ull;
+                fq[2 * Ntot + d] = 0ull;
             }
             const float inv = 1.3877787807814457e-17f;  // 2^-56
             F0 = inv * __ll2float_rn(a0);
             F1 = inv * __ll2float_rn(a1);
             F2 = inv * __ll2float_rn(a2);
         }
-        if (act && grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, omega, F0, F1, F2);
+        if (act && grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, F0, F1, F2);
     }
 }
 
@@ -234,7 +250,7 @@ static Planes<St> planes_of(const Sim &s, const void *src, void *dst) {
     return pl;
 }
 
-// Run F<StoreX>() for the handle's storage type.
+// Run f(StoreX{}) for the handle's storage type.
 template <typename F>
 static cudaError_t by_storage(const Sim &s, F &&f) {
     switch (s.precision) {
@@ -244,36 +260,88 @@ static cudaError_t by_storage(const Sim &s, F &&f) {
     }
 }
 
-// rows per block: 1 for FP32 storage, 2 for the 2-byte types
-template <typename St>
-constexpr int rows_per_block() { return sizeof(typename St::T) == 4 ? 1 : 2; }
+// Rows of SEG nodes per block: the default is 1 for FP32 storage and 2 for
+// the 2-byte types (more independent loads in flight per thread where each
+// load is half as wide); lbp_autotune picks among 1, 2 and 4 by timing.
+int default_rows_per_block(int precision) { return precision == LBP_F32 ? 1 : 2; }
 
-cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st) {
+template <typename F>
+static cudaError_t by_rows(int R, F &&f) {
+    switch (R) {
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        default: return f(std::integral_constant<int, 1>{});
+    }
+}
+
+// Replica table for a launch whose blocks cover R rows of SEG nodes.
+template <int MAXR>
+static RepTable<MAXR> rep_table(const Sim &s, int R) {
+    RepTable<MAXR> t;
+    memset(&t, 0, sizeof(t));
+    t.nrep = s.nrep;
+    unsigned off = 0;
+    for (int r = 0; r < s.nrep; ++r) {
+        t.rep[r] = s.reps[r];
+        t.item_off[r] = off;
+        const unsigned rows = (unsigned)s.reps[r].ny * (unsigned)s.reps[r].nz;
+        off += (rows + R - 1) / R * (unsigned)s.reps[r].nchunks;
+    }
+    t.item_off[s.nrep] = off;
+    return t;
+}
+
+// Run f(RepTable<1 or MAX_BATCH>) for a single box or a batch.
+template <typename F>
+static cudaError_t by_batch(const Sim &s, int R, F &&f) {
+    if (s.nrep == 1) return f(rep_table<1>(s, R));
+    return f(rep_table<MAX_BATCH>(s, R));
+}
+
+cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
+                                      int rows, cudaStream_t st) {
     constexpr int BX = SC_BX;
-    const int nchunks = (s.nx + BX - 1) / BX;
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
-        constexpr int R = rows_per_block<St>();
-        const long long items = ((long long)s.ny * s.nz + R - 1) / R * nchunks;
-        k_stream_collide<BX, St, R><<<(unsigned)items, BX, 0, st>>>(
-            planes_of<St>(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks, s.d_step);
-        return cudaGetLastError();
+        return by_rows(rows, [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            return by_batch(s, R, [&](const auto &rt) {
+                constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
+                k_stream_collide<BX, St, R, MAXR><<<rt.item_off[rt.nrep], BX, 0, st>>>(
+                    planes_of<St>(s, src, dst), rt, bump);
+                return cudaGetLastError();
+            });
+        });
+    });
+}
+
+cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st) {
+    return launch_stream_collide_cfg(s, src, dst, s.d_step, s.rows, st);
+}
+
+cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
+                                             const unsigned long long *rec_cur,
+                                             unsigned long long *rec_prev, long long *bump, int rows,
+                                             cudaStream_t st) {
+    constexpr int BX = SC_BX;
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        return by_rows(rows, [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            return by_batch(s, R, [&](const auto &rt) {
+                constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
+                k_stream_collide_forced<BX, St, R, MAXR><<<rt.item_off[rt.nrep], BX, 0, st>>>(
+                    planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                return cudaGetLastError();
+            });
+        });
     });
 }
 
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st) {
-    constexpr int BX = SC_BX;
-    const int nchunks = (s.nx + BX - 1) / BX;
-    return by_storage(s, [&](auto tag) {
-        using St = decltype(tag);
-        constexpr int R = rows_per_block<St>();
-        const long long items = ((long long)s.ny * s.nz + R - 1) / R * nchunks;
-        k_stream_collide_forced<BX, St, R><<<(unsigned)items, BX, 0, st>>>(
-            planes_of<St>(s, src, dst), s.nx, s.ny, s.nz, (float)(1.0 / s.tau), nchunks,
-            s.rec[parity], s.rec[parity ^ 1], s.fq, s.d_step);
-        return cudaGetLastError();
-    });
+    return launch_stream_collide_forced_cfg(s, src, dst, s.rec[parity], s.rec[parity ^ 1], s.d_step,
+                                            s.rows, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,14 +405,16 @@ cudaError_t launch_to_f64(Sim &s, const void *src, double *f, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Moments of the streamed populations (Eqs. 12-13) and p = rho~/3, in FP64.
 // ---------------------------------------------------------------------------
-template <typename St>
+template <typename St, int MAXR>
 __global__ void k_fields(const typename St::T *__restrict__ src, double *rho, double *u, double *p,
-                         int nx, int ny, int nz, long long P) {
-    const long long N = (long long)nx * ny * nz;
+                         const RepTable<MAXR> rt, long long N, long long P) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx);
-        const long long yz = i / nx;
+        const Rep &rp = rt.rep[find_node_rep(rt, i)];
+        const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
+        const long long li = i - rp.node_off;
+        const int x = (int)(li % nx);
+        const long long yz = li / nx;
         const int y = (int)(yz % ny);
         const int z = (int)(yz / ny);
         double drho = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
@@ -354,8 +424,8 @@ __global__ void k_fields(const typename St::T *__restrict__ src, double *rho, do
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
             zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-            const double g =
-                (double)St::load(src + (long long)a * P + ((long long)zs * ny + ys) * nx + xs, a);
+            const long long sidx = rp.node_off + ((long long)zs * ny + ys) * nx + xs;
+            const double g = (double)St::load(src + (long long)a * P + sidx, a);
             drho += g;
             ux += ex(a) * g;
             uy += ey(a) * g;
@@ -375,9 +445,12 @@ cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, doubl
                           cudaStream_t st) {
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
-        k_fields<St><<<grid_for(s.N, 256, s.num_sms), 256, 0, st>>>(
-            static_cast<const typename St::T *>(src), rho, u, p, s.nx, s.ny, s.nz, s.P);
-        return cudaGetLastError();
+        return by_batch(s, 1, [&](const auto &rt) {
+            constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
+            k_fields<St, MAXR><<<grid_for(s.N, 256, s.num_sms), 256, 0, st>>>(
+                static_cast<const typename St::T *>(src), rho, u, p, rt, s.N, s.P);
+            return cudaGetLastError();
+        });
     });
 }
 

@@ -12,6 +12,7 @@
 // and replayed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -25,6 +26,7 @@ using namespace lbp;
 
 struct lbp_sim : public lbp::Sim {
     std::vector<double> h_gamma, h_radius;  // host copies for parameter updates
+    std::vector<int> h_prep;                // replica of each particle
 };
 
 namespace {
@@ -193,25 +195,59 @@ const char *lbp_last_error(void) { return g_err.c_str(); }
 
 lbp_status lbp_create(const lbp_lattice_desc *desc, void *stream, lbp_sim **out) {
     if (!desc || !out) return fail(LBP_EINVAL, "lbp_create: null argument");
+    return lbp_create_batch(desc, 1, stream, out);
+}
+
+lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *stream, lbp_sim **out) {
+    if (!descs || !out) return fail(LBP_EINVAL, "lbp_create: null argument");
     *out = nullptr;
-    if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
-        return fail(LBP_EINVAL, "lbp_create: box sizes must be >= 1 (got %d %d %d)", desc->nx,
-                    desc->ny, desc->nz);
-    const long long N = (long long)desc->nx * desc->ny * desc->nz;
-    if (N > 2147483647ll) return fail(LBP_EINVAL, "lbp_create: nx*ny*nz = %lld exceeds 2^31-1", N);
-    if (!(desc->tau > 0.5) || !std::isfinite(desc->tau))
-        return fail(LBP_EINVAL, "lbp_create: tau must be finite and > 1/2 (nu = (tau-1/2)/3 > 0)");
-    if (desc->precision != LBP_F32 && desc->precision != LBP_BF16 && desc->precision != LBP_F16)
-        return fail(LBP_EINVAL, "lbp_create: unsupported precision %d", desc->precision);
+    if (nrep < 1 || nrep > MAX_BATCH)
+        return fail(LBP_EINVAL, "lbp_create_batch: nrep must be in [1, %d] (got %d)", MAX_BATCH, nrep);
+    long long N = 0, nseg = 0;
+    for (int r = 0; r < nrep; ++r) {
+        const lbp_lattice_desc *desc = descs + r;
+        if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
+            return fail(LBP_EINVAL, "lbp_create: box %d sizes must be >= 1 (got %d %d %d)", r,
+                        desc->nx, desc->ny, desc->nz);
+        if (!(desc->tau > 0.5) || !std::isfinite(desc->tau))
+            return fail(LBP_EINVAL, "lbp_create: box %d: tau must be finite and > 1/2 (nu = (tau-1/2)/3 > 0)", r);
+        if (desc->precision != LBP_F32 && desc->precision != LBP_BF16 && desc->precision != LBP_F16)
+            return fail(LBP_EINVAL, "lbp_create: unsupported precision %d", desc->precision);
+        if (desc->precision != descs[0].precision)
+            return fail(LBP_EINVAL, "lbp_create_batch: all boxes must share one precision");
+        N += (long long)desc->nx * desc->ny * desc->nz;
+        nseg += (long long)desc->ny * desc->nz * ((desc->nx + SEG - 1) / SEG);
+        if (N > 2147483647ll)
+            return fail(LBP_EINVAL, "lbp_create: %lld nodes in total exceed 2^31-1", N);
+    }
 
     lbp_sim *s = new lbp_sim();
-    s->nx = desc->nx;
-    s->ny = desc->ny;
-    s->nz = desc->nz;
+    s->nrep = nrep;
+    long long noff = 0, soff = 0;
+    for (int r = 0; r < nrep; ++r) {
+        const lbp_lattice_desc &d = descs[r];
+        Rep &rp = s->reps[r];
+        rp.nx = d.nx;
+        rp.ny = d.ny;
+        rp.nz = d.nz;
+        rp.nchunks = (d.nx + SEG - 1) / SEG;
+        rp.node_off = noff;
+        rp.seg_off = soff;
+        rp.omega = (float)(1.0 / d.tau);
+        rp.pad = 0;
+        s->taus[r] = d.tau;
+        noff += (long long)d.nx * d.ny * d.nz;
+        soff += (long long)d.ny * d.nz * rp.nchunks;
+    }
+    s->nx = descs[0].nx;
+    s->ny = descs[0].ny;
+    s->nz = descs[0].nz;
     s->N = N;
     s->P = (N + 63) / 64 * 64;
-    s->tau = desc->tau;
-    s->precision = desc->precision;
+    s->nseg = nseg;
+    s->tau = descs[0].tau;
+    s->precision = descs[0].precision;
+    s->rows = default_rows_per_block(s->precision);
     s->user = (cudaStream_t)stream;
     s->sqrt3 = std::sqrt(3.0);
     auto bail = [&](lbp_status st) {
@@ -265,7 +301,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
-                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->fq, s->rec[0],
+                    s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
     for (void *b : bufs)
@@ -348,7 +384,15 @@ static lbp_status fetch_host(lbp_sim *s, std::vector<double> &dst, const double 
 lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v,
                              const double *mass, const double *gamma, const double *radius,
                              int on_device) {
+    return lbp_particles_add_to(s, 0, n, r, v, mass, gamma, radius, on_device);
+}
+
+lbp_status lbp_particles_add_to(lbp_sim *s, int replica, int n, const double *r, const double *v,
+                                const double *mass, const double *gamma, const double *radius,
+                                int on_device) {
     CHECK_SIM(s);
+    if (replica < 0 || replica >= s->nrep)
+        return fail(LBP_EINVAL, "lbp_particles_add: replica %d outside [0, %d)", replica, s->nrep);
     if (n < 0) return fail(LBP_EINVAL, "lbp_particles_add: n < 0");
     if (n == 0) return LBP_OK;
     if (!r || !v || !mass || !gamma)
@@ -364,8 +408,8 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
     TRY(fetch_host(s, hm, mass, n, on_device));
     TRY(fetch_host(s, hg, gamma, n, on_device));
     if (radius) TRY(fetch_host(s, hR, radius, n, on_device));
-    const int L[3] = {s->nx, s->ny, s->nz};
-    const double nu = nu_of(s->tau);
+    const int L[3] = {s->reps[replica].nx, s->reps[replica].ny, s->reps[replica].nz};
+    const double nu = nu_of(s->taus[replica]);
     for (int i = 0; i < n; ++i) {
         for (int k = 0; k < 3; ++k) {
             const double x = hr[3 * i + k];
@@ -424,11 +468,18 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
             cudaFree(s->pinned);
         }
         s->pinned = np8;
+        int *nrp = nullptr;
+        TRY(dalloc(&nrp, (size_t)cap));
+        CK(cudaMemset(nrp, 0, sizeof(int) * cap));
+        if (s->prep) {
+            CK(cudaMemcpy(nrp, s->prep, sizeof(int) * s->np, cudaMemcpyDeviceToDevice));
+            cudaFree(s->prep);
+        }
+        s->prep = nrp;
 
         // force records (two step parities) and the dense overflow
         // accumulator (3 x 64-bit per node), allocated with the first particle
         if (!s->fq) {
-            s->nseg = (long long)s->ny * s->nz * ((s->nx + SEG - 1) / SEG);
             TRY(dalloc(&s->fq, 3 * (size_t)s->N));
             CK(cudaMemset(s->fq, 0, sizeof(unsigned long long) * 3 * (size_t)s->N));
             for (int q = 0; q < 2; ++q) {
@@ -457,13 +508,38 @@ lbp_status lbp_particles_add(lbp_sim *s, int n, const double *r, const double *v
     CK(cudaMemcpy(s->gamma + s->np, hg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->radius + s->np, hR.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->sig + s->np, sg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    std::vector<int> hp(n, replica);
+    CK(cudaMemcpy(s->prep + s->np, hp.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     s->h_gamma.insert(s->h_gamma.end(), hg.begin(), hg.end());
     s->h_radius.insert(s->h_radius.end(), hR.begin(), hR.end());
+    s->h_prep.insert(s->h_prep.end(), hp.begin(), hp.end());
     s->np = np_new;
     // the VACF ring is laid out per particle count: adding particles turns it off
     s->vacf_lag = -1;
     drop_graphs(s);
     return leave(s);
+}
+
+lbp_status lbp_replica_info(lbp_sim *s, int replica, int *dims, double *tau, int64_t *node_offset) {
+    CHECK_SIM(s);
+    if (replica < 0 || replica >= s->nrep)
+        return fail(LBP_EINVAL, "lbp_replica_info: replica %d outside [0, %d)", replica, s->nrep);
+    const Rep &rp = s->reps[replica];
+    if (dims) {
+        dims[0] = rp.nx;
+        dims[1] = rp.ny;
+        dims[2] = rp.nz;
+    }
+    if (tau) *tau = s->taus[replica];
+    if (node_offset) *node_offset = rp.node_off;
+    return LBP_OK;
+}
+
+lbp_status lbp_replica_count(lbp_sim *s, int *nrep) {
+    CHECK_SIM(s);
+    if (!nrep) return fail(LBP_EINVAL, "lbp_replica_count: null nrep");
+    *nrep = s->nrep;
+    return LBP_OK;
 }
 
 lbp_status lbp_particles_count(lbp_sim *s, int *n) {
@@ -541,11 +617,13 @@ lbp_status lbp_particles_set_state(lbp_sim *s, const double *r, const double *v,
     if (r) {
         std::vector<double> hr;
         TRY(fetch_host(s, hr, r, 3 * (size_t)s->np, on_device));
-        const int L[3] = {s->nx, s->ny, s->nz};
         for (int i = 0; i < s->np; ++i)
-            for (int k = 0; k < 3; ++k)
+            for (int k = 0; k < 3; ++k) {
+                const Rep &rp = s->reps[s->h_prep[i]];
+                const int L[3] = {rp.nx, rp.ny, rp.nz};
                 if (!(hr[3 * i + k] >= 0.0) || !(hr[3 * i + k] < (double)L[k]))
                     return fail(LBP_EINVAL, "lbp_particles_set_state: r[%d][%d] outside the box", i, k);
+            }
     }
     if (v) {
         std::vector<double> hv;
@@ -650,6 +728,10 @@ lbp_status lbp_get_step_index(lbp_sim *s, int64_t *step) {
 }
 
 lbp_status lbp_vacf_configure(lbp_sim *s, int max_lag) {
+    return lbp_vacf_configure_ex(s, max_lag, 0);
+}
+
+lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     CHECK_SIM(s);
     if (max_lag < -1) return fail(LBP_EINVAL, "lbp_vacf_configure: max_lag < -1");
     TRY(enter(s));
@@ -673,31 +755,111 @@ lbp_status lbp_vacf_configure(lbp_sim *s, int max_lag) {
     s->vacf_cap = max_lag + B;
     s->vacf_nchunks = (int)((ncomp + vacf_chunk_components() - 1) / vacf_chunk_components());
     TRY(dalloc(&s->ring, (size_t)s->vacf_cap * ncomp));
-    TRY(dalloc(&s->vacf_sum, (size_t)max_lag + 1));
+    const size_t nsum = (per_particle ? (size_t)s->np : 1) * ((size_t)max_lag + 1);
+    if (per_particle && (nsum > ((size_t)1 << 28) || s->np > 65535))
+        return fail(LBP_EINVAL,
+                    "lbp_vacf_configure_ex: per particle needs n_particles <= 65535 and n_particles * (max_lag + 1) <= 2^28");
+    TRY(dalloc(&s->vacf_sum, nsum));
     TRY(dalloc(&s->vacf_cnt, (size_t)max_lag + 1));
     TRY(dalloc(&s->vacf_part, (size_t)s->vacf_nchunks * (max_lag + 1)));
-    CK(cudaMemsetAsync(s->vacf_sum, 0, sizeof(double) * (max_lag + 1), s->s0));
+    CK(cudaMemsetAsync(s->vacf_sum, 0, sizeof(double) * nsum, s->s0));
     CK(cudaMemsetAsync(s->vacf_cnt, 0, sizeof(long long) * (max_lag + 1), s->s0));
     long long hv[4] = {s->step, 0, 0, 0};
     CK(cudaMemcpyAsync(s->d_vacf, hv, sizeof(hv), cudaMemcpyHostToDevice, s->s0));
     CK(cudaStreamSynchronize(s->s0));
     s->vacf_lag = max_lag;
+    s->vacf_pp = per_particle ? 1 : 0;
     s->vacf_t0 = s->step;
     s->vacf_done_host = 0;
+    return leave(s);
+}
+
+static lbp_status vacf_read_impl(lbp_sim *s, double *csum, int64_t *counts, int on_device,
+                                 int nsets) {
+    TRY(enter(s));
+    CK(launch_vacf_block(*s, true, s->s0));
+    s->vacf_done_host = s->step - s->vacf_t0;
+    const size_t K1 = (size_t)s->vacf_lag + 1;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (csum) CK(cudaMemcpyAsync(csum, s->vacf_sum, sizeof(double) * K1 * (size_t)nsets, kind, s->s0));
+    if (counts) CK(cudaMemcpyAsync(counts, s->vacf_cnt, sizeof(long long) * K1, kind, s->s0));
+    if (!on_device) CK(cudaStreamSynchronize(s->s0));
     return leave(s);
 }
 
 lbp_status lbp_vacf_read(lbp_sim *s, double *csum, int64_t *counts, int on_device) {
     CHECK_SIM(s);
     if (s->vacf_lag < 0) return fail(LBP_ESTATE, "lbp_vacf_read: VACF not configured");
+    if (s->vacf_pp) return fail(LBP_ESTATE, "lbp_vacf_read: configured per particle; use lbp_vacf_read_per_particle");
+    return vacf_read_impl(s, csum, counts, on_device, 1);
+}
+
+lbp_status lbp_vacf_read_per_particle(lbp_sim *s, double *csum, int64_t *counts, int on_device) {
+    CHECK_SIM(s);
+    if (s->vacf_lag < 0 || !s->vacf_pp)
+        return fail(LBP_ESTATE, "lbp_vacf_read_per_particle: VACF not configured per particle");
+    return vacf_read_impl(s, csum, counts, on_device, s->np);
+}
+
+lbp_status lbp_set_block_rows(lbp_sim *s, int rows) {
+    CHECK_SIM(s);
+    if (rows != 1 && rows != 2 && rows != 4) return fail(LBP_EINVAL, "lbp_set_block_rows: rows must be 1, 2 or 4");
     TRY(enter(s));
-    CK(launch_vacf_block(*s, true, s->s0));
-    s->vacf_done_host = s->step - s->vacf_t0;
-    const size_t K1 = (size_t)s->vacf_lag + 1;
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (csum) CK(cudaMemcpyAsync(csum, s->vacf_sum, sizeof(double) * K1, kind, s->s0));
-    if (counts) CK(cudaMemcpyAsync(counts, s->vacf_cnt, sizeof(long long) * K1, kind, s->s0));
-    if (!on_device) CK(cudaStreamSynchronize(s->s0));
+    CK(cudaStreamSynchronize(s->s0));
+    s->rows = rows;
+    drop_graphs(s);
+    return leave(s);
+}
+
+lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, double *ms) {
+    CHECK_SIM(s);
+    if (launches < 1 || launches > 1000) return fail(LBP_EINVAL, "lbp_autotune: launches must be in [1, 1000]");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    static const int cand[3] = {1, 2, 4};
+    // scratch: two all-zero force-record copies (no force anywhere, so the
+    // dense overflow accumulator is never read) and a step counter to bump
+    const size_t rec_words = s->np > 0 ? (size_t)s->nseg * REC_WORDS : 0;
+    unsigned long long *scr = nullptr;
+    TRY(dalloc(&scr, 2 * rec_words + 1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double t[3] = {0.0, 0.0, 0.0};
+    cudaError_t e = cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (2 * rec_words + 1), s->s0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    long long *bump = reinterpret_cast<long long *>(scr + 2 * rec_words);
+    // reads the current populations, writes the other buffer, which the next
+    // step overwrites whole: the handle's state is unchanged
+    const void *src = s->f[s->cur];
+    void *dst = s->f[s->cur ^ 1];
+    auto one = [&](int R) {
+        return s->np > 0 ? launch_stream_collide_forced_cfg(*s, src, dst, scr, scr + rec_words, bump, R, s->s0)
+                         : launch_stream_collide_cfg(*s, src, dst, bump, R, s->s0);
+    };
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass)
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = one(cand[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s->s0);
+            for (int l = 0; l < launches && e == cudaSuccess; ++l) e = one(cand[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s->s0);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float el = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
+            const double per = (double)el / launches;
+            if (e == cudaSuccess) t[c] = pass == 0 ? per : std::min(t[c], per);
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(scr);
+    if (e != cudaSuccess) return fail(LBP_ECUDA, "lbp_autotune: %s", cudaGetErrorString(e));
+    int best = 0;
+    for (int c = 1; c < 3; ++c)
+        if (t[c] < t[best]) best = c;
+    s->rows = cand[best];
+    drop_graphs(s);
+    if (rows) *rows = s->rows;
+    if (ms)
+        for (int c = 0; c < 3; ++c) ms[c] = t[c];
     return leave(s);
 }
 
@@ -719,7 +881,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
     CHECK_SIM(s);
     if (n < 0 || (n > 0 && !out)) return fail(LBP_EINVAL, "lbp_diagnostics: bad output");
     CK(cudaStreamSynchronize(s->s0));
-    int64_t v[3] = {0, REC_SLOTS, s->nseg};
+    int64_t v[4] = {0, REC_SLOTS, s->nseg, s->rows};
     if (s->rec[0]) {
         // shares beyond the slots of the records of the last completed step
         std::vector<unsigned long long> words((size_t)s->nseg * REC_WORDS);
@@ -730,7 +892,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
             if (c > REC_SLOTS) v[0] += c - REC_SLOTS;
         }
     }
-    for (int i = 0; i < n && i < 3; ++i) out[i] = v[i];
+    for (int i = 0; i < n && i < 4; ++i) out[i] = v[i];
     return LBP_OK;
 }
 

@@ -117,13 +117,62 @@ __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned 
     }
 }
 
+// ------------------------------------------------------------ replicas
+// A handle holds one or more independent periodic boxes ("replicas", the
+// batched ensemble).  Their populations are concatenated node-wise in the same
+// 15 planes; every kernel gets the replica table by value (a kernel parameter,
+// so the per-block lookup reads the constant bank, not global memory).
+struct Rep {
+    int nx, ny, nz, nchunks;  // box and SEG-node segments per row
+    long long node_off;       // first global node of the box
+    long long seg_off;        // first global force-record segment
+    float omega;              // 1 / tau
+    int pad;
+};
+
+constexpr int MAX_BATCH = 256;
+
+template <int MAXR>
+struct RepTable {
+    int nrep;
+    unsigned item_off[MAXR + 1];  // first block of each box in the launch, and the total
+    Rep rep[MAXR];
+};
+
+// replica of a block / of a global node: last r with off[r] <= v (uniform per block)
+template <int MAXR>
+__device__ __forceinline__ int find_block_rep(const RepTable<MAXR> &t, unsigned b) {
+    if (MAXR == 1) return 0;
+    int lo = 0, hi = t.nrep - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.item_off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MAXR>
+__device__ __forceinline__ int find_node_rep(const RepTable<MAXR> &t, long long node) {
+    if (MAXR == 1) return 0;
+    int lo = 0, hi = t.nrep - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.rep[mid].node_off <= node) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // --------------------------------------------------------------- handle
 struct Sim {
-    int nx = 0, ny = 0, nz = 0;
-    int64_t N = 0;  // nodes
+    int nx = 0, ny = 0, nz = 0;  // box of replica 0
+    int64_t N = 0;  // nodes of all replicas
+    int nrep = 1;
+    Rep reps[MAX_BATCH] = {};
+    double taus[MAX_BATCH] = {};
     int64_t P = 0;  // plane stride (elements), N rounded up to 64
     double tau = 1.0;
     int precision = LBP_F32;
+    int rows = 1;  // rows of SEG nodes per lattice-kernel block (1, 2 or 4)
     int dev = 0;
     int num_sms = 0;
 
@@ -142,6 +191,7 @@ struct Sim {
     int np = 0, cap = 0;
     double *r = nullptr, *v = nullptr, *fh = nullptr, *fr = nullptr, *fext = nullptr;
     double *mass = nullptr, *inv_mass = nullptr, *gamma = nullptr, *radius = nullptr, *sig = nullptr;
+    int *prep = nullptr;  // replica of each particle
     unsigned char *pinned = nullptr;
     double kT = 0.0;
     unsigned long long seed = 0;
@@ -153,10 +203,11 @@ struct Sim {
     // the stream-collide block of an overflowed segment reads and clears
     unsigned long long *fq = nullptr;  // [3][N], allocated with the first particle
     unsigned long long *rec[2] = {nullptr, nullptr};  // [segments][REC_WORDS], by step parity
-    long long nseg = 0;                                // ny * nz * ceil(nx / SEG)
+    long long nseg = 0;                                // segments of all replicas
 
     // VACF
     int vacf_lag = -1;
+    int vacf_pp = 0;              // 1: sums per particle ([np][K + 1])
     int vacf_cap = 0;             // ring length in samples
     float *ring = nullptr;        // [vacf_cap][3 * cap]
     long long *d_vacf = nullptr;  // [0] t0 step, [1] samples correlated, [2] samples written,
@@ -189,6 +240,14 @@ struct Sim {
 // lbm_kernels.cu
 cudaError_t prepare_lbm_kernels();
 cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st);
+// the lattice kernels with an explicit step counter, force records and rows per block
+cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
+                                      int rows, cudaStream_t st);
+cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
+                                             const unsigned long long *rec_cur,
+                                             unsigned long long *rec_prev, long long *bump, int rows,
+                                             cudaStream_t st);
+int default_rows_per_block(int precision);
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st);
 cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st);

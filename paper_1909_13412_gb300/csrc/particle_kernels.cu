@@ -45,7 +45,7 @@ namespace lbp {
 
 struct ParticleArgs {
     const void *g;   // deviation populations fhat^{n-1} (storage type of the handle)
-    int nx, ny, nz;
+    const int *prep; // replica (box) of each particle
     long long P;
     long long N;
     double *r, *v, *fh, *fr;
@@ -57,7 +57,6 @@ struct ParticleArgs {
     double sqrt3;
     int mode, exclude_inside;
     unsigned long long *rec; // force records of this step's parity
-    int nchunks;             // segments per row
     unsigned long long *fq;  // [3][N] fixed-point overflow accumulator
     float *ring;
     int ring_cap;
@@ -69,10 +68,11 @@ __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >
 
 constexpr int PB = 32;  // particles per block of k_particles
 
-template <typename St>
-__global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
+template <typename St, int MAXR>
+__global__ void __launch_bounds__(256) k_particles(const ParticleArgs A, const RepTable<MAXR> rt) {
     const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[PB][3];
+    __shared__ int s_rep[PB];
     __shared__ float s_u[PB][8][3];
     __shared__ long long s_fix[PB][3];
     __shared__ long long s_frac[PB][3];
@@ -80,7 +80,6 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
     const int t = threadIdx.x, lane = t & 31;
     const int i0 = blockIdx.x * PB;
     const long long step = *A.d_step;
-    const int nx = A.nx, ny = A.ny, nz = A.nz;
     const int cap = A.cap;
     if (A.ring && blockIdx.x == 0 && t == 0) {
         const long long m = step - A.d_vacf[0];
@@ -110,6 +109,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         fe1 = A.fext[cap + ip];
         fe2 = A.fext[2 * cap + ip];
         pin = A.pinned[ip] != 0;
+        s_rep[lane] = MAXR == 1 ? 0 : A.prep[ip];
         const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
         q0 = r0 - b0;
         q1 = r1 - b1;
@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
     const int ij = i0 + j;
     const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
     int X = 0, Y = 0, Z = 0;
+    const Rep &rj = rt.rep[ij < A.np ? s_rep[j] : 0];
+    const int nx = rj.nx, ny = rj.ny, nz = rj.nz;
     if (ij < A.np) {
         X = wrapi(s_base[j][0] + c0, nx);
         Y = wrapi(s_base[j][1] + c1, ny);
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
         for (int a = 1; a < Q; ++a) {
-            const long long src = (long long)a * A.P +
+            const long long src = (long long)a * A.P + rj.node_off +
                                   ((long long)zs[ez(a) + 1] * ny + ys[ey(a) + 1]) * nx + xs[ex(a) + 1];
             const float gv = St::load(G + src, a);
             if (ex(a)) sx += ex(a) > 0 ? gv : -gv;
@@ -261,7 +263,8 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
         const double Vo[3] = {V0, V1, V2};
         const double ro[3] = {r0, r1, r2};
         const double fe[3] = {fe0, fe1, fe2};
-        const int L[3] = {nx, ny, nz};
+        const Rep &ri = rt.rep[MAXR == 1 ? 0 : s_rep[lane]];
+        const int L[3] = {ri.nx, ri.ny, ri.nz};
         double Vn[3] = {V0, V1, V2};
         bool bad = false;
 #pragma unroll
@@ -312,7 +315,8 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
             sh[k] = v;
         }
         const long long row = (long long)Z * ny + Y;
-        unsigned long long *rec = A.rec + (size_t)(row * A.nchunks + X / SEG) * REC_WORDS;
+        unsigned long long *rec =
+            A.rec + (size_t)(rj.seg_off + row * rj.nchunks + X / SEG) * REC_WORDS;
         const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
         if (slot < (unsigned)REC_SLOTS) {
             reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
             rec[REC_F0 + 3 * slot + 1] = (unsigned long long)sh[1];
             rec[REC_F0 + 3 * slot + 2] = (unsigned long long)sh[2];
         } else {
-            const long long node = row * nx + X;
+            const long long node = rj.node_off + row * nx + X;
             atomicAdd(A.fq + node, (unsigned long long)sh[0]);
             atomicAdd(A.fq + A.N + node, (unsigned long long)sh[1]);
             atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)sh[2]);
@@ -328,13 +332,21 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A) {
     }
 }
 
+template <int MAXR>
+static void launch_particles_t(const Sim &s, const ParticleArgs &A, const RepTable<MAXR> &t,
+                               unsigned grid, cudaStream_t st) {
+    switch (s.precision) {
+        case LBP_BF16: k_particles<StoreBF16, MAXR><<<grid, 8 * PB, 0, st>>>(A, t); break;
+        case LBP_F16: k_particles<StoreF16, MAXR><<<grid, 8 * PB, 0, st>>>(A, t); break;
+        default: k_particles<StoreF32, MAXR><<<grid, 8 * PB, 0, st>>>(A, t); break;
+    }
+}
+
 cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st) {
     if (s.np == 0) return cudaSuccess;
     ParticleArgs A;
     A.g = src;
-    A.nx = s.nx;
-    A.ny = s.ny;
-    A.nz = s.nz;
+    A.prep = s.prep;
     A.P = s.P;
     A.N = s.N;
     A.r = s.r;
@@ -356,16 +368,24 @@ cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t s
     A.exclude_inside = s.exclude_inside;
     A.fq = s.fq;
     A.rec = s.rec[parity];
-    A.nchunks = (s.nx + SEG - 1) / SEG;
     A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
     const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
-    switch (s.precision) {
-        case LBP_BF16: k_particles<StoreBF16><<<grid, 8 * PB, 0, st>>>(A); break;
-        case LBP_F16: k_particles<StoreF16><<<grid, 8 * PB, 0, st>>>(A); break;
-        default: k_particles<StoreF32><<<grid, 8 * PB, 0, st>>>(A); break;
+    if (s.nrep == 1) {
+        RepTable<1> t;
+        t.nrep = 1;
+        t.item_off[0] = 0;
+        t.item_off[1] = 0;
+        t.rep[0] = s.reps[0];
+        launch_particles_t(s, A, t, grid, st);
+    } else {
+        RepTable<MAX_BATCH> t;  // kernel parameter
+        t.nrep = s.nrep;
+        for (int r = 0; r <= s.nrep; ++r) t.item_off[r] = 0;
+        for (int r = 0; r < s.nrep; ++r) t.rep[r] = s.reps[r];
+        launch_particles_t(s, A, t, grid, st);
     }
     return cudaGetLastError();
 }

@@ -139,8 +139,59 @@ __global__ void __launch_bounds__(256) k_vacf_reduce(const VacfArgs A, int nchun
     }
 }
 
+// Per-particle sums: csum[i][k] += sum_{t in block} V_i(t).V_i(t - k), one
+// thread per (lag, particle), products FP32, block sum FP32 (at most 192
+// terms), running sums FP64.  The last block advances the samples done.
+__global__ void __launch_bounds__(256) k_vacf_pp(const VacfArgs A) {
+    long long tb, te;
+    if (!vacf_range(A, tb, te)) return;
+    const int i = blockIdx.y;
+    const int np = A.np;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= A.K; k += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (long long t = tb > k ? tb : k; t < te; ++t) {
+            const float *a = A.ring + (t % A.cap) * 3 * (long long)np;
+            const float *b = A.ring + ((t - k) % A.cap) * 3 * (long long)np;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc = fmaf(a[c * np + i], b[c * np + i], acc);
+        }
+        A.sum[(long long)i * (A.K + 1) + k] += (double)acc;
+        if (i == 0) {
+            const long long first = tb > k ? tb : (long long)k;
+            if (te > first) A.cnt[k] += te - first;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int d = atomicAdd(A.done, 1u);
+        if (d == gridDim.x * gridDim.y - 1) {
+            A.d_vacf[1] = te;
+            *A.done = 0u;
+            __threadfence();
+        }
+    }
+}
+
 cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st) {
     if (s.vacf_lag < 0 || s.np == 0) return cudaSuccess;
+    if (s.vacf_pp) {
+        VacfArgs A;
+        A.ring = s.ring;
+        A.cap = s.vacf_cap;
+        A.ncomp = 3 * s.np;
+        A.K = s.vacf_lag;
+        A.d_vacf = s.d_vacf;
+        A.flush = flush ? 1 : 0;
+        A.part = nullptr;
+        A.sum = s.vacf_sum;
+        A.cnt = s.vacf_cnt;
+        A.np = s.np;
+        A.done = reinterpret_cast<unsigned int *>(s.d_vacf + 3);
+        dim3 g((s.vacf_lag + 1 + 255) / 256, s.np);
+        k_vacf_pp<<<g, 256, 0, st>>>(A);
+        return cudaGetLastError();
+    }
     VacfArgs A;
     A.ring = s.ring;
     A.cap = s.vacf_cap;

@@ -46,6 +46,10 @@ _vp = C.c_void_p
 _SIGS = {
     "lbp_create": [C.POINTER(lbp_lattice_desc), _vp, C.POINTER(_vp)],
     "lbp_destroy": [_vp],
+    "lbp_create_batch": [_vp, C.c_int, _vp, C.POINTER(_vp)],
+    "lbp_replica_info": [_vp, C.c_int, _vp, _vp, _vp],
+    "lbp_replica_count": [_vp, C.POINTER(C.c_int)],
+    "lbp_particles_add_to": [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int],
     "lbp_set_populations": [_vp, _vp, C.c_int],
     "lbp_read_populations": [_vp, _vp, C.c_int],
     "lbp_read_fields": [_vp, _vp, _vp, _vp, C.c_int],
@@ -61,6 +65,10 @@ _SIGS = {
     "lbp_get_step_index": [_vp, C.POINTER(C.c_int64)],
     "lbp_vacf_configure": [_vp, C.c_int],
     "lbp_vacf_read": [_vp, _vp, _vp, C.c_int],
+    "lbp_vacf_configure_ex": [_vp, C.c_int, C.c_int],
+    "lbp_autotune": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "lbp_set_block_rows": [_vp, C.c_int],
+    "lbp_vacf_read_per_particle": [_vp, _vp, _vp, C.c_int],
     "lbp_check": [_vp],
     "lbp_set_use_graphs": [_vp, C.c_int],
     "lbp_diagnostics": [_vp, _vp, C.c_int],
@@ -184,6 +192,42 @@ def lbp_create(nx, ny, nz, tau, precision=LBP_F32, stream=None) -> Handle:
     return Handle(out, int(nx), int(ny), int(nz))
 
 
+def lbp_create_batch(boxes, precision=LBP_F32, stream=None) -> Handle:
+    """boxes: sequence of (nx, ny, nz, tau).  The handle's N is the total node count."""
+    arr = (lbp_lattice_desc * len(boxes))(*[lbp_lattice_desc(int(a), int(b), int(c), float(t),
+                                                             int(precision)) for a, b, c, t in boxes])
+    out = C.c_void_p()
+    s = C.c_void_p(stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else 0))
+    _call("lbp_create_batch", C.cast(arr, C.c_void_p), len(boxes), s, C.byref(out))
+    h = Handle(out, 0, 0, 0)
+    h.N = sum(int(a) * int(b) * int(c) for a, b, c, _ in boxes)
+    h.boxes = [tuple(bx) for bx in boxes]
+    return h
+
+
+def lbp_replica_info(h: Handle, replica):
+    dims = (C.c_int * 3)()
+    tau = C.c_double()
+    off = C.c_int64()
+    _call("lbp_replica_info", h.ptr, int(replica), C.cast(dims, C.c_void_p), C.byref(tau), C.byref(off))
+    return (dims[0], dims[1], dims[2]), tau.value, off.value
+
+
+def lbp_replica_count(h: Handle) -> int:
+    n = C.c_int()
+    _call("lbp_replica_count", h.ptr, C.byref(n))
+    return n.value
+
+
+def lbp_particles_add_to(h: Handle, replica, r, v, mass, gamma, radius=None):
+    n = (r.numel() if _is_torch(r) else r.size) // 3
+    args = [_ptr(r, np.float64, 3 * n, "r"), _ptr(v, np.float64, 3 * n, "v"),
+            _ptr(mass, np.float64, n, "mass"), _ptr(gamma, np.float64, n, "gamma"),
+            _ptr(radius, np.float64, n, "radius")]
+    d = _same_side(*args)
+    _call("lbp_particles_add_to", h.ptr, int(replica), n, *[a[0] for a in args], d)
+
+
 def lbp_destroy(h: Handle):
     if h.ptr:
         _call("lbp_destroy", h.ptr)
@@ -283,14 +327,39 @@ def lbp_vacf_read(h: Handle, csum, counts):
     _call("lbp_vacf_read", h.ptr, a[0], b[0], d)
 
 
+def lbp_vacf_configure_ex(h: Handle, max_lag, per_particle):
+    _call("lbp_vacf_configure_ex", h.ptr, int(max_lag), int(bool(per_particle)))
+
+
+def lbp_vacf_read_per_particle(h: Handle, csum, counts):
+    """csum: [n_particles, max_lag + 1] FP64; counts: [max_lag + 1] int64."""
+    a = _ptr(csum, np.float64, None, "csum", True)
+    b = _ptr(counts, np.int64, None, "counts", True)
+    d = _same_side(a, b)
+    _call("lbp_vacf_read_per_particle", h.ptr, a[0], b[0], d)
+
+
 def lbp_check(h: Handle):
     _call("lbp_check", h.ptr)
 
 
 def lbp_diagnostics(h: Handle):
-    out = np.zeros(3, np.int64)
-    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 3)
-    return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2])}
+    out = np.zeros(4, np.int64)
+    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 4)
+    return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2]),
+            "rows_per_block": int(out[3])}
+
+
+def lbp_set_block_rows(h: Handle, rows):
+    _call("lbp_set_block_rows", h.ptr, int(rows))
+
+
+def lbp_autotune(h: Handle, launches=20):
+    """Pick the lattice kernel's rows per block by timing; returns (rows, [ms for 1, 2, 4 rows])."""
+    rows = C.c_int()
+    ms = (C.c_double * 3)()
+    _call("lbp_autotune", h.ptr, int(launches), C.byref(rows), ms)
+    return rows.value, list(ms)
 
 
 def lbp_set_use_graphs(h: Handle, enable):

@@ -118,6 +118,49 @@ PROFILE_128 = Workload("profile_128^3_2048p", (128, 128, 128), 0.8, 2048, kT=1e-
 BROWNIAN_64 = Workload("brownian_64^3_256p", (64, 64, 64), 0.8, 256, kT=1e-4, steps=5000)
 
 
+@dataclass
+class Ensemble:
+    """Independent periodic boxes (nx, ny, nz, tau) advanced together, n_per_box
+    particles in each: the replica ensemble the VACF average of Section 3 is
+    taken over, with box size L and viscosity nu varied between replicas."""
+    name: str
+    boxes: list
+    n_per_box: int = 1
+    M: float = 10.0
+    gamma: float = 0.5
+    kT: float = 1e-4
+    seed_pos: int = 1
+    seed_vel: int = 2
+    seed_noise: int = 3
+
+    @property
+    def nodes(self) -> int:
+        return sum(nx * ny * nz for nx, ny, nz, _ in self.boxes)
+
+    @property
+    def n_particles(self) -> int:
+        return self.n_per_box * len(self.boxes)
+
+    def particles(self, b: int) -> ParticleSet:
+        nx, ny, nz, tau = self.boxes[b]
+        R = stokes_radius(self.gamma, tau)
+        return uniform_particles(self.n_per_box, (nz, ny, nx), self.M, self.gamma, R, self.kT,
+                                 self.seed_pos * 1000 + b, self.seed_vel * 1000 + b)
+
+
+def _size_classes(classes, taus):
+    boxes = []
+    for count, L in classes:
+        boxes += [(L, L, L, taus[i % len(taus)]) for i in range(count)]
+    return boxes
+
+
+# 48 boxes of 64^3, 16 of 96^3 and 4 of 160^3 (43,122,688 nodes), tau cycling
+# over {0.6, 0.8, 1.0} within each size class, one Brownian particle per box.
+ENSEMBLE_68 = Ensemble("ensemble_48x64^3+16x96^3+4x160^3_1p",
+                       _size_classes([(48, 64), (16, 96), (4, 160)], (0.6, 0.8, 1.0)))
+
+
 def relaxation_particle(w: Workload, offset=(0.5, 0.5, 0.5), V0=(0.01, 0.0, 0.0)) -> ParticleSet:
     nz, ny, nx = w.shape_zyx
     r = np.array([[nx // 2 + offset[0], ny // 2 + offset[1], nz // 2 + offset[2]]], dtype=np.float64)

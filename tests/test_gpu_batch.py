@@ -1,0 +1,260 @@
+"""Batched ensembles: several independent periodic boxes in one handle.
+
+A batch (lbp_create_batch) lays the boxes' nodes one after another in the same
+population planes and advances them all with one lattice launch and one
+particle launch per step.  The boxes do not interact, so every box of a batch
+must evolve exactly as the same box simulated alone:
+
+  * populations, fields and particle states bitwise equal to separate
+    single-box handles, for every storage precision, when no random force is
+    drawn (kT = 0);
+  * with kT > 0 the random force of particle i uses the Philox counter
+    (step, i) with i its index in the handle, so box 0 (particles 0..n0-1 in
+    both) is still bitwise equal to its single-box run;
+  * per-particle VACF sums add up to the ensemble VACF and match the
+    trajectory read back step by step.
+"""
+import numpy as np
+import pytest
+
+from paper_1909_13412_gb300 import lbp
+from paper_1909_13412_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+Q = 15
+# D3Q15 weights in the library's direction order (rest, 6 faces, 8 corners)
+W = np.array([2 / 9] + [1 / 9] * 6 + [1 / 72] * 8)
+
+# uneven boxes: ragged x tails, x wider than one 128-node segment, odd row counts
+BOXES = [(20, 18, 16, 0.8), (33, 7, 12, 0.6), (130, 5, 4, 1.0), (8, 8, 8, 0.7)]
+NPART = [7, 3, 5, 0]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1909_13412_gb300 import build as lbp_build
+    lbp_build.build()
+    lbp.load()
+    torch.cuda.set_device(0)
+
+
+def box_state(b, box):
+    nx, ny, nz, tau = box
+    f = wl.perturbed_populations(W, (nz, ny, nx), 0.02, 100 + b)
+    ps = wl.uniform_particles(NPART[b], (nz, ny, nx), 6.0, 0.5, 0.0, 1e-4, 10 + b, 20 + b)
+    ps.R = np.full(ps.n, wl.stokes_radius(0.5, tau))
+    ps.V = np.random.default_rng(30 + b).normal(0.0, 0.01, (ps.n, 3))
+    return f, ps
+
+
+def run_single(b, box, prec, steps, kT, graphs):
+    nx, ny, nz, tau = box
+    f, ps = box_state(b, box)
+    h = lbp.lbp_create(nx, ny, nz, tau, precision=prec)
+    lbp.lbp_set_use_graphs(h, graphs)
+    lbp.lbp_set_populations(h, f)
+    if ps.n:
+        lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        lbp.lbp_particles_set_params(h, kT=kT, seed=5)
+    lbp.lbp_step(h, steps)
+    lbp.lbp_check(h)
+    fo = np.empty((Q, nz, ny, nx))
+    lbp.lbp_read_populations(h, fo)
+    parts = [np.empty((ps.n, 3)) for _ in range(4)]
+    if ps.n:
+        lbp.lbp_particles_read(h, *parts)
+    lbp.lbp_destroy(h)
+    return fo, parts
+
+
+def make_batch(prec, kT, graphs):
+    h = lbp.lbp_create_batch(BOXES, precision=prec)
+    lbp.lbp_set_use_graphs(h, graphs)
+    fall = np.concatenate([box_state(b, bx)[0].reshape(Q, -1) for b, bx in enumerate(BOXES)], axis=1)
+    lbp.lbp_set_populations(h, fall)
+    for b, bx in enumerate(BOXES):
+        _, ps = box_state(b, bx)
+        if ps.n:
+            lbp.lbp_particles_add_to(h, b, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=kT, seed=5)
+    return h
+
+
+def read_batch(h):
+    f = np.empty((Q, h.N))
+    lbp.lbp_read_populations(h, f)
+    n = lbp.lbp_particles_count(h)
+    parts = [np.empty((n, 3)) for _ in range(4)]
+    lbp.lbp_particles_read(h, *parts)
+    return f, parts
+
+
+def test_replica_info_and_offsets():
+    h = lbp.lbp_create_batch(BOXES)
+    assert lbp.lbp_replica_count(h) == len(BOXES)
+    off = 0
+    for b, (nx, ny, nz, tau) in enumerate(BOXES):
+        dims, t, o = lbp.lbp_replica_info(h, b)
+        assert dims == (nx, ny, nz) and t == tau and o == off
+        off += nx * ny * nz
+    assert h.N == off
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_replica_info(h, len(BOXES))
+    assert ei.value.status == lbp.LBP_EINVAL
+    lbp.lbp_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16, lbp.LBP_F16])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_batch_bitwise_equals_separate_boxes(prec, graphs):
+    steps = 40
+    h = make_batch(prec, 0.0, graphs)
+    lbp.lbp_step(h, steps)
+    lbp.lbp_check(h)
+    f, parts = read_batch(h)
+    lbp.lbp_destroy(h)
+    off, p0 = 0, 0
+    for b, bx in enumerate(BOXES):
+        nx, ny, nz, _ = bx
+        fs, ps = run_single(b, bx, prec, steps, 0.0, graphs)
+        n = nx * ny * nz
+        assert np.array_equal(f[:, off:off + n].reshape(Q, nz, ny, nx), fs), b
+        for k in range(4):
+            assert np.array_equal(parts[k][p0:p0 + NPART[b]], ps[k]), (b, k)
+        off += n
+        p0 += NPART[b]
+
+
+def test_batch_box0_with_noise_bitwise():
+    steps = 30
+    h = make_batch(lbp.LBP_F32, 1e-4, True)
+    lbp.lbp_step(h, steps)
+    f, parts = read_batch(h)
+    lbp.lbp_destroy(h)
+    nx, ny, nz, _ = BOXES[0]
+    fs, ps = run_single(0, BOXES[0], lbp.LBP_F32, steps, 1e-4, True)
+    assert np.array_equal(f[:, :nx * ny * nz].reshape(Q, nz, ny, nx), fs)
+    for k in range(4):
+        assert np.array_equal(parts[k][:NPART[0]], ps[k]), k
+    # the random force did act: the other boxes differ from their kT = 0 run
+    fs1, ps1 = run_single(1, BOXES[1], lbp.LBP_F32, steps, 0.0, True)
+    assert not np.array_equal(parts[1][NPART[0]:NPART[0] + NPART[1]], ps1[1])
+
+
+def test_batch_fields_are_the_boxes_fields():
+    h = make_batch(lbp.LBP_F32, 0.0, True)
+    lbp.lbp_step(h, 5)
+    rho = np.empty(h.N)
+    u = np.empty((3, h.N))
+    lbp.lbp_read_fields(h, rho, u)
+    f = np.empty((Q, h.N))
+    lbp.lbp_read_populations(h, f)
+    lbp.lbp_destroy(h)
+    off = 0
+    for b, (nx, ny, nz, tau) in enumerate(BOXES):
+        n = nx * ny * nz
+        hs = lbp.lbp_create(nx, ny, nz, tau)
+        lbp.lbp_set_populations(hs, np.ascontiguousarray(f[:, off:off + n]))
+        rs = np.empty(n)
+        us = np.empty((3, n))
+        lbp.lbp_read_fields(hs, rs, us)
+        lbp.lbp_destroy(hs)
+        assert np.array_equal(rho[off:off + n], rs), b
+        assert np.array_equal(u[:, off:off + n], us), b
+        off += n
+
+
+def test_particles_add_to_validates_against_its_box():
+    h = lbp.lbp_create_batch(BOXES)
+    one = lambda x: np.array([x], dtype=np.float64)
+    # inside box 2 (130 x 5 x 4) but outside box 1 (33 x 7 x 12) along x
+    r = np.array([[100.0, 1.0, 1.0]])
+    V = np.zeros((1, 3))
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_particles_add_to(h, 1, r, V, one(5.0), one(0.5), one(0.2))
+    assert ei.value.status == lbp.LBP_EINVAL
+    lbp.lbp_particles_add_to(h, 2, r, V, one(5.0), one(0.5), one(0.2))
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_particles_add_to(h, len(BOXES), r, V, one(5.0), one(0.5), one(0.2))
+    assert ei.value.status == lbp.LBP_EINVAL
+    assert lbp.lbp_particles_count(h) == 1
+    # a state update is checked against each particle's own box
+    with pytest.raises(lbp.LbpError):
+        lbp.lbp_particles_set_state(h, r=np.array([[131.0, 1.0, 1.0]]))
+    lbp.lbp_particles_set_state(h, r=np.array([[129.5, 4.5, 3.5]]))
+    lbp.lbp_destroy(h)
+
+
+def test_per_particle_vacf_sums_and_trajectory():
+    h = make_batch(lbp.LBP_F32, 1e-4, True)
+    n = lbp.lbp_particles_count(h)
+    K, T = 70, 150
+    lbp.lbp_vacf_configure_ex(h, K, 1)
+    traj = np.empty((T, n, 3))
+    V = np.empty((n, 3))
+    for t in range(T):
+        lbp.lbp_step(h, 1)
+        lbp.lbp_particles_read(h, v=V)
+        traj[t] = V
+    cs = np.empty((n, K + 1))
+    cnt = np.empty(K + 1, np.int64)
+    lbp.lbp_vacf_read_per_particle(h, cs, cnt)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_vacf_read(h, np.empty(K + 1), np.empty(K + 1, np.int64))
+    assert ei.value.status == lbp.LBP_ESTATE
+    lbp.lbp_destroy(h)
+    assert np.array_equal(cnt, T - np.arange(K + 1))
+    t32 = traj.astype(np.float32).astype(np.float64)
+    ref = np.empty((n, K + 1))
+    for k in range(K + 1):
+        ref[:, k] = np.einsum("tic,tic->i", t32[k:], t32[:T - k])
+    # FP32 products and block sums of at most 192 terms: relative 1e-5 of C_i(0)
+    scale = ref[:, :1]
+    assert np.all(np.abs(cs - ref) <= 1e-5 * scale + 1e-30)
+    # the per-particle and the ensemble estimators agree
+    h = make_batch(lbp.LBP_F32, 1e-4, True)
+    lbp.lbp_vacf_configure(h, K)
+    lbp.lbp_step(h, T)
+    tot = np.empty(K + 1)
+    cnt2 = np.empty(K + 1, np.int64)
+    lbp.lbp_vacf_read(h, tot, cnt2)
+    lbp.lbp_destroy(h)
+    assert np.array_equal(cnt2, n * cnt)
+    assert np.max(np.abs(tot - cs.sum(axis=0))) <= 1e-5 * tot[0]
+
+
+@pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16])
+def test_block_shapes_and_autotune_leave_results_unchanged(prec):
+    steps = 25
+    ref = None
+    for rows in (1, 2, 4, "auto"):
+        h = make_batch(prec, 1e-4, True)
+        lbp.lbp_step(h, 3)
+        if rows == "auto":
+            chosen, ms = lbp.lbp_autotune(h, 5)
+            assert chosen in (1, 2, 4) and all(m > 0 for m in ms)
+            assert chosen == (1, 2, 4)[int(np.argmin(ms))]
+        else:
+            lbp.lbp_set_block_rows(h, rows)
+        assert lbp.lbp_get_step_index(h) == 3
+        assert lbp.lbp_diagnostics(h)["rows_per_block"] == (chosen if rows == "auto" else rows)
+        lbp.lbp_step(h, steps)
+        lbp.lbp_check(h)
+        got = read_batch(h)
+        lbp.lbp_destroy(h)
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got[0], ref[0]), rows
+            for k in range(4):
+                assert np.array_equal(got[1][k], ref[1][k]), (rows, k)
+    with pytest.raises(lbp.LbpError):
+        h = lbp.lbp_create(8, 8, 8, 0.8)
+        try:
+            lbp.lbp_set_block_rows(h, 3)
+        finally:
+            lbp.lbp_destroy(h)
