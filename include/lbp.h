@@ -269,6 +269,56 @@ lbp_status lbp_philox4x64_10(const uint64_t *ctr, const uint64_t *key, uint64_t 
 lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp, int max_lag,
                                       int npairs, double *csum, int64_t *counts, void *stream);
 
+/* ---------------------------------------------------------------- adjoint
+ * Reverse-mode gradients of a run (no counterpart in the paper; the method's
+ * step is differentiated as written: Eqs. 1-2, 4-5, 8-9, 12-20).
+ *
+ * lbp_adjoint_record runs nsteps >= 1 ordinary steps from the current state
+ * (exactly as lbp_step would) and keeps, inside the handle, a checkpoint of the
+ * populations and of the particle positions and velocities every
+ * checkpoint_every >= 1 steps (memory: ceil(nsteps / checkpoint_every) copies
+ * of the populations plus 48 bytes per particle each).  v_traj and r_traj
+ * (optional, [nsteps][n_particles][3] FP64, host or device per on_device)
+ * receive V^{n+1} and r^{n+1} after every step n: the trajectory a loss is
+ * written on.  A new recording replaces the previous one.  Single-box handles
+ * with at least one particle only (LBP_EINVAL for a batch, LBP_ESTATE without
+ * particles).
+ *
+ * lbp_adjoint_backward takes dL/dV^{n+1} and dL/dr^{n+1} for every recorded
+ * step (g_v, g_r: [nsteps][n_particles][3] FP64, either may be NULL = zero)
+ * and returns, through the non-NULL members of grads, the gradient of L with
+ * respect to the inputs of the recorded run: tau (one value), kT (one value),
+ * each particle's gamma, radius and mass ([n_particles]), the velocities and
+ * positions at the first recorded step ([n_particles][3]) and the populations
+ * at the first recorded step ([15][N], ABI layout).  The reverse sweep
+ * re-runs each segment between checkpoints forward from its checkpoint
+ * (keeping that segment's states: checkpoint_every population copies), then
+ * steps the adjoint back through it; the handle's own state (populations,
+ * particles, step index) is left as the recording left it.  Requires that no
+ * step, particle change or new recording happened since lbp_adjoint_record
+ * (LBP_ESTATE otherwise).  Where the method is not differentiable (a particle
+ * changing cell, a corner skipped by the fit) the derivative is that of the
+ * branch the forward run took.  Arithmetic: lattice adjoint in FP32, particle
+ * adjoint and all accumulated gradients in FP64.  Results are bitwise
+ * reproducible unless more than 8 particle-cell corners fall in one 128-node
+ * row segment in one step (those extra contributions are then added with FP64
+ * atomics).  Synchronous.                                                    */
+typedef struct {
+    double *tau;     /* [1]                    dL/dtau                         */
+    double *kT;      /* [1]                    dL/dkT                          */
+    double *gamma;   /* [n_particles]          dL/dgamma_i                     */
+    double *radius;  /* [n_particles]          dL/dR_i                         */
+    double *mass;    /* [n_particles]          dL/dM_i                         */
+    double *v0;      /* [n_particles][3]       dL/dV_i at the first step       */
+    double *r0;      /* [n_particles][3]       dL/dr_i at the first step       */
+    double *f0;      /* [15][N]                dL/df at the first step         */
+} lbp_gradients;
+
+lbp_status lbp_adjoint_record(lbp_sim *sim, int64_t nsteps, int checkpoint_every, double *v_traj,
+                              double *r_traj, int on_device);
+lbp_status lbp_adjoint_backward(lbp_sim *sim, const double *g_v, const double *g_r, int on_device,
+                                const lbp_gradients *grads);
+
 /* Message of the calling thread's last failing call ("" if none).            */
 const char *lbp_last_error(void);
 

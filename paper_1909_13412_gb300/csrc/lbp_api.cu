@@ -176,6 +176,38 @@ lbp_status capture(lbp_sim *s, int parity, int due) {
     return LBP_OK;
 }
 
+// one time step on s0 (graph replay, timed or plain launches)
+lbp_status step_once(lbp_sim *s) {
+    // the VACF correlator runs when the step completes a block of B samples
+    const int B = vacf_block_samples();
+    bool due = false;
+    if (s->vacf_lag >= 0 && s->np > 0) {
+        const long long written = s->step - s->vacf_t0 + 1;
+        if (written - s->vacf_done_host >= B) {
+            due = true;
+            s->vacf_done_host += B;
+        }
+    }
+    if (s->timing) {
+        if (s->ntimed == lbp::Sim::MAX_TIMED) TRY(fold_timing(s));
+        TRY(enqueue_step(s, true, due));
+    } else if (s->use_graphs) {
+        if (!s->graph[s->cur][due]) TRY(capture(s, s->cur, due));
+        CK(cudaGraphLaunch(s->graph[s->cur][due], s->s0));
+    } else {
+        TRY(enqueue_step(s, false, due));
+    }
+    s->cur ^= 1;
+    s->step += 1;
+    return LBP_OK;
+}
+
+void free_tape(lbp_sim *s) {
+    if (s->tape.ck_f) cudaFree(s->tape.ck_f);
+    if (s->tape.ck_p) cudaFree(s->tape.ck_p);
+    s->tape = lbp::Tape();
+}
+
 lbp_status host_to_device(lbp_sim *s, void *dst, const void *src, size_t bytes, int on_device) {
     CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        s->s0));
@@ -300,6 +332,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s0) cudaStreamSynchronize(s->s0);
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
+    free_tape(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
@@ -319,6 +352,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
 
 lbp_status lbp_set_populations(lbp_sim *s, const double *f, int on_device) {
     CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
     if (!f) return fail(LBP_EINVAL, "lbp_set_populations: null f");
     TRY(enter(s));
     void *dst = s->f[s->cur];
@@ -391,6 +425,7 @@ lbp_status lbp_particles_add_to(lbp_sim *s, int replica, int n, const double *r,
                                 const double *mass, const double *gamma, const double *radius,
                                 int on_device) {
     CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
     if (replica < 0 || replica >= s->nrep)
         return fail(LBP_EINVAL, "lbp_particles_add: replica %d outside [0, %d)", replica, s->nrep);
     if (n < 0) return fail(LBP_EINVAL, "lbp_particles_add: n < 0");
@@ -551,6 +586,7 @@ lbp_status lbp_particles_count(lbp_sim *s, int *n) {
 
 lbp_status lbp_particles_set_params(lbp_sim *s, const lbp_particle_params *prm) {
     CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
     if (!prm) return fail(LBP_EINVAL, "lbp_particles_set_params: null params");
     if (!(prm->kT >= 0.0) || !std::isfinite(prm->kT))
         return fail(LBP_EINVAL, "lbp_particles_set_params: kT must be finite and >= 0");
@@ -595,6 +631,7 @@ static lbp_status upload_vec3(lbp_sim *s, double *dst_soa, const double *src_aos
 lbp_status lbp_particles_set_external_force(lbp_sim *s, const double *f_ext, const uint8_t *pinned,
                                             int on_device) {
     CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
     if (s->np == 0) return LBP_OK;
     TRY(enter(s));
     if (f_ext) {
@@ -613,6 +650,7 @@ lbp_status lbp_particles_set_external_force(lbp_sim *s, const double *f_ext, con
 
 lbp_status lbp_particles_set_state(lbp_sim *s, const double *r, const double *v, int on_device) {
     CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
     if (s->np == 0) return LBP_OK;
     if (r) {
         std::vector<double> hr;
@@ -681,34 +719,13 @@ lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
     if (nsteps < 0) return fail(LBP_EINVAL, "lbp_step: nsteps < 0");
     if (nsteps == 0) return LBP_OK;
     TRY(enter(s));
-    const int B = vacf_block_samples();
-    for (int64_t n = 0; n < nsteps; ++n) {
-        // the VACF correlator runs when the step completes a block of B samples
-        bool due = false;
-        if (s->vacf_lag >= 0 && s->np > 0) {
-            const long long written = s->step - s->vacf_t0 + 1;
-            if (written - s->vacf_done_host >= B) {
-                due = true;
-                s->vacf_done_host += B;
-            }
-        }
-        if (s->timing) {
-            if (s->ntimed == lbp::Sim::MAX_TIMED) TRY(fold_timing(s));
-            TRY(enqueue_step(s, true, due));
-        } else if (s->use_graphs) {
-            if (!s->graph[s->cur][due]) TRY(capture(s, s->cur, due));
-            CK(cudaGraphLaunch(s->graph[s->cur][due], s->s0));
-        } else {
-            TRY(enqueue_step(s, false, due));
-        }
-        s->cur ^= 1;
-        s->step += 1;
-    }
+    for (int64_t n = 0; n < nsteps; ++n) TRY(step_once(s));
     return leave(s);
 }
 
 lbp_status lbp_set_step_index(lbp_sim *s, int64_t step) {
     CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
     if (step < 0) return fail(LBP_EINVAL, "lbp_set_step_index: step < 0");
     TRY(enter(s));
     long long v = step;
@@ -860,6 +877,252 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, double *ms) {
     if (rows) *rows = s->rows;
     if (ms)
         for (int c = 0; c < 3; ++c) ms[c] = t[c];
+    return leave(s);
+}
+
+lbp_status lbp_adjoint_record(lbp_sim *s, int64_t nsteps, int checkpoint_every, double *v_traj,
+                              double *r_traj, int on_device) {
+    CHECK_SIM(s);
+    if (nsteps < 1 || checkpoint_every < 1)
+        return fail(LBP_EINVAL, "lbp_adjoint_record: need nsteps >= 1 and checkpoint_every >= 1");
+    if (s->nrep != 1) return fail(LBP_EINVAL, "lbp_adjoint_record: single-box handles only");
+    if (s->np < 1) return fail(LBP_ESTATE, "lbp_adjoint_record: add particles first (the recorded outputs are their trajectories)");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    free_tape(s);
+    lbp::Tape &tp = s->tape;
+    const size_t pop_bytes = (size_t)storage_bytes(s->precision) * Q * s->P;
+    const int64_t nck = (nsteps + checkpoint_every - 1) / checkpoint_every;
+    const size_t pcount = (size_t)6 * (s->cap > 0 ? s->cap : 1);
+    TRY(dalloc(&tp.ck_f, pop_bytes * (size_t)nck));
+    TRY(dalloc(&tp.ck_p, pcount * (size_t)nck));
+    const size_t traj = (size_t)nsteps * s->np * 3;
+    double *vt = v_traj, *rt = r_traj;
+    if (!on_device && (v_traj || r_traj) && traj > 0) {
+        TRY(stage(s, sizeof(double) * 2 * traj));
+        vt = v_traj ? s->stage : nullptr;
+        rt = r_traj ? s->stage + traj : nullptr;
+    }
+    tp.step0 = s->step;
+    tp.cur0 = s->cur;
+    tp.C = checkpoint_every;
+    tp.np = s->np;
+    tp.nck = nck;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (n % checkpoint_every == 0) {
+            const int64_t k = n / checkpoint_every;
+            CK(cudaMemcpyAsync(tp.ck_f + (size_t)k * pop_bytes, s->f[s->cur], pop_bytes,
+                               cudaMemcpyDeviceToDevice, s->s0));
+            if (s->np > 0) {
+                CK(cudaMemcpyAsync(tp.ck_p + (size_t)k * pcount, s->r, sizeof(double) * 3 * s->cap,
+                                   cudaMemcpyDeviceToDevice, s->s0));
+                CK(cudaMemcpyAsync(tp.ck_p + (size_t)k * pcount + 3 * s->cap, s->v,
+                                   sizeof(double) * 3 * s->cap, cudaMemcpyDeviceToDevice, s->s0));
+            }
+        }
+        TRY(step_once(s));
+        if (vt) CK(launch_soa_to_aos(s->v, vt + (size_t)n * s->np * 3, s->np, s->cap, s->s0));
+        if (rt) CK(launch_soa_to_aos(s->r, rt + (size_t)n * s->np * 3, s->np, s->cap, s->s0));
+    }
+    if (!on_device && traj > 0) {
+        if (v_traj) CK(cudaMemcpyAsync(v_traj, vt, sizeof(double) * traj, cudaMemcpyDeviceToHost, s->s0));
+        if (r_traj) CK(cudaMemcpyAsync(r_traj, rt, sizeof(double) * traj, cudaMemcpyDeviceToHost, s->s0));
+    }
+    CK(cudaStreamSynchronize(s->s0));
+    tp.T = nsteps;
+    tp.edits = s->edits;
+    return leave(s);
+}
+
+lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r, int on_device,
+                                const lbp_gradients *out) {
+    CHECK_SIM(s);
+    if (!out) return fail(LBP_EINVAL, "lbp_adjoint_backward: null grads");
+    const lbp::Tape &tp = s->tape;
+    if (tp.T == 0) return fail(LBP_ESTATE, "lbp_adjoint_backward: nothing recorded (lbp_adjoint_record)");
+    if (s->step != tp.step0 + tp.T || s->edits != tp.edits || s->np != tp.np)
+        return fail(LBP_ESTATE, "lbp_adjoint_backward: the handle changed since lbp_adjoint_record");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    const int np = s->np, cap = s->cap > 0 ? s->cap : 1, C = tp.C;
+    const int64_t T = tp.T;
+    const size_t pop_bytes = (size_t)storage_bytes(s->precision) * Q * s->P;
+    const size_t pcount = (size_t)6 * cap;
+    const size_t traj = (size_t)T * np * 3;
+    const int nblk = adj_lattice_blocks(*s);
+    const size_t rec_bytes = sizeof(unsigned long long) * REC_WORDS * (size_t)s->nseg;
+
+    // work buffers, freed on every exit path
+    char *seg = nullptr;
+    float *lam = nullptr;
+    double *dwork = nullptr;
+    struct Guard {
+        std::vector<void *> p;
+        ~Guard() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } guard;
+    TRY(dalloc(&seg, pop_bytes * (size_t)C));
+    guard.p.push_back(seg);
+    TRY(dalloc(&lam, (size_t)2 * Q * s->P));
+    guard.p.push_back(lam);
+    // doubles: seg_p [C][6 cap] | lam_v, lam_r [3 cap] | acc [4 np] | acc_om [nblk] |
+    //          save (r, v, fh, fr) [12 cap] | g_v, g_r staged [traj] each
+    const size_t n_segp = (size_t)C * pcount, n_lvr = (size_t)6 * cap, n_acc = (size_t)4 * (np > 0 ? np : 1),
+                 n_om = (size_t)nblk, n_save = (size_t)12 * cap;
+    const bool stage_g = !on_device && traj > 0;
+    const size_t n_g = stage_g ? 2 * traj : 0;
+    TRY(dalloc(&dwork, n_segp + n_lvr + n_acc + n_om + n_save + n_g));
+    guard.p.push_back(dwork);
+    double *f0tmp = nullptr;  // FP64 staging of dL/df0 for a host destination
+    if (out->f0 && !on_device) {
+        TRY(dalloc(&f0tmp, (size_t)Q * s->N));
+        guard.p.push_back(f0tmp);
+    }
+    double *seg_p = dwork, *lam_v = seg_p + n_segp, *lam_r = lam_v + 3 * (size_t)cap,
+           *acc = lam_v + n_lvr, *acc_om = acc + n_acc, *save = acc_om + n_om, *gst = save + n_save;
+    const double *gv = g_v, *gr = g_r;
+    if (stage_g) {
+        if (g_v) {
+            CK(cudaMemcpyAsync(gst, g_v, sizeof(double) * traj, cudaMemcpyHostToDevice, s->s0));
+            gv = gst;
+        }
+        if (g_r) {
+            CK(cudaMemcpyAsync(gst + traj, g_r, sizeof(double) * traj, cudaMemcpyHostToDevice, s->s0));
+            gr = gst + traj;
+        }
+    }
+    CK(cudaMemsetAsync(lam, 0, sizeof(float) * 2 * Q * s->P, s->s0));
+    CK(cudaMemsetAsync(lam_v, 0, sizeof(double) * (n_lvr + n_acc + n_om), s->s0));
+    // the state to put back: particles (the populations are not touched)
+    double *sv[4] = {s->r, s->v, s->fh, s->fr};
+    if (np > 0)
+        for (int k = 0; k < 4; ++k)
+            CK(cudaMemcpyAsync(save + (size_t)3 * cap * k, sv[k], sizeof(double) * 3 * cap,
+                               cudaMemcpyDeviceToDevice, s->s0));
+    const int saved_vacf = s->vacf_lag;
+    s->vacf_lag = -1;  // the replay writes no VACF samples
+    auto restore = [&]() {
+        s->vacf_lag = saved_vacf;
+        if (np > 0)
+            for (int k = 0; k < 4; ++k)
+                cudaMemcpyAsync(sv[k], save + (size_t)3 * cap * k, sizeof(double) * 3 * cap,
+                                cudaMemcpyDeviceToDevice, s->s0);
+        if (s->rec[0]) {
+            cudaMemsetAsync(s->rec[0], 0, rec_bytes, s->s0);
+            cudaMemsetAsync(s->rec[1], 0, rec_bytes, s->s0);
+        }
+        long long st = s->step;
+        cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice, s->s0);
+        cudaStreamSynchronize(s->s0);
+    };
+    cudaError_t e = cudaSuccess;
+    int L = 0;  // lam + L * 15 P holds dL/dfhat of the current step
+#define ADJ_CK(x)                   \
+    do {                            \
+        if (e == cudaSuccess) e = (x); \
+    } while (0)
+    for (int64_t k = tp.nck - 1; k >= 0 && e == cudaSuccess; --k) {
+        const int64_t n0 = k * C;
+        const int m = (int)(T - n0 < C ? T - n0 : C);
+        // replay the segment forward from its checkpoint, keeping every state
+        ADJ_CK(cudaMemcpyAsync(seg, tp.ck_f + (size_t)k * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, s->s0));
+        if (np > 0) {
+            ADJ_CK(cudaMemcpyAsync(s->r, tp.ck_p + (size_t)k * pcount, sizeof(double) * 3 * cap,
+                                   cudaMemcpyDeviceToDevice, s->s0));
+            ADJ_CK(cudaMemcpyAsync(s->v, tp.ck_p + (size_t)k * pcount + 3 * cap, sizeof(double) * 3 * cap,
+                                   cudaMemcpyDeviceToDevice, s->s0));
+        }
+        long long st0 = tp.step0 + n0;
+        ADJ_CK(cudaMemcpyAsync(s->d_step, &st0, sizeof(long long), cudaMemcpyHostToDevice, s->s0));
+        if (s->rec[0]) {
+            ADJ_CK(cudaMemsetAsync(s->rec[0], 0, rec_bytes, s->s0));
+            ADJ_CK(cudaMemsetAsync(s->rec[1], 0, rec_bytes, s->s0));
+        }
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
+            const int64_t n = n0 + j;
+            const int parity = tp.cur0 ^ (int)(n & 1);
+            if (np > 0) {
+                ADJ_CK(cudaMemcpyAsync(seg_p + (size_t)j * pcount, s->r, sizeof(double) * 3 * cap,
+                                       cudaMemcpyDeviceToDevice, s->s0));
+                ADJ_CK(cudaMemcpyAsync(seg_p + (size_t)j * pcount + 3 * cap, s->v, sizeof(double) * 3 * cap,
+                                       cudaMemcpyDeviceToDevice, s->s0));
+            }
+            if (j == m - 1) break;
+            const void *src = seg + (size_t)j * pop_bytes;
+            void *dst = seg + (size_t)(j + 1) * pop_bytes;
+            if (np > 0) {
+                ADJ_CK(launch_particles(*s, src, parity, s->s0));
+                ADJ_CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
+            } else {
+                ADJ_CK(launch_stream_collide(*s, src, dst, s->s0));
+            }
+        }
+        if (s->rec[0]) {
+            ADJ_CK(cudaMemsetAsync(s->rec[0], 0, rec_bytes, s->s0));
+            ADJ_CK(cudaMemsetAsync(s->rec[1], 0, rec_bytes, s->s0));
+        }
+        // step the adjoint back through the segment
+        for (int j = m - 1; j >= 0 && e == cudaSuccess; --j) {
+            const int64_t n = n0 + j;
+            const int q = j & 1;
+            const void *src = seg + (size_t)j * pop_bytes;
+            const float *lc = lam + (size_t)L * Q * s->P;
+            float *ln = lam + (size_t)(L ^ 1) * Q * s->P;
+            const double *rj = seg_p + (size_t)j * pcount, *vj = rj + 3 * cap;
+            ADJ_CK(launch_adj_particles(*s, src, lc, rj, vj, tp.step0 + n, gv ? gv + (size_t)n * np * 3 : nullptr,
+                                        gr ? gr + (size_t)n * np * 3 : nullptr, lam_v, lam_r, acc, q, s->s0));
+            ADJ_CK(launch_adj_lattice(*s, src, lc, ln, q, acc_om, s->s0));
+            L ^= 1;
+        }
+    }
+#undef ADJ_CK
+    // gradients
+    auto collect = [&]() -> lbp_status {
+        if (e != cudaSuccess) return fail(LBP_ECUDA, "lbp_adjoint_backward: %s", cudaGetErrorString(e));
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        std::vector<double> h_om(nblk), h_acc(4 * (size_t)np);
+        CK(cudaMemcpyAsync(h_om.data(), acc_om, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s->s0));
+        if (np > 0)
+            CK(cudaMemcpyAsync(h_acc.data(), acc, sizeof(double) * 4 * np, cudaMemcpyDeviceToHost, s->s0));
+        if (out->f0) {
+            CK(launch_f32_to_f64(*s, lam + (size_t)L * Q * s->P, on_device ? out->f0 : f0tmp, s->s0));
+            if (!on_device)
+                CK(cudaMemcpyAsync(out->f0, f0tmp, sizeof(double) * Q * s->N, cudaMemcpyDeviceToHost, s->s0));
+        }
+        if (np > 0) {
+            double *aos = seg_p;  // free now: C * 6 cap >= 6 np doubles
+            if (out->v0) {
+                CK(launch_soa_to_aos(lam_v, on_device ? out->v0 : aos, np, cap, s->s0));
+                if (!on_device)
+                    CK(cudaMemcpyAsync(out->v0, aos, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, s->s0));
+            }
+            if (out->r0) {
+                double *aos2 = aos + 3 * (size_t)np;
+                CK(launch_soa_to_aos(lam_r, on_device ? out->r0 : aos2, np, cap, s->s0));
+                if (!on_device)
+                    CK(cudaMemcpyAsync(out->r0, aos2, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, s->s0));
+            }
+            double *accs[3] = {out->gamma, out->radius, out->mass};
+            for (int k = 0; k < 3; ++k)
+                if (accs[k]) CK(cudaMemcpyAsync(accs[k], acc + (size_t)k * np, sizeof(double) * np, kind, s->s0));
+        }
+        CK(cudaStreamSynchronize(s->s0));
+        // fixed-order host sums of the per-block and per-particle accumulators
+        double dom = 0.0, dkT = 0.0;
+        for (int b = 0; b < nblk; ++b) dom += h_om[b];
+        for (int i = 0; i < np; ++i) dkT += h_acc[3 * (size_t)np + i];
+        const double omega = (double)s->reps[0].omega;
+        const double dtau = -dom * omega * omega;  // omega = 1/tau
+        const cudaMemcpyKind hk = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+        if (out->tau) CK(cudaMemcpy(out->tau, &dtau, sizeof(double), hk));
+        if (out->kT) CK(cudaMemcpy(out->kT, &dkT, sizeof(double), hk));
+        return LBP_OK;
+    };
+    const lbp_status st = collect();
+    restore();
+    if (st != LBP_OK) return st;
     return leave(s);
 }
 

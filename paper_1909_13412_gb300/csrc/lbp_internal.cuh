@@ -162,6 +162,21 @@ __device__ __forceinline__ int find_node_rep(const RepTable<MAXR> &t, long long 
     return lo;
 }
 
+// ------------------------------------------------------------ adjoint tape
+// What a recorded forward run keeps for its reverse sweep: a checkpoint of the
+// populations and of the particle positions and velocities every C steps.
+struct Tape {
+    int64_t T = 0;           // recorded steps (0: no tape)
+    int C = 0;               // steps between checkpoints
+    int64_t step0 = 0;       // step index of the first recorded step
+    int cur0 = 0;            // buffer parity at the first recorded step
+    int np = 0;              // particles during the recording
+    uint64_t edits = 0;      // the handle's edit count when the recording ended
+    int64_t nck = 0;         // checkpoints
+    char *ck_f = nullptr;    // [nck][15 P] populations (storage type)
+    double *ck_p = nullptr;  // [nck][6][cap]: r then V, [3][cap] each
+};
+
 // --------------------------------------------------------------- handle
 struct Sim {
     int nx = 0, ny = 0, nz = 0;  // box of replica 0
@@ -219,6 +234,9 @@ struct Sim {
     double *vacf_part = nullptr;  // [nchunks][K + 1]
     int vacf_nchunks = 0;
 
+    Tape tape;
+    uint64_t edits = 0;  // state-changing calls other than steps (set_*, add)
+
     // scratch for host <-> device conversions
     double *stage = nullptr;
     size_t stage_bytes = 0;
@@ -263,6 +281,15 @@ cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cud
 cudaError_t launch_cells(Sim &s, int *base, double *frac, cudaStream_t st);
 cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long long *key,
                           unsigned long long *out, int64_t n, cudaStream_t st);
+// adjoint_kernels.cu
+cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const double *r,
+                                 const double *v, long long step, const double *gv,
+                                 const double *gr, double *lam_v, double *lam_r, double *acc,
+                                 int parity, cudaStream_t st);
+cudaError_t launch_adj_lattice(Sim &s, const void *g, const float *lam, float *lam_out, int parity,
+                               double *acc_omega, cudaStream_t st);
+int adj_lattice_blocks(const Sim &s);
+cudaError_t launch_f32_to_f64(Sim &s, const float *src, double *dst, cudaStream_t st);
 // vacf_kernels.cu
 int vacf_block_samples();
 int vacf_chunk_components();

@@ -67,6 +67,8 @@ _SIGS = {
     "lbp_vacf_read": [_vp, _vp, _vp, C.c_int],
     "lbp_vacf_configure_ex": [_vp, C.c_int, C.c_int],
     "lbp_autotune": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "lbp_adjoint_record": [_vp, C.c_int64, C.c_int, _vp, _vp, C.c_int],
+    "lbp_adjoint_backward": [_vp, _vp, _vp, C.c_int, _vp],
     "lbp_set_block_rows": [_vp, C.c_int],
     "lbp_vacf_read_per_particle": [_vp, _vp, _vp, C.c_int],
     "lbp_check": [_vp],
@@ -337,6 +339,45 @@ def lbp_vacf_read_per_particle(h: Handle, csum, counts):
     b = _ptr(counts, np.int64, None, "counts", True)
     d = _same_side(a, b)
     _call("lbp_vacf_read_per_particle", h.ptr, a[0], b[0], d)
+
+
+class lbp_gradients(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("tau", "kT", "gamma", "radius", "mass", "v0", "r0", "f0")]
+
+
+GRADIENT_NAMES = ("tau", "kT", "gamma", "radius", "mass", "v0", "r0", "f0")
+
+
+def lbp_adjoint_record(h: Handle, nsteps, checkpoint_every, v_traj=None, r_traj=None):
+    """Run nsteps steps, keeping checkpoints every checkpoint_every steps; v_traj,
+    r_traj ([nsteps, n, 3] FP64) receive V^{n+1}, r^{n+1}."""
+    cnt = int(nsteps) * h.np * 3
+    a = _ptr(v_traj, np.float64, cnt, "v_traj", True)
+    b = _ptr(r_traj, np.float64, cnt, "r_traj", True)
+    d = _same_side(a, b)
+    _call("lbp_adjoint_record", h.ptr, int(nsteps), int(checkpoint_every), a[0], b[0], d)
+
+
+def lbp_adjoint_backward(h: Handle, nsteps, g_v=None, g_r=None, out=None):
+    """Reverse sweep over the recording.  out: dict name -> writable array/tensor
+    for any of GRADIENT_NAMES (shapes: tau, kT [1]; gamma, radius, mass [n];
+    v0, r0 [n, 3]; f0 [15, N]), all on the same side as g_v / g_r."""
+    n = h.np
+    cnt = int(nsteps) * n * 3
+    a = _ptr(g_v, np.float64, cnt, "g_v")
+    b = _ptr(g_r, np.float64, cnt, "g_r")
+    sizes = {"tau": 1, "kT": 1, "gamma": n, "radius": n, "mass": n, "v0": 3 * n, "r0": 3 * n, "f0": Q * h.N}
+    g = lbp_gradients()
+    ptrs = []
+    for name, x in (out or {}).items():
+        if name not in sizes:
+            raise KeyError(f"unknown gradient {name!r}")
+        pp = _ptr(x, np.float64, sizes[name], name, True)
+        setattr(g, name, pp[0])
+        ptrs.append(pp)
+    d = _same_side(a, b, *ptrs)
+    _call("lbp_adjoint_backward", h.ptr, a[0], b[0], d, C.byref(g))
+    return out
 
 
 def lbp_check(h: Handle):

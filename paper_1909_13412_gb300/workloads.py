@@ -161,6 +161,27 @@ ENSEMBLE_68 = Ensemble("ensemble_48x64^3+16x96^3+4x160^3_1p",
                        _size_classes([(48, 64), (16, 96), (4, 160)], (0.6, 0.8, 1.0)))
 
 
+# 64^3, 8 particles kicked to |V0| = 0.01 in seeded random directions, no
+# noise, 2000 steps with a checkpoint every 100: the differentiable run
+# (gradients of a velocity-relaxation loss by the adjoint).
+ADJOINT_64 = Workload("adjoint_64^3_8p", (64, 64, 64), 0.8, 8, kT=0.0, steps=2000,
+                      extra={"checkpoint_every": 100, "V0": 0.01, "seed_dir": 4})
+
+
+def kicked_particles(w: Workload) -> ParticleSet:
+    """w.n_particles particles near seeded cell centres (0.35..0.65 into the
+    cell, so that the ~0.2-0.3 of relaxation displacement keeps them in their
+    cell), velocity V0 along seeded random unit vectors, mass M, friction
+    gamma, Stokes radius at w.tau."""
+    nz, ny, nx = w.shape_zyx
+    g = np.random.default_rng(w.seed_pos)
+    cells = np.floor(g.random((w.n_particles, 3)) * np.array([nx, ny, nz]))
+    r = cells + g.uniform(0.35, 0.65, (w.n_particles, 3))
+    V = random_unit_vectors(w.n_particles, w.extra.get("seed_dir", 4)) * w.extra.get("V0", 0.01)
+    n = w.n_particles
+    return ParticleSet(r, V, np.full(n, w.M), np.full(n, w.gamma), np.full(n, w.R))
+
+
 def relaxation_particle(w: Workload, offset=(0.5, 0.5, 0.5), V0=(0.01, 0.0, 0.0)) -> ParticleSet:
     nz, ny, nx = w.shape_zyx
     r = np.array([[nx // 2 + offset[0], ny // 2 + offset[1], nz // 2 + offset[2]]], dtype=np.float64)
