@@ -251,6 +251,53 @@ def config_of(w, world, vacf_lag=VACF_LAG, precision="f32"):
             "l2": "no flush: 2 x 1.0 GB population buffers per step exceed the 129 MB L2"}
 
 
+# ---------------------------------------------------------------------------- adjoint
+ADJ_BYTES_PER_NODE = 3 * 15 * 4  # lam read + populations read + result write, FP32
+
+
+def adjoint_variant(lbp, torch, w, ps, steps, checkpoint_every, kT, seed):
+    """Record `steps` steps with checkpoints, then the reverse sweep of a
+    velocity-relaxation loss; times both, and the adjoint lattice kernel."""
+    nz, ny, nx = w.shape_zyx
+    h = lbp.lbp_create(nx, ny, nz, w.tau)
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=kT, seed=seed)
+    n = ps.n
+    vt = torch.empty((steps, n, 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    lbp.lbp_adjoint_record(h, steps, checkpoint_every, vt, None)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t = torch.arange(1, steps + 1, dtype=torch.float64, device="cuda")
+    v0 = torch.tensor(ps.V, device="cuda")
+    target = v0[None] * torch.exp(-t * (w.gamma / w.M))[:, None, None]
+    g_v = (2.0 / vt.numel()) * (vt - target)  # d/dV of the mean squared deviation
+    out = {k: torch.empty(s_, dtype=torch.float64, device="cuda")
+           for k, s_ in (("tau", (1,)), ("gamma", (n,)), ("v0", (n, 3)))}
+    lbp.lbp_timing_enable(h, True)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    lbp.lbp_adjoint_backward(h, steps, g_v.contiguous(), None, out)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    adj_ms, adj_n = lbp.lbp_timing_read(h)
+    lbp.lbp_timing_enable(h, False)
+    lbp.lbp_destroy(h)
+    rec_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    avg = adj_ms / max(adj_n, 1)
+    ach = ADJ_BYTES_PER_NODE * w.nodes / (avg * 1e-3) / 1e9
+    return {"workload": w.name, "steps": steps, "checkpoint_every": checkpoint_every, "kT": kT,
+            "record_ms": rec_ms, "backward_ms": bwd_ms, "backward_over_record": bwd_ms / rec_ms,
+            "value": w.nodes * steps / (bwd_ms * 1e-3) / 1e6,
+            "unit": "MLUPS (adjoint steps incl. segment replay)",
+            "adjoint_lattice_ms": avg, "adjoint_lattice_launches": adj_n,
+            "bytes_per_node": ADJ_BYTES_PER_NODE, "achieved_gbs": ach, "frac": ach / measured_peaks()[0],
+            "dL_dtau": float(out["tau"][0])}
+
+
 # ---------------------------------------------------------------------------- GPU run
 def run_gpu(args, w):
     import torch
@@ -357,6 +404,15 @@ def run_gpu(args, w):
                                "frac": bach / measured_peaks()[0],
                                "particle_updates_per_s": world * e.n_particles * bsteps / (bms * 1e-3),
                                "autotune": btuned}
+
+        # the differentiable run: 64^3, 8 kicked particles, 2000 steps, checkpoint
+        # every 100; and the adjoint at 256^3 (population copies larger than L2)
+        wa = wl.ADJOINT_64
+        variants["adjoint_64"] = adjoint_variant(lbp, torch, wa, wl.kicked_particles(wa), wa.steps,
+                                                 wa.extra["checkpoint_every"], 0.0, 0)
+        wb = wl.BROWNIAN_256
+        variants["adjoint_256"] = adjoint_variant(lbp, torch, wb, wb.particles(), 100, 20, wb.kT,
+                                                  wb.seed_noise)
 
     if rank != 0:
         if dist:

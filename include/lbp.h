@@ -131,6 +131,12 @@ lbp_status lbp_destroy(lbp_sim *sim);
  * FP64).  Eq. 19 output state.                                                 */
 lbp_status lbp_set_populations(lbp_sim *sim, const double *f, int on_device);
 
+/* Fluid state from density and velocity fields: every node is set to the
+ * equilibrium of Eq. 17, f_a = f^eq_a(rho~, u), as the current post-collision
+ * populations.  rho: [N] (NULL: rho~ = 1), u: [3][N] (NULL: u = 0), FP64,
+ * host or device per on_device; N counts the nodes of all boxes of a batch.  */
+lbp_status lbp_set_fluid(lbp_sim *sim, const double *rho, const double *u, int on_device);
+
 /* Read the stored post-collision populations fhat into f ([15][nz][ny][nx]).  */
 lbp_status lbp_read_populations(lbp_sim *sim, double *f, int on_device);
 
@@ -219,6 +225,13 @@ lbp_status lbp_check(lbp_sim *sim);
  * nodes per lattice-kernel block (see lbp_autotune).  n = entries of out.    */
 lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
 
+/* Uniform body force density g = (gx, gy, gz) added on every node of box
+ * `replica` (-1: every box) in the collision, as the force term of Eqs. 18-19
+ * (3 w_a g.e_a per node, on top of the particles' reaction forces).  Used,
+ * e.g., to hold a mean flow against the drag of pinned particles.  Stored
+ * and applied in FP32.  Default 0.                                           */
+lbp_status lbp_set_body_force(lbp_sim *sim, int replica, const double *g);
+
 /* Block-shape autotuner of the fused stream-collide kernel.  Times the kernel
  * this handle's steps launch (with the particle coupling if it has particles)
  * on its own lattice for each candidate shape -- 1, 2 or 4 rows of 128 nodes
@@ -240,8 +253,10 @@ lbp_status lbp_set_block_rows(lbp_sim *sim, int rows);
 lbp_status lbp_set_use_graphs(lbp_sim *sim, int enable);
 
 /* Kernel timing: while enabled, lbp_step records CUDA events around every
- * launch of the stream-collide kernel; lbp_timing_read waits for them and
- * returns the summed duration (ms) and the number of launches since enable.   */
+ * launch of the stream-collide kernel, and lbp_adjoint_backward around every
+ * launch of the adjoint lattice kernel (not around its forward replay);
+ * lbp_timing_read waits for them and returns the summed duration (ms) and the
+ * number of launches since enable.                                           */
 lbp_status lbp_timing_enable(lbp_sim *sim, int enable);
 lbp_status lbp_timing_read(lbp_sim *sim, double *ms_total, int64_t *launches);
 

@@ -56,6 +56,7 @@ def lib():
         L.or_moments.argtypes = [_dp, _dp, _dp, C.c_int64]
         L.or_feq.argtypes = [C.c_double, _dp, _dp]
         L.or_collide.argtypes = [_dp, _dp, _dp, vp, C.c_double, C.c_int64, _dp]
+        L.or_set_body_force.argtypes = [vp, _dp]
         L.or_corners.argtypes = [_dp, _i32p, _dp, _dp]
         L.or_stokeslet_fit.argtypes = [_dp, _dp, _dp, C.c_double, C.c_int, _dp]
         L.or_stokeslet_fit.restype = C.c_double
@@ -243,6 +244,10 @@ class Sim:
         F = None if Fext is None else _c(Fext).reshape(-1)
         P = None if pinned is None else _c(pinned, np.uint8)
         lib().or_set_external(self._h, _ptr(F), _ptr(P))
+
+    def set_body_force(self, G):
+        """Uniform external force density on every node (the F of Eq. 18)."""
+        lib().or_set_body_force(self._h, _c(G).reshape(3))
 
     def set_particles(self, r=None, V=None):
         rr = None if r is None else _c(r).reshape(-1)

@@ -297,6 +297,7 @@ typedef struct {
     uint64_t seed;
     int mode, exclude_inside;
     int64_t step;
+    double G[3]; /* uniform body force density on every node (Eq. 18) */
 } or_sim;
 
 or_sim *or_create(int nx, int ny, int nz, double tau)
@@ -385,6 +386,13 @@ void or_set_external(or_sim *s, const double *Fext, const unsigned char *pinned)
     }
 }
 
+/* Uniform external force density on the fluid, added to F of Eq. 18 on every
+ * node (e.g. to hold a mean flow against the drag of a pinned particle). */
+void or_set_body_force(or_sim *s, const double *G)
+{
+    for (int k = 0; k < 3; ++k) s->G[k] = G[k];
+}
+
 void or_set_particles(or_sim *s, const double *r, const double *V)
 {
     if (r) memcpy(s->r, r, sizeof(double) * 3 * s->np);
@@ -409,7 +417,9 @@ static void one_step(or_sim *s)
     /* 1-2: streaming and moments of f^n */
     or_stream(s->fhat, s->f, nx, ny, nz);
     or_moments(s->f, s->rho, s->u, N);
-    memset(s->F, 0, sizeof(double) * 3 * N);
+    /* force density on the fluid: the uniform body force, then the particles' */
+    for (int k = 0; k < 3; ++k)
+        for (int64_t i = 0; i < N; ++i) s->F[k * N + i] = s->G[k];
 
     for (int i = 0; i < s->np; ++i) {
         double *r = s->r + 3 * i, *V = s->V + 3 * i;

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, const RepT
     }
 #pragma unroll
     for (int h = 0; h < R; ++h)
-        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, 0.f, 0.f, 0.f);
+        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, rp.gx, rp.gy, rp.gz);
 }
 
 // Sum, exactly in 64-bit fixed point, the record entries whose x is this
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw[h], 0) & 0xffffffffull);
-        float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+        float F0 = rp.gx, F1 = rp.gy, F2 = rp.gz;  // uniform body force of the box
         if (cnt > 0 && grp * R + h < nrows) {
             long long a0 = 0, a1 = 0, a2 = 0;
             record_sum(rw[h], cnt, x, a0, a1, a2);
@@ -226,9 +226,9 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
                 fq[2 * Ntot + d] = 0ull;
             }
             const float inv = 1.3877787807814457e-17f;  // 2^-56
-            F0 = inv * __ll2float_rn(a0);
-            F1 = inv * __ll2float_rn(a1);
-            F2 = inv * __ll2float_rn(a2);
+            F0 += inv * __ll2float_rn(a0);
+            F1 += inv * __ll2float_rn(a1);
+            F2 += inv * __ll2float_rn(a2);
         }
         if (act && grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, F0, F1, F2);
     }
@@ -371,6 +371,24 @@ __global__ void k_to_f64(const typename St::T *__restrict__ g, double *__restric
     }
 }
 
+// Eq. 17 at every node: g_a = f^eq_a(rho~, u) - w_a, computed in FP64 and
+// stored in the handle's storage type.  rho: [N] or null (1); u: [3][N] or null (0).
+template <typename St>
+__global__ void k_set_equilibrium(const double *__restrict__ rho, const double *__restrict__ u,
+                                  typename St::T *__restrict__ g, long long N, long long P) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double dr = rho ? rho[i] - 1.0 : 0.0;
+        const double ux = u ? u[i] : 0.0, uy = u ? u[N + i] : 0.0, uz = u ? u[2 * N + i] : 0.0;
+        const double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double eu = ex(a) * ux + ey(a) * uy + ez(a) * uz;
+            St::store(g + (long long)a * P + i, a, (float)(wgt(a) * (dr + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu)));
+        }
+    }
+}
+
 static unsigned grid_for(long long work, int threads, int num_sms) {
     long long g = (work + threads - 1) / threads;
     const long long cap = (long long)num_sms * 16;
@@ -389,6 +407,16 @@ cudaError_t launch_from_f64(Sim &s, const double *f, void *dst, cudaStream_t st)
         using St = decltype(tag);
         k_from_f64<St><<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(
             f, static_cast<typename St::T *>(dst), s.N, s.P);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_set_equilibrium(Sim &s, const double *rho, const double *u, void *dst,
+                                   cudaStream_t st) {
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_set_equilibrium<St><<<grid_for(s.N, 256, s.num_sms), 256, 0, st>>>(
+            rho, u, static_cast<typename St::T *>(dst), s.N, s.P);
         return cudaGetLastError();
     });
 }

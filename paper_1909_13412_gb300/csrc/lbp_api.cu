@@ -266,6 +266,7 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
         rp.node_off = noff;
         rp.seg_off = soff;
         rp.omega = (float)(1.0 / d.tau);
+        rp.gx = rp.gy = rp.gz = 0.f;
         rp.pad = 0;
         s->taus[r] = d.tau;
         noff += (long long)d.nx * d.ny * d.nz;
@@ -362,6 +363,30 @@ lbp_status lbp_set_populations(lbp_sim *s, const double *f, int on_device) {
         TRY(stage(s, sizeof(double) * Q * s->N));
         CK(cudaMemcpyAsync(s->stage, f, sizeof(double) * Q * s->N, cudaMemcpyHostToDevice, s->s0));
         CK(launch_from_f64(*s, s->stage, dst, s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    }
+    return leave(s);
+}
+
+lbp_status lbp_set_fluid(lbp_sim *s, const double *rho, const double *u, int on_device) {
+    CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
+    TRY(enter(s));
+    void *dst = s->f[s->cur];
+    if (on_device || (!rho && !u)) {
+        CK(launch_set_equilibrium(*s, rho, u, dst, s->s0));
+    } else {
+        TRY(stage(s, sizeof(double) * 4 * s->N));
+        const double *dr = nullptr, *du = nullptr;
+        if (rho) {
+            CK(cudaMemcpyAsync(s->stage, rho, sizeof(double) * s->N, cudaMemcpyHostToDevice, s->s0));
+            dr = s->stage;
+        }
+        if (u) {
+            CK(cudaMemcpyAsync(s->stage + s->N, u, sizeof(double) * 3 * s->N, cudaMemcpyHostToDevice, s->s0));
+            du = s->stage + s->N;
+        }
+        CK(launch_set_equilibrium(*s, dr, du, dst, s->s0));
         CK(cudaStreamSynchronize(s->s0));
     }
     return leave(s);
@@ -818,6 +843,26 @@ lbp_status lbp_vacf_read_per_particle(lbp_sim *s, double *csum, int64_t *counts,
     return vacf_read_impl(s, csum, counts, on_device, s->np);
 }
 
+lbp_status lbp_set_body_force(lbp_sim *s, int replica, const double *g) {
+    CHECK_SIM(s);
+    s->edits += 1;  // invalidates an adjoint recording
+    if (!g) return fail(LBP_EINVAL, "lbp_set_body_force: null g");
+    if (replica < -1 || replica >= s->nrep)
+        return fail(LBP_EINVAL, "lbp_set_body_force: replica %d outside [-1, %d)", replica, s->nrep);
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(g[k])) return fail(LBP_EINVAL, "lbp_set_body_force: non-finite component");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    for (int r = 0; r < s->nrep; ++r)
+        if (replica < 0 || r == replica) {
+            s->reps[r].gx = (float)g[0];
+            s->reps[r].gy = (float)g[1];
+            s->reps[r].gz = (float)g[2];
+        }
+    drop_graphs(s);  // the graphs hold the replica table by value
+    return leave(s);
+}
+
 lbp_status lbp_set_block_rows(lbp_sim *s, int rows) {
     CHECK_SIM(s);
     if (rows != 1 && rows != 2 && rows != 4) return fail(LBP_EINVAL, "lbp_set_block_rows: rows must be 1, 2 or 4");
@@ -1073,7 +1118,16 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
             const double *rj = seg_p + (size_t)j * pcount, *vj = rj + 3 * cap;
             ADJ_CK(launch_adj_particles(*s, src, lc, rj, vj, tp.step0 + n, gv ? gv + (size_t)n * np * 3 : nullptr,
                                         gr ? gr + (size_t)n * np * 3 : nullptr, lam_v, lam_r, acc, q, s->s0));
+            const bool timed = s->timing && e == cudaSuccess;
+            if (timed) {
+                if (s->ntimed == lbp::Sim::MAX_TIMED && fold_timing(s) != LBP_OK) e = cudaErrorUnknown;
+                ADJ_CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
+            }
             ADJ_CK(launch_adj_lattice(*s, src, lc, ln, q, acc_om, s->s0));
+            if (timed) {
+                ADJ_CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
+                if (e == cudaSuccess) s->ntimed += 1;
+            }
             L ^= 1;
         }
     }

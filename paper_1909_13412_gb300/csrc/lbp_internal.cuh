@@ -127,6 +127,7 @@ struct Rep {
     long long node_off;       // first global node of the box
     long long seg_off;        // first global force-record segment
     float omega;              // 1 / tau
+    float gx, gy, gz;         // uniform body force density on every node of the box (Eq. 18)
     int pad;
 };
 
@@ -271,6 +272,8 @@ cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int
 cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st);
 cudaError_t launch_from_f64(Sim &s, const double *f, void *dst, cudaStream_t st);
 cudaError_t launch_to_f64(Sim &s, const void *src, double *f, cudaStream_t st);
+cudaError_t launch_set_equilibrium(Sim &s, const double *rho, const double *u, void *dst,
+                                   cudaStream_t st);
 cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, double *p,
                           cudaStream_t st);
 // particle_kernels.cu

@@ -70,6 +70,8 @@ _SIGS = {
     "lbp_adjoint_record": [_vp, C.c_int64, C.c_int, _vp, _vp, C.c_int],
     "lbp_adjoint_backward": [_vp, _vp, _vp, C.c_int, _vp],
     "lbp_set_block_rows": [_vp, C.c_int],
+    "lbp_set_body_force": [_vp, C.c_int, _vp],
+    "lbp_set_fluid": [_vp, _vp, _vp, C.c_int],
     "lbp_vacf_read_per_particle": [_vp, _vp, _vp, C.c_int],
     "lbp_check": [_vp],
     "lbp_set_use_graphs": [_vp, C.c_int],
@@ -241,6 +243,14 @@ def lbp_set_populations(h: Handle, f):
     _call("lbp_set_populations", h.ptr, p, d)
 
 
+def lbp_set_fluid(h: Handle, rho=None, u=None):
+    """Set every node to f^eq(rho~, u) (Eq. 17); rho [N], u [3, N] FP64 or None."""
+    a = _ptr(rho, np.float64, h.N, "rho")
+    b = _ptr(u, np.float64, 3 * h.N, "u")
+    d = _same_side(a, b)
+    _call("lbp_set_fluid", h.ptr, a[0], b[0], d)
+
+
 def lbp_read_populations(h: Handle, f):
     p, d = _ptr(f, np.float64, Q * h.N, "f", writable=True)
     _call("lbp_read_populations", h.ptr, p, d)
@@ -389,6 +399,11 @@ def lbp_diagnostics(h: Handle):
     _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 4)
     return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2]),
             "rows_per_block": int(out[3])}
+
+
+def lbp_set_body_force(h: Handle, g, replica=-1):
+    arr = (C.c_double * 3)(*[float(x) for x in g])
+    _call("lbp_set_body_force", h.ptr, int(replica), C.cast(arr, C.c_void_p))
 
 
 def lbp_set_block_rows(h: Handle, rows):

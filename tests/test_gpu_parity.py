@@ -262,6 +262,53 @@ def test_coupled_brownian_particles(mode, exclude):
     lbp.lbp_check(h)
 
 
+def test_set_fluid_is_the_equilibrium_of_eq17():
+    """lbp_set_fluid(rho, u) sets f = f^eq(rho~, u) at every node (oracle's Eq. 17)."""
+    shape = (5, 6, 7)
+    nz, ny, nx = shape
+    N = nx * ny * nz
+    g = np.random.default_rng(4)
+    rho = 1.0 + 0.01 * g.uniform(-1, 1, N)
+    u = 0.02 * g.uniform(-1, 1, (3, N))
+    h = gpu_sim(shape, 0.8)
+    lbp.lbp_set_fluid(h, rho, u)
+    f = gpu_pops(h).reshape(15, N)
+    want = np.stack([oracle.feq(rho[i], u[:, i]) for i in range(N)], axis=1)
+    assert np.max(np.abs(f - want)) <= 1e-7 * np.max(np.abs(want - W[:, None]))
+    lbp.lbp_set_fluid(h, None, None)
+    assert np.array_equal(gpu_pops(h), np.broadcast_to(W4, (15,) + shape))
+    lbp.lbp_destroy(h)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_uniform_body_force_with_pinned_particle(graphs):
+    """Eq. 18 with a uniform body force on every node plus a pinned particle's
+    reaction force: a uniform flow driven past a held sphere, 80 steps."""
+    shape = (12, 13, 15)
+    ps = wl.uniform_particles(3, shape, 10.0, 0.5, wl.stokes_radius(0.5, 0.6), 0.0, 5, 6)
+    G = np.array([2e-6, -1e-6, 5e-7])
+    pinned = np.array([1, 0, 0], np.uint8)
+    h = gpu_sim(shape, 0.6, ps, graphs=graphs)
+    o = oracle_sim(shape, 0.6, ps)
+    lbp.lbp_set_body_force(h, G)
+    o.set_body_force(G)
+    lbp.lbp_particles_set_external_force(h, None, pinned)
+    o.set_external(None, pinned)
+    lbp.lbp_step(h, 80)
+    o.step(80)
+    r, V, FH, FR = gpu_particles(h)
+    ro, Vo, FHo, FRo = o.particles()
+    assert np.array_equal(r[0], ps.r[0]) and np.array_equal(V[0], ps.V[0])
+    assert np.max(np.abs(V - Vo)) <= 1e-5 * np.max(np.abs(Vo))
+    assert np.max(np.abs(FH - FHo)) <= 1e-5 * np.max(np.abs(FHo))
+    fo = o.fhat()
+    assert np.max(np.abs(gpu_pops(h) - fo)) <= 1e-5 * dev_scale(fo) + F64_FLOOR
+    # the body force did drive a flow: mean momentum close to 80 G less the drag
+    rho, u, _ = o.fields()
+    assert np.all(np.sign(u.reshape(3, -1).mean(1)) == np.sign(G))
+    lbp.lbp_check(h)
+
+
 @pytest.mark.parametrize("shape,n", [((3, 4, 5), 60), ((6, 5, 130), 400)])
 def test_dense_particles_overflow_the_force_records(shape, n):
     """Many particles per 128-node row segment: shares beyond a segment's 8

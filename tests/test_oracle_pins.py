@@ -445,3 +445,19 @@ def test_long_time_tail_amplitude():
     # a power law (an exponential exp(-gamma t / M) of Eq. 6 would be ~1e-9 here);
     # the finite box steepens it slightly beyond -3/2
     assert -1.85 < slope < -1.35
+
+
+def test_uniform_body_force_adds_its_momentum_every_step():
+    """Eqs. 18-19: a uniform force density G on every node adds exactly G of
+    momentum per node and step to a uniform fluid, and no mass."""
+    nx, ny, nz, n = 6, 5, 4, 7
+    o = oracle.Sim(nx, ny, nz, 0.7)
+    G = np.array([1.5e-5, -2.0e-5, 0.7e-5])
+    o.set_body_force(G)
+    o.step(n)
+    f = o.fhat()
+    E, _ = oracle.d3q15()
+    mom = np.einsum("ak,azyx->kzyx", E.astype(float), f)
+    assert np.allclose(mom, n * G[:, None, None, None], rtol=0, atol=1e-15)
+    assert np.allclose(f.sum(0), 1.0, rtol=0, atol=1e-14)
+    o.close()
