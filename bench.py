@@ -51,7 +51,7 @@ LAUNCHES_PER_STEP = 2  # particles, stream-collide (+2 VACF kernels every 64 ste
 
 def workload(name):
     return {"brownian_256": wl.BROWNIAN_256, "brownian_128": wl.BROWNIAN_128,
-            "brownian_64": wl.BROWNIAN_64, "profile_128": wl.PROFILE_128,
+            "brownian_64": wl.BROWNIAN_64, "profile_128": wl.PROFILE_128, "profile_192": wl.PROFILE_192,
             "ensemble_68": wl.ENSEMBLE_68}[name]
 
 
@@ -318,8 +318,10 @@ def run_gpu(args, w):
     def make(precision, wk=w):
         h = make_handle(lbp, wk, precision, wk.seed_noise + rank, args.vacf_lag)
         # block shape of the lattice kernel, picked by timing (outside the timed region)
-        rows, tms = lbp.lbp_autotune(h, 10)
-        h.tuned = {"rows_per_block": rows, "ms_by_rows": dict(zip((1, 2, 4), tms))}
+        rows, pair, tms = lbp.lbp_autotune(h, 10)
+        h.tuned = {"rows_per_block": rows, "nodes_per_thread": pair + 1,
+                   "ms_by_shape": {f"{n}x{r}": t for (n, r), t in
+                                   zip(((1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4)), tms) if t > 0}}
         return h
 
     def timed(h, steps, warmup, clocks=None):

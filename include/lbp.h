@@ -222,7 +222,8 @@ lbp_status lbp_check(lbp_sim *sim);
  * and took the overflow path (both counts are implementation details of the
  * force accumulation; the results do not depend on them), out[1] = capacity of
  * a record in shares, out[2] = number of row segments, out[3] = rows of 128
- * nodes per lattice-kernel block (see lbp_autotune).  n = entries of out.    */
+ * nodes per lattice-kernel block, out[4] = nodes per thread of that kernel
+ * (see lbp_autotune).  n = entries of out.                                   */
 lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
 
 /* Uniform body force density g = (gx, gy, gz) added on every node of box
@@ -235,18 +236,26 @@ lbp_status lbp_set_body_force(lbp_sim *sim, int replica, const double *g);
 /* Block-shape autotuner of the fused stream-collide kernel.  Times the kernel
  * this handle's steps launch (with the particle coupling if it has particles)
  * on its own lattice for each candidate shape -- 1, 2 or 4 rows of 128 nodes
- * per block of 128 threads -- as `launches` back-to-back launches (1..1000)
- * after two warm-up launches, twice, and keeps the shape with the smallest
- * mean launch time for all later steps.  rows (optional) receives the chosen
- * rows per block; ms (optional, 3 doubles) the mean launch times in ms for
- * 1, 2 and 4 rows.  The simulation state is unchanged: the launches read the
- * current populations, write only the buffer the next step overwrites, see an
- * all-zero copy of the force records and bump a scratch step counter.
- * Synchronous.  The default before any call: 1 row for LBP_F32, 2 otherwise. */
-lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, double *ms);
+ * per block, each with one node per thread (128-thread blocks) and, for the
+ * 2-byte storage types when every box has an even nx, with two neighbouring
+ * nodes per thread (64-thread blocks, 4-byte loads and stores) -- as
+ * `launches` back-to-back launches (1..1000) after two warm-up launches,
+ * twice, and keeps the shape with the smallest mean launch time for all later
+ * steps.  rows, pair (optional) receive the chosen rows per block and nodes
+ * per thread minus one; ms (optional, 6 doubles) the mean launch times in ms
+ * for (one node per thread: 1, 2, 4 rows; two nodes: 1, 2, 4 rows), -1 where
+ * a shape does not apply.  The simulation state is unchanged: the launches
+ * read the current populations, write only the buffer the next step
+ * overwrites, see an all-zero copy of the force records and bump a scratch
+ * step counter.  Synchronous.  Defaults before any call: two nodes per thread
+ * and 1 row where that applies, else 1 row for LBP_F32 and 2 rows otherwise. */
+lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, int *pair, double *ms);
 
-/* Fix the rows per block by hand (1, 2 or 4; else LBP_EINVAL).  Results do
- * not depend on it: each node's arithmetic is the same for every shape.     */
+/* Fix the block shape by hand: rows per block 1, 2 or 4 and pair = 1 for two
+ * nodes per thread (LBP_EINVAL where that does not apply).  Results do not
+ * depend on the shape: each node's arithmetic is the same for every shape.
+ * lbp_set_block_rows changes the rows only.                                   */
+lbp_status lbp_set_block_shape(lbp_sim *sim, int rows, int pair);
 lbp_status lbp_set_block_rows(lbp_sim *sim, int rows);
 
 /* Use CUDA graphs for lbp_step (default 1).                                  */

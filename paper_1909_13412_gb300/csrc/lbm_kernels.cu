@@ -41,11 +41,11 @@ struct Planes {
     typename St::T *d[Q];
 };
 
-// collision of one node and the store of its 15 post-collision deviations;
-// (F0, F1, F2) is the body force of Eq. 18 at the node (zero if none)
-template <typename St>
-__device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
-                                              float omega, float F0, float F1, float F2) {
+// collision of one node: the 15 post-collision deviations of the node whose
+// pulled deviations are g; (F0, F1, F2) is the body force of Eq. 18 at the
+// node (zero if none)
+__device__ __forceinline__ void collide_values(const float g[Q], float omega, float F0, float F1,
+                                               float F2, float o[Q]) {
     float drho = 0.f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) drho += g[a];
@@ -56,16 +56,16 @@ __device__ __forceinline__ void collide_store(const float g[Q], const Planes<St>
     const float uz = (g[5] - g[6]) + c78 - c910 + c1112 + c1314;
     const float base = drho - 1.5f * (ux * ux + uy * uy + uz * uz);
     const float om1 = 1.f - omega;
-    St::store(pl.d[0] + d, 0, om1 * g[0] + omega * ((2.f / 9.f) * base));
+    o[0] = om1 * g[0] + omega * ((2.f / 9.f) * base);
     // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, weight W
-#define LBP_PAIR(A, W, EU, FE)                                         \
-    {                                                                  \
-        const float eu = (EU);                                         \
-        const float sym = (W) * (base + 4.5f * eu * eu);               \
-        const float anti = (3.f * (W)) * eu;                           \
-        const float fe = (3.f * (W)) * (FE);                           \
-        St::store(pl.d[A] + d, A, om1 * g[A] + omega * (sym + anti) + fe);         \
-        St::store(pl.d[A + 1] + d, A + 1, om1 * g[A + 1] + omega * (sym - anti) - fe); \
+#define LBP_PAIR(A, W, EU, FE)                                \
+    {                                                         \
+        const float eu = (EU);                                \
+        const float sym = (W) * (base + 4.5f * eu * eu);      \
+        const float anti = (3.f * (W)) * eu;                  \
+        const float fe = (3.f * (W)) * (FE);                  \
+        o[A] = om1 * g[A] + omega * (sym + anti) + fe;        \
+        o[A + 1] = om1 * g[A + 1] + omega * (sym - anti) - fe; \
     }
     LBP_PAIR(1, 1.f / 9.f, ux, F0)
     LBP_PAIR(3, 1.f / 9.f, uy, F1)
@@ -75,6 +75,15 @@ __device__ __forceinline__ void collide_store(const float g[Q], const Planes<St>
     LBP_PAIR(11, 1.f / 72.f, ux - uy + uz, F0 - F1 + F2)
     LBP_PAIR(13, 1.f / 72.f, -ux + uy + uz, -F0 + F1 + F2)
 #undef LBP_PAIR
+}
+
+template <typename St>
+__device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
+                                              float omega, float F0, float F1, float F2) {
+    float o[Q];
+    collide_values(g, omega, F0, F1, F2, o);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) St::store(pl.d[a] + d, a, o[a]);
 }
 
 // Index arithmetic shared by both variants: node d of (x, row) and the
@@ -234,6 +243,143 @@ __global__ void __launch_bounds__(BX) k_stream_collide_forced(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Paired-node variant for the 2-byte storage types (every box with even nx).
+// A thread owns two neighbouring nodes (x, x + 1), x even, and moves each
+// plane's pair of 2-byte deviations with one 4-byte load and one 4-byte store;
+// a 64-thread block covers one SEG-node segment of R rows.  The pull streaming
+// in x is done in registers: for e_x = +1 the pair (x - 1, x) is the high
+// half of the left lane's pair and the low half of the lane's own, for
+// e_x = -1 the pair (x + 1, x + 2) is the high half of its own and the low
+// half of the right lane's (warp shuffles); the lanes at a warp's or a row's
+// end load the neighbouring pair themselves (periodic in x).  This halves the
+// load and store instructions per node and leaves the conversions packed, so
+// the kernel is no longer bound by instruction issue.  Per node the
+// arithmetic is that of collide_values: results equal the one-node kernels'
+// bit for bit.
+// ---------------------------------------------------------------------------
+template <typename St>
+__device__ __forceinline__ void unpack2(unsigned v, int a, float &lo, float &hi);
+template <>
+__device__ __forceinline__ void unpack2<StoreBF16>(unsigned v, int, float &lo, float &hi) {
+    lo = __uint_as_float(v << 16);
+    hi = __uint_as_float(v & 0xffff0000u);
+}
+template <>
+__device__ __forceinline__ void unpack2<StoreF16>(unsigned v, int a, float &lo, float &hi) {
+    const float sc = wgtf(a) * (1.f / F16_SCALE);
+    lo = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))) * sc;
+    hi = __half2float(__ushort_as_half((unsigned short)(v >> 16))) * sc;
+}
+template <typename St>
+__device__ __forceinline__ unsigned pack2(float lo, float hi, int a);
+template <>
+__device__ __forceinline__ unsigned pack2<StoreBF16>(float lo, float hi, int) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&p);
+}
+template <>
+__device__ __forceinline__ unsigned pack2<StoreF16>(float lo, float hi, int a) {
+    const float sc = F16_SCALE / wgtf(a);
+    const __half2 p = __floats2half2_rn(lo * sc, hi * sc);
+    return *reinterpret_cast<const unsigned *>(&p);
+}
+
+constexpr int PAIR_BX = SEG / 2;  // threads per block of the paired kernel
+
+template <typename St, int R, int MAXR, bool FORCED>
+__global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
+    Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
+    const int r = find_block_rep(rt, blockIdx.x);
+    const Rep &rp = rt.rep[r];
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
+    const unsigned nrows = (unsigned)ny * (unsigned)nz;
+    const int lane = threadIdx.x & 31;
+    const unsigned item = blockIdx.x - rt.item_off[r];
+    const unsigned grp = item / (unsigned)nchunks;
+    const int chunk = (int)(item - grp * (unsigned)nchunks);
+    const size_t seg0 = (size_t)rp.seg_off;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+    if (FORCED && threadIdx.x < R && grp * R + threadIdx.x < nrows)
+        rec_prev[(seg0 + (size_t)(grp * R + threadIdx.x) * nchunks + chunk) * REC_WORDS] = 0ull;
+    const int xw = chunk * SEG + 2 * (threadIdx.x & ~31);  // first node of the warp
+    if (xw >= nx) return;
+    const int x0 = xw + 2 * lane;
+    const bool act = x0 < nx;
+    const int x = act ? x0 : nx - 2;       // even; inactive lanes read a valid pair
+    const int xl = x == 0 ? nx - 2 : x - 2;  // left and right pairs, periodic
+    const int xr = x + 2 == nx ? 0 : x + 2;
+    const bool own_left = lane == 0;               // no left lane in the warp
+    const bool own_right = lane == 31 || x0 + 2 >= nx;  // no (active) right lane
+    const int base = (int)rp.node_off;
+    float g[R][2][Q];
+    unsigned long long rw[R];
+    int drow[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
+        const NodeIdx n = node_index(0, row, nx, ny, nz);
+        drow[h] = base + n.d;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int rb = drow[h] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1];  // source row start
+            const unsigned *src = reinterpret_cast<const unsigned *>(pl.s[a] + rb);
+            const unsigned v = __ldg(src + (x >> 1));
+            unsigned w = v;
+            if (ex(a) > 0) {
+                // pull from x - 1: (x - 1, x) = (hi of left pair, lo of own)
+                unsigned left = __shfl_up_sync(0xffffffffu, v, 1);
+                if (own_left) left = __ldg(src + (xl >> 1));
+                w = __byte_perm(left, v, 0x5432);
+            } else if (ex(a) < 0) {
+                // pull from x + 1: (x + 1, x + 2) = (hi of own, lo of right pair)
+                unsigned right = __shfl_down_sync(0xffffffffu, v, 1);
+                if (own_right) right = __ldg(src + (xr >> 1));
+                w = __byte_perm(v, right, 0x5432);
+            }
+            unpack2<St>(w, a, g[h][0][a], g[h][1][a]);
+        }
+        if (FORCED) rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        float F[2][3] = {{rp.gx, rp.gy, rp.gz}, {rp.gx, rp.gy, rp.gz}};
+        if (FORCED) {
+            const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw[h], 0) & 0xffffffffull);
+            if (cnt > 0 && grp * R + h < nrows) {
+                long long s0[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
+                record_sum(rw[h], cnt, x, s0[0], s0[1], s0[2]);
+                record_sum(rw[h], cnt, x + 1, s1[0], s1[1], s1[2]);
+                if (cnt > REC_SLOTS && act) {
+                    const int d = drow[h] + x;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        s0[k] += (long long)fq[k * Ntot + d];
+                        s1[k] += (long long)fq[k * Ntot + d + 1];
+                        fq[k * Ntot + d] = 0ull;
+                        fq[k * Ntot + d + 1] = 0ull;
+                    }
+                }
+                const float inv = 1.3877787807814457e-17f;  // 2^-56
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    F[0][k] += inv * __ll2float_rn(s0[k]);
+                    F[1][k] += inv * __ll2float_rn(s1[k]);
+                }
+            }
+        }
+        if (act && grp * R + h < nrows) {
+            float o0[Q], o1[Q];
+            collide_values(g[h][0], rp.omega, F[0][0], F[0][1], F[0][2], o0);
+            collide_values(g[h][1], rp.omega, F[1][0], F[1][1], F[1][2], o1);
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                reinterpret_cast<unsigned *>(pl.d[a] + drow[h])[x >> 1] = pack2<St>(o0[a], o1[a], a);
+        }
+    }
+}
+
 constexpr int SC_BX = SEG;
 
 cudaError_t prepare_lbm_kernels() { return cudaSuccess; }
@@ -298,25 +444,59 @@ static cudaError_t by_batch(const Sim &s, int R, F &&f) {
     return f(rep_table<MAX_BATCH>(s, R));
 }
 
-cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
-                                      int rows, cudaStream_t st) {
+bool pair_kernel_ok(const Sim &s) {
+    if (s.precision == LBP_F32) return false;
+    for (int r = 0; r < s.nrep; ++r)
+        if (s.reps[r].nx % 2) return false;
+    return true;
+}
+
+// the paired-node kernel (2-byte storage, even nx) or the one-node kernel
+template <bool FORCED>
+static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned long long *rec_cur,
+                             unsigned long long *rec_prev, long long *bump, int rows, int pair,
+                             cudaStream_t st) {
     constexpr int BX = SC_BX;
+    const bool use_pair = pair && pair_kernel_ok(s);
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
         return by_rows(rows, [&](auto rc) {
             constexpr int R = decltype(rc)::value;
             return by_batch(s, R, [&](const auto &rt) {
                 constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
-                k_stream_collide<BX, St, R, MAXR><<<rt.item_off[rt.nrep], BX, 0, st>>>(
-                    planes_of<St>(s, src, dst), rt, bump);
+                const unsigned grid = rt.item_off[rt.nrep];
+                if constexpr (!std::is_same<St, StoreF32>::value) {
+                    if (use_pair) {
+                        k_stream_collide_pair<St, R, MAXR, FORCED><<<grid, PAIR_BX, 0, st>>>(
+                            planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                        return cudaGetLastError();
+                    }
+                }
+                if constexpr (FORCED)
+                    k_stream_collide_forced<BX, St, R, MAXR><<<grid, BX, 0, st>>>(
+                        planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                else
+                    k_stream_collide<BX, St, R, MAXR><<<grid, BX, 0, st>>>(planes_of<St>(s, src, dst), rt, bump);
                 return cudaGetLastError();
             });
         });
     });
 }
 
+cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
+                                      int rows, int pair, cudaStream_t st) {
+    return launch_sc<false>(s, src, dst, nullptr, nullptr, bump, rows, pair, st);
+}
+
+cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
+                                             const unsigned long long *rec_cur,
+                                             unsigned long long *rec_prev, long long *bump, int rows,
+                                             int pair, cudaStream_t st) {
+    return launch_sc<true>(s, src, dst, rec_cur, rec_prev, bump, rows, pair, st);
+}
+
 cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st) {
-    return launch_stream_collide_cfg(s, src, dst, s.d_step, s.rows, st);
+    return launch_stream_collide_cfg(s, src, dst, s.d_step, s.rows, s.pair, st);
 }
 
 cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
@@ -341,7 +521,7 @@ cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st) {
     return launch_stream_collide_forced_cfg(s, src, dst, s.rec[parity], s.rec[parity ^ 1], s.d_step,
-                                            s.rows, st);
+                                            s.rows, s.pair, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -280,7 +280,8 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     s->nseg = nseg;
     s->tau = descs[0].tau;
     s->precision = descs[0].precision;
-    s->rows = default_rows_per_block(s->precision);
+    s->pair = pair_kernel_ok(*s) ? 1 : 0;
+    s->rows = s->pair ? 1 : default_rows_per_block(s->precision);
     s->user = (cudaStream_t)stream;
     s->sqrt3 = std::sqrt(3.0);
     auto bail = [&](lbp_status st) {
@@ -863,29 +864,40 @@ lbp_status lbp_set_body_force(lbp_sim *s, int replica, const double *g) {
     return leave(s);
 }
 
-lbp_status lbp_set_block_rows(lbp_sim *s, int rows) {
+lbp_status lbp_set_block_shape(lbp_sim *s, int rows, int pair) {
     CHECK_SIM(s);
-    if (rows != 1 && rows != 2 && rows != 4) return fail(LBP_EINVAL, "lbp_set_block_rows: rows must be 1, 2 or 4");
+    if (rows != 1 && rows != 2 && rows != 4) return fail(LBP_EINVAL, "lbp_set_block_shape: rows must be 1, 2 or 4");
+    if (pair != 0 && pair != 1) return fail(LBP_EINVAL, "lbp_set_block_shape: pair must be 0 or 1");
+    if (pair && !pair_kernel_ok(*s))
+        return fail(LBP_EINVAL, "lbp_set_block_shape: two nodes per thread needs 2-byte storage and even nx in every box");
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
     s->rows = rows;
+    s->pair = pair;
     drop_graphs(s);
     return leave(s);
 }
 
-lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, double *ms) {
+lbp_status lbp_set_block_rows(lbp_sim *s, int rows) {
+    CHECK_SIM(s);
+    return lbp_set_block_shape(s, rows, s->pair && pair_kernel_ok(*s) ? 1 : 0);
+}
+
+lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *pair, double *ms) {
     CHECK_SIM(s);
     if (launches < 1 || launches > 1000) return fail(LBP_EINVAL, "lbp_autotune: launches must be in [1, 1000]");
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
-    static const int cand[3] = {1, 2, 4};
+    static const int cand_r[3] = {1, 2, 4};
+    const int npair = pair_kernel_ok(*s) ? 2 : 1;
     // scratch: two all-zero force-record copies (no force anywhere, so the
     // dense overflow accumulator is never read) and a step counter to bump
     const size_t rec_words = s->np > 0 ? (size_t)s->nseg * REC_WORDS : 0;
     unsigned long long *scr = nullptr;
     TRY(dalloc(&scr, 2 * rec_words + 1));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double t[3] = {0.0, 0.0, 0.0};
+    double t[6];
+    for (int c = 0; c < 6; ++c) t[c] = -1.0;
     cudaError_t e = cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (2 * rec_words + 1), s->s0);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -894,34 +906,38 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, double *ms) {
     // step overwrites whole: the handle's state is unchanged
     const void *src = s->f[s->cur];
     void *dst = s->f[s->cur ^ 1];
-    auto one = [&](int R) {
-        return s->np > 0 ? launch_stream_collide_forced_cfg(*s, src, dst, scr, scr + rec_words, bump, R, s->s0)
-                         : launch_stream_collide_cfg(*s, src, dst, bump, R, s->s0);
+    auto one = [&](int R, int P) {
+        return s->np > 0 ? launch_stream_collide_forced_cfg(*s, src, dst, scr, scr + rec_words, bump, R, P, s->s0)
+                         : launch_stream_collide_cfg(*s, src, dst, bump, R, P, s->s0);
     };
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass)
-        for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = one(cand[c]);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, s->s0);
-            for (int l = 0; l < launches && e == cudaSuccess; ++l) e = one(cand[c]);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s->s0);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float el = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
-            const double per = (double)el / launches;
-            if (e == cudaSuccess) t[c] = pass == 0 ? per : std::min(t[c], per);
-        }
+        for (int P = 0; P < npair && e == cudaSuccess; ++P)
+            for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+                for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = one(cand_r[c], P);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s->s0);
+                for (int l = 0; l < launches && e == cudaSuccess; ++l) e = one(cand_r[c], P);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s->s0);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float el = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
+                const double per = (double)el / launches;
+                const int k = 3 * P + c;
+                if (e == cudaSuccess) t[k] = pass == 0 ? per : std::min(t[k], per);
+            }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(scr);
     if (e != cudaSuccess) return fail(LBP_ECUDA, "lbp_autotune: %s", cudaGetErrorString(e));
     int best = 0;
-    for (int c = 1; c < 3; ++c)
-        if (t[c] < t[best]) best = c;
-    s->rows = cand[best];
+    for (int k = 1; k < 3 * npair; ++k)
+        if (t[k] < t[best]) best = k;
+    s->rows = cand_r[best % 3];
+    s->pair = best / 3;
     drop_graphs(s);
     if (rows) *rows = s->rows;
+    if (pair) *pair = s->pair;
     if (ms)
-        for (int c = 0; c < 3; ++c) ms[c] = t[c];
+        for (int k = 0; k < 6; ++k) ms[k] = t[k];
     return leave(s);
 }
 
@@ -1198,7 +1214,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
     CHECK_SIM(s);
     if (n < 0 || (n > 0 && !out)) return fail(LBP_EINVAL, "lbp_diagnostics: bad output");
     CK(cudaStreamSynchronize(s->s0));
-    int64_t v[4] = {0, REC_SLOTS, s->nseg, s->rows};
+    int64_t v[5] = {0, REC_SLOTS, s->nseg, s->rows, (int64_t)(s->pair && pair_kernel_ok(*s) ? 2 : 1)};
     if (s->rec[0]) {
         // shares beyond the slots of the records of the last completed step
         std::vector<unsigned long long> words((size_t)s->nseg * REC_WORDS);
@@ -1209,7 +1225,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
             if (c > REC_SLOTS) v[0] += c - REC_SLOTS;
         }
     }
-    for (int i = 0; i < n && i < 4; ++i) out[i] = v[i];
+    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
     return LBP_OK;
 }
 

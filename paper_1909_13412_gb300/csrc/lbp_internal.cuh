@@ -189,6 +189,7 @@ struct Sim {
     double tau = 1.0;
     int precision = LBP_F32;
     int rows = 1;  // rows of SEG nodes per lattice-kernel block (1, 2 or 4)
+    int pair = 1;  // two nodes per thread (2-byte storage, even nx) or one
     int dev = 0;
     int num_sms = 0;
 
@@ -261,12 +262,13 @@ cudaError_t prepare_lbm_kernels();
 cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st);
 // the lattice kernels with an explicit step counter, force records and rows per block
 cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
-                                      int rows, cudaStream_t st);
+                                      int rows, int pair, cudaStream_t st);
 cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
                                              const unsigned long long *rec_cur,
                                              unsigned long long *rec_prev, long long *bump, int rows,
-                                             cudaStream_t st);
+                                             int pair, cudaStream_t st);
 int default_rows_per_block(int precision);
+bool pair_kernel_ok(const Sim &s);  // 2-byte storage and every box with even nx
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st);
 cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st);

@@ -66,7 +66,8 @@ _SIGS = {
     "lbp_vacf_configure": [_vp, C.c_int],
     "lbp_vacf_read": [_vp, _vp, _vp, C.c_int],
     "lbp_vacf_configure_ex": [_vp, C.c_int, C.c_int],
-    "lbp_autotune": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "lbp_autotune": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "lbp_set_block_shape": [_vp, C.c_int, C.c_int],
     "lbp_adjoint_record": [_vp, C.c_int64, C.c_int, _vp, _vp, C.c_int],
     "lbp_adjoint_backward": [_vp, _vp, _vp, C.c_int, _vp],
     "lbp_set_block_rows": [_vp, C.c_int],
@@ -395,10 +396,10 @@ def lbp_check(h: Handle):
 
 
 def lbp_diagnostics(h: Handle):
-    out = np.zeros(4, np.int64)
-    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 4)
+    out = np.zeros(5, np.int64)
+    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 5)
     return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2]),
-            "rows_per_block": int(out[3])}
+            "rows_per_block": int(out[3]), "nodes_per_thread": int(out[4])}
 
 
 def lbp_set_body_force(h: Handle, g, replica=-1):
@@ -411,11 +412,17 @@ def lbp_set_block_rows(h: Handle, rows):
 
 
 def lbp_autotune(h: Handle, launches=20):
-    """Pick the lattice kernel's rows per block by timing; returns (rows, [ms for 1, 2, 4 rows])."""
-    rows = C.c_int()
-    ms = (C.c_double * 3)()
-    _call("lbp_autotune", h.ptr, int(launches), C.byref(rows), ms)
-    return rows.value, list(ms)
+    """Pick the lattice kernel's block shape by timing; returns (rows, pair, ms)
+    with ms the 6 mean launch times (one node per thread: 1, 2, 4 rows; two
+    nodes per thread: 1, 2, 4 rows; -1 where a shape does not apply)."""
+    rows, pair = C.c_int(), C.c_int()
+    ms = (C.c_double * 6)()
+    _call("lbp_autotune", h.ptr, int(launches), C.byref(rows), C.byref(pair), ms)
+    return rows.value, pair.value, list(ms)
+
+
+def lbp_set_block_shape(h: Handle, rows, pair):
+    _call("lbp_set_block_shape", h.ptr, int(rows), int(pair))
 
 
 def lbp_set_use_graphs(h: Handle, enable):

@@ -227,21 +227,42 @@ def test_per_particle_vacf_sums_and_trajectory():
     assert np.max(np.abs(tot - cs.sum(axis=0))) <= 1e-5 * tot[0]
 
 
-@pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16])
-def test_block_shapes_and_autotune_leave_results_unchanged(prec):
+def make_box(prec, kT, shape=(20, 18, 16, 0.8)):
+    nx, ny, nz, tau = shape
+    f, ps = box_state(0, shape)
+    h = lbp.lbp_create(nx, ny, nz, tau, precision=prec)
+    lbp.lbp_set_populations(h, f)
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=kT, seed=5)
+    return h
+
+
+@pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16, lbp.LBP_F16])
+@pytest.mark.parametrize("batch", [False, True])
+def test_block_shapes_and_autotune_leave_results_unchanged(prec, batch):
+    """Every block shape (rows per block; one or two nodes per thread) and the
+    autotuner's pick give bitwise the same run: a single even-nx box (where the
+    2-byte types have the paired-node kernel) and the uneven batch (odd nx in
+    one box: one node per thread only)."""
     steps = 25
+    pair_ok = prec != lbp.LBP_F32 and not batch
+    shapes = [(r, 0) for r in (1, 2, 4)] + ([(r, 1) for r in (1, 2, 4)] if pair_ok else []) + ["auto"]
     ref = None
-    for rows in (1, 2, 4, "auto"):
-        h = make_batch(prec, 1e-4, True)
+    for shape in shapes:
+        h = make_batch(prec, 1e-4, True) if batch else make_box(prec, 1e-4)
         lbp.lbp_step(h, 3)
-        if rows == "auto":
-            chosen, ms = lbp.lbp_autotune(h, 5)
-            assert chosen in (1, 2, 4) and all(m > 0 for m in ms)
-            assert chosen == (1, 2, 4)[int(np.argmin(ms))]
+        if shape == "auto":
+            rows, pair, ms = lbp.lbp_autotune(h, 5)
+            valid = [m for m in ms if m > 0]
+            assert len(valid) == (6 if pair_ok else 3)
+            assert ms[3 * pair + (1, 2, 4).index(rows)] == min(valid)
+            want = (rows, pair + 1)
         else:
-            lbp.lbp_set_block_rows(h, rows)
+            lbp.lbp_set_block_shape(h, *shape)
+            want = (shape[0], shape[1] + 1)
+        d = lbp.lbp_diagnostics(h)
+        assert (d["rows_per_block"], d["nodes_per_thread"]) == want
         assert lbp.lbp_get_step_index(h) == 3
-        assert lbp.lbp_diagnostics(h)["rows_per_block"] == (chosen if rows == "auto" else rows)
         lbp.lbp_step(h, steps)
         lbp.lbp_check(h)
         got = read_batch(h)
@@ -249,12 +270,13 @@ def test_block_shapes_and_autotune_leave_results_unchanged(prec):
         if ref is None:
             ref = got
         else:
-            assert np.array_equal(got[0], ref[0]), rows
+            assert np.array_equal(got[0], ref[0]), shape
             for k in range(4):
-                assert np.array_equal(got[1][k], ref[1][k]), (rows, k)
+                assert np.array_equal(got[1][k], ref[1][k]), (shape, k)
+    h = make_batch(prec, 0.0, True)
     with pytest.raises(lbp.LbpError):
-        h = lbp.lbp_create(8, 8, 8, 0.8)
-        try:
-            lbp.lbp_set_block_rows(h, 3)
-        finally:
-            lbp.lbp_destroy(h)
+        lbp.lbp_set_block_rows(h, 3)
+    if prec != lbp.LBP_F32:
+        with pytest.raises(lbp.LbpError):  # nx = 33 in one box
+            lbp.lbp_set_block_shape(h, 1, 1)
+    lbp.lbp_destroy(h)
