@@ -318,10 +318,11 @@ def run_gpu(args, w):
     def make(precision, wk=w):
         h = make_handle(lbp, wk, precision, wk.seed_noise + rank, args.vacf_lag)
         # block shape of the lattice kernel, picked by timing (outside the timed region)
-        rows, pair, tms = lbp.lbp_autotune(h, 10)
-        h.tuned = {"rows_per_block": rows, "nodes_per_thread": pair + 1,
-                   "ms_by_shape": {f"{n}x{r}": t for (n, r), t in
-                                   zip(((1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4)), tms) if t > 0}}
+        rows, variant, tms = lbp.lbp_autotune(h, 10)
+        names = ("1node_1row", "1node_2rows", "1node_4rows", "2nodes_1row", "2nodes_2rows", "2nodes_4rows",
+                 "bulk_staged")
+        h.tuned = {"variant": names[3 * variant + (1, 2, 4).index(rows)] if variant < 2 else names[6],
+                   "ms_by_shape": {n: t for n, t in zip(names, tms) if t > 0}}
         return h
 
     def timed(h, steps, warmup, clocks=None):
@@ -373,9 +374,10 @@ def run_gpu(args, w):
 
     # the other storage types on the same workload (shorter runs)
     variants = {}
+    want = (lambda name: not args.variant or name in args.variant)
     if not args.no_variants and not isinstance(w, wl.Ensemble):
         for prec in ("f32", "bf16", "f16"):
-            if prec == args.precision:
+            if prec == args.precision or not want(prec):
                 continue
             hv = make(prec)
             vsteps = max(1, min(args.steps, 500))
@@ -388,6 +390,7 @@ def run_gpu(args, w):
                               "stream_collide_ms": vk3, "achieved_gbs": vach,
                               "frac": vach / measured_peaks()[0],
                               "bytes_per_node": BYTES_PER_NODE[prec], "autotune": hv.tuned}
+    if not args.no_variants and not isinstance(w, wl.Ensemble) and want("batched"):
         # the batched uneven ensemble: one handle, one lattice launch per step
         e = wl.ENSEMBLE_68
         hb = make(args.precision, e)
@@ -407,14 +410,15 @@ def run_gpu(args, w):
                                "particle_updates_per_s": world * e.n_particles * bsteps / (bms * 1e-3),
                                "autotune": btuned}
 
-        # the differentiable run: 64^3, 8 kicked particles, 2000 steps, checkpoint
-        # every 100; and the adjoint at 256^3 (population copies larger than L2)
+    if not args.no_variants and not isinstance(w, wl.Ensemble) and want("adjoint_64"):
+        # the differentiable run: 64^3, 8 kicked particles, 2000 steps, checkpoint every 100
         wa = wl.ADJOINT_64
         variants["adjoint_64"] = adjoint_variant(lbp, torch, wa, wl.kicked_particles(wa), wa.steps,
                                                  wa.extra["checkpoint_every"], 0.0, 0)
-        wb = wl.BROWNIAN_256
-        variants["adjoint_256"] = adjoint_variant(lbp, torch, wb, wb.particles(), 100, 20, wb.kT,
-                                                  wb.seed_noise)
+    if not args.no_variants and not isinstance(w, wl.Ensemble) and want("adjoint"):
+        # the reverse sweep on the bench workload itself (population copies larger than L2)
+        key = "adjoint_256" if w is wl.BROWNIAN_256 else "adjoint_" + w.name
+        variants[key] = adjoint_variant(lbp, torch, w, w.particles(), 100, 20, w.kT, w.seed_noise)
 
     if rank != 0:
         if dist:
@@ -461,6 +465,8 @@ def main():
     ap.add_argument("--vacf-lag", type=int, default=VACF_LAG)
     ap.add_argument("--precision", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant", action="append", default=[],
+                    help="run only these variants (bf16, f16, f32, batched, adjoint_64, adjoint); default all")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "lbp":
         args.warmup = 3

@@ -215,15 +215,15 @@ lbp_status lbp_vacf_read_per_particle(lbp_sim *sim, double *csum, int64_t *count
 
 /* Wait for the handle's queued work and report device-side errors: LBP_ENAN if
  * a particle state became non-finite, LBP_ERANGE on fixed-point overflow.     */
-lbp_status lbp_check(lbp_sim *sim);
+lbp_status lbp_check(lbp_sim *sim);  /* also LBP_ETIMEOUT: a bounded device wait ran out */
 
 /* Diagnostics of the last completed step (waits for the handle's work):
  * out[0] = reaction-force shares that did not fit their row segment's record
  * and took the overflow path (both counts are implementation details of the
  * force accumulation; the results do not depend on them), out[1] = capacity of
  * a record in shares, out[2] = number of row segments, out[3] = rows of 128
- * nodes per lattice-kernel block, out[4] = nodes per thread of that kernel
- * (see lbp_autotune).  n = entries of out.                                   */
+ * nodes per lattice-kernel block, out[4] = its variant (see lbp_autotune).
+ * n = entries of out.                                                        */
 lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
 
 /* Uniform body force density g = (gx, gy, gz) added on every node of box
@@ -233,29 +233,33 @@ lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
  * and applied in FP32.  Default 0.                                           */
 lbp_status lbp_set_body_force(lbp_sim *sim, int replica, const double *g);
 
-/* Block-shape autotuner of the fused stream-collide kernel.  Times the kernel
+/* Kernel-shape autotuner of the fused stream-collide pass.  Times the kernel
  * this handle's steps launch (with the particle coupling if it has particles)
- * on its own lattice for each candidate shape -- 1, 2 or 4 rows of 128 nodes
- * per block, each with one node per thread (128-thread blocks) and, for the
- * 2-byte storage types when every box has an even nx, with two neighbouring
- * nodes per thread (64-thread blocks, 4-byte loads and stores) -- as
- * `launches` back-to-back launches (1..1000) after two warm-up launches,
- * twice, and keeps the shape with the smallest mean launch time for all later
- * steps.  rows, pair (optional) receive the chosen rows per block and nodes
- * per thread minus one; ms (optional, 6 doubles) the mean launch times in ms
- * for (one node per thread: 1, 2, 4 rows; two nodes: 1, 2, 4 rows), -1 where
- * a shape does not apply.  The simulation state is unchanged: the launches
+ * on its own lattice for each candidate and keeps the fastest for all later
+ * steps.  Candidates (variant, rows):
+ *   variant 0: one node per thread, 1, 2 or 4 rows of 128 nodes per block;
+ *   variant 1: two neighbouring nodes per thread with 4-byte loads and stores,
+ *              1, 2 or 4 rows (2-byte storage, every box with even nx);
+ *   variant 2: persistent CTAs that stage each plane's source row segments in
+ *              shared memory with bulk asynchronous copies (every box's nx a
+ *              multiple of 16 bytes of storage: 4 for LBP_F32, 8 otherwise).
+ * Each candidate runs `launches` back-to-back launches (1..1000) after two
+ * warm-up launches, twice, best pass kept.  rows, variant (optional) receive
+ * the pick; ms (optional, 7 doubles) the mean launch times in ms for
+ * (variant 0: 1, 2, 4 rows; variant 1: 1, 2, 4 rows; variant 2), -1 where a
+ * candidate does not apply.  The simulation state is unchanged: the launches
  * read the current populations, write only the buffer the next step
  * overwrites, see an all-zero copy of the force records and bump a scratch
- * step counter.  Synchronous.  Defaults before any call: two nodes per thread
- * and 1 row where that applies, else 1 row for LBP_F32 and 2 rows otherwise. */
-lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, int *pair, double *ms);
+ * step counter.  Synchronous; LBP_ETIMEOUT if a bounded device wait ran out.
+ * Default before any call: variant 0 with 1 row (LBP_F32) or 2 rows (the
+ * 2-byte types), the fastest on GB300 for the bench workloads.               */
+lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, int *variant, double *ms);
 
-/* Fix the block shape by hand: rows per block 1, 2 or 4 and pair = 1 for two
- * nodes per thread (LBP_EINVAL where that does not apply).  Results do not
- * depend on the shape: each node's arithmetic is the same for every shape.
- * lbp_set_block_rows changes the rows only.                                   */
-lbp_status lbp_set_block_shape(lbp_sim *sim, int rows, int pair);
+/* Fix the kernel shape by hand (LBP_EINVAL where the variant does not apply;
+ * variant 2 ignores rows).  Results do not depend on the shape: each node's
+ * arithmetic is the same in every variant.  lbp_set_block_rows changes the
+ * rows only (leaving variant 2 for variant 0).                                */
+lbp_status lbp_set_block_shape(lbp_sim *sim, int rows, int variant);
 lbp_status lbp_set_block_rows(lbp_sim *sim, int rows);
 
 /* Use CUDA graphs for lbp_step (default 1).                                  */

@@ -36,48 +36,6 @@ namespace lbp {
 // by DRAM bandwidth.  Measured on GB300 at 256^3: within 2% of a plain copy.
 // ---------------------------------------------------------------------------
 template <typename St>
-struct Planes {
-    const typename St::T *s[Q];
-    typename St::T *d[Q];
-};
-
-// collision of one node: the 15 post-collision deviations of the node whose
-// pulled deviations are g; (F0, F1, F2) is the body force of Eq. 18 at the
-// node (zero if none)
-__device__ __forceinline__ void collide_values(const float g[Q], float omega, float F0, float F1,
-                                               float F2, float o[Q]) {
-    float drho = 0.f;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) drho += g[a];
-    const float c78 = g[7] - g[8], c910 = g[9] - g[10], c1112 = g[11] - g[12],
-                c1314 = g[13] - g[14];
-    const float ux = (g[1] - g[2]) + c78 + c910 + c1112 - c1314;
-    const float uy = (g[3] - g[4]) + c78 + c910 - c1112 + c1314;
-    const float uz = (g[5] - g[6]) + c78 - c910 + c1112 + c1314;
-    const float base = drho - 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float om1 = 1.f - omega;
-    o[0] = om1 * g[0] + omega * ((2.f / 9.f) * base);
-    // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, weight W
-#define LBP_PAIR(A, W, EU, FE)                                \
-    {                                                         \
-        const float eu = (EU);                                \
-        const float sym = (W) * (base + 4.5f * eu * eu);      \
-        const float anti = (3.f * (W)) * eu;                  \
-        const float fe = (3.f * (W)) * (FE);                  \
-        o[A] = om1 * g[A] + omega * (sym + anti) + fe;        \
-        o[A + 1] = om1 * g[A + 1] + omega * (sym - anti) - fe; \
-    }
-    LBP_PAIR(1, 1.f / 9.f, ux, F0)
-    LBP_PAIR(3, 1.f / 9.f, uy, F1)
-    LBP_PAIR(5, 1.f / 9.f, uz, F2)
-    LBP_PAIR(7, 1.f / 72.f, ux + uy + uz, F0 + F1 + F2)
-    LBP_PAIR(9, 1.f / 72.f, ux + uy - uz, F0 + F1 - F2)
-    LBP_PAIR(11, 1.f / 72.f, ux - uy + uz, F0 - F1 + F2)
-    LBP_PAIR(13, 1.f / 72.f, -ux + uy + uz, -F0 + F1 + F2)
-#undef LBP_PAIR
-}
-
-template <typename St>
 __device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
                                               float omega, float F0, float F1, float F2) {
     float o[Q];
@@ -451,13 +409,54 @@ bool pair_kernel_ok(const Sim &s) {
     return true;
 }
 
-// the paired-node kernel (2-byte storage, even nx) or the one-node kernel
+bool staged_kernel_ok(const Sim &s) {
+    const int H = 16 / storage_bytes(s.precision);
+    for (int r = 0; r < s.nrep; ++r)
+        if (s.reps[r].nx % H || s.reps[r].nx > STAGED_NODES) return false;
+    return true;
+}
+
+// Replica table of the staged kernel: items of whole rows (Rep::pad = rows per item).
+template <int MAXR>
+static RepTable<MAXR> rep_table_staged(const Sim &s) {
+    RepTable<MAXR> t;
+    memset(&t, 0, sizeof(t));
+    t.nrep = s.nrep;
+    unsigned off = 0;
+    for (int r = 0; r < s.nrep; ++r) {
+        t.rep[r] = s.reps[r];
+        const int rows = staged_rows(s.reps[r].nx, s.reps[r].ny);
+        t.rep[r].pad = rows;
+        t.item_off[r] = off;
+        off += (unsigned)s.reps[r].nz * (unsigned)((s.reps[r].ny + rows - 1) / rows);
+    }
+    t.item_off[s.nrep] = off;
+    return t;
+}
+
+bool variant_ok(const Sim &s, int variant) {
+    return variant == 0 || (variant == 1 && pair_kernel_ok(s)) || (variant == 2 && staged_kernel_ok(s));
+}
+
+// variant 0: one node per thread; 1: two nodes per thread (2-byte storage,
+// even nx); 2: bulk-copy staged persistent kernel (lbm_staged.cu)
 template <bool FORCED>
 static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned long long *rec_cur,
-                             unsigned long long *rec_prev, long long *bump, int rows, int pair,
+                             unsigned long long *rec_prev, long long *bump, int rows, int variant,
                              cudaStream_t st) {
     constexpr int BX = SC_BX;
-    const bool use_pair = pair && pair_kernel_ok(s);
+    if (!variant_ok(s, variant)) variant = 0;
+    if (variant == 2) {
+        return by_storage(s, [&](auto tag) {
+            using St = decltype(tag);
+            if (s.nrep == 1)
+                return launch_staged_t<St, 1, FORCED>(planes_of<St>(s, src, dst), rep_table_staged<1>(s), rec_cur,
+                                                      rec_prev, s.fq, s.N, bump, s.d_err, s.num_sms, st);
+            return launch_staged_t<St, MAX_BATCH, FORCED>(planes_of<St>(s, src, dst), rep_table_staged<MAX_BATCH>(s),
+                                                          rec_cur, rec_prev, s.fq, s.N, bump, s.d_err, s.num_sms, st);
+        });
+    }
+    const bool use_pair = variant == 1;
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
         return by_rows(rows, [&](auto rc) {
@@ -484,19 +483,19 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
 }
 
 cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
-                                      int rows, int pair, cudaStream_t st) {
-    return launch_sc<false>(s, src, dst, nullptr, nullptr, bump, rows, pair, st);
+                                      int rows, int variant, cudaStream_t st) {
+    return launch_sc<false>(s, src, dst, nullptr, nullptr, bump, rows, variant, st);
 }
 
 cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
                                              const unsigned long long *rec_cur,
                                              unsigned long long *rec_prev, long long *bump, int rows,
-                                             int pair, cudaStream_t st) {
-    return launch_sc<true>(s, src, dst, rec_cur, rec_prev, bump, rows, pair, st);
+                                             int variant, cudaStream_t st) {
+    return launch_sc<true>(s, src, dst, rec_cur, rec_prev, bump, rows, variant, st);
 }
 
 cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st) {
-    return launch_stream_collide_cfg(s, src, dst, s.d_step, s.rows, s.pair, st);
+    return launch_stream_collide_cfg(s, src, dst, s.d_step, s.rows, s.variant, st);
 }
 
 cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
@@ -521,7 +520,7 @@ cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st) {
     return launch_stream_collide_forced_cfg(s, src, dst, s.rec[parity], s.rec[parity ^ 1], s.d_step,
-                                            s.rows, s.pair, st);
+                                            s.rows, s.variant, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,315 @@
+// lbm_staged.cu -- the fused stream-collide pass with bulk asynchronous copies
+// (the TMA engine's cp.async.bulk) staging the pulled populations in shared
+// memory (sm_103a).
+//
+// Same update as lbm_kernels.cu (pull streaming of Eq. 20, moments of
+// Eqs. 12-13, BGK collision with the force term of Eqs. 15, 17-19, per node
+// the arithmetic of collide_values, so results are identical bit for bit), but
+// the loads no longer come from registers.  A persistent CTA walks the items
+// of the lattice -- an item is R whole x-rows of one z-plane (R nx <= STAGED_NODES)
+// -- through a pipeline of shared-memory stages.  A producer warp refills a
+// stage as soon as the eight consumer warps release it (an "empty" mbarrier);
+// for each item its lane 0 issues, per population plane a, one bulk copy of
+// the item's source rows (the
+// rows shifted by -e_y, -e_z; two copies where the shift wraps around in y)
+// and one copy of the rows' force records; they complete on the stage's
+// "full" mbarrier with a byte count.  The consumer warps wait on it, read their 15
+// pulled values from shared memory -- the x-shift, periodic, is an index
+// there, since whole rows are staged -- collide and store to global memory.
+// Stages of ~15 KB (2-byte storage) or ~30 KB (FP32), several per SM, keep
+// ~150 KB per SM in flight without registers held for them; copies of whole
+// rows (1-2 KB) keep the number of bulk operations low.
+//
+// Requirements (checked on the host): every box has nx <= STAGED_NODES and
+// nx a multiple of 16 bytes of storage, so that every copy starts and ends on
+// a 16-byte boundary.  Every wait on an mbarrier is bounded: after
+// WAIT_CYCLES clock cycles the CTA sets ERR_TIMEOUT, waits (bounded again) for
+// the copies it issued, and leaves.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "lbp_internal.cuh"
+
+namespace lbp {
+
+namespace {
+
+// bound of one mbarrier wait, in SM clock cycles (~0.5 s at 2 GHz); each
+// try_wait poll may itself suspend the thread for a short, hardware-chosen time
+constexpr long long WAIT_CYCLES = 1ll << 30;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: true when the phase completed
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+}  // namespace
+
+template <typename St>
+struct StagedGeom {
+    static constexpr int E = (int)sizeof(typename St::T);
+    static constexpr int STAGES = E == 4 ? 3 : 4;
+    static constexpr int PLANE_BYTES = STAGED_NODES * E;
+    static constexpr int REC_BYTES = STAGED_RECS * REC_WORDS * 8;  // records of an item's rows
+    static constexpr int STAGE_BYTES = Q * PLANE_BYTES + REC_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8;  // + full and empty barriers
+};
+
+// Item i -> (replica, z, first row y0, rows R) of the staged launch.
+template <int MAXR>
+__device__ __forceinline__ void staged_item(const RepTable<MAXR> &rt, unsigned item, int &r, int &z,
+                                            int &y0, int &R) {
+    r = find_block_rep(rt, item);
+    const Rep &rp = rt.rep[r];
+    const unsigned it = item - rt.item_off[r];
+    const int rows = rp.pad;  // rows per item of this box
+    const int per_plane = (rp.ny + rows - 1) / rows;
+    z = (int)(it / (unsigned)per_plane);
+    y0 = (int)(it - (unsigned)z * per_plane) * rows;
+    R = rp.ny - y0 < rows ? rp.ny - y0 : rows;
+}
+
+// issue the copies of one item into one stage (one thread)
+template <typename St, int MAXR, bool FORCED>
+__device__ __forceinline__ void issue_item(const Planes<St> &pl, const RepTable<MAXR> &rt,
+                                           const unsigned long long *rec_cur, unsigned item, char *stage,
+                                           unsigned bar) {
+    using G = StagedGeom<St>;
+    constexpr int E = G::E;
+    int r, z, y0, R;
+    staged_item(rt, item, r, z, y0, R);
+    const Rep &rp = rt.rep[r];
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
+    const unsigned row_bytes = (unsigned)(nx * E);
+    unsigned bytes = Q * R * row_bytes;
+    if (FORCED) bytes += (unsigned)(R * rp.nchunks * REC_WORDS * 8);
+    mbar_expect_tx(bar, bytes);  // every byte expected before any lands
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        int zs = z - ez(a);
+        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+        int ys = y0 - ey(a);  // first source row, periodic
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+        const typename St::T *plane = pl.s[a] + rp.node_off + (long long)zs * ny * nx;
+        const unsigned dst = smem_addr(stage + a * G::PLANE_BYTES);
+        const int first = ny - ys < R ? ny - ys : R;  // rows before the wrap
+        bulk_g2s(dst, plane + (long long)ys * nx, (unsigned)first * row_bytes, bar);
+        if (first < R) bulk_g2s(dst + first * row_bytes, plane, (unsigned)(R - first) * row_bytes, bar);
+    }
+    if (FORCED) {
+        const unsigned long long *rec =
+            rec_cur + ((size_t)rp.seg_off + ((size_t)z * ny + y0) * rp.nchunks) * REC_WORDS;
+        bulk_g2s(smem_addr(stage + Q * G::PLANE_BYTES), rec, (unsigned)(R * rp.nchunks * REC_WORDS * 8), bar);
+    }
+}
+
+template <typename St, int MAXR, bool FORCED>
+__global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
+    Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err) {
+    using G = StagedGeom<St>;
+    constexpr int STAGES = G::STAGES;
+    constexpr int NCW = STAGED_THREADS / 32;  // consumer warps; warp NCW is the producer
+    extern __shared__ __align__(128) char smem[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + STAGES * G::STAGE_BYTES);
+    unsigned long long *empty = full + STAGES;
+    const unsigned total = rt.item_off[rt.nrep];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (blockIdx.x == 0 && t == 0) *bump += 1;
+    if (t == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(smem_addr(full + st), 1);
+            mbar_init(smem_addr(empty + st), NCW);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();  // the only CTA-wide barrier
+
+    if (warp == NCW) {
+        // ---- producer: refill a stage as soon as the consumers release it
+        if (lane == 0) {
+            unsigned k = 0;
+            for (unsigned item = blockIdx.x; item < total; item += gridDim.x, ++k) {
+                const int st = (int)(k % STAGES);
+                if (k >= (unsigned)STAGES && !mbar_wait(smem_addr(empty + st), ((k / STAGES) - 1) & 1u)) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                }
+                fence_proxy_async();
+                issue_item<St, MAXR, FORCED>(pl, rt, rec_cur, item, smem + st * G::STAGE_BYTES,
+                                             smem_addr(full + st));
+            }
+        }
+        return;
+    }
+
+    // ---- consumers
+    unsigned k = 0;
+    for (unsigned item = blockIdx.x; item < total; item += gridDim.x, ++k) {
+        const int st = (int)(k % STAGES);
+        const unsigned parity = (k / STAGES) & 1u;
+        char *stage = smem + st * G::STAGE_BYTES;
+        if (!mbar_wait(smem_addr(full + st), parity)) {
+            atomicOr(err, ERR_TIMEOUT);
+            // the copies into this stage may still land: wait once more (bounded)
+            mbar_wait(smem_addr(full + st), parity);
+            break;
+        }
+        int r, z, y0, R;
+        staged_item(rt, item, r, z, y0, R);
+        const Rep &rp = rt.rep[r];
+        const int nx = rp.nx, nch = rp.nchunks;
+        const long long row0 = (long long)z * rp.ny + y0;  // first row of the item in its box
+        if (FORCED && t < R * nch) rec_prev[((size_t)rp.seg_off + (size_t)row0 * nch + t) * REC_WORDS] = 0ull;
+        const unsigned long long *recs = reinterpret_cast<const unsigned long long *>(stage + Q * G::PLANE_BYTES);
+        for (int n = t; n < R * nx; n += STAGED_THREADS) {
+            const int yy = n / nx, x = n - yy * nx;
+            const int xp = x == nx - 1 ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+            const int rb = yy * nx;
+            float g[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const typename St::T *p = reinterpret_cast<const typename St::T *>(stage + a * G::PLANE_BYTES);
+                g[a] = St::load_shared(p + rb + (ex(a) > 0 ? xm : (ex(a) < 0 ? xp : x)), a);
+            }
+            float F0 = rp.gx, F1 = rp.gy, F2 = rp.gz;
+            const long long d = rp.node_off + (row0 + yy) * nx + x;
+            if (FORCED) {
+                const unsigned long long *rec = recs + (size_t)(yy * nch + x / SEG) * REC_WORDS;
+                const int cnt = (int)(unsigned)(rec[0] & 0xffffffffull);
+                if (cnt > 0) {
+                    long long a0 = 0, a1 = 0, a2 = 0;
+                    const int used = cnt < REC_SLOTS ? cnt : REC_SLOTS;
+                    const int *xs = reinterpret_cast<const int *>(rec + REC_X0);
+                    for (int sl = 0; sl < used; ++sl)
+                        if (xs[sl] == x) {
+                            a0 += (long long)rec[REC_F0 + 3 * sl];
+                            a1 += (long long)rec[REC_F0 + 3 * sl + 1];
+                            a2 += (long long)rec[REC_F0 + 3 * sl + 2];
+                        }
+                    if (cnt > REC_SLOTS) {
+                        a0 += (long long)fq[d];
+                        a1 += (long long)fq[Ntot + d];
+                        a2 += (long long)fq[2 * Ntot + d];
+                        fq[d] = 0ull;
+                        fq[Ntot + d] = 0ull;
+                        fq[2 * Ntot + d] = 0ull;
+                    }
+                    const float inv = 1.3877787807814457e-17f;  // 2^-56
+                    F0 += inv * __ll2float_rn(a0);
+                    F1 += inv * __ll2float_rn(a1);
+                    F2 += inv * __ll2float_rn(a2);
+                }
+            }
+            float o[Q];
+            collide_values(g, rp.omega, F0, F1, F2, o);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) St::store(pl.d[a] + d, a, o[a]);
+        }
+        // this warp is done with the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(empty + st));
+    }
+}
+
+// The launcher: one persistent CTA per free slot (occupancy of this kernel).
+template <typename St, int MAXR, bool FORCED>
+cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, const unsigned long long *rec_cur,
+                            unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump,
+                            int *err, int num_sms, cudaStream_t st) {
+    using G = StagedGeom<St>;
+    auto kern = k_stream_collide_staged<St, MAXR, FORCED>;
+    static int per_sm = 0;  // per instantiation
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, STAGED_THREADS + 32, G::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const unsigned total = rt.item_off[rt.nrep];
+    unsigned grid = (unsigned)(per_sm * num_sms);
+    if (grid > total) grid = total;
+    if (grid == 0) return cudaSuccess;
+    kern<<<grid, STAGED_THREADS + 32, G::SMEM, st>>>(pl, rt, rec_cur, rec_prev, fq, Ntot, bump, err);
+    return cudaGetLastError();
+}
+
+// rows per item of a box: as many whole rows as fit STAGED_NODES nodes and
+// STAGED_RECS force records (at most ny)
+int staged_rows(int nx, int ny) {
+    const int nch = (nx + SEG - 1) / SEG;
+    int r = STAGED_NODES / nx;
+    if (r * nch > STAGED_RECS) r = STAGED_RECS / nch;
+    if (r < 1) r = 1;
+    return r < ny ? r : ny;
+}
+
+#define LBP_STAGED_INST(ST, MAXR, F)                                                                        \
+    template cudaError_t launch_staged_t<ST, MAXR, F>(const Planes<ST> &, const RepTable<MAXR> &,          \
+                                                      const unsigned long long *, unsigned long long *,     \
+                                                      unsigned long long *, long long, long long *, int *, \
+                                                      int, cudaStream_t);
+LBP_STAGED_INST(StoreF32, 1, true)
+LBP_STAGED_INST(StoreF32, 1, false)
+LBP_STAGED_INST(StoreF32, MAX_BATCH, true)
+LBP_STAGED_INST(StoreF32, MAX_BATCH, false)
+LBP_STAGED_INST(StoreBF16, 1, true)
+LBP_STAGED_INST(StoreBF16, 1, false)
+LBP_STAGED_INST(StoreBF16, MAX_BATCH, true)
+LBP_STAGED_INST(StoreBF16, MAX_BATCH, false)
+LBP_STAGED_INST(StoreF16, 1, true)
+LBP_STAGED_INST(StoreF16, 1, false)
+LBP_STAGED_INST(StoreF16, MAX_BATCH, true)
+LBP_STAGED_INST(StoreF16, MAX_BATCH, false)
+#undef LBP_STAGED_INST
+
+}  // namespace lbp

@@ -76,11 +76,10 @@ lbp_status leave(lbp_sim *s) {
 
 void drop_graphs(lbp_sim *s) {
     for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j)
-            if (s->graph[i][j]) {
-                cudaGraphExecDestroy(s->graph[i][j]);
-                s->graph[i][j] = nullptr;
-            }
+        if (s->graph[i]) {
+            cudaGraphExecDestroy(s->graph[i]);
+            s->graph[i] = nullptr;
+        }
 }
 
 lbp_status stage(lbp_sim *s, size_t bytes) {
@@ -118,19 +117,11 @@ bool radius_ok(double R, int exclude) {
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
 // one time step (see the sequence at the top of this file)
-lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
+lbp_status enqueue_step(lbp_sim *s, bool timed) {
     const void *src = s->f[s->cur];
     void *dst = s->f[s->cur ^ 1];
     const int parity = s->cur;
-    if (s->np > 0) {
-        CK(launch_particles(*s, src, parity, s->s0));
-        if (vacf_due) {
-            CK(cudaEventRecord(s->ev_fork, s->s0));
-            CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
-            CK(launch_vacf_block(*s, false, s->s1));
-            CK(cudaEventRecord(s->ev_join, s->s1));
-        }
-    }
+    if (s->np > 0) CK(launch_particles(*s, src, parity, s->s0));
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
     if (s->np > 0)
         CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
@@ -140,7 +131,28 @@ lbp_status enqueue_step(lbp_sim *s, bool timed, bool vacf_due) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
     }
-    if (vacf_due) CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
+    return LBP_OK;
+}
+
+// The VACF block of samples just completed runs on the side stream s1 while
+// s0 goes on stepping; s0 waits for it only when the next block is due, i.e.
+// before the step whose sample would overwrite the oldest sample it reads (the
+// ring holds max_lag + 2 blocks).
+lbp_status join_vacf(lbp_sim *s) {
+    if (s->vacf_pending) {
+        CK(cudaStreamWaitEvent(s->s0, s->ev_join, 0));
+        s->vacf_pending = 0;
+    }
+    return LBP_OK;
+}
+
+lbp_status fork_vacf(lbp_sim *s) {
+    TRY(join_vacf(s));
+    CK(cudaEventRecord(s->ev_fork, s->s0));
+    CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
+    CK(launch_vacf_block(*s, false, s->s1));
+    CK(cudaEventRecord(s->ev_join, s->s1));
+    s->vacf_pending = 1;
     return LBP_OK;
 }
 
@@ -157,12 +169,12 @@ lbp_status fold_timing(lbp_sim *s) {
     return LBP_OK;
 }
 
-lbp_status capture(lbp_sim *s, int parity, int due) {
+lbp_status capture(lbp_sim *s, int parity) {
     cudaGraph_t g = nullptr;
     const int saved = s->cur;
     s->cur = parity;
     CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
-    lbp_status st = enqueue_step(s, false, due != 0);
+    lbp_status st = enqueue_step(s, false);
     cudaError_t e = cudaStreamEndCapture(s->s0, &g);
     s->cur = saved;
     if (st != LBP_OK) {
@@ -170,7 +182,7 @@ lbp_status capture(lbp_sim *s, int parity, int due) {
         return st;
     }
     CK(e);
-    e = cudaGraphInstantiate(&s->graph[parity][due], g, 0);
+    e = cudaGraphInstantiate(&s->graph[parity], g, 0);
     cudaGraphDestroy(g);
     CK(e);
     return LBP_OK;
@@ -190,13 +202,14 @@ lbp_status step_once(lbp_sim *s) {
     }
     if (s->timing) {
         if (s->ntimed == lbp::Sim::MAX_TIMED) TRY(fold_timing(s));
-        TRY(enqueue_step(s, true, due));
+        TRY(enqueue_step(s, true));
     } else if (s->use_graphs) {
-        if (!s->graph[s->cur][due]) TRY(capture(s, s->cur, due));
-        CK(cudaGraphLaunch(s->graph[s->cur][due], s->s0));
+        if (!s->graph[s->cur]) TRY(capture(s, s->cur));
+        CK(cudaGraphLaunch(s->graph[s->cur], s->s0));
     } else {
-        TRY(enqueue_step(s, false, due));
+        TRY(enqueue_step(s, false));
     }
+    if (due) TRY(fork_vacf(s));
     s->cur ^= 1;
     s->step += 1;
     return LBP_OK;
@@ -280,8 +293,9 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     s->nseg = nseg;
     s->tau = descs[0].tau;
     s->precision = descs[0].precision;
-    s->pair = pair_kernel_ok(*s) ? 1 : 0;
-    s->rows = s->pair ? 1 : default_rows_per_block(s->precision);
+    // the measured best on GB300 without tuning (lbp_autotune measures the rest)
+    s->variant = 0;
+    s->rows = default_rows_per_block(s->precision);
     s->user = (cudaStream_t)stream;
     s->sqrt3 = std::sqrt(3.0);
     auto bail = [&](lbp_status st) {
@@ -293,8 +307,14 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     cudaError_t e = cudaGetDevice(&s->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->dev);
     if (e == cudaSuccess) e = prepare_lbm_kernels();
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s0, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s1, cudaStreamNonBlocking);
+    // the step's own kernels at the highest stream priority, the side stream (the
+    // VACF correlator, compute-bound) at the lowest: when both have blocks
+    // waiting, the HBM-bound lattice pass gets the SM slots first and the
+    // correlator fills what it leaves idle
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s0, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s1, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
@@ -778,6 +798,7 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     CHECK_SIM(s);
     if (max_lag < -1) return fail(LBP_EINVAL, "lbp_vacf_configure: max_lag < -1");
     TRY(enter(s));
+    TRY(join_vacf(s));
     CK(cudaStreamSynchronize(s->s0));
     drop_graphs(s);
     s->vacf_lag = -1;
@@ -792,10 +813,10 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     if (s->np == 0) return fail(LBP_ESTATE, "lbp_vacf_configure: add particles first");
     const int B = vacf_block_samples();
     const long long ncomp = 3ll * s->np;
-    const size_t ring_bytes = sizeof(float) * (size_t)(max_lag + B) * (size_t)ncomp;
+    const size_t ring_bytes = sizeof(float) * (size_t)(max_lag + 2 * B) * (size_t)ncomp;
     if (ring_bytes > ((size_t)64 << 30))
         return fail(LBP_EINVAL, "lbp_vacf_configure: ring of %zu bytes exceeds 64 GiB", ring_bytes);
-    s->vacf_cap = max_lag + B;
+    s->vacf_cap = max_lag + 2 * B;  // one block more than the window: see join_vacf
     s->vacf_nchunks = (int)((ncomp + vacf_chunk_components() - 1) / vacf_chunk_components());
     TRY(dalloc(&s->ring, (size_t)s->vacf_cap * ncomp));
     const size_t nsum = (per_particle ? (size_t)s->np : 1) * ((size_t)max_lag + 1);
@@ -820,6 +841,7 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
 static lbp_status vacf_read_impl(lbp_sim *s, double *csum, int64_t *counts, int on_device,
                                  int nsets) {
     TRY(enter(s));
+    TRY(join_vacf(s));
     CK(launch_vacf_block(*s, true, s->s0));
     s->vacf_done_host = s->step - s->vacf_t0;
     const size_t K1 = (size_t)s->vacf_lag + 1;
@@ -864,40 +886,44 @@ lbp_status lbp_set_body_force(lbp_sim *s, int replica, const double *g) {
     return leave(s);
 }
 
-lbp_status lbp_set_block_shape(lbp_sim *s, int rows, int pair) {
+lbp_status lbp_set_block_shape(lbp_sim *s, int rows, int variant) {
     CHECK_SIM(s);
     if (rows != 1 && rows != 2 && rows != 4) return fail(LBP_EINVAL, "lbp_set_block_shape: rows must be 1, 2 or 4");
-    if (pair != 0 && pair != 1) return fail(LBP_EINVAL, "lbp_set_block_shape: pair must be 0 or 1");
-    if (pair && !pair_kernel_ok(*s))
-        return fail(LBP_EINVAL, "lbp_set_block_shape: two nodes per thread needs 2-byte storage and even nx in every box");
+    if (variant < 0 || variant > 2 || !variant_ok(*s, variant))
+        return fail(LBP_EINVAL,
+                    "lbp_set_block_shape: variant %d does not apply (1 needs 2-byte storage and even nx, 2 needs nx a "
+                    "multiple of 16 bytes of storage, in every box)", variant);
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
-    s->rows = rows;
-    s->pair = pair;
+    s->rows = variant == 2 ? 1 : rows;
+    s->variant = variant;
     drop_graphs(s);
     return leave(s);
 }
 
 lbp_status lbp_set_block_rows(lbp_sim *s, int rows) {
     CHECK_SIM(s);
-    return lbp_set_block_shape(s, rows, s->pair && pair_kernel_ok(*s) ? 1 : 0);
+    return lbp_set_block_shape(s, rows, s->variant == 2 ? 0 : s->variant);
 }
 
-lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *pair, double *ms) {
+lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *variant, double *ms) {
     CHECK_SIM(s);
     if (launches < 1 || launches > 1000) return fail(LBP_EINVAL, "lbp_autotune: launches must be in [1, 1000]");
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
+    // candidates: (variant, rows); index k = 3 variant + (0, 1, 2 for 1, 2, 4 rows); the
+    // staged kernel has one shape (k = 6)
     static const int cand_r[3] = {1, 2, 4};
-    const int npair = pair_kernel_ok(*s) ? 2 : 1;
+    bool apply[7];
+    for (int k = 0; k < 7; ++k) apply[k] = variant_ok(*s, k / 3);
     // scratch: two all-zero force-record copies (no force anywhere, so the
     // dense overflow accumulator is never read) and a step counter to bump
     const size_t rec_words = s->np > 0 ? (size_t)s->nseg * REC_WORDS : 0;
     unsigned long long *scr = nullptr;
     TRY(dalloc(&scr, 2 * rec_words + 1));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double t[6];
-    for (int c = 0; c < 6; ++c) t[c] = -1.0;
+    double t[7];
+    for (int k = 0; k < 7; ++k) t[k] = -1.0;
     cudaError_t e = cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (2 * rec_words + 1), s->s0);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -906,38 +932,42 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *pair, double *
     // step overwrites whole: the handle's state is unchanged
     const void *src = s->f[s->cur];
     void *dst = s->f[s->cur ^ 1];
-    auto one = [&](int R, int P) {
-        return s->np > 0 ? launch_stream_collide_forced_cfg(*s, src, dst, scr, scr + rec_words, bump, R, P, s->s0)
-                         : launch_stream_collide_cfg(*s, src, dst, bump, R, P, s->s0);
+    auto one = [&](int R, int V) {
+        return s->np > 0 ? launch_stream_collide_forced_cfg(*s, src, dst, scr, scr + rec_words, bump, R, V, s->s0)
+                         : launch_stream_collide_cfg(*s, src, dst, bump, R, V, s->s0);
     };
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass)
-        for (int P = 0; P < npair && e == cudaSuccess; ++P)
-            for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-                for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = one(cand_r[c], P);
-                if (e == cudaSuccess) e = cudaEventRecord(e0, s->s0);
-                for (int l = 0; l < launches && e == cudaSuccess; ++l) e = one(cand_r[c], P);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, s->s0);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float el = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
-                const double per = (double)el / launches;
-                const int k = 3 * P + c;
-                if (e == cudaSuccess) t[k] = pass == 0 ? per : std::min(t[k], per);
-            }
+        for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+            if (!apply[k]) continue;
+            const int V = k / 3, R = k < 6 ? cand_r[k % 3] : 1;
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = one(R, V);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s->s0);
+            for (int l = 0; l < launches && e == cudaSuccess; ++l) e = one(R, V);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s->s0);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float el = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&el, e0, e1);
+            const double per = (double)el / launches;
+            if (e == cudaSuccess) t[k] = pass == 0 ? per : std::min(t[k], per);
+        }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(scr);
     if (e != cudaSuccess) return fail(LBP_ECUDA, "lbp_autotune: %s", cudaGetErrorString(e));
-    int best = 0;
-    for (int k = 1; k < 3 * npair; ++k)
-        if (t[k] < t[best]) best = k;
-    s->rows = cand_r[best % 3];
-    s->pair = best / 3;
+    // a bounded wait inside the staged kernel that ran out shows in the error flag
+    int err = 0;
+    CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & ERR_TIMEOUT) return fail(LBP_ETIMEOUT, "lbp_autotune: a bounded wait in the staged kernel ran out");
+    int best = -1;
+    for (int k = 0; k < 7; ++k)
+        if (t[k] > 0 && (best < 0 || t[k] < t[best])) best = k;
+    s->variant = best / 3;
+    s->rows = best < 6 ? cand_r[best % 3] : 1;
     drop_graphs(s);
     if (rows) *rows = s->rows;
-    if (pair) *pair = s->pair;
+    if (variant) *variant = s->variant;
     if (ms)
-        for (int k = 0; k < 6; ++k) ms[k] = t[k];
+        for (int k = 0; k < 7; ++k) ms[k] = t[k];
     return leave(s);
 }
 
@@ -1204,6 +1234,7 @@ lbp_status lbp_check(lbp_sim *s) {
     CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         CK(cudaMemset(s->d_err, 0, sizeof(int)));
+        if (err & ERR_TIMEOUT) return fail(LBP_ETIMEOUT, "lbp_check: a bounded wait on an mbarrier in the staged lattice kernel ran out");
         if (err & ERR_NAN) return fail(LBP_ENAN, "lbp_check: a particle velocity or position became non-finite or left the box");
         return fail(LBP_ERANGE, "lbp_check: a friction force exceeded the fixed-point range (|F_H| >= 32)");
     }
@@ -1214,7 +1245,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
     CHECK_SIM(s);
     if (n < 0 || (n > 0 && !out)) return fail(LBP_EINVAL, "lbp_diagnostics: bad output");
     CK(cudaStreamSynchronize(s->s0));
-    int64_t v[5] = {0, REC_SLOTS, s->nseg, s->rows, (int64_t)(s->pair && pair_kernel_ok(*s) ? 2 : 1)};
+    int64_t v[5] = {0, REC_SLOTS, s->nseg, s->rows, (int64_t)s->variant};
     if (s->rec[0]) {
         // shares beyond the slots of the records of the last completed step
         std::vector<unsigned long long> words((size_t)s->nseg * REC_WORDS);

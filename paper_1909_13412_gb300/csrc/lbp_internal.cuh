@@ -50,11 +50,13 @@ constexpr float F16_SCALE = 1024.f;
 struct StoreF32 {
     using T = float;
     static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
+    static __device__ __forceinline__ float load_shared(const T *p, int) { return *p; }
     static __device__ __forceinline__ void store(T *p, int, float v) { *p = v; }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float load(const T *p, int) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float load_shared(const T *p, int) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void store(T *p, int, float v) { *p = __float2bfloat16_rn(v); }
 };
 struct StoreF16 {
@@ -62,12 +64,61 @@ struct StoreF16 {
     static __device__ __forceinline__ float load(const T *p, int a) {
         return __half2float(__ldg(p)) * (wgtf(a) * (1.f / F16_SCALE));
     }
+    static __device__ __forceinline__ float load_shared(const T *p, int a) {
+        return __half2float(*p) * (wgtf(a) * (1.f / F16_SCALE));
+    }
     static __device__ __forceinline__ void store(T *p, int a, float v) {
         *p = __float2half_rn(v * (F16_SCALE / wgtf(a)));
     }
 };
 
 __host__ __device__ constexpr int storage_bytes(int precision) { return precision == LBP_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------ collision
+// Per-population plane pointers of the source (pulled from) and destination
+// buffers of one lattice pass.
+template <typename St>
+struct Planes {
+    const typename St::T *s[Q];
+    typename St::T *d[Q];
+};
+
+// Collision of one node (Eqs. 15, 17-19 in deviation form, see
+// lbm_kernels.cu): the 15 post-collision deviations of the node whose
+// pulled deviations are g; (F0, F1, F2) is the body force of Eq. 18 at the
+// node (zero if none)
+__device__ __forceinline__ void collide_values(const float g[Q], float omega, float F0, float F1,
+                                               float F2, float o[Q]) {
+    float drho = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) drho += g[a];
+    const float c78 = g[7] - g[8], c910 = g[9] - g[10], c1112 = g[11] - g[12],
+                c1314 = g[13] - g[14];
+    const float ux = (g[1] - g[2]) + c78 + c910 + c1112 - c1314;
+    const float uy = (g[3] - g[4]) + c78 + c910 - c1112 + c1314;
+    const float uz = (g[5] - g[6]) + c78 - c910 + c1112 + c1314;
+    const float base = drho - 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float om1 = 1.f - omega;
+    o[0] = om1 * g[0] + omega * ((2.f / 9.f) * base);
+    // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, weight W
+#define LBP_PAIR(A, W, EU, FE)                                \
+    {                                                         \
+        const float eu = (EU);                                \
+        const float sym = (W) * (base + 4.5f * eu * eu);      \
+        const float anti = (3.f * (W)) * eu;                  \
+        const float fe = (3.f * (W)) * (FE);                  \
+        o[A] = om1 * g[A] + omega * (sym + anti) + fe;        \
+        o[A + 1] = om1 * g[A + 1] + omega * (sym - anti) - fe; \
+    }
+    LBP_PAIR(1, 1.f / 9.f, ux, F0)
+    LBP_PAIR(3, 1.f / 9.f, uy, F1)
+    LBP_PAIR(5, 1.f / 9.f, uz, F2)
+    LBP_PAIR(7, 1.f / 72.f, ux + uy + uz, F0 + F1 + F2)
+    LBP_PAIR(9, 1.f / 72.f, ux + uy - uz, F0 + F1 - F2)
+    LBP_PAIR(11, 1.f / 72.f, ux - uy + uz, F0 - F1 + F2)
+    LBP_PAIR(13, 1.f / 72.f, -ux + uy + uz, -F0 + F1 + F2)
+#undef LBP_PAIR
+}
 
 // Reaction forces are summed per node in 64-bit fixed point so that the sum
 // is exact and independent of the order in which particles add to it.
@@ -91,6 +142,7 @@ constexpr int REC_F0 = 5;
 // error bits in Sim::d_err
 constexpr int ERR_NAN = 1;
 constexpr int ERR_RANGE = 2;
+constexpr int ERR_TIMEOUT = 4;  // a bounded wait on an mbarrier ran out
 
 // ------------------------------------------------------------------ Philox
 // Philox-4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -128,7 +180,7 @@ struct Rep {
     long long seg_off;        // first global force-record segment
     float omega;              // 1 / tau
     float gx, gy, gz;         // uniform body force density on every node of the box (Eq. 18)
-    int pad;
+    int pad;                  // rows per item of the staged lattice kernel (set per launch)
 };
 
 constexpr int MAX_BATCH = 256;
@@ -189,7 +241,7 @@ struct Sim {
     double tau = 1.0;
     int precision = LBP_F32;
     int rows = 1;  // rows of SEG nodes per lattice-kernel block (1, 2 or 4)
-    int pair = 1;  // two nodes per thread (2-byte storage, even nx) or one
+    int variant = 0;  // lattice kernel: 0 one node per thread, 1 two nodes, 2 bulk-copy staged
     int dev = 0;
     int num_sms = 0;
 
@@ -245,7 +297,8 @@ struct Sim {
 
     // graphs
     int use_graphs = 1;
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][vacf block due]
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, by buffer parity
+    int vacf_pending = 0;  // a VACF block runs on s1 (ev_join marks its end)
 
     // kernel timing
     int timing = 0;
@@ -262,13 +315,14 @@ cudaError_t prepare_lbm_kernels();
 cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream_t st);
 // the lattice kernels with an explicit step counter, force records and rows per block
 cudaError_t launch_stream_collide_cfg(Sim &s, const void *src, void *dst, long long *bump,
-                                      int rows, int pair, cudaStream_t st);
+                                      int rows, int variant, cudaStream_t st);
 cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
                                              const unsigned long long *rec_cur,
                                              unsigned long long *rec_prev, long long *bump, int rows,
-                                             int pair, cudaStream_t st);
+                                             int variant, cudaStream_t st);
 int default_rows_per_block(int precision);
 bool pair_kernel_ok(const Sim &s);  // 2-byte storage and every box with even nx
+bool variant_ok(const Sim &s, int variant);
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st);
 cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st);
@@ -286,6 +340,16 @@ cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cud
 cudaError_t launch_cells(Sim &s, int *base, double *frac, cudaStream_t st);
 cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long long *key,
                           unsigned long long *out, int64_t n, cudaStream_t st);
+// lbm_staged.cu
+template <typename St, int MAXR, bool FORCED>
+cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, const unsigned long long *rec_cur,
+                            unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump,
+                            int *err, int num_sms, cudaStream_t st);
+bool staged_kernel_ok(const Sim &s);  // every box: nx a multiple of 16 bytes of storage, nx <= STAGED_NODES
+int staged_rows(int nx, int ny);      // rows per item of the staged kernel
+constexpr int STAGED_NODES = 512;     // nodes per item (whole rows) of the staged kernel
+constexpr int STAGED_RECS = 16;       // force records per item of the staged kernel
+constexpr int STAGED_THREADS = 256;
 // adjoint_kernels.cu
 cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const double *r,
                                  const double *v, long long step, const double *gv,

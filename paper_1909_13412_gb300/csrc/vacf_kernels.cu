@@ -69,6 +69,11 @@ __global__ void __launch_bounds__(256) k_vacf_corr(const VacfArgs A) {
 #pragma unroll
     for (int m = 0; m < VLW; ++m) acc[m] = 0.f;
 
+    // ring slots of the first rows of sA and sW (one 64-bit modulo per CTA;
+    // later rows wrap by one subtraction: a block spans fewer than cap rows)
+    const int cap = A.cap;
+    const int slotA0 = (int)(tb % cap);
+    const int slotW0 = s_lo >= 0 ? (int)(s_lo % cap) : 0;
     for (int js = 0; js < VJCH; js += VJ) {
         const int jb = jc0 + js;
         if (jb >= A.ncomp) break;
@@ -77,7 +82,11 @@ __global__ void __launch_bounds__(256) k_vacf_corr(const VacfArgs A) {
             const int t = e / VJ, l = e - t * VJ;
             const int jj = jb + l;
             float v = 0.f;
-            if (t < nb && jj < A.ncomp) v = A.ring[((tb + t) % A.cap) * A.ncomp + jj];
+            if (t < nb && jj < A.ncomp) {
+                int slot = slotA0 + t;
+                if (slot >= cap) slot -= cap;
+                v = A.ring[(long long)slot * A.ncomp + jj];
+            }
             sA[t][l] = v;
         }
         for (int e = threadIdx.x; e < VWIN * VJ; e += blockDim.x) {
@@ -85,25 +94,31 @@ __global__ void __launch_bounds__(256) k_vacf_corr(const VacfArgs A) {
             const int jj = jb + l;
             const long long s = s_lo + sr;
             float v = 0.f;
-            if (s >= 0 && s < te && jj < A.ncomp) v = A.ring[(s % A.cap) * A.ncomp + jj];
+            // rows older than te - cap were overwritten; they only meet lags > K
+            if (s >= 0 && s >= te - cap && s < te && jj < A.ncomp) {
+                // slot of sample s: s mod cap (slotW0 + sr < 3 cap, s < 2 cap here)
+                int slot = s_lo >= 0 ? slotW0 + sr : (int)s;
+                while (slot >= cap) slot -= cap;
+                v = A.ring[(long long)slot * A.ncomp + jj];
+            }
             sW[sr][l] = v;
         }
         __syncthreads();
-        // window for lags k = k0 + VLW*warp + m at sample t: sW[t + VKT-1 - VLW*warp - m]
+        // window for lags k = k0 + VLW*warp + m at sample t: sW[t + VKT-1 - VLW*warp - m].
+        // 16 samples at a time: their 16 values and the 31 window values they
+        // meet sit in registers with static indices, 256 FMAs per 47 loads.
         const int base0 = VKT - 1 - VLW * warp;
-        float w[VLW];
+#pragma unroll 1
+        for (int tc = 0; tc < VB; tc += VLW) {
+            float a[VLW], w[2 * VLW - 1];
 #pragma unroll
-        for (int m = 0; m < VLW; ++m) w[m] = sW[base0 - m][lane];
+            for (int i = 0; i < VLW; ++i) a[i] = sA[tc + i][lane];
 #pragma unroll
-        for (int t = 0; t < VB; ++t) {
-            const float a = sA[t][lane];
+            for (int i = 0; i < 2 * VLW - 1; ++i) w[i] = sW[base0 + tc - (VLW - 1) + i][lane];
 #pragma unroll
-            for (int m = 0; m < VLW; ++m) acc[m] = fmaf(a, w[m], acc[m]);
-            if (t + 1 < VB) {
+            for (int i = 0; i < VLW; ++i)
 #pragma unroll
-                for (int m = VLW - 1; m > 0; --m) w[m] = w[m - 1];
-                w[0] = sW[base0 + t + 1][lane];
-            }
+                for (int m = 0; m < VLW; ++m) acc[m] = fmaf(a[i], w[i - m + VLW - 1], acc[m]);
         }
     }
     // combine the lanes in FP64, fixed tree
@@ -149,11 +164,15 @@ __global__ void __launch_bounds__(256) k_vacf_pp(const VacfArgs A) {
     const int np = A.np;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= A.K; k += gridDim.x * blockDim.x) {
         float acc = 0.f;
-        for (long long t = tb > k ? tb : k; t < te; ++t) {
-            const float *a = A.ring + (t % A.cap) * 3 * (long long)np;
-            const float *b = A.ring + ((t - k) % A.cap) * 3 * (long long)np;
+        const long long t1 = tb > k ? tb : k;
+        int sa = (int)(t1 % A.cap), sb = (int)((t1 - k) % A.cap);
+        for (long long t = t1; t < te; ++t) {
+            const float *a = A.ring + (long long)sa * 3 * np;
+            const float *b = A.ring + (long long)sb * 3 * np;
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc = fmaf(a[c * np + i], b[c * np + i], acc);
+            if (++sa == A.cap) sa = 0;
+            if (++sb == A.cap) sb = 0;
         }
         A.sum[(long long)i * (A.K + 1) + k] += (double)acc;
         if (i == 0) {

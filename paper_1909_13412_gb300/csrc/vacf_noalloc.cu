@@ -69,20 +69,20 @@ __global__ void __launch_bounds__(256) k_corr_noalloc(const float *__restrict__ 
             sW[sr][l] = (s >= 0 && s < te && jj < ncomp) ? samples[s * ncomp + jj] : 0.f;
         }
         __syncthreads();
+        // 16 samples at a time against the 31 window values they meet, in
+        // registers with static indices
         const int base0 = NKT - 1 - NLW * warp;
-        float w[NLW];
+#pragma unroll 1
+        for (int tc = 0; tc < NB; tc += NLW) {
+            float a[NLW], w[2 * NLW - 1];
 #pragma unroll
-        for (int m = 0; m < NLW; ++m) w[m] = sW[base0 - m][lane];
+            for (int i = 0; i < NLW; ++i) a[i] = sA[tc + i][lane];
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {
-            const float a = sA[t][lane];
+            for (int i = 0; i < 2 * NLW - 1; ++i) w[i] = sW[base0 + tc - (NLW - 1) + i][lane];
 #pragma unroll
-            for (int m = 0; m < NLW; ++m) acc[m] = fmaf(a, w[m], acc[m]);
-            if (t + 1 < NB) {
+            for (int i = 0; i < NLW; ++i)
 #pragma unroll
-                for (int m = NLW - 1; m > 0; --m) w[m] = w[m - 1];
-                w[0] = sW[base0 + t + 1][lane];
-            }
+                for (int m = 0; m < NLW; ++m) acc[m] = fmaf(a[i], w[i - m + NLW - 1], acc[m]);
         }
     }
 #pragma unroll

@@ -399,7 +399,7 @@ def lbp_diagnostics(h: Handle):
     out = np.zeros(5, np.int64)
     _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 5)
     return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2]),
-            "rows_per_block": int(out[3]), "nodes_per_thread": int(out[4])}
+            "rows_per_block": int(out[3]), "variant": int(out[4])}
 
 
 def lbp_set_body_force(h: Handle, g, replica=-1):
@@ -412,17 +412,17 @@ def lbp_set_block_rows(h: Handle, rows):
 
 
 def lbp_autotune(h: Handle, launches=20):
-    """Pick the lattice kernel's block shape by timing; returns (rows, pair, ms)
-    with ms the 6 mean launch times (one node per thread: 1, 2, 4 rows; two
-    nodes per thread: 1, 2, 4 rows; -1 where a shape does not apply)."""
-    rows, pair = C.c_int(), C.c_int()
-    ms = (C.c_double * 6)()
-    _call("lbp_autotune", h.ptr, int(launches), C.byref(rows), C.byref(pair), ms)
-    return rows.value, pair.value, list(ms)
+    """Pick the lattice kernel's shape by timing; returns (rows, variant, ms)
+    with ms the 7 mean launch times (variant 0: 1, 2, 4 rows; variant 1: 1, 2,
+    4 rows; variant 2), -1 where a candidate does not apply."""
+    rows, variant = C.c_int(), C.c_int()
+    ms = (C.c_double * 7)()
+    _call("lbp_autotune", h.ptr, int(launches), C.byref(rows), C.byref(variant), ms)
+    return rows.value, variant.value, list(ms)
 
 
-def lbp_set_block_shape(h: Handle, rows, pair):
-    _call("lbp_set_block_shape", h.ptr, int(rows), int(pair))
+def lbp_set_block_shape(h: Handle, rows, variant):
+    _call("lbp_set_block_shape", h.ptr, int(rows), int(variant))
 
 
 def lbp_set_use_graphs(h: Handle, enable):

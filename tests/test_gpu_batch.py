@@ -237,31 +237,40 @@ def make_box(prec, kT, shape=(20, 18, 16, 0.8)):
     return h
 
 
+SHAPE_BOXES = {"20x18x16": (20, 18, 16, 0.8), "24x10x9": (24, 10, 9, 0.7), "136x5x4": (136, 5, 4, 0.9)}
+
+
 @pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16, lbp.LBP_F16])
-@pytest.mark.parametrize("batch", [False, True])
-def test_block_shapes_and_autotune_leave_results_unchanged(prec, batch):
-    """Every block shape (rows per block; one or two nodes per thread) and the
-    autotuner's pick give bitwise the same run: a single even-nx box (where the
-    2-byte types have the paired-node kernel) and the uneven batch (odd nx in
-    one box: one node per thread only)."""
+@pytest.mark.parametrize("where", ["20x18x16", "24x10x9", "136x5x4", "batch"])
+def test_kernel_shapes_and_autotune_leave_results_unchanged(prec, where):
+    """Every kernel shape -- one node per thread with 1, 2, 4 rows; two nodes
+    per thread (2-byte storage, even nx); the bulk-copy staged kernel (nx a
+    multiple of 16 bytes of storage) -- and the autotuner's pick give bitwise
+    the same run.  The boxes cover ragged segments (136 = 128 + 8), periodic
+    halos at both ends of a row, and the uneven batch (nx = 33 in one box:
+    variant 0 only)."""
     steps = 25
-    pair_ok = prec != lbp.LBP_F32 and not batch
-    shapes = [(r, 0) for r in (1, 2, 4)] + ([(r, 1) for r in (1, 2, 4)] if pair_ok else []) + ["auto"]
+    batch = where == "batch"
+    H = 4 if prec == lbp.LBP_F32 else 8
+    nxs = [b[0] for b in BOXES] if batch else [SHAPE_BOXES[where][0]]
+    ok = {0: True, 1: prec != lbp.LBP_F32 and all(n % 2 == 0 for n in nxs), 2: all(n % H == 0 for n in nxs)}
+    shapes = [(r, v) for v in (0, 1) if ok[v] for r in (1, 2, 4)] + ([(1, 2)] if ok[2] else []) + ["auto"]
     ref = None
     for shape in shapes:
-        h = make_batch(prec, 1e-4, True) if batch else make_box(prec, 1e-4)
+        h = make_batch(prec, 1e-4, True) if batch else make_box(prec, 1e-4, SHAPE_BOXES[where])
         lbp.lbp_step(h, 3)
         if shape == "auto":
-            rows, pair, ms = lbp.lbp_autotune(h, 5)
+            rows, variant, ms = lbp.lbp_autotune(h, 5)
             valid = [m for m in ms if m > 0]
-            assert len(valid) == (6 if pair_ok else 3)
-            assert ms[3 * pair + (1, 2, 4).index(rows)] == min(valid)
-            want = (rows, pair + 1)
+            assert len(valid) == 3 * ok[0] + 3 * ok[1] + ok[2]
+            k = 6 if variant == 2 else 3 * variant + (1, 2, 4).index(rows)
+            assert ms[k] == min(valid)
+            want = (rows, variant)
         else:
             lbp.lbp_set_block_shape(h, *shape)
-            want = (shape[0], shape[1] + 1)
+            want = shape
         d = lbp.lbp_diagnostics(h)
-        assert (d["rows_per_block"], d["nodes_per_thread"]) == want
+        assert (d["rows_per_block"], d["variant"]) == want
         assert lbp.lbp_get_step_index(h) == 3
         lbp.lbp_step(h, steps)
         lbp.lbp_check(h)
@@ -273,10 +282,16 @@ def test_block_shapes_and_autotune_leave_results_unchanged(prec, batch):
             assert np.array_equal(got[0], ref[0]), shape
             for k in range(4):
                 assert np.array_equal(got[1][k], ref[1][k]), (shape, k)
-    h = make_batch(prec, 0.0, True)
+    for v in (1, 2):
+        if not ok[v]:
+            h = make_batch(prec, 0.0, True) if batch else make_box(prec, 0.0, SHAPE_BOXES[where])
+            with pytest.raises(lbp.LbpError):
+                lbp.lbp_set_block_shape(h, 1, v)
+            lbp.lbp_destroy(h)
+
+
+def test_block_rows_validation():
+    h = make_batch(lbp.LBP_F32, 0.0, True)
     with pytest.raises(lbp.LbpError):
         lbp.lbp_set_block_rows(h, 3)
-    if prec != lbp.LBP_F32:
-        with pytest.raises(lbp.LbpError):  # nx = 33 in one box
-            lbp.lbp_set_block_shape(h, 1, 1)
     lbp.lbp_destroy(h)
