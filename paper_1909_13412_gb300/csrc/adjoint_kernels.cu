@@ -14,10 +14,12 @@
 // these kernels produce dL/dfhat^{n-1}, dL/dV^n, dL/dr^n and add this step's
 // share of dL/domega, dL/dgamma_i, dL/dR_i, dL/dM_i and dL/dkT.
 //
-// k_adj_particles : one particle per thread for the FP64 part, eight threads
-//   per particle for the gathers.  It re-evaluates the particle's forward step
-//   in FP64 from the recorded state, gathers lam_F(x_p) = sum_a 3 w_a e_a
-//   lam_a(x_p) at its corners (the adjoint of the body-force term), and runs
+// k_adj_gather + k_adj_fp64 : eight threads per particle gather u(x_p) and
+//   lam_F(x_p) = sum_a 3 w_a e_a lam_a(x_p) at its corners (the adjoint of the
+//   body-force term) into a small scratch array; then one thread per particle,
+//   in 64-thread blocks so that many warps share each SM's FP64 pipe (the FP64
+//   chain is long and latency-bound), re-evaluates the particle's forward step
+//   in FP64 from the recorded state and runs
 //   the chain rule backwards through the update, the random force, the
 //   spreading weights and the Stokeslet fit.  What the fit sends back to the
 //   fluid is lam_u(x_p), the adjoint of the node velocity at each corner: it
@@ -66,18 +68,18 @@ struct AdjPArgs {
     double *acc;             // [4][np]: dL/dgamma, dL/dR, dL/dM, dL/dkT (added)
     unsigned long long *rec; // records of this adjoint step
     double *fqd;             // [3][N] overflow accumulator (FP64)
+    float *ug;               // [np][8][6] scratch: u(x_p) and lam_F(x_p) per corner
 };
 
 __device__ __forceinline__ int wrap_i(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Gathers (eight threads per particle): u(x_p) of the streamed f (pull) and
+// lam_F(x_p) = sum_a 3 w_a e_a lam_a(x_p) (aligned) at the eight corners, to
+// A.ug[i][p][0..2] and A.ug[i][p][3..5].
 template <typename St>
-__global__ void __launch_bounds__(256) k_adj_particles(const AdjPArgs A) {
+__global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A) {
     const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[APB][3];
-    __shared__ float s_u[APB][8][3];
-    __shared__ float s_lf[APB][8][3];
-    __shared__ double s_lu[APB][8][3];
-    __shared__ int s_spread[APB];
     const int t = threadIdx.x, lane = t & 31;
     const int i0 = blockIdx.x * APB;
     const int cap = A.cap;
@@ -112,24 +114,31 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjPArgs A) {
             if (ey(a)) { sy += ey(a) > 0 ? gv : -gv; ly += ey(a) > 0 ? lv : -lv; }
             if (ez(a)) { sz += ez(a) > 0 ? gv : -gv; lz += ez(a) > 0 ? lv : -lv; }
         }
-        s_u[j][p][0] = sx;
-        s_u[j][p][1] = sy;
-        s_u[j][p][2] = sz;
-        s_lf[j][p][0] = lx;
-        s_lf[j][p][1] = ly;
-        s_lf[j][p][2] = lz;
+        float *o = A.ug + ((size_t)ij * 8 + p) * 6;
+        o[0] = sx;
+        o[1] = sy;
+        o[2] = sz;
+        o[3] = lx;
+        o[4] = ly;
+        o[5] = lz;
     }
-    __syncthreads();
+}
 
-    // ---- FP64 adjoint of the particle's step (one thread per particle)
-    if (t < 32 && ip < A.np) {
-        const int i = ip;
+// The FP64 adjoint of one particle's step, one particle per thread in small
+// blocks (so that many warps per SM share the FP64 pipe), then its lam_u(x_p)
+// appended to the records of the corners' row segments.
+__global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cap = A.cap;
+    if (i < A.np) {
         double r[3], V[3], q[3], lV[3], lr[3], fe[3];
+        int base[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             r[k] = A.r[k * cap + i];
             V[k] = A.v[k * cap + i];
-            q[k] = r[k] - (double)s_base[lane][k];
+            base[k] = (int)floor(r[k]);
+            q[k] = r[k] - (double)base[k];
             fe[k] = A.fext[k * cap + i];
             lV[k] = A.lam_v[k * cap + i] + (A.gv ? A.gv[3 * i + k] : 0.0);
             lr[k] = A.lam_r[k * cap + i] + (A.gr ? A.gr[3 * i + k] : 0.0);
@@ -140,10 +149,11 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjPArgs A) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             double w = 1.0;
+            const float *g = A.ug + ((size_t)i * 8 + c) * 6;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                u[c][k] = (double)s_u[lane][c][k];
-                lF[c][k] = (double)s_lf[lane][c][k];
+                u[c][k] = (double)g[k];
+                lF[c][k] = (double)g[3 + k];
                 w *= ((c >> k) & 1) ? q[k] : 1.0 - q[k];
             }
             Wp[c] = w;
@@ -340,31 +350,30 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjPArgs A) {
         A.acc[A.np + i] += gR;
         A.acc[2 * A.np + i] += gM;
         A.acc[3 * A.np + i] += gK;
+        // lam_u(x_p) to the record of each corner's row segment
+        if (spread) {
+            const int nx = A.nx, ny = A.ny, nz = A.nz;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) s_lu[lane][c][k] = lu[c][k];
-        s_spread[lane] = spread ? 1 : 0;
-    }
-    __syncthreads();
-
-    // ---- lam_u(x_p) to the record of the corner's row segment
-    if (ij < A.np && s_spread[j]) {
-        const double l0 = s_lu[j][p][0], l1 = s_lu[j][p][1], l2 = s_lu[j][p][2];
-        if (l0 != 0.0 || l1 != 0.0 || l2 != 0.0) {
-            const long long row = (long long)Z * ny + Y;
-            unsigned long long *rec = A.rec + (size_t)(row * A.nchunks + X / SEG) * REC_WORDS;
-            const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
-            if (slot < (unsigned)REC_SLOTS) {
-                reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
-                rec[REC_F0 + 3 * slot] = (unsigned long long)__double_as_longlong(l0);
-                rec[REC_F0 + 3 * slot + 1] = (unsigned long long)__double_as_longlong(l1);
-                rec[REC_F0 + 3 * slot + 2] = (unsigned long long)__double_as_longlong(l2);
-            } else {
-                const long long node = row * nx + X;
-                atomicAdd(A.fqd + node, l0);
-                atomicAdd(A.fqd + A.N + node, l1);
-                atomicAdd(A.fqd + 2 * A.N + node, l2);
+            for (int c = 0; c < 8; ++c) {
+                const double l0 = lu[c][0], l1 = lu[c][1], l2 = lu[c][2];
+                if (l0 == 0.0 && l1 == 0.0 && l2 == 0.0) continue;
+                const int X = wrap_i(base[0] + (c & 1), nx);
+                const int Y = wrap_i(base[1] + ((c >> 1) & 1), ny);
+                const int Z = wrap_i(base[2] + ((c >> 2) & 1), nz);
+                const long long row = (long long)Z * ny + Y;
+                unsigned long long *rec = A.rec + (size_t)(row * A.nchunks + X / SEG) * REC_WORDS;
+                const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
+                if (slot < (unsigned)REC_SLOTS) {
+                    reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
+                    rec[REC_F0 + 3 * slot] = (unsigned long long)__double_as_longlong(l0);
+                    rec[REC_F0 + 3 * slot + 1] = (unsigned long long)__double_as_longlong(l1);
+                    rec[REC_F0 + 3 * slot + 2] = (unsigned long long)__double_as_longlong(l2);
+                } else {
+                    const long long node = row * nx + X;
+                    atomicAdd(A.fqd + node, l0);
+                    atomicAdd(A.fqd + A.N + node, l1);
+                    atomicAdd(A.fqd + 2 * A.N + node, l2);
+                }
             }
         }
     }
@@ -523,7 +532,7 @@ static cudaError_t by_storage_adj(int precision, F &&f) {
 cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const double *r,
                                  const double *v, long long step, const double *gv,
                                  const double *gr, double *lam_v, double *lam_r, double *acc,
-                                 int parity, cudaStream_t st) {
+                                 int parity, float *ug, cudaStream_t st) {
     if (s.np == 0) return cudaSuccess;
     AdjPArgs A;
     A.g = g;
@@ -557,12 +566,16 @@ cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const 
     A.acc = acc;
     A.rec = s.rec[parity];
     A.fqd = reinterpret_cast<double *>(s.fq);
+    A.ug = ug;
     const unsigned grid = (unsigned)((s.np + APB - 1) / APB);
-    return by_storage_adj(s.precision, [&](auto tag) {
+    cudaError_t e = by_storage_adj(s.precision, [&](auto tag) {
         using St = decltype(tag);
-        k_adj_particles<St><<<grid, 8 * APB, 0, st>>>(A);
+        k_adj_gather<St><<<grid, 8 * APB, 0, st>>>(A);
         return cudaGetLastError();
     });
+    if (e != cudaSuccess) return e;
+    k_adj_fp64<<<(unsigned)((s.np + 63) / 64), 64, 0, st>>>(A);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adj_lattice(Sim &s, const void *g, const float *lam, float *lam_out, int parity,

@@ -1058,6 +1058,9 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
     guard.p.push_back(seg);
     TRY(dalloc(&lam, (size_t)2 * Q * s->P));
     guard.p.push_back(lam);
+    float *ug = nullptr;  // per-corner gathers of the particle adjoint
+    TRY(dalloc(&ug, (size_t)48 * (np > 0 ? np : 1)));
+    guard.p.push_back(ug);
     // doubles: seg_p [C][6 cap] | lam_v, lam_r [3 cap] | acc [4 np] | acc_om [nblk] |
     //          save (r, v, fh, fr) [12 cap] | g_v, g_r staged [traj] each
     const size_t n_segp = (size_t)C * pcount, n_lvr = (size_t)6 * cap, n_acc = (size_t)4 * (np > 0 ? np : 1),
@@ -1163,7 +1166,7 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
             float *ln = lam + (size_t)(L ^ 1) * Q * s->P;
             const double *rj = seg_p + (size_t)j * pcount, *vj = rj + 3 * cap;
             ADJ_CK(launch_adj_particles(*s, src, lc, rj, vj, tp.step0 + n, gv ? gv + (size_t)n * np * 3 : nullptr,
-                                        gr ? gr + (size_t)n * np * 3 : nullptr, lam_v, lam_r, acc, q, s->s0));
+                                        gr ? gr + (size_t)n * np * 3 : nullptr, lam_v, lam_r, acc, q, ug, s->s0));
             const bool timed = s->timing && e == cudaSuccess;
             if (timed) {
                 if (s->ntimed == lbp::Sim::MAX_TIMED && fold_timing(s) != LBP_OK) e = cudaErrorUnknown;

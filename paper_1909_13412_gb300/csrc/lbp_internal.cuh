@@ -354,7 +354,7 @@ constexpr int STAGED_THREADS = 256;
 cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const double *r,
                                  const double *v, long long step, const double *gv,
                                  const double *gr, double *lam_v, double *lam_r, double *acc,
-                                 int parity, cudaStream_t st);
+                                 int parity, float *ug, cudaStream_t st);
 cudaError_t launch_adj_lattice(Sim &s, const void *g, const float *lam, float *lam_out, int parity,
                                double *acc_omega, cudaStream_t st);
 int adj_lattice_blocks(const Sim &s);
