@@ -358,13 +358,12 @@ def run_gpu(args, w):
     fext = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
     r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     v_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(args.steps, 200))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        lbp.lbp_particles_set_external_force(h, fext)
-        lbp.lbp_step(h, 1)
-        lbp.lbp_particles_read(h, r=r_h, v=v_h)
+        # one public call per step: forces in, one step, positions and velocities out
+        lbp.lbp_step_exchange(h, fext, r_h, v_h)
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_max_s, = max_over_ranks([e2e_s], "cuda", dist)

@@ -188,6 +188,16 @@ lbp_status lbp_particles_count(lbp_sim *sim, int *n);
 /* Advance nsteps >= 0 time steps (asynchronous on the handle's stream).       */
 lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
 
+/* One step with the exchange a host-side controller needs, in one call and
+ * one synchronisation: f_ext ([n][3], NULL: unchanged) becomes the external
+ * force of this and later steps (as lbp_particles_set_external_force), one
+ * step runs, and r and v ([n][3] each, NULL: not read) receive the positions
+ * and velocities after it (as lbp_particles_read).  Host buffers should be
+ * page-locked for the copies to overlap nothing but each other; the call
+ * returns when the host outputs are written (on_device = 0) or, for device
+ * pointers, with the work queued on the handle's stream.                      */
+lbp_status lbp_step_exchange(lbp_sim *sim, const double *f_ext, double *r, double *v, int on_device);
+
 /* The step index n that the next step uses as its Philox counter.            */
 lbp_status lbp_set_step_index(lbp_sim *sim, int64_t step);
 lbp_status lbp_get_step_index(lbp_sim *sim, int64_t *step);

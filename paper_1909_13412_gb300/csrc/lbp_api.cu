@@ -355,7 +355,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (s->s1) cudaStreamSynchronize(s->s1);
     drop_graphs(s);
     free_tape(s);
-    void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext,
+    void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext, s->xbuf,
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
@@ -766,6 +766,40 @@ lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
     if (nsteps == 0) return LBP_OK;
     TRY(enter(s));
     for (int64_t n = 0; n < nsteps; ++n) TRY(step_once(s));
+    return leave(s);
+}
+
+lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double *v, int on_device) {
+    CHECK_SIM(s);
+    TRY(enter(s));
+    const int n = s->np;
+    if (n > 0 && (f_ext || r || v)) {
+        if (s->xbuf_cap < s->cap) {
+            CK(cudaStreamSynchronize(s->s0));
+            if (s->xbuf) cudaFree(s->xbuf);
+            s->xbuf = nullptr;
+            s->xbuf_cap = 0;
+            TRY(dalloc(&s->xbuf, (size_t)9 * s->cap));
+            s->xbuf_cap = s->cap;
+        }
+    }
+    const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (n > 0 && f_ext) {
+        s->edits += 1;  // as lbp_particles_set_external_force
+        CK(cudaMemcpyAsync(s->xbuf, f_ext, sizeof(double) * 3 * n, in, s->s0));
+        CK(launch_aos_to_soa(s->xbuf, s->fext, n, s->cap, 0, s->s0));
+    }
+    TRY(step_once(s));
+    if (n > 0 && r) {
+        CK(launch_soa_to_aos(s->r, s->xbuf + 3 * (size_t)n, n, s->cap, s->s0));
+        CK(cudaMemcpyAsync(r, s->xbuf + 3 * (size_t)n, sizeof(double) * 3 * n, out, s->s0));
+    }
+    if (n > 0 && v) {
+        CK(launch_soa_to_aos(s->v, s->xbuf + 6 * (size_t)n, n, s->cap, s->s0));
+        CK(cudaMemcpyAsync(v, s->xbuf + 6 * (size_t)n, sizeof(double) * 3 * n, out, s->s0));
+    }
+    if (!on_device) CK(cudaStreamSynchronize(s->s0));
     return leave(s);
 }
 

@@ -291,6 +291,9 @@ struct Sim {
     Tape tape;
     uint64_t edits = 0;  // state-changing calls other than steps (set_*, add)
 
+    double *xbuf = nullptr;  // [9][cap]: f_ext, r, V of lbp_step_exchange (array-of-structures)
+    int xbuf_cap = 0;
+
     // scratch for host <-> device conversions
     double *stage = nullptr;
     size_t stage_bytes = 0;

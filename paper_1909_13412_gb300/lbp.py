@@ -68,6 +68,7 @@ _SIGS = {
     "lbp_vacf_configure_ex": [_vp, C.c_int, C.c_int],
     "lbp_autotune": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "lbp_set_block_shape": [_vp, C.c_int, C.c_int],
+    "lbp_step_exchange": [_vp, _vp, _vp, _vp, C.c_int],
     "lbp_adjoint_record": [_vp, C.c_int64, C.c_int, _vp, _vp, C.c_int],
     "lbp_adjoint_backward": [_vp, _vp, _vp, C.c_int, _vp],
     "lbp_set_block_rows": [_vp, C.c_int],
@@ -317,6 +318,17 @@ def lbp_particles_count(h: Handle) -> int:
 
 def lbp_step(h: Handle, nsteps=1):
     _call("lbp_step", h.ptr, int(nsteps))
+
+
+def lbp_step_exchange(h: Handle, f_ext=None, r=None, v=None):
+    """Upload external forces, advance one step, read positions and velocities
+    ([n, 3] FP64 each, any may be None) -- one call, one synchronisation."""
+    n = h.np
+    a = _ptr(f_ext, np.float64, 3 * n, "f_ext")
+    b = _ptr(r, np.float64, 3 * n, "r", True)
+    c = _ptr(v, np.float64, 3 * n, "v", True)
+    d = _same_side(a, b, c)
+    _call("lbp_step_exchange", h.ptr, a[0], b[0], c[0], d)
 
 
 def lbp_set_step_index(h: Handle, step):

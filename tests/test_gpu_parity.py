@@ -262,6 +262,43 @@ def test_coupled_brownian_particles(mode, exclude):
     lbp.lbp_check(h)
 
 
+@pytest.mark.parametrize("device", [False, True])
+def test_step_exchange_equals_the_separate_calls(device):
+    """lbp_step_exchange(f_ext, r, v) = set_external_force + step + particles_read,
+    bitwise, step after step; f_ext = None keeps the previous forces."""
+    shape = (12, 13, 14)
+    ps = wl.uniform_particles(9, shape, 8.0, 0.5, wl.stokes_radius(0.5, 0.8), 1e-4, 3, 4)
+    ha = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=9)
+    hb = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=9)
+    g = np.random.default_rng(1)
+    n = ps.n
+    for k in range(6):
+        f = None if k == 3 else g.normal(0, 1e-5, (n, 3))
+        if f is not None:
+            lbp.lbp_particles_set_external_force(ha, f)
+        lbp.lbp_step(ha, 1)
+        ra, va = np.empty((n, 3)), np.empty((n, 3))
+        lbp.lbp_particles_read(ha, r=ra, v=va)
+        if device:
+            ft = None if f is None else torch.tensor(f, device="cuda")
+            rb = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+            vb = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+            lbp.lbp_step_exchange(hb, ft, rb, vb)
+            torch.cuda.synchronize()
+            rb, vb = rb.cpu().numpy(), vb.cpu().numpy()
+        else:
+            rb, vb = np.empty((n, 3)), np.empty((n, 3))
+            lbp.lbp_step_exchange(hb, f, rb if k != 4 else None, vb)
+            if k == 4:
+                lbp.lbp_particles_read(hb, r=rb)
+        assert np.array_equal(ra, rb) and np.array_equal(va, vb), k
+    assert lbp.lbp_get_step_index(hb) == 6
+    fa, fb = gpu_pops(ha), gpu_pops(hb)
+    assert np.array_equal(fa, fb)
+    lbp.lbp_destroy(ha)
+    lbp.lbp_destroy(hb)
+
+
 def test_set_fluid_is_the_equilibrium_of_eq17():
     """lbp_set_fluid(rho, u) sets f = f^eq(rho~, u) at every node (oracle's Eq. 17)."""
     shape = (5, 6, 7)
