@@ -62,3 +62,27 @@ def test_null_handle_is_rejected(lib):
     st = lib.lbp_step(C.c_void_p(0), 1)
     assert st == lbp.LBP_EINVAL
     assert lib.lbp_destroy(C.c_void_p(0)) == lbp.LBP_OK
+
+
+@pytest.mark.parametrize("boxes,prec", [
+    ([(4, 4, 4, 0.8)] * 257, 0),                       # more than 256 boxes
+    ([(4, 4, 4, 0.8), (4, 4, 0, 0.8)], 0),             # one empty box
+    ([(4, 4, 4, 0.8), (4, 4, 4, 0.5)], 0),             # one box with nu = 0
+    ([(1024, 1024, 1024, 0.8), (1024, 1024, 1024, 0.8)], 0),  # 2^31 nodes in all
+    ([], 0),                                           # no box
+])
+def test_create_batch_rejects_invalid_ensembles_before_touching_the_gpu(lib, boxes, prec):
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_create_batch(boxes, precision=prec)
+    assert ei.value.status == lbp.LBP_EINVAL
+    assert lbp.lbp_last_error()
+
+
+def test_create_batch_rejects_mixed_storage(lib):
+    import ctypes as C
+    descs = (lbp.lbp_lattice_desc * 2)(lbp.lbp_lattice_desc(4, 4, 4, 0.8, lbp.LBP_F32),
+                                       lbp.lbp_lattice_desc(4, 4, 4, 0.8, lbp.LBP_BF16))
+    out = C.c_void_p()
+    st = lib.lbp_create_batch(C.cast(descs, C.c_void_p), 2, C.c_void_p(0), C.byref(out))
+    assert st == lbp.LBP_EINVAL and not out.value
+    assert "precision" in lbp.lbp_last_error()
