@@ -404,8 +404,10 @@ __device__ __forceinline__ void adj_record_sum(const unsigned long long *rec, un
     }
 }
 
+// At least 6 blocks per SM: 80 registers (32 bytes spilled) instead of 96,
+// measured 6.5% faster at 256^3 (more bytes in flight per SM).
 template <typename St>
-__global__ void __launch_bounds__(SEG) k_adj_lattice(const typename St::T *__restrict__ G,
+__global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__restrict__ G,
                                                      const float *__restrict__ lam, float *lam_out,
                                                      long long P, int nx, int ny, int nz, int nchunks,
                                                      float omega, const unsigned long long *rec_cur,
