@@ -32,11 +32,13 @@
 //     lam_u     = w sum_a w_a lam_a (3 e_a + 9 (e_a.u) e_a - 3 u) + lam_u(particles)
 //     lam_f_a   = (1 - w) lam_a + lam_rho + e_a.lam_u
 //     dL/dw    += sum_a lam_a (f^eq_a - f_a)
-//   and, streaming being a permutation, dL/dfhat^{n-1}_a(x - e_a) = lam_f_a(x):
-//   every node writes its 15 results to the 15 nodes it pulled from (each
-//   target written exactly once).  It reads lam (aligned), the populations
-//   fhat^{n-1} (pulled, as forward) and writes the result: 180 bytes per node
-//   in FP32.  The record entries of a node are summed in an order fixed by
+//   and, streaming being a permutation, dL/dfhat^{n-1}_a(x - e_a) = lam_f_a(x).
+//   The adjoint buffer holds dL/df (the streamed populations) rather than
+//   dL/dfhat, so that every node stores its 15 results at its own address
+//   (aligned, like the forward pass) and reads dL/dfhat^n_a(x) as the value at
+//   x + e_a (a shifted read, which the forward pass shows costs nothing).  It
+//   reads that, the populations fhat^{n-1} (pulled, as forward) and writes
+//   the result: 180 bytes per node in FP32.  The record entries of a node are summed in an order fixed by
 //   their values, so the result does not depend on which particle appended
 //   first; entries that did not fit a record go to a dense FP64 buffer (FP64
 //   atomics, order-dependent in that rare case).  dL/dw is summed per block in
@@ -109,7 +111,9 @@ __global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A) {
             const long long src = (long long)a * A.P + ((long long)zs[ez(a) + 1] * ny + ys[ey(a) + 1]) * nx +
                                   xs[ex(a) + 1];
             const float gv = St::load(G + src, a);
-            const float lv = (3.f * wgtf(a)) * __ldg(A.lam + (long long)a * A.P + node);
+            // dL/dfhat_a(x_p) = dL/df^{n+1}_a(x_p + e_a) (the buffer's layout)
+            const long long lnode = ((long long)zs[1 - ez(a)] * ny + ys[1 - ey(a)]) * nx + xs[1 - ex(a)];
+            const float lv = (3.f * wgtf(a)) * __ldg(A.lam + (long long)a * A.P + lnode);
             if (ex(a)) { sx += ex(a) > 0 ? gv : -gv; lx += ex(a) > 0 ? lv : -lv; }
             if (ey(a)) { sy += ey(a) > 0 ? gv : -gv; ly += ey(a) > 0 ? lv : -lv; }
             if (ez(a)) { sz += ez(a) > 0 ? gv : -gv; lz += ez(a) > 0 ? lv : -lv; }
@@ -431,9 +435,11 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
     float g[Q], l[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        const int o = ox[ex(a) + 1] + oy[ey(a) + 1] + oz[ez(a) + 1];
+        const int o = ox[ex(a) + 1] + oy[ey(a) + 1] + oz[ez(a) + 1];   // x - e_a
+        const int op = ox[1 - ex(a)] + oy[1 - ey(a)] + oz[1 - ez(a)];  // x + e_a
         g[a] = St::load(G + (long long)a * P + d + o, a);
-        l[a] = __ldg(lam + (long long)a * P + d);
+        // dL/dfhat^n_a(x) = dL/df^{n+1}_a(x + e_a): the buffer holds the latter
+        l[a] = __ldg(lam + (long long)a * P + d + op);
     }
     const unsigned long long rw = __ldg(rec_cur + ((size_t)row * nchunks + chunk) * REC_WORDS + lane);
     // particle contributions lam_u(x)
@@ -503,9 +509,8 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
     if (act) {
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const int o = ox[ex(a) + 1] + oy[ey(a) + 1] + oz[ez(a) + 1];
             const float v = om1 * l[a] + lrho + (float)ex(a) * lux + (float)ey(a) * luy + (float)ez(a) * luz;
-            lam_out[(long long)a * P + d + o] = v;
+            lam_out[(long long)a * P + d] = v;  // dL/df^n_a(x), aligned
         }
     }
     // dL/domega: FP64 block sum into the block's own slot
@@ -598,20 +603,30 @@ int adj_lattice_blocks(const Sim &s) {
     return rp.ny * rp.nz * rp.nchunks;
 }
 
-__global__ void k_f32_to_f64(const float *src, double *dst, long long N, long long P) {
+// dL/dfhat_a(y) of the first recorded state = dL/df_a(y + e_a) of its first
+// step (the buffer's layout), to the FP64 [15][N] ABI layout
+__global__ void k_adj_out(const float *src, double *dst, int nx, int ny, int nz, long long N, long long P) {
     const long long total = (long long)Q * N;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int a = (int)(t / N);
         const long long i = t - (long long)a * N;
-        dst[t] = (double)src[(long long)a * P + i];
+        const int x = (int)(i % nx);
+        const long long yz = i / nx;
+        const int y = (int)(yz % ny), z = (int)(yz / ny);
+        int xs = x + ex(a), ys = y + ey(a), zs = z + ez(a);
+        xs = xs == nx ? 0 : (xs < 0 ? nx - 1 : xs);
+        ys = ys == ny ? 0 : (ys < 0 ? ny - 1 : ys);
+        zs = zs == nz ? 0 : (zs < 0 ? nz - 1 : zs);
+        dst[t] = (double)src[(long long)a * P + ((long long)zs * ny + ys) * nx + xs];
     }
 }
 
 cudaError_t launch_f32_to_f64(Sim &s, const float *src, double *dst, cudaStream_t st) {
     long long g = ((long long)Q * s.N + 255) / 256;
     if (g > (long long)s.num_sms * 16) g = (long long)s.num_sms * 16;
-    k_f32_to_f64<<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, s.N, s.P);
+    k_adj_out<<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, s.reps[0].nx, s.reps[0].ny, s.reps[0].nz,
+                                                        s.N, s.P);
     return cudaGetLastError();
 }
 
