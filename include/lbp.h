@@ -330,7 +330,7 @@ lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp
  * positions at the first recorded step ([n_particles][3]) and the populations
  * at the first recorded step ([15][N], ABI layout).  The reverse sweep
  * re-runs each segment between checkpoints forward from its checkpoint
- * (keeping that segment's states: checkpoint_every population copies), then
+ * (keeping that segment's later states: checkpoint_every - 1 population copies), then
  * steps the adjoint back through it; the handle's own state (populations,
  * particles, step index) is left as the recording left it.  Requires that no
  * step, particle change or new recording happened since lbp_adjoint_record

@@ -1088,7 +1088,8 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
                 if (q) cudaFree(q);
         }
     } guard;
-    TRY(dalloc(&seg, pop_bytes * (size_t)C));
+    // the states of a segment after its first (the first is the checkpoint itself)
+    TRY(dalloc(&seg, pop_bytes * (size_t)(C > 1 ? C - 1 : 1)));
     guard.p.push_back(seg);
     TRY(dalloc(&lam, (size_t)2 * Q * s->P));
     guard.p.push_back(lam);
@@ -1155,7 +1156,9 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
         const int64_t n0 = k * C;
         const int m = (int)(T - n0 < C ? T - n0 : C);
         // replay the segment forward from its checkpoint, keeping every state
-        ADJ_CK(cudaMemcpyAsync(seg, tp.ck_f + (size_t)k * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, s->s0));
+        // state j of the segment: the checkpoint for j = 0, else replay slot j - 1
+        char *ck = tp.ck_f + (size_t)k * pop_bytes;
+        auto state = [&](int j) -> char * { return j == 0 ? ck : seg + (size_t)(j - 1) * pop_bytes; };
         if (np > 0) {
             ADJ_CK(cudaMemcpyAsync(s->r, tp.ck_p + (size_t)k * pcount, sizeof(double) * 3 * cap,
                                    cudaMemcpyDeviceToDevice, s->s0));
@@ -1178,8 +1181,8 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
                                        cudaMemcpyDeviceToDevice, s->s0));
             }
             if (j == m - 1) break;
-            const void *src = seg + (size_t)j * pop_bytes;
-            void *dst = seg + (size_t)(j + 1) * pop_bytes;
+            const void *src = state(j);
+            void *dst = state(j + 1);
             if (np > 0) {
                 ADJ_CK(launch_particles(*s, src, parity, s->s0));
                 ADJ_CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
@@ -1195,7 +1198,7 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
         for (int j = m - 1; j >= 0 && e == cudaSuccess; --j) {
             const int64_t n = n0 + j;
             const int q = j & 1;
-            const void *src = seg + (size_t)j * pop_bytes;
+            const void *src = state(j);
             const float *lc = lam + (size_t)L * Q * s->P;
             float *ln = lam + (size_t)(L ^ 1) * Q * s->P;
             const double *rj = seg_p + (size_t)j * pcount, *vj = rj + 3 * cap;

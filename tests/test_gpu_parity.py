@@ -555,3 +555,49 @@ def test_reduced_precision_subrun_error(prec, tol_v, tol_u):
     assert np.max(np.abs(V - Vo)) <= tol_v * np.max(np.abs(Vo))
     assert np.max(np.abs(u.reshape(uo.shape) - uo)) <= tol_u * np.max(np.abs(uo))
     lbp.lbp_check(h)
+
+
+# ---------------------------------------------------------------- full size
+@pytest.mark.parametrize("prec,tol_v,tol_f", [(lbp.LBP_F32, 1e-5, 1e-5), (lbp.LBP_BF16, 2e-2, 1e-2),
+                                              (lbp.LBP_F16, 2e-3, 2e-3)])
+def test_full_size_bench_workload_against_the_oracle(prec, tol_v, tol_f):
+    """The bench workload at its full size (256^3, 16384 Brownian particles,
+    kT = 1e-4) in the launch configuration the bench times (autotuned kernel
+    shape, CUDA graphs, VACF accumulating to lag 5000), two steps from a
+    perturbed state, against the FP64 oracle: every particle's F_R bit for bit,
+    F_H, V and r within the stated tolerance, and populations on 200000
+    sampled nodes.  Tolerances per storage type: FP32 as the small-box tests;
+    BF16 and FP16 at the one-step storage errors stated in the design doc."""
+    w = wl.BROWNIAN_256
+    nz, ny, nx = w.shape_zyx
+    ps = w.particles()
+    f0 = wl.perturbed_populations(W, w.shape_zyx, 0.01, 31)
+    h = lbp.lbp_create(nx, ny, nz, w.tau, precision=prec)
+    lbp.lbp_set_populations(h, f0)
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise)
+    lbp.lbp_vacf_configure(h, 5000)
+    lbp.lbp_autotune(h, 3)
+    # the oracle starts from what the GPU stores (the 2-byte types round f0)
+    fs = gpu_pops(h)
+    o = oracle_sim(w.shape_zyx, w.tau, ps, kT=w.kT, seed=w.seed_noise)
+    o.set_fhat(fs)
+    del fs
+    lbp.lbp_step(h, 2)
+    o.step(2)
+    r, V, FH, FR = gpu_particles(h)
+    ro, Vo, FHo, FRo = o.particles()
+    assert np.array_equal(FR, FRo)
+    assert np.max(np.abs(V - Vo)) <= tol_v * np.max(np.abs(Vo))
+    assert np.max(np.abs(FH - FHo)) <= tol_v * np.max(np.abs(FHo))
+    d = np.abs(r - ro)
+    d = np.minimum(d, np.array([nx, ny, nz], float) - d)
+    assert np.max(d) <= tol_v
+    f = gpu_pops(h).reshape(15, -1)
+    fo = o.fhat().reshape(15, -1)
+    o.close()
+    idx = np.random.default_rng(5).choice(f.shape[1], 200000, replace=False)
+    scale = np.max(np.abs(fo[:, idx] - W[:, None]))
+    assert np.max(np.abs(f[:, idx] - fo[:, idx])) <= tol_f * scale + F64_FLOOR
+    lbp.lbp_check(h)
+    lbp.lbp_destroy(h)
