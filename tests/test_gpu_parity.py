@@ -601,3 +601,78 @@ def test_full_size_bench_workload_against_the_oracle(prec, tol_v, tol_f):
     assert np.max(np.abs(f[:, idx] - fo[:, idx])) <= tol_f * scale + F64_FLOOR
     lbp.lbp_check(h)
     lbp.lbp_destroy(h)
+
+
+def test_full_size_vacf_run_against_its_own_trajectory():
+    """The VACF run at its full size (128^3, 2000 Brownian particles, lag 5000),
+    6000 steps: the library's VACF sums equal the all-origins correlation of the
+    trajectory read back step by step (FP32 velocities, products summed in FP64
+    by FFT), to 1e-5 of C(0); pair counts exact."""
+    w = wl.BROWNIAN_128
+    nz, ny, nx = w.shape_zyx
+    ps = w.particles()
+    K, T = w.vacf_lag, 6000
+    h = lbp.lbp_create(nx, ny, nz, w.tau)
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=w.kT, seed=w.seed_noise)
+    lbp.lbp_vacf_configure(h, K)
+    lbp.lbp_autotune(h, 3)
+    n = ps.n
+    traj = np.empty((T, n, 3), np.float32)
+    V = np.empty((n, 3))
+    for t in range(T):
+        lbp.lbp_step_exchange(h, None, None, V)
+        traj[t] = V
+    cs = np.empty(K + 1)
+    cnt = np.empty(K + 1, np.int64)
+    lbp.lbp_vacf_read(h, cs, cnt)
+    lbp.lbp_check(h)
+    lbp.lbp_destroy(h)
+    x = traj.reshape(T, 3 * n).astype(np.float64)
+    L = 1 << int(np.ceil(np.log2(2 * T)))
+    F = np.fft.rfft(x, n=L, axis=0)
+    ref = np.fft.irfft((F * np.conj(F)).sum(axis=1), n=L)[:K + 1]
+    assert np.array_equal(cnt, n * (T - np.arange(K + 1)))
+    assert np.max(np.abs(cs - ref)) <= 1e-5 * ref[0]
+
+
+def test_full_size_ensemble_equals_its_boxes_alone():
+    """The ensemble at its full size (48 x 64^3 + 16 x 96^3 + 4 x 160^3, one
+    Brownian particle each, tau in {0.6, 0.8, 1.0}), in the bench's launch
+    configuration (autotuned shape, graphs, per-particle VACF), five steps:
+    every box and its particle bitwise equal to the same box run alone (box 0,
+    whose particle has index 0 in both, with the random force on; the others
+    with kT = 0, since a particle's Philox counter is its index in the handle)."""
+    e = wl.ENSEMBLE_68
+    steps = 5
+    for kT in (e.kT, 0.0):
+        h = lbp.lbp_create_batch(e.boxes)
+        for b in range(len(e.boxes)):
+            p = e.particles(b)
+            lbp.lbp_particles_add_to(h, b, p.r, p.V, p.M, p.gamma, p.R)
+        lbp.lbp_particles_set_params(h, kT=kT, seed=e.seed_noise)
+        lbp.lbp_vacf_configure_ex(h, 5000, 1)
+        lbp.lbp_autotune(h, 3)
+        lbp.lbp_step(h, steps)
+        f = np.empty((15, h.N))
+        lbp.lbp_read_populations(h, f)
+        V = np.empty((len(e.boxes), 3))
+        lbp.lbp_particles_read(h, v=V)
+        lbp.lbp_destroy(h)
+        off = 0
+        for b, (bx, by, bz, tau) in enumerate(e.boxes):
+            nb = bx * by * bz
+            if (kT > 0) == (b == 0):
+                p = e.particles(b)
+                hs = lbp.lbp_create(bx, by, bz, tau)
+                lbp.lbp_particles_add(hs, p.r, p.V, p.M, p.gamma, p.R)
+                lbp.lbp_particles_set_params(hs, kT=kT, seed=e.seed_noise)
+                lbp.lbp_step(hs, steps)
+                fs = np.empty((15, nb))
+                lbp.lbp_read_populations(hs, fs)
+                Vs = np.empty((1, 3))
+                lbp.lbp_particles_read(hs, v=Vs)
+                lbp.lbp_destroy(hs)
+                assert np.array_equal(f[:, off:off + nb], fs), b
+                assert np.array_equal(V[b], Vs[0]), b
+            off += nb
