@@ -5,11 +5,11 @@
 //
 //      s0:  k_particles (fhat^{n-1} -> F_H, V, r, force records)
 //           -> k_stream_collide_forced (fhat^{n-1} + records -> fhat^n)
-//      s1:  every 64th step the VACF block, forked after k_particles and
-//           joined at the end of the step, so it overlaps the lattice pass.
+//      s1:  after every 64th step the VACF block, which overlaps the next
+//           steps; s0 waits for it only before the following block is forked.
 //
-// A step is captured into a CUDA graph per (buffer parity, VACF block due)
-// and replayed.
+// A step is captured into a CUDA graph per buffer parity and replayed; the
+// VACF fork stays outside the graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -75,11 +75,16 @@ lbp_status leave(lbp_sim *s) {
 }
 
 void drop_graphs(lbp_sim *s) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (s->graph[i]) {
             cudaGraphExecDestroy(s->graph[i]);
             s->graph[i] = nullptr;
         }
+        if (s->xgraph[i]) {
+            cudaGraphExecDestroy(s->xgraph[i]);
+            s->xgraph[i] = nullptr;
+        }
+    }
 }
 
 lbp_status stage(lbp_sim *s, size_t bytes) {
@@ -116,17 +121,33 @@ bool radius_ok(double R, int exclude) {
 
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
-// one time step (see the sequence at the top of this file)
-lbp_status enqueue_step(lbp_sim *s, bool timed) {
+lbp_status exchange_out(lbp_sim *s, double *r, double *v, cudaMemcpyKind kind, cudaStream_t st);
+
+// one time step (see the sequence at the top of this file).  With `readback`
+// (r, v host buffers, either may be NULL) the positions and velocities the
+// particle kernel has just written go to the host on s2 while s0 runs the
+// lattice pass; ev_xdone marks the end of that branch.
+struct Readback {
+    double *r, *v;
+};
+lbp_status enqueue_step(lbp_sim *s, bool timed, const Readback *readback = nullptr) {
     const void *src = s->f[s->cur];
     void *dst = s->f[s->cur ^ 1];
     const int parity = s->cur;
     if (s->np > 0) CK(launch_particles(*s, src, parity, s->s0));
+    if (readback) {
+        CK(cudaEventRecord(s->ev_xmid, s->s0));
+        CK(cudaStreamWaitEvent(s->s2, s->ev_xmid, 0));
+        TRY(exchange_out(s, readback->r, readback->v, cudaMemcpyDeviceToHost, s->s2));
+        CK(cudaEventRecordWithFlags(s->ev_xdone, s->s2, cudaEventRecordExternal));
+        CK(cudaEventRecord(s->ev_xjoin, s->s2));
+    }
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
     if (s->np > 0)
         CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
     else
         CK(launch_stream_collide(*s, src, dst, s->s0));
+    if (readback) CK(cudaStreamWaitEvent(s->s0, s->ev_xjoin, 0));
     if (timed) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
@@ -188,8 +209,10 @@ lbp_status capture(lbp_sim *s, int parity) {
     return LBP_OK;
 }
 
-// one time step on s0 (graph replay, timed or plain launches)
-lbp_status step_once(lbp_sim *s) {
+// one time step on s0 (graph replay, timed or plain launches); `whole`, when
+// given, is a graph that holds this step with copies around it and replaces
+// the step graph of this parity
+lbp_status step_once(lbp_sim *s, cudaGraphExec_t whole = nullptr) {
     // the VACF correlator runs when the step completes a block of B samples
     const int B = vacf_block_samples();
     bool due = false;
@@ -200,7 +223,9 @@ lbp_status step_once(lbp_sim *s) {
             s->vacf_done_host += B;
         }
     }
-    if (s->timing) {
+    if (whole) {
+        CK(cudaGraphLaunch(whole, s->s0));
+    } else if (s->timing) {
         if (s->ntimed == lbp::Sim::MAX_TIMED) TRY(fold_timing(s));
         TRY(enqueue_step(s, true));
     } else if (s->use_graphs) {
@@ -214,6 +239,75 @@ lbp_status step_once(lbp_sim *s) {
     s->step += 1;
     return LBP_OK;
 }
+
+// the exchange's copies and conversions before and after one step, on s0
+lbp_status exchange_in(lbp_sim *s, const double *f_ext, cudaMemcpyKind kind) {
+    const int n = s->np;
+    if (n > 0 && f_ext) {
+        CK(cudaMemcpyAsync(s->xbuf, f_ext, sizeof(double) * 3 * n, kind, s->s0));
+        CK(launch_aos_to_soa(s->xbuf, s->fext, n, s->cap, 0, s->s0));
+    }
+    return LBP_OK;
+}
+
+lbp_status exchange_out(lbp_sim *s, double *r, double *v, cudaMemcpyKind kind, cudaStream_t st) {
+    const int n = s->np;
+    if (n > 0 && r) {
+        CK(launch_soa_to_aos(s->r, s->xbuf + 3 * (size_t)n, n, s->cap, st));
+        CK(cudaMemcpyAsync(r, s->xbuf + 3 * (size_t)n, sizeof(double) * 3 * n, kind, st));
+    }
+    if (n > 0 && v) {
+        CK(launch_soa_to_aos(s->v, s->xbuf + 6 * (size_t)n, n, s->cap, st));
+        CK(cudaMemcpyAsync(v, s->xbuf + 6 * (size_t)n, sizeof(double) * 3 * n, kind, st));
+    }
+    return LBP_OK;
+}
+
+// [copy in, step with the read-back branch] from and to page-locked host
+// buffers as one graph for the current buffer parity, kept while the same
+// buffers come back
+lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v, cudaGraphExec_t *out) {
+    const int par = s->cur;
+    const void *key[3] = {f_ext, r, v};
+    bool same = s->xgraph[par] && s->xkey_np[par] == s->np;
+    for (int k = 0; k < 3 && same; ++k) same = s->xkey[par][k] == key[k];
+    if (!same) {
+        if (s->xgraph[par]) {
+            cudaGraphExecDestroy(s->xgraph[par]);
+            s->xgraph[par] = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
+        const Readback rb{r, v};
+        lbp_status st = exchange_in(s, f_ext, cudaMemcpyHostToDevice);
+        if (st == LBP_OK) st = enqueue_step(s, false, &rb);
+        cudaError_t e = cudaStreamEndCapture(s->s0, &g);
+        if (st != LBP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CK(e);
+        e = cudaGraphInstantiate(&s->xgraph[par], g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        for (int k = 0; k < 3; ++k) s->xkey[par][k] = key[k];
+        s->xkey_np[par] = s->np;
+    }
+    *out = s->xgraph[par];
+    return LBP_OK;
+}
+
+// page-locked (or registered) host memory, which a graph's copy nodes may use
+bool host_pinned(const void *p) {
+    if (!p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
 
 void free_tape(lbp_sim *s) {
     if (s->tape.ck_f) cudaFree(s->tape.ck_f);
@@ -315,10 +409,14 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s0, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s1, cudaStreamNonBlocking, prio_low);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s2, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_xmid, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_xjoin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_xdone, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fail(LBP_ECUDA, "lbp_create: %s", cudaGetErrorString(e));
         return bail(LBP_ECUDA);
@@ -353,6 +451,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (!s) return LBP_OK;
     if (s->s0) cudaStreamSynchronize(s->s0);
     if (s->s1) cudaStreamSynchronize(s->s1);
+    if (s->s2) cudaStreamSynchronize(s->s2);
     drop_graphs(s);
     free_tape(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext, s->xbuf,
@@ -363,11 +462,12 @@ lbp_status lbp_destroy(lbp_sim *s) {
         if (b) cudaFree(b);
     for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
         if (s->tev[i]) cudaEventDestroy(s->tev[i]);
-    cudaEvent_t evs[] = {s->ev_in, s->ev_out, s->ev_fork, s->ev_join};
+    cudaEvent_t evs[] = {s->ev_in, s->ev_out, s->ev_fork, s->ev_join, s->ev_xmid, s->ev_xjoin, s->ev_xdone};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
     if (s->s0) cudaStreamDestroy(s->s0);
     if (s->s1) cudaStreamDestroy(s->s1);
+    if (s->s2) cudaStreamDestroy(s->s2);
     delete s;
     return LBP_OK;
 }
@@ -769,6 +869,7 @@ lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
     return leave(s);
 }
 
+
 lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double *v, int on_device) {
     CHECK_SIM(s);
     TRY(enter(s));
@@ -779,26 +880,28 @@ lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double 
             if (s->xbuf) cudaFree(s->xbuf);
             s->xbuf = nullptr;
             s->xbuf_cap = 0;
+            drop_graphs(s);  // the exchange graphs hold the old buffer
             TRY(dalloc(&s->xbuf, (size_t)9 * s->cap));
             s->xbuf_cap = s->cap;
         }
     }
+    if (n > 0 && f_ext) s->edits += 1;  // as lbp_particles_set_external_force
+    const bool as_graph = !on_device && n > 0 && s->use_graphs && !s->timing && host_pinned(f_ext) &&
+                          host_pinned(r) && host_pinned(v);
+    if (as_graph) {
+        // returns once f_ext has been consumed and r, v are on the host; the
+        // step's lattice pass may still run, and later work on s0 follows it
+        cudaGraphExec_t whole = nullptr;
+        TRY(exchange_graph(s, f_ext, r, v, &whole));
+        TRY(step_once(s, whole));
+        CK(cudaEventSynchronize(s->ev_xdone));
+        return leave(s);
+    }
     const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (n > 0 && f_ext) {
-        s->edits += 1;  // as lbp_particles_set_external_force
-        CK(cudaMemcpyAsync(s->xbuf, f_ext, sizeof(double) * 3 * n, in, s->s0));
-        CK(launch_aos_to_soa(s->xbuf, s->fext, n, s->cap, 0, s->s0));
-    }
+    TRY(exchange_in(s, f_ext, in));
     TRY(step_once(s));
-    if (n > 0 && r) {
-        CK(launch_soa_to_aos(s->r, s->xbuf + 3 * (size_t)n, n, s->cap, s->s0));
-        CK(cudaMemcpyAsync(r, s->xbuf + 3 * (size_t)n, sizeof(double) * 3 * n, out, s->s0));
-    }
-    if (n > 0 && v) {
-        CK(launch_soa_to_aos(s->v, s->xbuf + 6 * (size_t)n, n, s->cap, s->s0));
-        CK(cudaMemcpyAsync(v, s->xbuf + 6 * (size_t)n, sizeof(double) * 3 * n, out, s->s0));
-    }
+    TRY(exchange_out(s, r, v, out, s->s0));
     if (!on_device) CK(cudaStreamSynchronize(s->s0));
     return leave(s);
 }

@@ -249,6 +249,10 @@ struct Sim {
     cudaStream_t s0 = nullptr;    // library main stream (non-blocking)
     cudaStream_t s1 = nullptr;    // library side stream (particles, VACF)
     cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
+    // lbp_step_exchange: the read-back branch (positions and velocities after
+    // the particle kernel, alongside the lattice pass) and its events
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_xmid = nullptr, ev_xjoin = nullptr, ev_xdone = nullptr;
 
     void *f[2] = {nullptr, nullptr};   // deviation populations, 15 planes of P (storage type)
     int cur = 0;                       // f[cur] holds fhat^n
@@ -301,6 +305,11 @@ struct Sim {
     // graphs
     int use_graphs = 1;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, by buffer parity
+    // lbp_step_exchange with page-locked host buffers: copies + step, by parity,
+    // with the buffer addresses and particle count it was captured for
+    cudaGraphExec_t xgraph[2] = {nullptr, nullptr};
+    const void *xkey[2][3] = {};
+    int xkey_np[2] = {0, 0};
     int vacf_pending = 0;  // a VACF block runs on s1 (ev_join marks its end)
 
     // kernel timing

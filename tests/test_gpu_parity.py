@@ -299,6 +299,49 @@ def test_step_exchange_equals_the_separate_calls(device):
     lbp.lbp_destroy(hb)
 
 
+def test_step_exchange_with_page_locked_buffers_equals_the_separate_calls():
+    """With page-locked host buffers lbp_step_exchange replays copies + step as
+    one graph per buffer parity; it stays bitwise equal to the separate calls
+    across two alternating buffer sets, f_ext = None (previous forces kept), a
+    parameter change between steps, and a VACF run whose 64-sample blocks are
+    forked mid-way."""
+    shape = (12, 13, 14)
+    ps = wl.uniform_particles(7, shape, 8.0, 0.5, wl.stokes_radius(0.5, 0.8), 1e-4, 3, 5)
+    ha = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=4)
+    hb = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=4)
+    K = 20
+    for h in (ha, hb):
+        lbp.lbp_vacf_configure(h, K)
+    n = ps.n
+    pin = lambda: torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    sets = [(pin(), pin(), pin()), (pin(), pin(), pin())]
+    g = np.random.default_rng(2)
+    for k in range(150):
+        keep = k % 7 == 6
+        f = g.normal(0, 1e-5, (n, 3))
+        fb, rb, vb = sets[(k // 3) % 2]
+        if k == 90:  # an edit between steps drops the cached graphs
+            for h in (ha, hb):
+                lbp.lbp_particles_set_params(h, kT=2e-4, seed=4)
+        if not keep:
+            lbp.lbp_particles_set_external_force(ha, f)
+        lbp.lbp_step(ha, 1)
+        ra, va = np.empty((n, 3)), np.empty((n, 3))
+        lbp.lbp_particles_read(ha, r=ra, v=va)
+        fb[:] = f
+        lbp.lbp_step_exchange(hb, None if keep else fb, rb, vb)
+        assert np.array_equal(ra, rb) and np.array_equal(va, vb), k
+    assert lbp.lbp_get_step_index(hb) == 150
+    assert np.array_equal(gpu_pops(ha), gpu_pops(hb))
+    ca, na = np.zeros(K + 1), np.zeros(K + 1, np.int64)
+    cb, nb = np.zeros(K + 1), np.zeros(K + 1, np.int64)
+    lbp.lbp_vacf_read(ha, ca, na)
+    lbp.lbp_vacf_read(hb, cb, nb)
+    assert na[0] > 0 and np.array_equal(na, nb) and np.array_equal(ca, cb)
+    for h in (ha, hb):
+        lbp.lbp_destroy(h)
+
+
 def test_set_fluid_is_the_equilibrium_of_eq17():
     """lbp_set_fluid(rho, u) sets f = f^eq(rho~, u) at every node (oracle's Eq. 17)."""
     shape = (5, 6, 7)
