@@ -317,11 +317,15 @@ def run_gpu(args, w):
 
     def make(precision, wk=w):
         h = make_handle(lbp, wk, precision, wk.seed_noise + rank, args.vacf_lag)
-        # block shape of the lattice kernel, picked by timing (outside the timed region)
+        # block shape of the lattice kernel, picked by timing (outside the timed
+        # region) after two steps, so that the candidates see this workload's
+        # particle forces in the records
+        lbp.lbp_step(h, 2)
         rows, variant, tms = lbp.lbp_autotune(h, 10)
-        names = ("1node_1row", "1node_2rows", "1node_4rows", "2nodes_1row", "2nodes_2rows", "2nodes_4rows",
-                 "bulk_staged")
-        h.tuned = {"variant": names[3 * variant + (1, 2, 4).index(rows)] if variant < 2 else names[6],
+        per_thread = {0: "1node", 1: "2nodes", 3: "4nodes"}
+        names = [per_thread[v] + ("_1row" if r == 1 else f"_{r}rows") if v != 2 else "bulk_staged"
+                 for v, r in lbp.AUTOTUNE_SHAPES]
+        h.tuned = {"variant": names[lbp.AUTOTUNE_SHAPES.index((variant, 1 if variant == 2 else rows))],
                    "ms_by_shape": {n: t for n, t in zip(names, tms) if t > 0}}
         return h
 

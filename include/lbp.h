@@ -259,17 +259,23 @@ lbp_status lbp_set_body_force(lbp_sim *sim, int replica, const double *g);
  *              1, 2 or 4 rows (2-byte storage, every box with even nx);
  *   variant 2: persistent CTAs that stage each plane's source row segments in
  *              shared memory with bulk asynchronous copies (every box's nx a
- *              multiple of 16 bytes of storage: 4 for LBP_F32, 8 otherwise).
+ *              multiple of 16 bytes of storage: 4 for LBP_F32, 8 otherwise);
+ *   variant 3: four neighbouring nodes per thread with 8-byte loads and
+ *              stores, one warp per 128-node row segment, 1, 2 or 4 rows
+ *              (2-byte storage, every box's nx a multiple of 4).
  * Each candidate runs `launches` back-to-back launches (1..1000) after two
  * warm-up launches, twice, best pass kept.  rows, variant (optional) receive
- * the pick; ms (optional, 7 doubles) the mean launch times in ms for
- * (variant 0: 1, 2, 4 rows; variant 1: 1, 2, 4 rows; variant 2), -1 where a
- * candidate does not apply.  The simulation state is unchanged: the launches
- * read the current populations, write only the buffer the next step
- * overwrites, see an all-zero copy of the force records and bump a scratch
- * step counter.  Synchronous; LBP_ETIMEOUT if a bounded device wait ran out.
- * Default before any call: variant 0 with 1 row (LBP_F32) or 2 rows (the
- * 2-byte types), the fastest on GB300 for the bench workloads.               */
+ * the pick; ms (optional, LBP_AUTOTUNE_CANDIDATES doubles) the mean launch
+ * times in ms for (variant 0: 1, 2, 4 rows; variant 1: 1, 2, 4 rows;
+ * variant 2; variant 3: 1, 2, 4 rows), -1 where a candidate does not apply.
+ * The simulation state is unchanged: the launches read the current
+ * populations, write only the buffer the next step overwrites, read a copy of
+ * the last step's force records (all zero before the first step; run a few
+ * steps first for timings that include the particle coupling) and bump a
+ * scratch step counter.
+ * Synchronous; LBP_ETIMEOUT if a bounded device wait ran out.  Default before
+ * any call: variant 0 with 1 row (LBP_F32) or 2 rows (the 2-byte types).     */
+#define LBP_AUTOTUNE_CANDIDATES 10
 lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, int *variant, double *ms);
 
 /* Fix the kernel shape by hand (LBP_EINVAL where the variant does not apply;

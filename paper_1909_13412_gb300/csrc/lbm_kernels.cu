@@ -338,6 +338,157 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
     }
 }
 
+// Sum, exactly, the record entries whose x is one of x .. x + 3 (one pass
+// over the slots for four nodes; the same integer sums as record_sum).
+__device__ __forceinline__ void record_sum4(unsigned long long rw, int cnt, int x, long long s[4][3]) {
+    const int used = cnt < REC_SLOTS ? cnt : REC_SLOTS;
+    for (int sl = 0; sl < used; ++sl) {
+        const unsigned long long xw2 = __shfl_sync(0xffffffffu, rw, REC_X0 + (sl >> 1));
+        const int k = (int)(unsigned)(xw2 >> (32 * (sl & 1))) - x;
+        const long long v0 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl);
+        const long long v1 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 1);
+        const long long v2 = (long long)__shfl_sync(0xffffffffu, rw, REC_F0 + 3 * sl + 2);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+            if (k == kk) {
+                s[kk][0] += v0;
+                s[kk][1] += v1;
+                s[kk][2] += v2;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Four-node variant for the 2-byte storage types (every box with nx a
+// multiple of 4).  One warp per SEG-node row segment (and R rows): lane l owns
+// the nodes x .. x + 3, x = segment start + 4 l, and moves each plane's four
+// 2-byte deviations with one 8-byte load and one 8-byte store, so a warp
+// touches the segment's 256 contiguous bytes per plane.  The pull in x is done
+// in registers as in the paired kernel: for e_x = +1 the node left of x is the
+// top element of the left lane's group, for e_x = -1 the node right of x + 3
+// is the bottom element of the right lane's group (warp shuffles); the lanes
+// at a warp's or a row's end load that one element themselves (periodic in
+// x).  A thread keeps 15 R 8-byte loads in flight in 30 R registers, twice the
+// bytes per register of the paired kernel, and collides the pairs (x, x + 1)
+// and (x + 2, x + 3) in turn, packing the results over the pulled values.
+// Per node the arithmetic is that of collide_values, and the force sums are
+// the same exact integer sums: results equal the other kernels' bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int QUAD_WARPS = 4;  // row segments (warps) per block
+
+template <typename St>
+__device__ __forceinline__ unsigned load_elem(const typename St::T *p) {
+    return (unsigned)__ldg(reinterpret_cast<const unsigned short *>(p));
+}
+
+template <typename St, int R, int MAXR, bool FORCED>
+__global__ void __launch_bounds__(32 * QUAD_WARPS) k_stream_collide_quad(
+    Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+    const unsigned item = blockIdx.x * QUAD_WARPS + (threadIdx.x >> 5);
+    if (item >= rt.item_off[MAXR == 1 ? 1 : rt.nrep]) return;  // whole warp past the last segment
+    const int r = find_block_rep(rt, item);
+    const Rep &rp = rt.rep[r];
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
+    const unsigned nrows = (unsigned)ny * (unsigned)nz;
+    const int lane = threadIdx.x & 31;
+    const unsigned it = item - rt.item_off[r];
+    const unsigned grp = it / (unsigned)nchunks;
+    const int chunk = (int)(it - grp * (unsigned)nchunks);
+    const size_t seg0 = (size_t)rp.seg_off;
+    if (FORCED && lane < R && grp * R + lane < nrows)
+        rec_prev[(seg0 + (size_t)(grp * R + lane) * nchunks + chunk) * REC_WORDS] = 0ull;
+    const int x0 = chunk * SEG + 4 * lane;
+    const bool act = x0 < nx;
+    const int x = act ? x0 : nx - 4;         // inactive lanes read a valid group
+    const int xl = x == 0 ? nx - 1 : x - 1;  // periodic neighbours of the group
+    const int xr = x + 4 == nx ? 0 : x + 4;
+    const bool own_left = lane == 0;                    // no left lane in the warp
+    const bool own_right = lane == 31 || x0 + 4 >= nx;  // no (active) right lane
+    const int base = (int)rp.node_off;
+    uint2 p[R][Q];
+    unsigned long long rw[R];
+    int drow[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
+        const NodeIdx n = node_index(0, row, nx, ny, nz);
+        drow[h] = base + n.d;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const typename St::T *src = pl.s[a] + (drow[h] + n.oy[ey(a) + 1] + n.oz[ez(a) + 1]);
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(src + x));
+            if (ex(a) > 0) {
+                // pull from x - 1: (x - 1, x, x + 1, x + 2)
+                const unsigned e = own_left ? load_elem<St>(src + xl) : 0u;
+                unsigned left = __shfl_up_sync(0xffffffffu, v.y, 1);
+                if (own_left) left = e << 16;
+                p[h][a] = make_uint2(__byte_perm(left, v.x, 0x5432), __byte_perm(v.x, v.y, 0x5432));
+            } else if (ex(a) < 0) {
+                // pull from x + 1: (x + 1, x + 2, x + 3, x + 4)
+                const unsigned e = own_right ? load_elem<St>(src + xr) : 0u;
+                unsigned right = __shfl_down_sync(0xffffffffu, v.x, 1);
+                if (own_right) right = e;
+                p[h][a] = make_uint2(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, right, 0x5432));
+            } else {
+                p[h][a] = v;
+            }
+        }
+        if (FORCED) rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const bool row_ok = grp * R + h < nrows;
+        float F[4][3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            F[k][0] = rp.gx;
+            F[k][1] = rp.gy;
+            F[k][2] = rp.gz;
+        }
+        if (FORCED) {
+            const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw[h], 0) & 0xffffffffull);
+            if (cnt > 0 && row_ok) {
+                long long sum[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                record_sum4(rw[h], cnt, x, sum);
+                if (cnt > REC_SLOTS && act) {
+                    const int d = drow[h] + x;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            sum[k][c] += (long long)fq[c * Ntot + d + k];
+                            fq[c * Ntot + d + k] = 0ull;
+                        }
+                }
+                const float inv = 1.3877787807814457e-17f;  // 2^-56
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) F[k][c] += inv * __ll2float_rn(sum[k][c]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float g0[Q], g1[Q], o0[Q], o1[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) unpack2<St>(j ? p[h][a].y : p[h][a].x, a, g0[a], g1[a]);
+            collide_values(g0, rp.omega, F[2 * j][0], F[2 * j][1], F[2 * j][2], o0);
+            collide_values(g1, rp.omega, F[2 * j + 1][0], F[2 * j + 1][1], F[2 * j + 1][2], o1);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const unsigned w = pack2<St>(o0[a], o1[a], a);
+                if (j) p[h][a].y = w; else p[h][a].x = w;
+            }
+        }
+        if (act && row_ok) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) *reinterpret_cast<uint2 *>(pl.d[a] + drow[h] + x) = p[h][a];
+        }
+    }
+}
+
 constexpr int SC_BX = SEG;
 
 cudaError_t prepare_lbm_kernels() { return cudaSuccess; }
@@ -409,6 +560,13 @@ bool pair_kernel_ok(const Sim &s) {
     return true;
 }
 
+bool quad_kernel_ok(const Sim &s) {
+    if (s.precision == LBP_F32) return false;
+    for (int r = 0; r < s.nrep; ++r)
+        if (s.reps[r].nx % 4) return false;
+    return true;
+}
+
 bool staged_kernel_ok(const Sim &s) {
     const int H = 16 / storage_bytes(s.precision);
     for (int r = 0; r < s.nrep; ++r)
@@ -435,11 +593,13 @@ static RepTable<MAXR> rep_table_staged(const Sim &s) {
 }
 
 bool variant_ok(const Sim &s, int variant) {
-    return variant == 0 || (variant == 1 && pair_kernel_ok(s)) || (variant == 2 && staged_kernel_ok(s));
+    return variant == 0 || (variant == 1 && pair_kernel_ok(s)) || (variant == 2 && staged_kernel_ok(s)) ||
+           (variant == 3 && quad_kernel_ok(s));
 }
 
 // variant 0: one node per thread; 1: two nodes per thread (2-byte storage,
-// even nx); 2: bulk-copy staged persistent kernel (lbm_staged.cu)
+// even nx); 2: bulk-copy staged persistent kernel (lbm_staged.cu); 3: four
+// nodes per thread, one warp per row segment (2-byte storage, nx % 4 == 0)
 template <bool FORCED>
 static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned long long *rec_cur,
                              unsigned long long *rec_prev, long long *bump, int rows, int variant,
@@ -456,7 +616,7 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
                                                           rec_cur, rec_prev, s.fq, s.N, bump, s.d_err, s.num_sms, st);
         });
     }
-    const bool use_pair = variant == 1;
+    const bool use_pair = variant == 1, use_quad = variant == 3;
     return by_storage(s, [&](auto tag) {
         using St = decltype(tag);
         return by_rows(rows, [&](auto rc) {
@@ -468,6 +628,12 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
                     if (use_pair) {
                         k_stream_collide_pair<St, R, MAXR, FORCED><<<grid, PAIR_BX, 0, st>>>(
                             planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                        return cudaGetLastError();
+                    }
+                    if (use_quad) {
+                        k_stream_collide_quad<St, R, MAXR, FORCED>
+                            <<<(grid + QUAD_WARPS - 1) / QUAD_WARPS, 32 * QUAD_WARPS, 0, st>>>(
+                                planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
                         return cudaGetLastError();
                     }
                 }

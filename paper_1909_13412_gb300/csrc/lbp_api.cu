@@ -1026,10 +1026,11 @@ lbp_status lbp_set_body_force(lbp_sim *s, int replica, const double *g) {
 lbp_status lbp_set_block_shape(lbp_sim *s, int rows, int variant) {
     CHECK_SIM(s);
     if (rows != 1 && rows != 2 && rows != 4) return fail(LBP_EINVAL, "lbp_set_block_shape: rows must be 1, 2 or 4");
-    if (variant < 0 || variant > 2 || !variant_ok(*s, variant))
+    if (variant < 0 || variant > 3 || !variant_ok(*s, variant))
         return fail(LBP_EINVAL,
                     "lbp_set_block_shape: variant %d does not apply (1 needs 2-byte storage and even nx, 2 needs nx a "
-                    "multiple of 16 bytes of storage, in every box)", variant);
+                    "multiple of 16 bytes of storage, 3 needs 2-byte storage and nx a multiple of 4, in every box)",
+                    variant);
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
     s->rows = variant == 2 ? 1 : rows;
@@ -1048,20 +1049,29 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *variant, doubl
     if (launches < 1 || launches > 1000) return fail(LBP_EINVAL, "lbp_autotune: launches must be in [1, 1000]");
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
-    // candidates: (variant, rows); index k = 3 variant + (0, 1, 2 for 1, 2, 4 rows); the
-    // staged kernel has one shape (k = 6)
-    static const int cand_r[3] = {1, 2, 4};
-    bool apply[7];
-    for (int k = 0; k < 7; ++k) apply[k] = variant_ok(*s, k / 3);
-    // scratch: two all-zero force-record copies (no force anywhere, so the
-    // dense overflow accumulator is never read) and a step counter to bump
+    // candidates k = 0..9: (variant, rows) = (0: 1, 2, 4 rows), (1: 1, 2, 4),
+    // (2: one shape), (3: 1, 2, 4)
+    constexpr int NC = LBP_AUTOTUNE_CANDIDATES;
+    static const int cand_v[NC] = {0, 0, 0, 1, 1, 1, 2, 3, 3, 3};
+    static const int cand_r[NC] = {1, 2, 4, 1, 2, 4, 1, 1, 2, 4};
+    bool apply[NC];
+    for (int k = 0; k < NC; ++k) apply[k] = variant_ok(*s, cand_v[k]);
+    // scratch: a copy of the force records of the last step (all zero before
+    // the first), so that the candidates sum the particle forces a step sums,
+    // an all-zero record set for the counts they clear, and a step counter to
+    // bump.  The dense overflow accumulator is all zero between steps (each
+    // lattice pass clears what it reads), so its reads and clears by the
+    // candidates change nothing.
     const size_t rec_words = s->np > 0 ? (size_t)s->nseg * REC_WORDS : 0;
     unsigned long long *scr = nullptr;
     TRY(dalloc(&scr, 2 * rec_words + 1));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double t[7];
-    for (int k = 0; k < 7; ++k) t[k] = -1.0;
+    double t[NC];
+    for (int k = 0; k < NC; ++k) t[k] = -1.0;
     cudaError_t e = cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (2 * rec_words + 1), s->s0);
+    if (e == cudaSuccess && rec_words)
+        e = cudaMemcpyAsync(scr, s->rec[s->cur ^ 1], sizeof(unsigned long long) * rec_words,
+                            cudaMemcpyDeviceToDevice, s->s0);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     long long *bump = reinterpret_cast<long long *>(scr + 2 * rec_words);
@@ -1074,9 +1084,9 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *variant, doubl
                          : launch_stream_collide_cfg(*s, src, dst, bump, R, V, s->s0);
     };
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass)
-        for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+        for (int k = 0; k < NC && e == cudaSuccess; ++k) {
             if (!apply[k]) continue;
-            const int V = k / 3, R = k < 6 ? cand_r[k % 3] : 1;
+            const int V = cand_v[k], R = cand_r[k];
             for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = one(R, V);
             if (e == cudaSuccess) e = cudaEventRecord(e0, s->s0);
             for (int l = 0; l < launches && e == cudaSuccess; ++l) e = one(R, V);
@@ -1096,15 +1106,15 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *variant, doubl
     CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err & ERR_TIMEOUT) return fail(LBP_ETIMEOUT, "lbp_autotune: a bounded wait in the staged kernel ran out");
     int best = -1;
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < NC; ++k)
         if (t[k] > 0 && (best < 0 || t[k] < t[best])) best = k;
-    s->variant = best / 3;
-    s->rows = best < 6 ? cand_r[best % 3] : 1;
+    s->variant = cand_v[best];
+    s->rows = cand_r[best];
     drop_graphs(s);
     if (rows) *rows = s->rows;
     if (variant) *variant = s->variant;
     if (ms)
-        for (int k = 0; k < 7; ++k) ms[k] = t[k];
+        for (int k = 0; k < NC; ++k) ms[k] = t[k];
     return leave(s);
 }
 

@@ -423,12 +423,16 @@ def lbp_set_block_rows(h: Handle, rows):
     _call("lbp_set_block_rows", h.ptr, int(rows))
 
 
+# (variant, rows) of the autotuner's candidates, in the order of its ms array
+AUTOTUNE_SHAPES = ((0, 1), (0, 2), (0, 4), (1, 1), (1, 2), (1, 4), (2, 1), (3, 1), (3, 2), (3, 4))
+
+
 def lbp_autotune(h: Handle, launches=20):
     """Pick the lattice kernel's shape by timing; returns (rows, variant, ms)
-    with ms the 7 mean launch times (variant 0: 1, 2, 4 rows; variant 1: 1, 2,
-    4 rows; variant 2), -1 where a candidate does not apply."""
+    with ms the mean launch times of the AUTOTUNE_SHAPES candidates, -1 where
+    a candidate does not apply."""
     rows, variant = C.c_int(), C.c_int()
-    ms = (C.c_double * 7)()
+    ms = (C.c_double * len(AUTOTUNE_SHAPES))()
     _call("lbp_autotune", h.ptr, int(launches), C.byref(rows), C.byref(variant), ms)
     return rows.value, variant.value, list(ms)
 

@@ -237,24 +237,29 @@ def make_box(prec, kT, shape=(20, 18, 16, 0.8)):
     return h
 
 
-SHAPE_BOXES = {"20x18x16": (20, 18, 16, 0.8), "24x10x9": (24, 10, 9, 0.7), "136x5x4": (136, 5, 4, 0.9)}
+SHAPE_BOXES = {"20x18x16": (20, 18, 16, 0.8), "24x10x9": (24, 10, 9, 0.7), "136x5x4": (136, 5, 4, 0.9),
+               "22x6x5": (22, 6, 5, 0.8), "4x6x5": (4, 6, 5, 0.8)}
 
 
 @pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16, lbp.LBP_F16])
-@pytest.mark.parametrize("where", ["20x18x16", "24x10x9", "136x5x4", "batch"])
+@pytest.mark.parametrize("where", ["20x18x16", "24x10x9", "136x5x4", "22x6x5", "4x6x5", "batch"])
 def test_kernel_shapes_and_autotune_leave_results_unchanged(prec, where):
     """Every kernel shape -- one node per thread with 1, 2, 4 rows; two nodes
     per thread (2-byte storage, even nx); the bulk-copy staged kernel (nx a
-    multiple of 16 bytes of storage) -- and the autotuner's pick give bitwise
-    the same run.  The boxes cover ragged segments (136 = 128 + 8), periodic
-    halos at both ends of a row, and the uneven batch (nx = 33 in one box:
-    variant 0 only)."""
+    multiple of 16 bytes of storage); four nodes per thread (2-byte storage,
+    nx a multiple of 4) -- and the autotuner's pick give bitwise the same run.
+    The boxes cover ragged segments (136 = 128 + 8), periodic halos at both
+    ends of a row, a row of one four-node group (nx = 4), nx = 22 (pairs but
+    no groups of four), and the uneven batch (nx = 33 in one box: variant 0
+    only)."""
     steps = 25
     batch = where == "batch"
     H = 4 if prec == lbp.LBP_F32 else 8
     nxs = [b[0] for b in BOXES] if batch else [SHAPE_BOXES[where][0]]
-    ok = {0: True, 1: prec != lbp.LBP_F32 and all(n % 2 == 0 for n in nxs), 2: all(n % H == 0 for n in nxs)}
-    shapes = [(r, v) for v in (0, 1) if ok[v] for r in (1, 2, 4)] + ([(1, 2)] if ok[2] else []) + ["auto"]
+    ok = {0: True, 1: prec != lbp.LBP_F32 and all(n % 2 == 0 for n in nxs), 2: all(n % H == 0 for n in nxs),
+          3: prec != lbp.LBP_F32 and all(n % 4 == 0 for n in nxs)}
+    shapes = [(r, v) for v in (0, 1) if ok[v] for r in (1, 2, 4)] + ([(1, 2)] if ok[2] else []) + \
+        [(r, 3) for r in (1, 2, 4) if ok[3]] + ["auto"]
     ref = None
     for shape in shapes:
         h = make_batch(prec, 1e-4, True) if batch else make_box(prec, 1e-4, SHAPE_BOXES[where])
@@ -262,8 +267,8 @@ def test_kernel_shapes_and_autotune_leave_results_unchanged(prec, where):
         if shape == "auto":
             rows, variant, ms = lbp.lbp_autotune(h, 5)
             valid = [m for m in ms if m > 0]
-            assert len(valid) == 3 * ok[0] + 3 * ok[1] + ok[2]
-            k = 6 if variant == 2 else 3 * variant + (1, 2, 4).index(rows)
+            assert len(valid) == 3 * ok[0] + 3 * ok[1] + ok[2] + 3 * ok[3]
+            k = lbp.AUTOTUNE_SHAPES.index((variant, 1 if variant == 2 else rows))
             assert ms[k] == min(valid)
             want = (rows, variant)
         else:
@@ -282,7 +287,7 @@ def test_kernel_shapes_and_autotune_leave_results_unchanged(prec, where):
             assert np.array_equal(got[0], ref[0]), shape
             for k in range(4):
                 assert np.array_equal(got[1][k], ref[1][k]), (shape, k)
-    for v in (1, 2):
+    for v in (1, 2, 3):
         if not ok[v]:
             h = make_batch(prec, 0.0, True) if batch else make_box(prec, 0.0, SHAPE_BOXES[where])
             with pytest.raises(lbp.LbpError):
