@@ -38,14 +38,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1909_13412_gb300 import workloads as wl  # noqa: E402
+from paper_1909_13412_gb300.lbp import AUTOTUNE_SHAPES  # noqa: E402  (names only; loads no library)
 
 METRIC = "MLUPS and % HBM roofline per GB300 at fixed accuracy vs FP64 oracle; plain vs BF16/batched"
 # algorithmic bytes per node update: 15 loads + 15 stores of the stored deviation
 BYTES_PER_NODE = {"f32": 2 * 15 * 4, "bf16": 2 * 15 * 2, "f16": 2 * 15 * 2}
 PRECISION_CODE = {"f32": 0, "bf16": 1, "f16": 2}
 K3_SOURCE = os.path.join(ROOT, "paper_1909_13412_gb300", "csrc", "lbm_kernels.cu")
-K3_PROFILE = os.path.join(ROOT, "profiles", "stream_collide_forced_256.md")
+# committed ncu summaries with the DRAM bytes per lattice launch at 256^3, per storage type
+K3_PROFILE = {"f32": os.path.join(ROOT, "profiles", "stream_collide_forced_256.md"),
+              "bf16": os.path.join(ROOT, "profiles", "stream_collide_quad_bf16_256.md")}
 VACF_LAG = 5000
+
+
+# names of the lattice kernel's shapes, in the autotuner's order, and (variant, rows) by name
+SHAPE_NAMES = [{0: "1node", 1: "2nodes", 3: "4nodes"}[v] + ("_1row" if r == 1 else f"_{r}rows")
+               if v != 2 else "bulk_staged" for v, r in AUTOTUNE_SHAPES]
+SHAPES = dict(zip(SHAPE_NAMES, AUTOTUNE_SHAPES))
 LAUNCHES_PER_STEP = 2  # particles, stream-collide (+2 VACF kernels every 64 steps)
 
 
@@ -103,15 +112,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic():
+def recorded_traffic(precision, shape):
     """DRAM bytes per stream-collide launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
-    if not os.path.exists(K3_PROFILE):
+    was taken on the current kernel source and, where it names one, with this
+    kernel shape (else None)."""
+    path = K3_PROFILE.get(precision)
+    if not path or not os.path.exists(path):
         return None
-    text = open(K3_PROFILE).read()
+    text = open(path).read()
     m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram_bytes_per_launch_256:\s*([0-9.eE+]+)", text)
-    if not (m_sha and m_b):
+    m_shape = re.search(r"kernel_shape:\s*(\w+)", text)
+    if not (m_sha and m_b) or (m_shape and m_shape.group(1) != shape):
         return None
     sha = hashlib.sha256(open(K3_SOURCE, "rb").read()).hexdigest()
     return float(m_b.group(1)) if sha == m_sha.group(1) else None
@@ -317,16 +329,19 @@ def run_gpu(args, w):
 
     def make(precision, wk=w):
         h = make_handle(lbp, wk, precision, wk.seed_noise + rank, args.vacf_lag)
+        if args.kernel_shape:
+            # a fixed shape (reproducible profiles: no timing-dependent pick)
+            variant, rows = SHAPES[args.kernel_shape]
+            lbp.lbp_set_block_shape(h, rows, variant)
+            h.tuned = {"variant": args.kernel_shape, "fixed": True}
+            return h
         # block shape of the lattice kernel, picked by timing (outside the timed
         # region) after two steps, so that the candidates see this workload's
         # particle forces in the records
         lbp.lbp_step(h, 2)
         rows, variant, tms = lbp.lbp_autotune(h, 10)
-        per_thread = {0: "1node", 1: "2nodes", 3: "4nodes"}
-        names = [per_thread[v] + ("_1row" if r == 1 else f"_{r}rows") if v != 2 else "bulk_staged"
-                 for v, r in lbp.AUTOTUNE_SHAPES]
-        h.tuned = {"variant": names[lbp.AUTOTUNE_SHAPES.index((variant, 1 if variant == 2 else rows))],
-                   "ms_by_shape": {n: t for n, t in zip(names, tms) if t > 0}}
+        h.tuned = {"variant": SHAPE_NAMES[AUTOTUNE_SHAPES.index((variant, 1 if variant == 2 else rows))],
+                   "ms_by_shape": {n: t for n, t in zip(SHAPE_NAMES, tms) if t > 0}}
         return h
 
     def timed(h, steps, warmup, clocks=None):
@@ -394,6 +409,8 @@ def run_gpu(args, w):
                               "steps": vsteps, "ms_per_step": vms / vsteps,
                               "stream_collide_ms": vk3, "achieved_gbs": vach,
                               "frac": vach / measured_peaks()[0],
+                              "traffic": recorded_traffic(prec, hv.tuned["variant"]) if w is wl.BROWNIAN_256
+                              else None,
                               "bytes_per_node": BYTES_PER_NODE[prec], "autotune": hv.tuned}
     if not args.no_variants and not isinstance(w, wl.Ensemble) and want("batched"):
         # the batched uneven ensemble: one handle, one lattice launch per step
@@ -431,7 +448,7 @@ def run_gpu(args, w):
         return 0
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_NODE[args.precision] * w.nodes / (k3_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic() if (args.precision == "f32" and w is wl.BROWNIAN_256) else None
+    traffic = recorded_traffic(args.precision, tuned["variant"]) if w is wl.BROWNIAN_256 else None
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -469,6 +486,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vacf-lag", type=int, default=VACF_LAG)
     ap.add_argument("--precision", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--kernel-shape", choices=SHAPE_NAMES, default=None,
+                    help="fix the lattice kernel's shape instead of autotuning it")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant", action="append", default=[],
                     help="run only these variants (bf16, f16, f32, batched, adjoint_64, adjoint); default all")

@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
                         fq[2 * Ntot + d] = 0ull;
                     }
                     const float inv = 1.3877787807814457e-17f;  // 2^-56
-                    F0 += inv * __ll2float_rn(a0);
-                    F1 += inv * __ll2float_rn(a1);
-                    F2 += inv * __ll2float_rn(a2);
+                    F0 = __fmaf_rn(inv, fix_to_float(a0), F0);
+                    F1 = __fmaf_rn(inv, fix_to_float(a1), F1);
+                    F2 = __fmaf_rn(inv, fix_to_float(a2), F2);
                 }
             }
             float o[Q];

@@ -86,38 +86,56 @@ struct Planes {
 // Collision of one node (Eqs. 15, 17-19 in deviation form, see
 // lbm_kernels.cu): the 15 post-collision deviations of the node whose
 // pulled deviations are g; (F0, F1, F2) is the body force of Eq. 18 at the
-// node (zero if none)
+// node (zero if none).  Every operation is written out with its rounding (no
+// contraction left to the compiler), so that every kernel that inlines this
+// function performs the same operations in the same order, bit for bit:
+//     rho~ - 1 = sum_a g_a (in index order),   u = sum_a e_a g_a,
+//     base = (rho~ - 1) - 3/2 u.u,
+//     o_0 = (1 - omega) g_0 + omega (2/9 base),
+//     o_A, o_A+1 = (1 - omega) g + omega (sym +- anti) +- fe per opposite pair,
+//     sym = W (base + 9/2 (e.u)^2), anti = 3 W e.u, fe = 3 W e.F.
 __device__ __forceinline__ void collide_values(const float g[Q], float omega, float F0, float F1,
                                                float F2, float o[Q]) {
-    float drho = 0.f;
+    float drho = g[0];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) drho += g[a];
-    const float c78 = g[7] - g[8], c910 = g[9] - g[10], c1112 = g[11] - g[12],
-                c1314 = g[13] - g[14];
-    const float ux = (g[1] - g[2]) + c78 + c910 + c1112 - c1314;
-    const float uy = (g[3] - g[4]) + c78 + c910 - c1112 + c1314;
-    const float uz = (g[5] - g[6]) + c78 - c910 + c1112 + c1314;
-    const float base = drho - 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float om1 = 1.f - omega;
-    o[0] = om1 * g[0] + omega * ((2.f / 9.f) * base);
+    for (int a = 1; a < Q; ++a) drho = __fadd_rn(drho, g[a]);
+    const float c78 = __fsub_rn(g[7], g[8]), c910 = __fsub_rn(g[9], g[10]),
+                c1112 = __fsub_rn(g[11], g[12]), c1314 = __fsub_rn(g[13], g[14]);
+    const float ux = __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(g[1], g[2]), c78), c910), c1112), c1314);
+    const float uy = __fadd_rn(__fsub_rn(__fadd_rn(__fadd_rn(__fsub_rn(g[3], g[4]), c78), c910), c1112), c1314);
+    const float uz = __fadd_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(g[5], g[6]), c78), c910), c1112), c1314);
+    const float uu = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+    const float base = __fmaf_rn(-1.5f, uu, drho);
+    const float om1 = __fsub_rn(1.f, omega);
+    o[0] = __fmaf_rn(om1, g[0], __fmul_rn(omega, __fmul_rn(2.f / 9.f, base)));
     // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, weight W
-#define LBP_PAIR(A, W, EU, FE)                                \
-    {                                                         \
-        const float eu = (EU);                                \
-        const float sym = (W) * (base + 4.5f * eu * eu);      \
-        const float anti = (3.f * (W)) * eu;                  \
-        const float fe = (3.f * (W)) * (FE);                  \
-        o[A] = om1 * g[A] + omega * (sym + anti) + fe;        \
-        o[A + 1] = om1 * g[A + 1] + omega * (sym - anti) - fe; \
+#define LBP_PAIR(A, W, EU, FE)                                                                   \
+    {                                                                                            \
+        const float eu = (EU);                                                                   \
+        const float sym = __fmul_rn((W), __fmaf_rn(4.5f, __fmul_rn(eu, eu), base));              \
+        const float anti = __fmul_rn(3.f * (W), eu);                                             \
+        const float fe = __fmul_rn(3.f * (W), (FE));                                             \
+        o[A] = __fadd_rn(__fmaf_rn(om1, g[A], __fmul_rn(omega, __fadd_rn(sym, anti))), fe);      \
+        o[A + 1] = __fsub_rn(__fmaf_rn(om1, g[A + 1], __fmul_rn(omega, __fsub_rn(sym, anti))), fe); \
     }
     LBP_PAIR(1, 1.f / 9.f, ux, F0)
     LBP_PAIR(3, 1.f / 9.f, uy, F1)
     LBP_PAIR(5, 1.f / 9.f, uz, F2)
-    LBP_PAIR(7, 1.f / 72.f, ux + uy + uz, F0 + F1 + F2)
-    LBP_PAIR(9, 1.f / 72.f, ux + uy - uz, F0 + F1 - F2)
-    LBP_PAIR(11, 1.f / 72.f, ux - uy + uz, F0 - F1 + F2)
-    LBP_PAIR(13, 1.f / 72.f, -ux + uy + uz, -F0 + F1 + F2)
+    LBP_PAIR(7, 1.f / 72.f, __fadd_rn(__fadd_rn(ux, uy), uz), __fadd_rn(__fadd_rn(F0, F1), F2))
+    LBP_PAIR(9, 1.f / 72.f, __fsub_rn(__fadd_rn(ux, uy), uz), __fsub_rn(__fadd_rn(F0, F1), F2))
+    LBP_PAIR(11, 1.f / 72.f, __fadd_rn(__fsub_rn(ux, uy), uz), __fadd_rn(__fsub_rn(F0, F1), F2))
+    LBP_PAIR(13, 1.f / 72.f, __fadd_rn(__fsub_rn(uy, ux), uz), __fadd_rn(__fsub_rn(F1, F0), F2))
 #undef LBP_PAIR
+}
+
+// The float nearest (within one unit in the last place) to a 64-bit integer,
+// from its two 32-bit halves: the direct 64-bit conversion runs on the FP64
+// pipe, which is narrow on this GPU.  Every lattice kernel converts its
+// fixed-point force sums with this one function.
+__device__ __forceinline__ float fix_to_float(long long a) {
+    const unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+    const float f = __fmaf_rn((float)(unsigned)(m >> 32), 4294967296.f, (float)(unsigned)m);
+    return a < 0 ? -f : f;
 }
 
 // Reaction forces are summed per node in 64-bit fixed point so that the sum

@@ -114,7 +114,7 @@ BROWNIAN_256 = Workload("brownian_256^3_16384p", (256, 256, 256), 0.8, 16384, kT
 # case (0.25 GB of populations, still larger than L2) for detailed profiles.
 PROFILE_128 = Workload("profile_128^3_2048p", (128, 128, 128), 0.8, 2048, kT=1e-4, steps=100)
 
-# 192^3 with 6912 particles (the bench's particle density): 2 x 425 MB of
+# 192^3 with 6912 particles (the bench's particle density): 2 x 212 MB of
 # 2-byte populations, larger than L2, for detailed profiles of those kernels.
 PROFILE_192 = Workload("profile_192^3_6912p", (192, 192, 192), 0.8, 6912, kT=1e-4, steps=100)
 
