@@ -68,8 +68,11 @@ __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >
 
 constexpr int PB = 32;  // particles per block of k_particles
 
+// 64 registers (four blocks of 256 threads per SM) keep the 16384-particle
+// grid of the 256^3 workload (512 blocks) in a single wave on 152 SMs (at 80
+// registers, three blocks per SM, it took two).
 template <typename St, int MAXR>
-__global__ void __launch_bounds__(256) k_particles(const ParticleArgs A, const RepTable<MAXR> rt) {
+__global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, const RepTable<MAXR> rt) {
     const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[PB][3];
     __shared__ int s_rep[PB];
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(256) k_particles(const ParticleArgs A, const R
     const int ij = i0 + j;
     const int c0 = p & 1, c1 = (p >> 1) & 1, c2 = (p >> 2) & 1;
     int X = 0, Y = 0, Z = 0;
-    const Rep &rj = rt.rep[ij < A.np ? s_rep[j] : 0];
+    const Rep &rj = rt.rep[MAXR == 1 || ij >= A.np ? 0 : s_rep[j]];
     const int nx = rj.nx, ny = rj.ny, nz = rj.nz;
     if (ij < A.np) {
         X = wrapi(s_base[j][0] + c0, nx);
