@@ -401,6 +401,7 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     cudaError_t e = cudaGetDevice(&s->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->dev);
     if (e == cudaSuccess) e = prepare_lbm_kernels();
+    if (e == cudaSuccess) e = prepare_vacf_kernels();
     // the step's own kernels at the highest stream priority, the side stream (the
     // VACF correlator, compute-bound) at the lowest: when both have blocks
     // waiting, the HBM-bound lattice pass gets the SM slots first and the

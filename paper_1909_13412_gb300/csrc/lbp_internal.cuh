@@ -391,6 +391,7 @@ int adj_lattice_blocks(const Sim &s);
 cudaError_t launch_f32_to_f64(Sim &s, const float *src, double *dst, cudaStream_t st);
 // vacf_kernels.cu
 int vacf_block_samples();
+cudaError_t prepare_vacf_kernels();  // opt-in shared memory of the tensor-core correlator
 int vacf_chunk_components();
 cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st);
 

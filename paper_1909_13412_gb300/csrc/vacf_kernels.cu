@@ -6,13 +6,10 @@
 // adds, for the B new samples t and every lag k <= K, the products
 // V(t).V(t - k): a dense contraction over the 3 n_p velocity components.
 //
-// k_vacf_corr : CTA = 128 lags x 1024 components; warp = 16 consecutive lags,
-//               lane = one component of a 32-wide sub-chunk staged in shared
-//               memory.  A lane keeps the 16 window values V(t - k) it needs
-//               in registers and slides them by one sample per t, so each
-//               (t, component) costs two shared loads for 16 FMAs.  Products
-//               and the per-lane sums are FP32; the lane sums are combined in
-//               FP64 with a fixed shuffle tree into one partial per (chunk, k).
+// k_vacf_mma  : CTA = 128 lags x 1024 components: the products of the 64 new
+//               samples with the 191 window samples as a matrix product on the
+//               tensor cores (TF32 in three terms, FP32 accuracy), the lag sums
+//               of its band in FP64 into one partial per (chunk, k).
 // k_vacf_reduce : adds the chunk partials in chunk order (FP64) to the
 //               running sums and pair counts, then marks the samples done.
 #include <cuda_runtime.h>
@@ -23,8 +20,6 @@ namespace lbp {
 
 constexpr int VB = 64;        // samples per correlation block
 constexpr int VKT = 128;      // lags per CTA
-constexpr int VLW = 16;       // lags per warp
-constexpr int VJ = 32;        // components per sub-chunk (one per lane)
 constexpr int VJCH = 1024;    // components per CTA
 constexpr int VWIN = VB + VKT - 1;
 
@@ -53,83 +48,179 @@ __device__ __forceinline__ bool vacf_range(const VacfArgs &A, long long &tb, lon
     return te - tb == VB;
 }
 
-__global__ void __launch_bounds__(256) k_vacf_corr(const VacfArgs A) {
+// ---------------------------------------------------------------------------
+// k_vacf_mma: the same block correlation on the tensor cores.  For the CTA's
+// 128 lags and 1024 components the products of the B = 64 new samples t with
+// the 191 window samples s form a matrix product
+//     P[t][s] = sum_j V_j(t) V_j(s)       (64 x 192, inner dimension 1024),
+// and lag k0 + kk collects the band s = t + 127 - kk:  C(k) = sum_t P[t][.].
+// The product runs as mma.sync m16n8k8 with TF32 operands in three terms,
+// a.b = a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = a rounded to TF32, a_lo =
+// the rest rounded to TF32), which keeps FP32 accuracy (the dropped a_lo b_lo
+// is below 2^-22 of the product); accumulation is FP32 in the tensor core.
+// Eight warps: warp w takes the 16 samples of M tile w/2 and 9 of the 18 N
+// tiles of 8 window rows that meet its band (the rest of the 24 are zero
+// contributions).  The band of P goes through shared memory and each of 128
+// threads sums its lag over t in FP64, in sample order, into the chunk's
+// partial (the reduce kernel adds the chunks in chunk order): the result does
+// not depend on scheduling.
+// ---------------------------------------------------------------------------
+constexpr int MJ = 32;           // components per staged sub-chunk
+constexpr int MLD = MJ + 4;      // staged row stride (floats): conflict-free fragment loads
+constexpr int MWR = 192;         // window rows staged (VWIN = 191, one zero row)
+constexpr int MWRA = MWR + 8;    // rows allocated: the fragment loads of a warp's last
+                                 // N tile pair read one 8-row tile past the staged rows
+constexpr int MPLD = MWR + 4;    // row stride of the P tile in the epilogue
+constexpr int MMA_SMEM = 2 * (VB + MWRA) * MLD * 4;  // hi and lo copies: 76,032 bytes
+static_assert(VB * MPLD * 4 <= MMA_SMEM, "the P tile reuses the staging space");
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float d[4], const unsigned a[4], const unsigned b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// value v split into its TF32 head and tail, stored at index i of hi / lo
+__device__ __forceinline__ void stage_split(unsigned *hi, unsigned *lo, int i, float v) {
+    const unsigned h = tf32_rna(v);
+    hi[i] = h;
+    lo[i] = tf32_rna(v - __uint_as_float(h));
+}
+
+// four 8 x 4 blocks of 32-bit values (8 x 8 of 16-bit) from shared memory,
+// one register each; thread i gives the address of row i % 8 of block i / 8
+__device__ __forceinline__ void ldsm_x4(unsigned r[4], const unsigned *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__global__ void __launch_bounds__(256) k_vacf_mma(const VacfArgs A) {
     long long tb, te;
     if (!vacf_range(A, tb, te)) return;
     const int nb = (int)(te - tb);
-    __shared__ float sA[VB][VJ];
-    __shared__ float sW[VWIN][VJ];
+    extern __shared__ float vsm[];
+    unsigned *hA = reinterpret_cast<unsigned *>(vsm);
+    unsigned *lA = hA + VB * MLD;
+    unsigned *hW = lA + VB * MLD;
+    unsigned *lW = hW + MWRA * MLD;
+    __shared__ long long s_row[VB + MWR];  // ring offset of each staged row, -1: zero row
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k0 = blockIdx.x * VKT;
     const int jc0 = blockIdx.y * VJCH;
-    // absolute sample index of sW row 0
-    const long long s_lo = tb - k0 - (VKT - 1);
-
-    float acc[VLW];
-#pragma unroll
-    for (int m = 0; m < VLW; ++m) acc[m] = 0.f;
-
-    // ring slots of the first rows of sA and sW (one 64-bit modulo per CTA;
-    // later rows wrap by one subtraction: a block spans fewer than cap rows)
+    const long long s_lo = tb - k0 - (VKT - 1);  // sample of window row 0
+    const int mt = warp >> 1;                   // M tile: samples 16 mt .. 16 mt + 15
+    const int nt0 = 2 * mt + 9 * (warp & 1);    // first of the warp's 9 N tiles
     const int cap = A.cap;
-    const int slotA0 = (int)(tb % cap);
-    const int slotW0 = s_lo >= 0 ? (int)(s_lo % cap) : 0;
-    for (int js = 0; js < VJCH; js += VJ) {
+
+    // ring rows of the 64 new samples and the 192 window rows, once per CTA
+    for (int rr = threadIdx.x; rr < VB + MWR; rr += blockDim.x) {
+        long long off = -1;
+        if (rr < VB) {
+            if (rr < nb) off = (long long)((tb + rr) % cap) * A.ncomp;
+        } else {
+            const int sr = rr - VB;
+            const long long smp = s_lo + sr;
+            // rows older than te - cap were overwritten; they only meet lags > K
+            if (sr < VWIN && smp >= 0 && smp >= te - cap && smp < te) off = (long long)(smp % cap) * A.ncomp;
+        }
+        s_row[rr] = off;
+    }
+
+    float acc[9][4];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+
+    // ldmatrix row addresses: A fragment of M tile mt (rows g and g + 8, columns
+    // c and c + 4 of the 8-column step) and B fragments of N tile pairs
+    const int mrow = lane & 7, mblk = lane >> 3;
+    const int a_off = (16 * mt + mrow + 8 * (mblk & 1)) * MLD + 4 * (mblk >> 1);
+    const int b_off = (8 * (nt0 + (mblk >> 1)) + mrow) * MLD + 4 * (mblk & 1);
+
+    // staging: warp w holds rows w, w + 8, ..., w + 248 of a sub-chunk (lane =
+    // component) in registers; the next sub-chunk's loads are issued before
+    // the current one's products, so they are in flight during them
+    float v[32];
+    auto load_rows = [&](int jb) {
+        const bool colok = jb + lane < A.ncomp;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const long long off = s_row[warp + 8 * i];
+            v[i] = (off >= 0 && colok) ? __ldg(A.ring + off + jb + lane) : 0.f;
+        }
+    };
+    __syncthreads();  // s_row
+    load_rows(jc0);
+    for (int js = 0; js < VJCH; js += MJ) {
         const int jb = jc0 + js;
         if (jb >= A.ncomp) break;
-        __syncthreads();
-        for (int e = threadIdx.x; e < VB * VJ; e += blockDim.x) {
-            const int t = e / VJ, l = e - t * VJ;
-            const int jj = jb + l;
-            float v = 0.f;
-            if (t < nb && jj < A.ncomp) {
-                int slot = slotA0 + t;
-                if (slot >= cap) slot -= cap;
-                v = A.ring[(long long)slot * A.ncomp + jj];
-            }
-            sA[t][l] = v;
-        }
-        for (int e = threadIdx.x; e < VWIN * VJ; e += blockDim.x) {
-            const int sr = e / VJ, l = e - sr * VJ;
-            const int jj = jb + l;
-            const long long s = s_lo + sr;
-            float v = 0.f;
-            // rows older than te - cap were overwritten; they only meet lags > K
-            if (s >= 0 && s >= te - cap && s < te && jj < A.ncomp) {
-                // slot of sample s: s mod cap (slotW0 + sr < 3 cap, s < 2 cap here)
-                int slot = s_lo >= 0 ? slotW0 + sr : (int)s;
-                while (slot >= cap) slot -= cap;
-                v = A.ring[(long long)slot * A.ncomp + jj];
-            }
-            sW[sr][l] = v;
+        __syncthreads();  // the previous products are done with the staged tiles
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int rr = warp + 8 * i;  // rows 0..63: new samples (i < 8); then the window
+            if (i < 8)
+                stage_split(hA, lA, rr * MLD + lane, v[i]);
+            else
+                stage_split(hW, lW, (rr - VB) * MLD + lane, v[i]);
         }
         __syncthreads();
-        // window for lags k = k0 + VLW*warp + m at sample t: sW[t + VKT-1 - VLW*warp - m].
-        // 16 samples at a time: their 16 values and the 31 window values they
-        // meet sit in registers with static indices, 256 FMAs per 47 loads.
-        const int base0 = VKT - 1 - VLW * warp;
-#pragma unroll 1
-        for (int tc = 0; tc < VB; tc += VLW) {
-            float a[VLW], w[2 * VLW - 1];
+        if (js + MJ < VJCH && jb + MJ < A.ncomp) load_rows(jb + MJ);
 #pragma unroll
-            for (int i = 0; i < VLW; ++i) a[i] = sA[tc + i][lane];
+        for (int k8 = 0; k8 < MJ; k8 += 8) {
+            unsigned ah[4], al[4];
+            ldsm_x4(ah, hA + a_off + k8);
+            ldsm_x4(al, lA + a_off + k8);
 #pragma unroll
-            for (int i = 0; i < 2 * VLW - 1; ++i) w[i] = sW[base0 + tc - (VLW - 1) + i][lane];
-#pragma unroll
-            for (int i = 0; i < VLW; ++i)
-#pragma unroll
-                for (int m = 0; m < VLW; ++m) acc[m] = fmaf(a[i], w[i - m + VLW - 1], acc[m]);
+            for (int q = 0; q < 9; q += 2) {
+                // N tiles nt0 + q and nt0 + q + 1 (the last pair also loads the tile
+                // after the warp's nine -- rows up to 199, inside the allocation --
+                // and does not use it)
+                unsigned bh[4], bl[4];
+                ldsm_x4(bh, hW + b_off + 8 * q * MLD + k8);
+                ldsm_x4(bl, lW + b_off + 8 * q * MLD + k8);
+                mma_tf32(acc[q], al, bh);
+                mma_tf32(acc[q], ah, bl);
+                mma_tf32(acc[q], ah, bh);
+                if (q + 1 < 9) {
+                    mma_tf32(acc[q + 1], al, bh + 2);
+                    mma_tf32(acc[q + 1], ah, bl + 2);
+                    mma_tf32(acc[q + 1], ah, bh + 2);
+                }
+            }
         }
     }
-    // combine the lanes in FP64, fixed tree
+    __syncthreads();
+    // the tile P[t][s] (only the band is read back) and the lag sums over t
+    float *sP = vsm;
+    const int g = lane >> 2, c = lane & 3;
 #pragma unroll
-    for (int m = 0; m < VLW; ++m) {
-        double v = (double)acc[m];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        const int k = k0 + VLW * warp + m;
-        if (lane == 0 && k <= A.K) A.part[(long long)blockIdx.y * (A.K + 1) + k] = v;
+    for (int q = 0; q < 9; ++q) {
+        const int t = 16 * mt + g, sr = 8 * (nt0 + q) + 2 * c;
+        sP[t * MPLD + sr] = acc[q][0];
+        sP[t * MPLD + sr + 1] = acc[q][1];
+        sP[(t + 8) * MPLD + sr] = acc[q][2];
+        sP[(t + 8) * MPLD + sr + 1] = acc[q][3];
     }
+    __syncthreads();
+    if (threadIdx.x < VKT) {
+        const int kk = threadIdx.x, k = k0 + kk;
+        double v = 0.0;
+        for (int t = 0; t < nb; ++t) v += (double)sP[t * MPLD + t + (VKT - 1) - kk];
+        if (k <= A.K) A.part[(long long)blockIdx.y * (A.K + 1) + k] = v;
+    }
+}
+
+cudaError_t prepare_vacf_kernels() {
+    return cudaFuncSetAttribute(k_vacf_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
 }
 
 __global__ void __launch_bounds__(256) k_vacf_reduce(const VacfArgs A, int nchunks) {
@@ -224,7 +315,7 @@ cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st) {
     A.np = s.np;
     A.done = reinterpret_cast<unsigned int *>(s.d_vacf + 3);
     dim3 g1((s.vacf_lag + VKT) / VKT, s.vacf_nchunks);
-    k_vacf_corr<<<g1, 256, 0, st>>>(A);
+    k_vacf_mma<<<g1, 256, MMA_SMEM, st>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int g2 = (s.vacf_lag + 1 + 255) / 256;
