@@ -29,11 +29,11 @@ namespace lbp {
 // write streams stay local in DRAM) and balances the tail.  The 15 loads of a
 // node are independent, so every thread keeps 60 bytes in flight.  Address
 // arithmetic is 32-bit offsets from per-population plane pointers passed as
-// kernel parameters, and the collision is written per opposite pair
-// (a, a+1), e_{a+1} = -e_a:
-//     geq_a, geq_{a+1} = w [(rho~-1) - 3/2 u.u + 9/2 (e.u)^2] +- 3 w e.u,
-// which keeps the instruction count low enough that the kernel stays bound
-// by DRAM bandwidth.  Measured on GB300 at 256^3: within 2% of a plain copy.
+// kernel parameters, and the collision (collide_values) is written per
+// opposite pair (a, a+1), e_{a+1} = -e_a, with 1/tau folded into per-class
+// constants: eight operations a pair.  The FP32 kernel stays bound by DRAM
+// bandwidth (measured on GB300 at 256^3: within 2% of a plain copy); the
+// 2-byte kernels, which move half the bytes, are bound by instruction issue.
 // ---------------------------------------------------------------------------
 template <typename St>
 __device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
@@ -74,8 +74,11 @@ __device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int n
 // arithmetic.  R = 2 for the 2-byte storage types, whose 15 loads per node
 // alone keep too few bytes in flight; R = 1 for FP32.  The block finds its box
 // in the replica table (a kernel parameter; one entry for a single box).
+// Two rows per block are held to 64 registers (eight blocks of 128 threads per
+// SM): the batched ensemble's short rows need the occupancy (0.793 ms per
+// launch there, against 0.833 ms at the compiler's 72 registers).
 template <int BX, typename St, int R, int MAXR>
-__global__ void __launch_bounds__(BX) k_stream_collide(Planes<St> pl, const RepTable<MAXR> rt,
+__global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide(Planes<St> pl, const RepTable<MAXR> rt,
                                                        long long *bump) {
     const int r = find_block_rep(rt, blockIdx.x);
     const Rep &rp = rt.rep[r];
@@ -140,7 +143,7 @@ __device__ __forceinline__ void record_sum(unsigned long long rw, int cnt, int x
 // step, which the next step's particle kernel refills.
 // ---------------------------------------------------------------------------
 template <int BX, typename St, int R, int MAXR>
-__global__ void __launch_bounds__(BX) k_stream_collide_forced(
+__global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
     Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
     unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
     static_assert(BX == SEG, "one block per force-record segment");

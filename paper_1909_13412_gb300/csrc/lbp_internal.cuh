@@ -86,14 +86,14 @@ struct Planes {
 // Collision of one node (Eqs. 15, 17-19 in deviation form, see
 // lbm_kernels.cu): the 15 post-collision deviations of the node whose
 // pulled deviations are g; (F0, F1, F2) is the body force of Eq. 18 at the
-// node (zero if none).  Every operation is written out with its rounding (no
+// node (zero if none).  Per opposite pair (A, A+1), e_{A+1} = -e_A, weight W:
+//     o_A, o_{A+1} = (1 - omega) g + S +- X,
+//     S = omega W (base + 9/2 (e.u)^2),   X = 3 omega W e.u + 3 W e.F,
+// with base = (rho~ - 1) - 3/2 u.u, and o_0 = (1 - omega) g_0 + (2/9) omega base:
+// omega is folded into the per-class constants omega W, so a pair costs eight
+// operations.  Every operation is written out with its rounding (no
 // contraction left to the compiler), so that every kernel that inlines this
-// function performs the same operations in the same order, bit for bit:
-//     rho~ - 1 = sum_a g_a (in index order),   u = sum_a e_a g_a,
-//     base = (rho~ - 1) - 3/2 u.u,
-//     o_0 = (1 - omega) g_0 + omega (2/9 base),
-//     o_A, o_A+1 = (1 - omega) g + omega (sym +- anti) +- fe per opposite pair,
-//     sym = W (base + 9/2 (e.u)^2), anti = 3 W e.u, fe = 3 W e.F.
+// function performs the same operations in the same order, bit for bit.
 __device__ __forceinline__ void collide_values(const float g[Q], float omega, float F0, float F1,
                                                float F2, float o[Q]) {
     float drho = g[0];
@@ -107,24 +107,27 @@ __device__ __forceinline__ void collide_values(const float g[Q], float omega, fl
     const float uu = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
     const float base = __fmaf_rn(-1.5f, uu, drho);
     const float om1 = __fsub_rn(1.f, omega);
-    o[0] = __fmaf_rn(om1, g[0], __fmul_rn(omega, __fmul_rn(2.f / 9.f, base)));
-    // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, weight W
-#define LBP_PAIR(A, W, EU, FE)                                                                   \
-    {                                                                                            \
-        const float eu = (EU);                                                                   \
-        const float sym = __fmul_rn((W), __fmaf_rn(4.5f, __fmul_rn(eu, eu), base));              \
-        const float anti = __fmul_rn(3.f * (W), eu);                                             \
-        const float fe = __fmul_rn(3.f * (W), (FE));                                             \
-        o[A] = __fadd_rn(__fmaf_rn(om1, g[A], __fmul_rn(omega, __fadd_rn(sym, anti))), fe);      \
-        o[A + 1] = __fsub_rn(__fmaf_rn(om1, g[A + 1], __fmul_rn(omega, __fsub_rn(sym, anti))), fe); \
+    // per-class constants (uniform over the box)
+    const float wo_f = __fmul_rn(omega, 1.f / 9.f), wo_c = __fmul_rn(omega, 1.f / 72.f);
+    const float s_f = __fmul_rn(wo_f, base), s_c = __fmul_rn(wo_c, base);
+    o[0] = __fmaf_rn(om1, g[0], __fmul_rn(__fmul_rn(omega, 2.f / 9.f), base));
+    // pair (A, A+1): velocity e_A with e.u = EU and e.F = FE, class constants WO
+    // (omega W), SB (omega W base) and W
+#define LBP_PAIR(A, W, WO, SB, EU, FE)                                                     \
+    {                                                                                      \
+        const float eu = (EU);                                                             \
+        const float S = __fmaf_rn(__fmul_rn(4.5f, (WO)), __fmul_rn(eu, eu), (SB));         \
+        const float X = __fmaf_rn(__fmul_rn(3.f, (WO)), eu, __fmul_rn(3.f * (W), (FE)));   \
+        o[A] = __fmaf_rn(om1, g[A], __fadd_rn(S, X));                                      \
+        o[A + 1] = __fmaf_rn(om1, g[A + 1], __fsub_rn(S, X));                              \
     }
-    LBP_PAIR(1, 1.f / 9.f, ux, F0)
-    LBP_PAIR(3, 1.f / 9.f, uy, F1)
-    LBP_PAIR(5, 1.f / 9.f, uz, F2)
-    LBP_PAIR(7, 1.f / 72.f, __fadd_rn(__fadd_rn(ux, uy), uz), __fadd_rn(__fadd_rn(F0, F1), F2))
-    LBP_PAIR(9, 1.f / 72.f, __fsub_rn(__fadd_rn(ux, uy), uz), __fsub_rn(__fadd_rn(F0, F1), F2))
-    LBP_PAIR(11, 1.f / 72.f, __fadd_rn(__fsub_rn(ux, uy), uz), __fadd_rn(__fsub_rn(F0, F1), F2))
-    LBP_PAIR(13, 1.f / 72.f, __fadd_rn(__fsub_rn(uy, ux), uz), __fadd_rn(__fsub_rn(F1, F0), F2))
+    LBP_PAIR(1, 1.f / 9.f, wo_f, s_f, ux, F0)
+    LBP_PAIR(3, 1.f / 9.f, wo_f, s_f, uy, F1)
+    LBP_PAIR(5, 1.f / 9.f, wo_f, s_f, uz, F2)
+    LBP_PAIR(7, 1.f / 72.f, wo_c, s_c, __fadd_rn(__fadd_rn(ux, uy), uz), __fadd_rn(__fadd_rn(F0, F1), F2))
+    LBP_PAIR(9, 1.f / 72.f, wo_c, s_c, __fsub_rn(__fadd_rn(ux, uy), uz), __fsub_rn(__fadd_rn(F0, F1), F2))
+    LBP_PAIR(11, 1.f / 72.f, wo_c, s_c, __fadd_rn(__fsub_rn(ux, uy), uz), __fadd_rn(__fsub_rn(F0, F1), F2))
+    LBP_PAIR(13, 1.f / 72.f, wo_c, s_c, __fadd_rn(__fsub_rn(uy, ux), uz), __fadd_rn(__fsub_rn(F1, F0), F2))
 #undef LBP_PAIR
 }
 

@@ -174,6 +174,13 @@ __global__ void __launch_bounds__(256) k_vacf_mma(const VacfArgs A) {
         }
         __syncthreads();
         if (js + MJ < VJCH && jb + MJ < A.ncomp) load_rows(jb + MJ);
+        // the tensor core adds into its FP32 accumulator with truncation, which
+        // biases long chains of additions; each sub-chunk's 12 products per
+        // entry go to a fresh accumulator that is then added, rounded to
+        // nearest, to the running sum
+        float pacc[9][4];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) pacc[q][0] = pacc[q][1] = pacc[q][2] = pacc[q][3] = 0.f;
 #pragma unroll
         for (int k8 = 0; k8 < MJ; k8 += 8) {
             unsigned ah[4], al[4];
@@ -187,16 +194,20 @@ __global__ void __launch_bounds__(256) k_vacf_mma(const VacfArgs A) {
                 unsigned bh[4], bl[4];
                 ldsm_x4(bh, hW + b_off + 8 * q * MLD + k8);
                 ldsm_x4(bl, lW + b_off + 8 * q * MLD + k8);
-                mma_tf32(acc[q], al, bh);
-                mma_tf32(acc[q], ah, bl);
-                mma_tf32(acc[q], ah, bh);
+                mma_tf32(pacc[q], al, bh);
+                mma_tf32(pacc[q], ah, bl);
+                mma_tf32(pacc[q], ah, bh);
                 if (q + 1 < 9) {
-                    mma_tf32(acc[q + 1], al, bh + 2);
-                    mma_tf32(acc[q + 1], ah, bl + 2);
-                    mma_tf32(acc[q + 1], ah, bh + 2);
+                    mma_tf32(pacc[q + 1], al, bh + 2);
+                    mma_tf32(pacc[q + 1], ah, bl + 2);
+                    mma_tf32(pacc[q + 1], ah, bh + 2);
                 }
             }
         }
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[q][r] = __fadd_rn(acc[q][r], pacc[q][r]);
     }
     __syncthreads();
     // the tile P[t][s] (only the band is read back) and the lag sums over t

@@ -501,6 +501,30 @@ def test_vacf_matches_oracle_on_the_same_trajectory():
     assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
 
 
+def test_vacf_spans_lag_tiles_and_component_chunks_with_ragged_tails():
+    """The block correlation with several 128-lag tiles and 1024-component
+    chunks, both ragged (K = 300: 128 + 128 + 45 lags; 400 particles: 1024 +
+    176 components), three full 64-sample blocks and a partial one flushed by
+    the read: sums within 1e-6 of C(0) of the oracle's FP64 correlation of the
+    same (FP32) trajectory, pair counts exact."""
+    shape = (16, 20, 24)
+    ps = wl.uniform_particles(400, shape, 6.0, 0.5, 0.2, 1e-4, 5, 6)
+    h = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=3)
+    K = 300
+    lbp.lbp_vacf_configure(h, K)
+    traj = []
+    for _ in range(3 * 64 + 37):
+        lbp.lbp_step(h, 1)
+        traj.append(gpu_particles(h)[1])
+    cs = np.empty(K + 1)
+    cnt = np.empty(K + 1, np.int64)
+    lbp.lbp_vacf_read(h, cs, cnt)
+    lbp.lbp_destroy(h)
+    ref, refc = oracle.vacf(np.array(traj, np.float32).astype(np.float64), K)
+    assert np.array_equal(cnt, refc)
+    assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
+
+
 def test_vacf_requires_particles():
     h = gpu_sim((4, 4, 4), 0.8)
     with pytest.raises(lbp.LbpError) as ei:
