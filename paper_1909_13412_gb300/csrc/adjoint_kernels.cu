@@ -42,7 +42,7 @@
 //   their values, so the result does not depend on which particle appended
 //   first; entries that did not fit a record go to a dense FP64 buffer (FP64
 //   atomics, order-dependent in that rare case).  dL/dw is summed per block in
-//   FP64 into the block's own accumulator slot (no atomics).
+//   FP32 and added in FP64 to the block's own accumulator slot (no atomics).
 #include <cuda_runtime.h>
 
 #include "lbp_internal.cuh"
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
                                                      float omega, const unsigned long long *rec_cur,
                                                      unsigned long long *rec_prev, double *fqd,
                                                      long long N, double *acc_omega) {
-    __shared__ double s_red[SEG / 32];
+    __shared__ float s_red[SEG / 32];
     const unsigned row = blockIdx.x / (unsigned)nchunks;
     const int chunk = (int)(blockIdx.x - row * (unsigned)nchunks);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -513,17 +513,19 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
             lam_out[(long long)a * P + d] = v;  // dL/df^n_a(x), aligned
         }
     }
-    // dL/domega: FP64 block sum into the block's own slot
-    double v = act ? (double)dom : 0.0;
+    // dL/domega: the block's 128 terms summed in FP32 (fixed tree), added in
+    // FP64 to the block's own slot.  (A tree of FP64 shuffles kept the narrow
+    // FP64 pipe of this GPU busy at every block's end.)
+    float v = act ? dom : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) s_red[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
+        float s = 0.f;
 #pragma unroll
         for (int w = 0; w < SEG / 32; ++w) s += s_red[w];
-        acc_omega[blockIdx.x] += s;
+        acc_omega[blockIdx.x] += (double)s;
     }
 }
 
