@@ -195,12 +195,14 @@ lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
  * and velocities after it (as lbp_particles_read).  The call returns when the
  * host outputs are written (on_device = 0) or, for device pointers, with the
  * work queued on the handle's stream.
- * With page-locked host buffers (cudaHostAlloc / cudaHostRegister) and graphs
- * on, the copies, conversions and the step replay as one CUDA graph per buffer
- * parity, cached on the three buffer addresses; positions and velocities are
- * final after the step's particle kernel (Eqs. 1-2), so they come back while
- * the lattice pass of the same step still runs, and the call may return
- * before that pass ends.  Every later call on the handle is ordered after it,
+ * With page-locked host buffers mapped into the device's address space
+ * (cudaHostAlloc / cudaHostRegister with unified addressing) and graphs on,
+ * the layout conversions read f_ext from and write r and v to the host
+ * buffers directly, and they replay with the step as one CUDA graph per
+ * buffer parity, cached on the three buffer addresses; positions and
+ * velocities are final after the step's particle kernel (Eqs. 1-2), so they
+ * go out while the lattice pass of the same step still runs, and the call
+ * may return before that pass ends.  Every later call on the handle is ordered after it,
  * and the handle's user stream waits for it.  Pageable buffers take plain
  * stream-ordered copies and return after the whole step.                      */
 lbp_status lbp_step_exchange(lbp_sim *sim, const double *f_ext, double *r, double *v, int on_device);

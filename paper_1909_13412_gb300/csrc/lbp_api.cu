@@ -121,14 +121,12 @@ bool radius_ok(double R, int exclude) {
 
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
-lbp_status exchange_out(lbp_sim *s, double *r, double *v, cudaMemcpyKind kind, cudaStream_t st);
-
 // one time step (see the sequence at the top of this file).  With `readback`
 // (r, v host buffers, either may be NULL) the positions and velocities the
 // particle kernel has just written go to the host on s2 while s0 runs the
 // lattice pass; ev_xdone marks the end of that branch.
 struct Readback {
-    double *r, *v;
+    double *r, *v;  // device-accessible addresses of page-locked host buffers
 };
 lbp_status enqueue_step(lbp_sim *s, bool timed, const Readback *readback = nullptr) {
     const void *src = s->f[s->cur];
@@ -136,9 +134,12 @@ lbp_status enqueue_step(lbp_sim *s, bool timed, const Readback *readback = nullp
     const int parity = s->cur;
     if (s->np > 0) CK(launch_particles(*s, src, parity, s->s0));
     if (readback) {
+        // the layout conversion writes the host buffers directly (over the
+        // CPU-GPU link), so the branch is two small kernels and no copies
         CK(cudaEventRecord(s->ev_xmid, s->s0));
         CK(cudaStreamWaitEvent(s->s2, s->ev_xmid, 0));
-        TRY(exchange_out(s, readback->r, readback->v, cudaMemcpyDeviceToHost, s->s2));
+        if (readback->r) CK(launch_soa_to_aos(s->r, readback->r, s->np, s->cap, s->s2));
+        if (readback->v) CK(launch_soa_to_aos(s->v, readback->v, s->np, s->cap, s->s2));
         CK(cudaEventRecordWithFlags(s->ev_xdone, s->s2, cudaEventRecordExternal));
         CK(cudaEventRecord(s->ev_xjoin, s->s2));
     }
@@ -263,9 +264,19 @@ lbp_status exchange_out(lbp_sim *s, double *r, double *v, cudaMemcpyKind kind, c
     return LBP_OK;
 }
 
-// [copy in, step with the read-back branch] from and to page-locked host
+// the device address of a mapped page-locked host buffer (null stays null)
+lbp_status device_view(double *&p) {
+    if (!p) return LBP_OK;
+    cudaPointerAttributes at;
+    CK(cudaPointerGetAttributes(&at, p));
+    p = static_cast<double *>(at.devicePointer);
+    return LBP_OK;
+}
+
+// [forces in, step with the read-back branch] from and to page-locked host
 // buffers as one graph for the current buffer parity, kept while the same
-// buffers come back
+// buffers come back: the layout conversions read and write the host buffers
+// directly, so the graph holds kernels only
 lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v, cudaGraphExec_t *out) {
     const int par = s->cur;
     const void *key[3] = {f_ext, r, v};
@@ -276,10 +287,18 @@ lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v,
             cudaGraphExecDestroy(s->xgraph[par]);
             s->xgraph[par] = nullptr;
         }
+        double *f_dev = const_cast<double *>(f_ext), *r_dev = r, *v_dev = v;
+        TRY(device_view(f_dev));
+        TRY(device_view(r_dev));
+        TRY(device_view(v_dev));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
-        const Readback rb{r, v};
-        lbp_status st = exchange_in(s, f_ext, cudaMemcpyHostToDevice);
+        const Readback rb{r_dev, v_dev};
+        lbp_status st = LBP_OK;
+        if (f_dev) {
+            cudaError_t e0 = launch_aos_to_soa(f_dev, s->fext, s->np, s->cap, 0, s->s0);
+            if (e0 != cudaSuccess) st = fail(LBP_ECUDA, "lbp_step_exchange: %s", cudaGetErrorString(e0));
+        }
         if (st == LBP_OK) st = enqueue_step(s, false, &rb);
         cudaError_t e = cudaStreamEndCapture(s->s0, &g);
         if (st != LBP_OK) {
@@ -297,7 +316,8 @@ lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v,
     return LBP_OK;
 }
 
-// page-locked (or registered) host memory, which a graph's copy nodes may use
+// page-locked (or registered) host memory mapped into the device's address
+// space, which kernels can read and write directly
 bool host_pinned(const void *p) {
     if (!p) return true;
     cudaPointerAttributes at;
@@ -305,7 +325,7 @@ bool host_pinned(const void *p) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeHost;
+    return at.type == cudaMemoryTypeHost && at.devicePointer != nullptr;
 }
 
 
