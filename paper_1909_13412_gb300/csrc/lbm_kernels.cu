@@ -672,25 +672,6 @@ cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream
     return launch_stream_collide_cfg(s, src, dst, s.d_step, s.rows, s.variant, st);
 }
 
-cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
-                                             const unsigned long long *rec_cur,
-                                             unsigned long long *rec_prev, long long *bump, int rows,
-                                             cudaStream_t st) {
-    constexpr int BX = SC_BX;
-    return by_storage(s, [&](auto tag) {
-        using St = decltype(tag);
-        return by_rows(rows, [&](auto rc) {
-            constexpr int R = decltype(rc)::value;
-            return by_batch(s, R, [&](const auto &rt) {
-                constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
-                k_stream_collide_forced<BX, St, R, MAXR><<<rt.item_off[rt.nrep], BX, 0, st>>>(
-                    planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
-                return cudaGetLastError();
-            });
-        });
-    });
-}
-
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
                                          cudaStream_t st) {
     return launch_stream_collide_forced_cfg(s, src, dst, s.rec[parity], s.rec[parity ^ 1], s.d_step,
