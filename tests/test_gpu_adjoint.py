@@ -12,6 +12,8 @@ torch.autograd.Function over them) against independent gradients.
     2000-step relaxation run (checkpoint every 100 steps): dL/dtau,
     dL/dgamma and two components of dL/dV0 of the velocity-relaxation loss,
     to 1e-4 relative.
+  * With FP16 or BF16 storage: the same reference, within bounds set by the
+    storage's rounding (2^-11 and 2^-8 of the stored deviations).
   * Bitwise: the gradients do not depend on the checkpoint interval and are
     the same on a second run; the backward pass leaves the handle's state
     unchanged; a changed handle is refused.
@@ -72,10 +74,10 @@ def reference(c, tau, kT, steps, seed, mode, exclude, pinned, loss_fn):
     return {k: (v.grad.numpy() if v.grad is not None else np.zeros(v.shape)) for k, v in x.items()}, Vt.detach().numpy()
 
 
-def gpu(c, tau, kT, steps, seed, mode, exclude, pinned, loss_fn, C):
+def gpu(c, tau, kT, steps, seed, mode, exclude, pinned, loss_fn, C, precision=lbp.LBP_F32):
     nz, ny, nx = SHAPE
     x = leaves(c, tau, kT)
-    spec = adjoint.RunSpec(nx, ny, nz, steps, C, seed, mode, int(exclude))
+    spec = adjoint.RunSpec(nx, ny, nz, steps, C, seed, mode, int(exclude), precision)
     pin = None if pinned is None else torch.tensor(pinned)
     Vt, rt = adjoint.trajectory(x["tau"], x["gamma"], x["radius"], x["mass"], x["v0"], x["r0"], spec,
                                 kT=x["kT"], f0=x["f0"], f_ext=torch.tensor(c["Fext"]), pinned=pin)
@@ -121,6 +123,32 @@ def test_adjoint_matches_fp64_reference(mode, exclude, kT):
     if mode == lbp.LBP_POINTWISE:
         names = [k for k in names if k != "radius"]
     assert_close(got, want, 1e-4, names)
+
+
+# forward-trajectory and gradient bounds (relative to the largest entry) for
+# 2-byte storage: FP16 rounds the scaled deviations to 2^-11, BF16 the
+# deviations to 2^-8; measured on GB300 (40 steps): FP16 forward 5e-6,
+# gradients <= 1.4e-4 (tau; the rest <= 2e-5); BF16 forward 3.7e-5, gradients
+# <= 2.8e-4 (tau; the rest <= 8e-5)
+TWO_BYTE_BOUNDS = {lbp.LBP_F16: (5e-5, 1e-3), lbp.LBP_BF16: (3e-4, 2e-3)}
+
+
+@pytest.mark.parametrize("prec", [lbp.LBP_F16, lbp.LBP_BF16])
+def test_adjoint_with_two_byte_storage(prec):
+    """The adjoint of a run whose populations are stored as FP16 or BF16
+    deviations: the recording and the reverse sweep use the handle's storage
+    (the replayed forward steps round exactly as the recorded ones) and the
+    lattice adjoint reads the rounded populations.  Against the FP64 reference
+    of the unrounded method the trajectories and every gradient carry the
+    storage's rounding, within the bounds above."""
+    c = case(seed=7)
+    steps = 40
+    loss = linear_loss(steps, 5, seed=2)
+    want, Vw = reference(c, 0.8, 1e-4, steps, 11, lbp.LBP_STOKESLET, 0, None, loss)
+    got, Vg = gpu(c, 0.8, 1e-4, steps, 11, lbp.LBP_STOKESLET, 0, None, loss, C=7, precision=prec)
+    fwd_tol, grad_tol = TWO_BYTE_BOUNDS[prec]
+    assert np.max(np.abs(Vg - Vw)) <= fwd_tol * np.max(np.abs(Vw))
+    assert_close(got, want, grad_tol)
 
 
 def test_adjoint_of_a_vacf_loss():
