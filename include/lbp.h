@@ -333,14 +333,14 @@ lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp
  * of the populations plus 48 bytes per particle each).  v_traj and r_traj
  * (optional, [nsteps][n_particles][3] FP64, host or device per on_device)
  * receive V^{n+1} and r^{n+1} after every step n: the trajectory a loss is
- * written on.  A new recording replaces the previous one.  Single-box handles
- * with at least one particle only (LBP_EINVAL for a batch, LBP_ESTATE without
- * particles).
+ * written on.  A new recording replaces the previous one.  Handles with at
+ * least one particle (LBP_ESTATE without particles); single boxes and
+ * batches of boxes alike.
  *
  * lbp_adjoint_backward takes dL/dV^{n+1} and dL/dr^{n+1} for every recorded
  * step (g_v, g_r: [nsteps][n_particles][3] FP64, either may be NULL = zero)
  * and returns, through the non-NULL members of grads, the gradient of L with
- * respect to the inputs of the recorded run: tau (one value), kT (one value),
+ * respect to the inputs of the recorded run: tau (one value per box), kT (one value),
  * each particle's gamma, radius and mass ([n_particles]), the velocities and
  * positions at the first recorded step ([n_particles][3]) and the populations
  * at the first recorded step ([15][N], ABI layout).  The reverse sweep
@@ -357,7 +357,7 @@ lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp
  * row segment in one step (those extra contributions are then added with FP64
  * atomics).  Synchronous.                                                    */
 typedef struct {
-    double *tau;     /* [1]                    dL/dtau                         */
+    double *tau;     /* [n_replicas]           dL/dtau of each box             */
     double *kT;      /* [1]                    dL/dkT                          */
     double *gamma;   /* [n_particles]          dL/dgamma_i                     */
     double *radius;  /* [n_particles]          dL/dR_i                         */

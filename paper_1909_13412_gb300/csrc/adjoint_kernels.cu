@@ -45,6 +45,8 @@
 //   FP32 and added in FP64 to the block's own accumulator slot (no atomics).
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "lbp_internal.cuh"
 
 namespace lbp {
@@ -55,7 +57,7 @@ struct AdjPArgs {
     const void *g;           // fhat^{n-1}, storage type St, 15 planes of P
     const float *lam;        // dL/dfhat^n, FP32, 15 planes of P
     long long P, N;
-    int nx, ny, nz, nchunks;
+    const int *prep;         // box of each particle (batches)
     const double *r, *v;     // r^n, V^n, [3][cap]
     int cap, np;
     const double *fext, *inv_mass, *gamma, *radius, *sig;
@@ -78,8 +80,8 @@ __device__ __forceinline__ int wrap_i(int i, int n) { return i < 0 ? i + n : (i 
 // Gathers (eight threads per particle): u(x_p) of the streamed f (pull) and
 // lam_F(x_p) = sum_a 3 w_a e_a lam_a(x_p) (aligned) at the eight corners, to
 // A.ug[i][p][0..2] and A.ug[i][p][3..5].
-template <typename St>
-__global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A) {
+template <typename St, int MAXR>
+__global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A, const RepTable<MAXR> rt) {
     const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[APB][3];
     const int t = threadIdx.x, lane = t & 31;
@@ -96,7 +98,9 @@ __global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A) {
     const int j = t >> 3, p = t & 7;
     const int ij = i0 + j;
     int X = 0, Y = 0, Z = 0;
-    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const Rep &rj = rt.rep[MAXR == 1 || ij >= A.np ? 0 : A.prep[ij]];
+    const int nx = rj.nx, ny = rj.ny, nz = rj.nz;
+    const long long off = rj.node_off;
     if (ij < A.np) {
         X = wrap_i(s_base[j][0] + (p & 1), nx);
         Y = wrap_i(s_base[j][1] + ((p >> 1) & 1), ny);
@@ -104,15 +108,14 @@ __global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A) {
         const int xs[3] = {wrap_i(X + 1, nx), X, wrap_i(X - 1, nx)};
         const int ys[3] = {wrap_i(Y + 1, ny), Y, wrap_i(Y - 1, ny)};
         const int zs[3] = {wrap_i(Z + 1, nz), Z, wrap_i(Z - 1, nz)};
-        const long long node = ((long long)Z * ny + Y) * nx + X;
         float sx = 0.f, sy = 0.f, sz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
 #pragma unroll
         for (int a = 1; a < Q; ++a) {
-            const long long src = (long long)a * A.P + ((long long)zs[ez(a) + 1] * ny + ys[ey(a) + 1]) * nx +
+            const long long src = (long long)a * A.P + off + ((long long)zs[ez(a) + 1] * ny + ys[ey(a) + 1]) * nx +
                                   xs[ex(a) + 1];
             const float gv = St::load(G + src, a);
             // dL/dfhat_a(x_p) = dL/df^{n+1}_a(x_p + e_a) (the buffer's layout)
-            const long long lnode = ((long long)zs[1 - ez(a)] * ny + ys[1 - ey(a)]) * nx + xs[1 - ex(a)];
+            const long long lnode = off + ((long long)zs[1 - ez(a)] * ny + ys[1 - ey(a)]) * nx + xs[1 - ex(a)];
             const float lv = (3.f * wgtf(a)) * __ldg(A.lam + (long long)a * A.P + lnode);
             if (ex(a)) { sx += ex(a) > 0 ? gv : -gv; lx += ex(a) > 0 ? lv : -lv; }
             if (ey(a)) { sy += ey(a) > 0 ? gv : -gv; ly += ey(a) > 0 ? lv : -lv; }
@@ -131,7 +134,8 @@ __global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A) {
 // The FP64 adjoint of one particle's step, one particle per thread in small
 // blocks (so that many warps per SM share the FP64 pipe), then its lam_u(x_p)
 // appended to the records of the corners' row segments.
-__global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A) {
+template <int MAXR>
+__global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTable<MAXR> rt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int cap = A.cap;
     if (i < A.np) {
@@ -356,7 +360,8 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A) {
         A.acc[3 * A.np + i] += gK;
         // lam_u(x_p) to the record of each corner's row segment
         if (spread) {
-            const int nx = A.nx, ny = A.ny, nz = A.nz;
+            const Rep &ri = rt.rep[MAXR == 1 ? 0 : A.prep[i]];
+            const int nx = ri.nx, ny = ri.ny, nz = ri.nz;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const double l0 = lu[c][0], l1 = lu[c][1], l2 = lu[c][2];
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A) {
                 const int Y = wrap_i(base[1] + ((c >> 1) & 1), ny);
                 const int Z = wrap_i(base[2] + ((c >> 2) & 1), nz);
                 const long long row = (long long)Z * ny + Y;
-                unsigned long long *rec = A.rec + (size_t)(row * A.nchunks + X / SEG) * REC_WORDS;
+                unsigned long long *rec = A.rec + (size_t)(ri.seg_off + row * ri.nchunks + X / SEG) * REC_WORDS;
                 const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
                 if (slot < (unsigned)REC_SLOTS) {
                     reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A) {
                     rec[REC_F0 + 3 * slot + 1] = (unsigned long long)__double_as_longlong(l1);
                     rec[REC_F0 + 3 * slot + 2] = (unsigned long long)__double_as_longlong(l2);
                 } else {
-                    const long long node = row * nx + X;
+                    const long long node = ri.node_off + row * nx + X;
                     atomicAdd(A.fqd + node, l0);
                     atomicAdd(A.fqd + A.N + node, l1);
                     atomicAdd(A.fqd + 2 * A.N + node, l2);
@@ -410,25 +415,32 @@ __device__ __forceinline__ void adj_record_sum(const unsigned long long *rec, un
 
 // At least 6 blocks per SM: 80 registers (32 bytes spilled) instead of 96,
 // measured 6.5% faster at 256^3 (more bytes in flight per SM).
-template <typename St>
+template <typename St, int MAXR>
 __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__restrict__ G,
                                                      const float *__restrict__ lam, float *lam_out,
-                                                     long long P, int nx, int ny, int nz, int nchunks,
-                                                     float omega, const unsigned long long *rec_cur,
+                                                     long long P, const RepTable<MAXR> rt,
+                                                     const unsigned long long *rec_cur,
                                                      unsigned long long *rec_prev, double *fqd,
                                                      long long N, double *acc_omega) {
     __shared__ float s_red[SEG / 32];
-    const unsigned row = blockIdx.x / (unsigned)nchunks;
-    const int chunk = (int)(blockIdx.x - row * (unsigned)nchunks);
+    // the block's box (batches: one block per row segment of every box, in box order)
+    const int rb = find_block_rep(rt, blockIdx.x);
+    const Rep &rp = rt.rep[rb];
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
+    const float omega = rp.omega;
+    const unsigned item = blockIdx.x - rt.item_off[rb];
+    const unsigned row = item / (unsigned)nchunks;
+    const int chunk = (int)(item - row * (unsigned)nchunks);
+    const size_t seg = (size_t)rp.seg_off + (size_t)row * nchunks + chunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) rec_prev[((size_t)row * nchunks + chunk) * REC_WORDS] = 0ull;
+    if (threadIdx.x == 0) rec_prev[seg * REC_WORDS] = 0ull;
     const int x0 = chunk * SEG + threadIdx.x;
     const bool act = x0 < nx;
     const int x = act ? x0 : nx - 1;
     // node index and the offsets of x - e (index e + 1), periodic
     const int z = (int)(row / (unsigned)ny), y = (int)(row - (unsigned)z * ny);
     const int slab = nx * ny;
-    const int d = (int)row * nx + x;
+    const int d = (int)rp.node_off + (int)row * nx + x;
     const int ox[3] = {x == nx - 1 ? 1 - nx : 1, 0, x == 0 ? nx - 1 : -1};
     const int oy[3] = {y == ny - 1 ? (1 - ny) * nx : nx, 0, y == 0 ? (ny - 1) * nx : -nx};
     const int oz[3] = {z == nz - 1 ? (1 - nz) * slab : slab, 0, z == 0 ? (nz - 1) * slab : -slab};
@@ -441,7 +453,7 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
         // dL/dfhat^n_a(x) = dL/df^{n+1}_a(x + e_a): the buffer holds the latter
         l[a] = __ldg(lam + (long long)a * P + d + op);
     }
-    const unsigned long long rw = __ldg(rec_cur + ((size_t)row * nchunks + chunk) * REC_WORDS + lane);
+    const unsigned long long rw = __ldg(rec_cur + seg * REC_WORDS + lane);
     // particle contributions lam_u(x)
     float pu0 = 0.f, pu1 = 0.f, pu2 = 0.f;
     const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw, 0) & 0xffffffffull);
@@ -454,7 +466,7 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
         }
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         if (mask && act)
-            adj_record_sum(rec_cur + ((size_t)row * nchunks + chunk) * REC_WORDS, mask, a0, a1, a2);
+            adj_record_sum(rec_cur + seg * REC_WORDS, mask, a0, a1, a2);
         if (cnt > REC_SLOTS && act) {
             a0 += fqd[d];
             a1 += fqd[N + d];
@@ -538,6 +550,31 @@ static cudaError_t by_storage_adj(int precision, F &&f) {
     }
 }
 
+// The box table of an adjoint launch: every box with its blocks of one
+// 128-node row segment each (item_off, for the lattice kernel) -- one entry
+// for a single box.
+template <int MAXR>
+static RepTable<MAXR> adj_table(const Sim &s) {
+    RepTable<MAXR> t;
+    memset(&t, 0, sizeof(t));
+    t.nrep = s.nrep;
+    unsigned off = 0;
+    for (int r = 0; r < s.nrep; ++r) {
+        t.rep[r] = s.reps[r];
+        t.item_off[r] = off;
+        off += (unsigned)s.reps[r].ny * (unsigned)s.reps[r].nz * (unsigned)s.reps[r].nchunks;
+    }
+    t.item_off[s.nrep] = off;
+    return t;
+}
+
+// Run f(RepTable<1 or MAX_BATCH>) for a single box or a batch.
+template <typename F>
+static cudaError_t by_batch_adj(const Sim &s, F &&f) {
+    if (s.nrep == 1) return f(adj_table<1>(s));
+    return f(adj_table<MAX_BATCH>(s));
+}
+
 cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const double *r,
                                  const double *v, long long step, const double *gv,
                                  const double *gr, double *lam_v, double *lam_r, double *acc,
@@ -548,10 +585,7 @@ cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const 
     A.lam = lam;
     A.P = s.P;
     A.N = s.N;
-    A.nx = s.reps[0].nx;
-    A.ny = s.reps[0].ny;
-    A.nz = s.reps[0].nz;
-    A.nchunks = s.reps[0].nchunks;
+    A.prep = s.prep;
     A.r = r;
     A.v = v;
     A.cap = s.cap;
@@ -577,42 +611,58 @@ cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const 
     A.fqd = reinterpret_cast<double *>(s.fq);
     A.ug = ug;
     const unsigned grid = (unsigned)((s.np + APB - 1) / APB);
-    cudaError_t e = by_storage_adj(s.precision, [&](auto tag) {
-        using St = decltype(tag);
-        k_adj_gather<St><<<grid, 8 * APB, 0, st>>>(A);
+    return by_batch_adj(s, [&](const auto &rt) {
+        constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
+        cudaError_t e = by_storage_adj(s.precision, [&](auto tag) {
+            using St = decltype(tag);
+            k_adj_gather<St, MAXR><<<grid, 8 * APB, 0, st>>>(A, rt);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        k_adj_fp64<MAXR><<<(unsigned)((s.np + 63) / 64), 64, 0, st>>>(A, rt);
         return cudaGetLastError();
     });
-    if (e != cudaSuccess) return e;
-    k_adj_fp64<<<(unsigned)((s.np + 63) / 64), 64, 0, st>>>(A);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_adj_lattice(Sim &s, const void *g, const float *lam, float *lam_out, int parity,
                                double *acc_omega, cudaStream_t st) {
-    const Rep &rp = s.reps[0];
-    const unsigned grid = (unsigned)rp.ny * (unsigned)rp.nz * (unsigned)rp.nchunks;
-    return by_storage_adj(s.precision, [&](auto tag) {
-        using St = decltype(tag);
-        k_adj_lattice<St><<<grid, SEG, 0, st>>>(
-            static_cast<const typename St::T *>(g), lam, lam_out, s.P, rp.nx, rp.ny, rp.nz, rp.nchunks,
-            rp.omega, s.rec[parity], s.rec[parity ^ 1], reinterpret_cast<double *>(s.fq), s.N, acc_omega);
-        return cudaGetLastError();
+    const unsigned grid = (unsigned)adj_lattice_blocks(s);
+    return by_batch_adj(s, [&](const auto &rt) {
+        constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
+        return by_storage_adj(s.precision, [&](auto tag) {
+            using St = decltype(tag);
+            k_adj_lattice<St, MAXR><<<grid, SEG, 0, st>>>(static_cast<const typename St::T *>(g), lam, lam_out,
+                                                          s.P, rt, s.rec[parity], s.rec[parity ^ 1],
+                                                          reinterpret_cast<double *>(s.fq), s.N, acc_omega);
+            return cudaGetLastError();
+        });
     });
 }
 
 int adj_lattice_blocks(const Sim &s) {
-    const Rep &rp = s.reps[0];
-    return rp.ny * rp.nz * rp.nchunks;
+    int n = 0;
+    for (int r = 0; r < s.nrep; ++r) n += s.reps[r].ny * s.reps[r].nz * s.reps[r].nchunks;
+    return n;
+}
+
+int adj_lattice_first_block(const Sim &s, int replica) {
+    int n = 0;
+    for (int r = 0; r < replica; ++r) n += s.reps[r].ny * s.reps[r].nz * s.reps[r].nchunks;
+    return n;
 }
 
 // dL/dfhat_a(y) of the first recorded state = dL/df_a(y + e_a) of its first
-// step (the buffer's layout), to the FP64 [15][N] ABI layout
-__global__ void k_adj_out(const float *src, double *dst, int nx, int ny, int nz, long long N, long long P) {
+// step (the buffer's layout), to the FP64 [15][N] ABI layout, every box periodic on its own
+template <int MAXR>
+__global__ void k_adj_out(const float *src, double *dst, const RepTable<MAXR> rt, long long N, long long P) {
     const long long total = (long long)Q * N;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int a = (int)(t / N);
-        const long long i = t - (long long)a * N;
+        const long long gi = t - (long long)a * N;
+        const Rep &rp = rt.rep[find_node_rep(rt, gi)];
+        const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
+        const long long i = gi - rp.node_off;
         const int x = (int)(i % nx);
         const long long yz = i / nx;
         const int y = (int)(yz % ny), z = (int)(yz / ny);
@@ -620,16 +670,18 @@ __global__ void k_adj_out(const float *src, double *dst, int nx, int ny, int nz,
         xs = xs == nx ? 0 : (xs < 0 ? nx - 1 : xs);
         ys = ys == ny ? 0 : (ys < 0 ? ny - 1 : ys);
         zs = zs == nz ? 0 : (zs < 0 ? nz - 1 : zs);
-        dst[t] = (double)src[(long long)a * P + ((long long)zs * ny + ys) * nx + xs];
+        dst[t] = (double)src[(long long)a * P + rp.node_off + ((long long)zs * ny + ys) * nx + xs];
     }
 }
 
 cudaError_t launch_f32_to_f64(Sim &s, const float *src, double *dst, cudaStream_t st) {
     long long g = ((long long)Q * s.N + 255) / 256;
     if (g > (long long)s.num_sms * 16) g = (long long)s.num_sms * 16;
-    k_adj_out<<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, s.reps[0].nx, s.reps[0].ny, s.reps[0].nz,
-                                                        s.N, s.P);
-    return cudaGetLastError();
+    return by_batch_adj(s, [&](const auto &rt) {
+        constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
+        k_adj_out<MAXR><<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, rt, s.N, s.P);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace lbp

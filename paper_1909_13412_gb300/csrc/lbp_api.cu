@@ -1144,7 +1144,6 @@ lbp_status lbp_adjoint_record(lbp_sim *s, int64_t nsteps, int checkpoint_every, 
     CHECK_SIM(s);
     if (nsteps < 1 || checkpoint_every < 1)
         return fail(LBP_EINVAL, "lbp_adjoint_record: need nsteps >= 1 and checkpoint_every >= 1");
-    if (s->nrep != 1) return fail(LBP_EINVAL, "lbp_adjoint_record: single-box handles only");
     if (s->np < 1) return fail(LBP_ESTATE, "lbp_adjoint_record: add particles first (the recorded outputs are their trajectories)");
     TRY(enter(s));
     CK(cudaStreamSynchronize(s->s0));
@@ -1383,14 +1382,20 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
                 if (accs[k]) CK(cudaMemcpyAsync(accs[k], acc + (size_t)k * np, sizeof(double) * np, kind, s->s0));
         }
         CK(cudaStreamSynchronize(s->s0));
-        // fixed-order host sums of the per-block and per-particle accumulators
-        double dom = 0.0, dkT = 0.0;
-        for (int b = 0; b < nblk; ++b) dom += h_om[b];
+        // fixed-order host sums of the per-block and per-particle accumulators;
+        // dL/dtau per box from the blocks of its row segments
+        std::vector<double> dtau(s->nrep);
+        for (int r = 0; r < s->nrep; ++r) {
+            const int b1 = r + 1 < s->nrep ? adj_lattice_first_block(*s, r + 1) : nblk;
+            double dom = 0.0;
+            for (int b = adj_lattice_first_block(*s, r); b < b1; ++b) dom += h_om[b];
+            const double omega = (double)s->reps[r].omega;
+            dtau[r] = -dom * omega * omega;  // omega = 1/tau
+        }
+        double dkT = 0.0;
         for (int i = 0; i < np; ++i) dkT += h_acc[3 * (size_t)np + i];
-        const double omega = (double)s->reps[0].omega;
-        const double dtau = -dom * omega * omega;  // omega = 1/tau
         const cudaMemcpyKind hk = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-        if (out->tau) CK(cudaMemcpy(out->tau, &dtau, sizeof(double), hk));
+        if (out->tau) CK(cudaMemcpy(out->tau, dtau.data(), sizeof(double) * s->nrep, hk));
         if (out->kT) CK(cudaMemcpy(out->kT, &dkT, sizeof(double), hk));
         return LBP_OK;
     };

@@ -391,6 +391,7 @@ cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const 
 cudaError_t launch_adj_lattice(Sim &s, const void *g, const float *lam, float *lam_out, int parity,
                                double *acc_omega, cudaStream_t st);
 int adj_lattice_blocks(const Sim &s);
+int adj_lattice_first_block(const Sim &s, int replica);  // first block of a box in the adjoint lattice launch
 cudaError_t launch_f32_to_f64(Sim &s, const float *src, double *dst, cudaStream_t st);
 // vacf_kernels.cu
 int vacf_block_samples();

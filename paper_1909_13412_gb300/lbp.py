@@ -383,13 +383,15 @@ def lbp_adjoint_record(h: Handle, nsteps, checkpoint_every, v_traj=None, r_traj=
 
 def lbp_adjoint_backward(h: Handle, nsteps, g_v=None, g_r=None, out=None):
     """Reverse sweep over the recording.  out: dict name -> writable array/tensor
-    for any of GRADIENT_NAMES (shapes: tau, kT [1]; gamma, radius, mass [n];
-    v0, r0 [n, 3]; f0 [15, N]), all on the same side as g_v / g_r."""
+    for any of GRADIENT_NAMES (shapes: tau [number of boxes]; kT [1]; gamma,
+    radius, mass [n]; v0, r0 [n, 3]; f0 [15, N]), all on the same side as
+    g_v / g_r."""
     n = h.np
     cnt = int(nsteps) * n * 3
     a = _ptr(g_v, np.float64, cnt, "g_v")
     b = _ptr(g_r, np.float64, cnt, "g_r")
-    sizes = {"tau": 1, "kT": 1, "gamma": n, "radius": n, "mass": n, "v0": 3 * n, "r0": 3 * n, "f0": Q * h.N}
+    sizes = {"tau": lbp_replica_count(h), "kT": 1, "gamma": n, "radius": n, "mass": n, "v0": 3 * n,
+             "r0": 3 * n, "f0": Q * h.N}
     g = lbp_gradients()
     ptrs = []
     for name, x in (out or {}).items():

@@ -300,3 +300,58 @@ def test_block_rows_validation():
     with pytest.raises(lbp.LbpError):
         lbp.lbp_set_block_rows(h, 3)
     lbp.lbp_destroy(h)
+
+
+def test_adjoint_of_a_batch_equals_its_boxes_alone():
+    """Reverse-mode gradients of a batch (lbp_adjoint_record / _backward on the
+    ensemble of uneven boxes, one of them without particles) equal, bit for
+    bit, those of every box recorded and run back alone: dL/dtau per box, the
+    particles' gamma, R, M, V0 and r0 gradients and dL/df0 on each box's
+    nodes; the particle-free box gets exactly zero (the loss does not depend on
+    it).  No noise, so that a particle's Philox counter (its index in the
+    handle) plays no part."""
+    steps, C = 30, 7
+    h = make_batch(lbp.LBP_F32, 0.0, True)
+    n = lbp.lbp_particles_count(h)
+    rng = np.random.default_rng(3)
+    gv = rng.normal(0.0, 1.0, (steps, n, 3))
+    gr = rng.normal(0.0, 1.0, (steps, n, 3))
+    vt = np.empty((steps, n, 3))
+    lbp.lbp_adjoint_record(h, steps, C, v_traj=vt)
+
+    def grads(nb, N):
+        return {"tau": None, "gamma": np.zeros(nb), "radius": np.zeros(nb), "mass": np.zeros(nb),
+                "v0": np.zeros((nb, 3)), "r0": np.zeros((nb, 3)), "f0": np.zeros((Q, N))}
+    out = grads(n, h.N)
+    out["tau"] = np.zeros(len(BOXES))
+    lbp.lbp_adjoint_backward(h, steps, gv, gr, out)
+    lbp.lbp_destroy(h)
+    p0 = node0 = 0
+    for b, box in enumerate(BOXES):
+        nx, ny, nz, tau = box
+        Nb = nx * ny * nz
+        nb = NPART[b]
+        fb = out["f0"][:, node0:node0 + Nb]
+        if nb == 0:
+            assert out["tau"][b] == 0.0 and not np.any(fb)
+        else:
+            f, ps = box_state(b, box)
+            hb = lbp.lbp_create(nx, ny, nz, tau)
+            lbp.lbp_set_populations(hb, f)
+            lbp.lbp_particles_add(hb, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+            lbp.lbp_particles_set_params(hb, kT=0.0, seed=5)
+            vb = np.empty((steps, nb, 3))
+            lbp.lbp_adjoint_record(hb, steps, C, v_traj=vb)
+            ob = grads(nb, Nb)
+            ob["tau"] = np.zeros(1)
+            lbp.lbp_adjoint_backward(hb, steps, np.ascontiguousarray(gv[:, p0:p0 + nb]),
+                                     np.ascontiguousarray(gr[:, p0:p0 + nb]), ob)
+            lbp.lbp_destroy(hb)
+            assert np.array_equal(vb, vt[:, p0:p0 + nb]), b
+            assert ob["tau"][0] == out["tau"][b], b
+            for k in ("gamma", "radius", "mass", "v0", "r0"):
+                assert np.array_equal(ob[k], out[k][p0:p0 + nb]), (b, k)
+            assert np.array_equal(ob["f0"], fb), b
+            assert ob["tau"][0] != 0.0
+        p0 += nb
+        node0 += Nb
