@@ -86,3 +86,17 @@ def test_create_batch_rejects_mixed_storage(lib):
     st = lib.lbp_create_batch(C.cast(descs, C.c_void_p), 2, C.c_void_p(0), C.byref(out))
     assert st == lbp.LBP_EINVAL and not out.value
     assert "precision" in lbp.lbp_last_error()
+
+
+def test_autotune_candidate_tables_agree():
+    """The header's candidate count, the binding's (variant, rows) table and the
+    bench's shape names describe the same ten kernel shapes."""
+    text = open(os.path.join(ROOT, "include", "lbp.h")).read()
+    m = re.search(r"#define\s+LBP_AUTOTUNE_CANDIDATES\s+(\d+)", text)
+    assert m and int(m.group(1)) == len(lbp.AUTOTUNE_SHAPES)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_shapes", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert len(bench.SHAPE_NAMES) == len(set(bench.SHAPE_NAMES)) == len(lbp.AUTOTUNE_SHAPES)
+    assert bench.SHAPES["4nodes_1row"] == (3, 1) and bench.SHAPES["bulk_staged"] == (2, 1)
