@@ -131,222 +131,219 @@ __global__ void __launch_bounds__(256) k_adj_gather(const AdjPArgs A, const RepT
     }
 }
 
-// The FP64 adjoint of one particle's step, one particle per thread in small
-// blocks (so that many warps per SM share the FP64 pipe), then its lam_u(x_p)
-// appended to the records of the corners' row segments.
+// Sum over the eight lanes of a particle (an aligned group of 8 lanes): every
+// lane gets the same value (the butterfly adds the same pairs in every lane).
+__device__ __forceinline__ double grp8_sum(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
+// The FP64 adjoint of one particle's step with eight lanes per particle, one
+// per corner of its cell: the per-corner terms of the fit (its forward
+// re-evaluation and its adjoint) and of the spreading run in parallel and meet
+// in group sums, which cuts the serial FP64 chain of a particle about
+// fourfold; the per-particle scalars (the Langevin update, the random force)
+// are evaluated in every lane of the group.  Blocks of 64 threads (8
+// particles), so that many warps share the narrow FP64 pipe.  Each lane
+// appends its corner's lam_u(x_p) to the record of that corner's row segment.
 template <int MAXR>
 __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTable<MAXR> rt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = (tid >> 3) < A.np;
+    const int i = valid ? tid >> 3 : A.np - 1;  // lanes past the last particle shadow it (no stores)
+    const int c = tid & 7;                      // the lane's corner: offsets (c & 1, c >> 1 & 1, c >> 2)
     const int cap = A.cap;
-    if (i < A.np) {
-        double r[3], V[3], q[3], lV[3], lr[3], fe[3];
-        int base[3];
+    double r[3], V[3], q[3], lV[3], lr[3], fe[3];
+    int base[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r[k] = A.r[k * cap + i];
+        V[k] = A.v[k * cap + i];
+        base[k] = (int)floor(r[k]);
+        q[k] = r[k] - (double)base[k];
+        fe[k] = A.fext[k * cap + i];
+        lV[k] = A.lam_v[k * cap + i] + (A.gv ? A.gv[3 * i + k] : 0.0);
+        lr[k] = A.lam_r[k * cap + i] + (A.gr ? A.gr[3 * i + k] : 0.0);
+    }
+    const double gam = A.gamma[i], R = A.radius[i], invM = A.inv_mass[i], sg = A.sig[i];
+    const bool pin = A.pinned[i] != 0;
+    // this corner's gathered u(x_p) and lam_F(x_p), and its trilinear weight
+    double u[3], lF[3], Wp = 1.0;
+    {
+        const float *g = A.ug + ((size_t)i * 8 + c) * 6;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            r[k] = A.r[k * cap + i];
-            V[k] = A.v[k * cap + i];
-            base[k] = (int)floor(r[k]);
-            q[k] = r[k] - (double)base[k];
-            fe[k] = A.fext[k * cap + i];
-            lV[k] = A.lam_v[k * cap + i] + (A.gv ? A.gv[3 * i + k] : 0.0);
-            lr[k] = A.lam_r[k * cap + i] + (A.gr ? A.gr[3 * i + k] : 0.0);
+            u[k] = (double)g[k];
+            lF[k] = (double)g[3 + k];
+            Wp *= ((c >> k) & 1) ? q[k] : 1.0 - q[k];
         }
-        const double gam = A.gamma[i], R = A.radius[i], invM = A.inv_mass[i], sg = A.sig[i];
-        const bool pin = A.pinned[i] != 0;
-        double u[8][3], lF[8][3], Wp[8];
+    }
+    double d[3];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            double w = 1.0;
-            const float *g = A.ug + ((size_t)i * 8 + c) * 6;
+    for (int k = 0; k < 3; ++k) d[k] = (double)((c >> k) & 1) - q[k];
+    // forward re-evaluation of F_H
+    double FH[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
+    double U = 0.0, num = 0.0, den = 0.0, nw = 0.0;
+    double ur[3] = {0.0, 0.0, 0.0};
+    bool fit = false;
+    // this corner's fit geometry (used by the forward and the adjoint fit)
+    bool use = false;
+    double rp = 0.0, ir = 0.0, ir3 = 0.0, x = 0.0, k1 = 0.0, k2 = 0.0, av[3] = {0.0, 0.0, 0.0};
+    const double cR = 0.75 * R;
+    if (A.mode == LBP_STOKESLET) {
+        double m[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) m[k] = grp8_sum(u[k] - V[k]) * 0.125;
+        nw = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        if (nw > 0.0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) e[k] = m[k] / nw;
+        }
+        rp = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        use = nw > 0.0 && !(rp < 1e-12 || (A.exclude_inside && rp < R));
+        double pn = 0.0, pd = 0.0;
+        if (use) {
+            ir = 1.0 / rp;
+            ir3 = ir * ir * ir;
+            x = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
+            k1 = 1.0 - cR * ir;
+            k2 = cR * x * ir3;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                u[c][k] = (double)g[k];
-                lF[c][k] = (double)g[3 + k];
-                w *= ((c >> k) & 1) ? q[k] : 1.0 - q[k];
+                av[k] = k1 * e[k] - k2 * d[k];
+                pn += (u[k] - V[k]) * av[k];
+                pd += av[k] * av[k];
             }
-            Wp[c] = w;
         }
-        // forward re-evaluation of F_H
-        double FH[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
-        double U = 0.0, num = 0.0, den = 0.0, nw = 0.0;
-        double ur[3] = {0.0, 0.0, 0.0};
-        bool fit = false;
-        if (A.mode == LBP_STOKESLET) {
-            double m[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) m[k] += u[c][k] - V[k];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) m[k] *= 0.125;
-            nw = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-            if (nw > 0.0) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) e[k] = m[k] / nw;
-                const double cR = 0.75 * R;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    double d[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) d[k] = (double)((c >> k) & 1) - q[k];
-                    const double rp = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                    if (rp < 1e-12 || (A.exclude_inside && rp < R)) continue;
-                    const double ir = 1.0 / rp, ir3 = ir * ir * ir;
-                    const double x = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
-                    const double k1 = 1.0 - cR * ir, k2 = cR * x * ir3;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const double a = k1 * e[k] - k2 * d[k];
-                        num += (u[c][k] - V[k]) * a;
-                        den += a * a;
-                    }
-                }
-                if (den != 0.0) {
-                    U = num / den;
-                    fit = true;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) FH[k] = gam * U * e[k];
-        } else if (A.mode == LBP_POINTWISE) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) ur[k] += Wp[c] * u[c][k];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) FH[k] = -gam * (V[k] - ur[k]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) FH[k] = -gam * V[k];
+        num = grp8_sum(pn);
+        den = grp8_sum(pd);
+        if (nw > 0.0 && den != 0.0) {
+            U = num / den;
+            fit = true;
         }
-        // the random force of this step (same Philox numbers as the forward step)
-        unsigned long long ctr[4] = {(unsigned long long)A.step, (unsigned long long)i, 0ull, 0ull};
-        philox4x64_10(ctr, A.seed, 0ull);
-        double xi[3], FR[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) FH[k] = gam * U * e[k];
+    } else if (A.mode == LBP_POINTWISE) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double tt = __fma_rn(__ull2double_rn(2ull * (ctr[k] >> 11) + 1ull), 0x1.0p-53, -1.0);
-            xi[k] = __dmul_rn(A.sqrt3, tt);
-            FR[k] = __dmul_rn(sg, xi[k]);
+            ur[k] = grp8_sum(Wp * u[k]);
+            FH[k] = -gam * (V[k] - ur[k]);
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) FH[k] = -gam * V[k];
+    }
+    // the random force of this step (same Philox numbers as the forward step)
+    unsigned long long ctr[4] = {(unsigned long long)A.step, (unsigned long long)i, 0ull, 0ull};
+    philox4x64_10(ctr, A.seed, 0ull);
+    double xi[3], FR[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double tt = __fma_rn(__ull2double_rn(2ull * (ctr[k] >> 11) + 1ull), 0x1.0p-53, -1.0);
+        xi[k] = __dmul_rn(A.sqrt3, tt);
+        FR[k] = __dmul_rn(sg, xi[k]);
+    }
 
-        // ---- backward
-        double lFH[3] = {0.0, 0.0, 0.0}, lq[3] = {0.0, 0.0, 0.0};
-        double gG = 0.0, gR = 0.0, gM = 0.0, gK = 0.0;
-        if (!pin) {
-            // r' = r + V'  then  V' = V + (F_H + F_R + F_ext)/M
-            double lFR_xi = 0.0, lF_tot = 0.0;
+    // ---- backward
+    double lFH[3] = {0.0, 0.0, 0.0}, lq[3] = {0.0, 0.0, 0.0};
+    double gG = 0.0, gR = 0.0, gM = 0.0, gK = 0.0;
+    if (!pin) {
+        // r' = r + V'  then  V' = V + (F_H + F_R + F_ext)/M
+        double lFR_xi = 0.0, lF_tot = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lV[k] += lr[k];
+            lFH[k] = lV[k] * invM;
+            lFR_xi += lV[k] * invM * xi[k];
+            lF_tot += lV[k] * (FH[k] + FR[k] + fe[k]);
+        }
+        gM = -lF_tot * invM * invM;
+        // F_R = sigma xi, sigma = sqrt(2 gamma kT)
+        if (sg > 0.0) {
+            gG += lFR_xi * (A.kT / sg);
+            gK += lFR_xi * (gam / sg);
+        }
+    }
+    const bool spread = A.mode != LBP_BROWNIAN;
+    // dW_p/dq_k of this corner
+    double dw[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dw[k] = ((c >> k) & 1) ? 1.0 : -1.0;
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2)
+            if (j2 != k) dw[k] *= ((c >> j2) & 1) ? q[j2] : 1.0 - q[j2];
+    }
+    if (spread) {
+        // F(x_p) += -F_H W_p(q)
+        const double fl = FH[0] * lF[0] + FH[1] * lF[1] + FH[2] * lF[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lFH[k] -= grp8_sum(Wp * lF[k]);
+            lq[k] -= grp8_sum(fl * dw[k]);
+        }
+    }
+    double lu[3] = {0.0, 0.0, 0.0};  // this corner's lam_u(x_p)
+    if (A.mode == LBP_STOKESLET) {
+        // the adjoint of the fit, with zero terms where there was none
+        const double eF = e[0] * lFH[0] + e[1] * lFH[1] + e[2] * lFH[2];
+        const double lU = fit ? gam * eF : 0.0;
+        if (fit) gG += U * eF;
+        double le[3] = {gam * U * lFH[0], gam * U * lFH[1], gam * U * lFH[2]};
+        const double lnum = fit ? lU / den : 0.0, lden = fit ? -lU * num / (den * den) : 0.0;
+        double ple[3] = {0.0, 0.0, 0.0}, pq[3] = {0.0, 0.0, 0.0}, plc = 0.0;
+        if (use && fit) {
+            const double ir5 = ir3 * ir * ir;
+            double la[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                lV[k] += lr[k];
-                lFH[k] = lV[k] * invM;
-                lFR_xi += lV[k] * invM * xi[k];
-                lF_tot += lV[k] * (FH[k] + FR[k] + fe[k]);
+                lu[k] += lnum * av[k];
+                la[k] = lnum * (u[k] - V[k]) + 2.0 * lden * av[k];
             }
-            gM = -lF_tot * invM * invM;
-            // F_R = sigma xi, sigma = sqrt(2 gamma kT)
-            if (sg > 0.0) {
-                gG += lFR_xi * (A.kT / sg);
-                gK += lFR_xi * (gam / sg);
+            const double dla = d[0] * la[0] + d[1] * la[1] + d[2] * la[2];
+            const double lk1 = e[0] * la[0] + e[1] * la[1] + e[2] * la[2];
+            const double lk2 = -dla;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ple[k] = k1 * la[k] - cR * ir3 * d[k] * dla;
+                pq[k] = -k2 * la[k] + lk1 * cR * ir3 * d[k] + lk2 * cR * (ir3 * e[k] - 3.0 * x * ir5 * d[k]);
             }
+            plc = -lk1 * ir + lk2 * x * ir3;
         }
-        const bool spread = A.mode != LBP_BROWNIAN;
-        if (spread) {
-            // F(x_p) += -F_H W_p(q)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const double fl = FH[0] * lF[c][0] + FH[1] * lF[c][1] + FH[2] * lF[c][2];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    lFH[k] -= Wp[c] * lF[c][k];
-                    // dW_p/dq_k
-                    double dw = ((c >> k) & 1) ? 1.0 : -1.0;
-#pragma unroll
-                    for (int j2 = 0; j2 < 3; ++j2)
-                        if (j2 != k) dw *= ((c >> j2) & 1) ? q[j2] : 1.0 - q[j2];
-                    lq[k] -= fl * dw;
-                }
-            }
+        for (int k = 0; k < 3; ++k) {
+            le[k] += grp8_sum(ple[k]);
+            lq[k] -= grp8_sum(pq[k]);
         }
-        double lu[8][3];
+        const double lc = grp8_sum(plc);
+        if (fit) {
+            gR += 0.75 * lc;
+            // e = m/|m| with m the mean of the w_p
+            const double ee = e[0] * le[0] + e[1] * le[1] + e[2] * le[2];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) lu[c][0] = lu[c][1] = lu[c][2] = 0.0;
-        if (A.mode == LBP_STOKESLET) {
-            if (fit) {
-                const double eF = e[0] * lFH[0] + e[1] * lFH[1] + e[2] * lFH[2];
-                gG += U * eF;
-                const double lU = gam * eF;
-                double le[3] = {gam * U * lFH[0], gam * U * lFH[1], gam * U * lFH[2]};
-                const double lnum = lU / den, lden = -lU * num / (den * den);
-                const double cR = 0.75 * R;
-                double lc = 0.0;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    double d[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) d[k] = (double)((c >> k) & 1) - q[k];
-                    const double rp = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                    if (rp < 1e-12 || (A.exclude_inside && rp < R)) continue;
-                    const double ir = 1.0 / rp, ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
-                    const double x = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
-                    const double k1 = 1.0 - cR * ir, k2 = cR * x * ir3;
-                    double a[3], la[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        a[k] = k1 * e[k] - k2 * d[k];
-                        lu[c][k] += lnum * a[k];
-                        la[k] = lnum * (u[c][k] - V[k]) + 2.0 * lden * a[k];
-                    }
-                    const double dla = d[0] * la[0] + d[1] * la[1] + d[2] * la[2];
-                    const double lk1 = e[0] * la[0] + e[1] * la[1] + e[2] * la[2];
-                    const double lk2 = -dla;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        le[k] += k1 * la[k] - cR * ir3 * d[k] * dla;
-                        const double ld = -k2 * la[k] + lk1 * cR * ir3 * d[k] +
-                                          lk2 * cR * (ir3 * e[k] - 3.0 * x * ir5 * d[k]);
-                        lq[k] -= ld;
-                    }
-                    lc += -lk1 * ir + lk2 * x * ir3;
-                }
-                gR += 0.75 * lc;
-                // e = m/|m| with m the mean of the w_p
-                const double ee = e[0] * le[0] + e[1] * le[1] + e[2] * le[2];
-                double lm[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) lm[k] = (le[k] - e[k] * ee) / nw * 0.125;
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) lu[c][k] += lm[k];
-                // w_p = u_p - V
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) lV[k] -= lu[c][k];
-            }
-        } else if (A.mode == LBP_POINTWISE) {
-            gG += -((V[0] - ur[0]) * lFH[0] + (V[1] - ur[1]) * lFH[1] + (V[2] - ur[2]) * lFH[2]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) lV[k] -= gam * lFH[k];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const double ul = u[c][0] * lFH[0] + u[c][1] * lFH[1] + u[c][2] * lFH[2];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    lu[c][k] = gam * Wp[c] * lFH[k];
-                    double dw = ((c >> k) & 1) ? 1.0 : -1.0;
-#pragma unroll
-                    for (int j2 = 0; j2 < 3; ++j2)
-                        if (j2 != k) dw *= ((c >> j2) & 1) ? q[j2] : 1.0 - q[j2];
-                    lq[k] += gam * ul * dw;
-                }
-            }
-        } else {
-            gG += -(V[0] * lFH[0] + V[1] * lFH[1] + V[2] * lFH[2]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) lV[k] -= gam * lFH[k];
+            for (int k = 0; k < 3; ++k) lu[k] += (le[k] - e[k] * ee) / nw * 0.125;
         }
+        // w_p = u_p - V
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lV[k] -= grp8_sum(lu[k]);
+    } else if (A.mode == LBP_POINTWISE) {
+        gG += -((V[0] - ur[0]) * lFH[0] + (V[1] - ur[1]) * lFH[1] + (V[2] - ur[2]) * lFH[2]);
+        const double ul = u[0] * lFH[0] + u[1] * lFH[1] + u[2] * lFH[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lV[k] -= gam * lFH[k];
+            lu[k] = gam * Wp * lFH[k];
+            lq[k] += grp8_sum(gam * ul * dw[k]);
+        }
+    } else {
+        gG += -(V[0] * lFH[0] + V[1] * lFH[1] + V[2] * lFH[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lV[k] -= gam * lFH[k];
+    }
+    if (!valid) return;  // past the shuffles: shadow lanes leave
+    if (c == 0) {
         // q = r - floor(r)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -358,32 +355,27 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
         A.acc[A.np + i] += gR;
         A.acc[2 * A.np + i] += gM;
         A.acc[3 * A.np + i] += gK;
-        // lam_u(x_p) to the record of each corner's row segment
-        if (spread) {
-            const Rep &ri = rt.rep[MAXR == 1 ? 0 : A.prep[i]];
-            const int nx = ri.nx, ny = ri.ny, nz = ri.nz;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const double l0 = lu[c][0], l1 = lu[c][1], l2 = lu[c][2];
-                if (l0 == 0.0 && l1 == 0.0 && l2 == 0.0) continue;
-                const int X = wrap_i(base[0] + (c & 1), nx);
-                const int Y = wrap_i(base[1] + ((c >> 1) & 1), ny);
-                const int Z = wrap_i(base[2] + ((c >> 2) & 1), nz);
-                const long long row = (long long)Z * ny + Y;
-                unsigned long long *rec = A.rec + (size_t)(ri.seg_off + row * ri.nchunks + X / SEG) * REC_WORDS;
-                const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
-                if (slot < (unsigned)REC_SLOTS) {
-                    reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
-                    rec[REC_F0 + 3 * slot] = (unsigned long long)__double_as_longlong(l0);
-                    rec[REC_F0 + 3 * slot + 1] = (unsigned long long)__double_as_longlong(l1);
-                    rec[REC_F0 + 3 * slot + 2] = (unsigned long long)__double_as_longlong(l2);
-                } else {
-                    const long long node = ri.node_off + row * nx + X;
-                    atomicAdd(A.fqd + node, l0);
-                    atomicAdd(A.fqd + A.N + node, l1);
-                    atomicAdd(A.fqd + 2 * A.N + node, l2);
-                }
-            }
+    }
+    // lam_u(x_p) of this corner to the record of its row segment
+    if (spread && !(lu[0] == 0.0 && lu[1] == 0.0 && lu[2] == 0.0)) {
+        const Rep &ri = rt.rep[MAXR == 1 ? 0 : A.prep[i]];
+        const int nx = ri.nx, ny = ri.ny, nz = ri.nz;
+        const int X = wrap_i(base[0] + (c & 1), nx);
+        const int Y = wrap_i(base[1] + ((c >> 1) & 1), ny);
+        const int Z = wrap_i(base[2] + ((c >> 2) & 1), nz);
+        const long long row = (long long)Z * ny + Y;
+        unsigned long long *rec = A.rec + (size_t)(ri.seg_off + row * ri.nchunks + X / SEG) * REC_WORDS;
+        const unsigned int slot = atomicAdd(reinterpret_cast<unsigned int *>(rec), 1u);
+        if (slot < (unsigned)REC_SLOTS) {
+            reinterpret_cast<int *>(rec + REC_X0)[slot] = X;
+            rec[REC_F0 + 3 * slot] = (unsigned long long)__double_as_longlong(lu[0]);
+            rec[REC_F0 + 3 * slot + 1] = (unsigned long long)__double_as_longlong(lu[1]);
+            rec[REC_F0 + 3 * slot + 2] = (unsigned long long)__double_as_longlong(lu[2]);
+        } else {
+            const long long node = ri.node_off + row * nx + X;
+            atomicAdd(A.fqd + node, lu[0]);
+            atomicAdd(A.fqd + A.N + node, lu[1]);
+            atomicAdd(A.fqd + 2 * A.N + node, lu[2]);
         }
     }
 }
@@ -619,7 +611,7 @@ cudaError_t launch_adj_particles(Sim &s, const void *g, const float *lam, const 
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
-        k_adj_fp64<MAXR><<<(unsigned)((s.np + 63) / 64), 64, 0, st>>>(A, rt);
+        k_adj_fp64<MAXR><<<(unsigned)((8 * s.np + 63) / 64), 64, 0, st>>>(A, rt);
         return cudaGetLastError();
     });
 }
