@@ -24,7 +24,7 @@
  *     7. BGK collision with body force (Eqs. 14, 15, 17, 18, 19)
  *   The state kept between steps is the post-collision fhat.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   D3Q15 table: e_0 = 0 (w 2/9), 6 faces (w 1/9), 8 corners (w 1/72).
  *   u is not divided by rho~ and rho~ multiplies only the leading term of
  *   f^eq (Eqs. 13, 17 literally).  The force term is plain 3 w_a F.e_a.
