@@ -6,7 +6,7 @@
 // adds, for the B new samples t and every lag k <= K, the products
 // V(t).V(t - k): a dense contraction over the 3 n_p velocity components.
 //
-// k_vacf_mma  : CTA = 128 lags x 1024 components: the products of the 64 new
+// k_vacf_mma  : CTA = 128 lags x 256 components: the products of the 64 new
 //               samples with the 191 window samples as a matrix product on the
 //               tensor cores (TF32 in three terms, FP32 accuracy), the lag sums
 //               of its band in FP64 into one partial per (chunk, k).
@@ -20,7 +20,7 @@ namespace lbp {
 
 constexpr int VB = 64;        // samples per correlation block
 constexpr int VKT = 128;      // lags per CTA
-constexpr int VJCH = 1024;    // components per CTA
+constexpr int VJCH = 256;     // components per CTA (short CTAs interleave with the lattice pass)
 constexpr int VWIN = VB + VKT - 1;
 
 int vacf_block_samples() { return VB; }
@@ -49,10 +49,10 @@ __device__ __forceinline__ bool vacf_range(const VacfArgs &A, long long &tb, lon
 }
 
 // ---------------------------------------------------------------------------
-// k_vacf_mma: the same block correlation on the tensor cores.  For the CTA's
-// 128 lags and 1024 components the products of the B = 64 new samples t with
+// k_vacf_mma: the block correlation on the tensor cores.  For the CTA's 128
+// lags and 256 components the products of the B = 64 new samples t with
 // the 191 window samples s form a matrix product
-//     P[t][s] = sum_j V_j(t) V_j(s)       (64 x 192, inner dimension 1024),
+//     P[t][s] = sum_j V_j(t) V_j(s)       (64 x 192, inner dimension 256),
 // and lag k0 + kk collects the band s = t + 127 - kk:  C(k) = sum_t P[t][.].
 // The product runs as mma.sync m16n8k8 with TF32 operands in three terms,
 // a.b = a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = a rounded to TF32, a_lo =
