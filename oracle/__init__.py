@@ -45,42 +45,47 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def bind(path: str):
+    """ctypes handle of a compiled oracle library at `path`, with every signature set."""
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.or_d3q15.argtypes = [_i32p, _dp]
+    L.or_stream.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int]
+    L.or_moments.argtypes = [_dp, _dp, _dp, C.c_int64]
+    L.or_feq.argtypes = [C.c_double, _dp, _dp]
+    L.or_collide.argtypes = [_dp, _dp, _dp, vp, C.c_double, C.c_int64, _dp]
+    L.or_set_body_force.argtypes = [vp, _dp]
+    L.or_corners.argtypes = [_dp, _i32p, _dp, _dp]
+    L.or_stokeslet_fit.argtypes = [_dp, _dp, _dp, C.c_double, C.c_int, _dp]
+    L.or_stokeslet_fit.restype = C.c_double
+    L.or_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
+    L.or_noise_xi.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, _dp]
+    L.or_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double]
+    L.or_create.restype = vp
+    L.or_destroy.argtypes = [vp]
+    L.or_set_fhat.argtypes = [vp, _dp]
+    L.or_get_fhat.argtypes = [vp, _dp]
+    L.or_set_step.argtypes = [vp, C.c_int64]
+    L.or_get_step.argtypes = [vp]
+    L.or_get_step.restype = C.c_int64
+    L.or_get_fields.argtypes = [vp, _dp, _dp, vp]
+    L.or_add_particles.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.or_set_params.argtypes = [vp, C.c_double, C.c_uint64, C.c_int, C.c_int]
+    L.or_set_external.argtypes = [vp, vp, vp]
+    L.or_set_particles.argtypes = [vp, vp, vp]
+    L.or_get_particles.argtypes = [vp, vp, vp, vp, vp]
+    L.or_step.argtypes = [vp, C.c_int64]
+    L.or_spread_only.argtypes = [vp, _dp]
+    L.or_vacf.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _i64p]
+    L.or_num_threads.restype = C.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        vp = C.c_void_p
-        L.or_d3q15.argtypes = [_i32p, _dp]
-        L.or_stream.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int]
-        L.or_moments.argtypes = [_dp, _dp, _dp, C.c_int64]
-        L.or_feq.argtypes = [C.c_double, _dp, _dp]
-        L.or_collide.argtypes = [_dp, _dp, _dp, vp, C.c_double, C.c_int64, _dp]
-        L.or_set_body_force.argtypes = [vp, _dp]
-        L.or_corners.argtypes = [_dp, _i32p, _dp, _dp]
-        L.or_stokeslet_fit.argtypes = [_dp, _dp, _dp, C.c_double, C.c_int, _dp]
-        L.or_stokeslet_fit.restype = C.c_double
-        L.or_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
-        L.or_noise_xi.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, _dp]
-        L.or_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double]
-        L.or_create.restype = vp
-        L.or_destroy.argtypes = [vp]
-        L.or_set_fhat.argtypes = [vp, _dp]
-        L.or_get_fhat.argtypes = [vp, _dp]
-        L.or_set_step.argtypes = [vp, C.c_int64]
-        L.or_get_step.argtypes = [vp]
-        L.or_get_step.restype = C.c_int64
-        L.or_get_fields.argtypes = [vp, _dp, _dp, vp]
-        L.or_add_particles.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, _dp]
-        L.or_set_params.argtypes = [vp, C.c_double, C.c_uint64, C.c_int, C.c_int]
-        L.or_set_external.argtypes = [vp, vp, vp]
-        L.or_set_particles.argtypes = [vp, vp, vp]
-        L.or_get_particles.argtypes = [vp, vp, vp, vp, vp]
-        L.or_step.argtypes = [vp, C.c_int64]
-        L.or_spread_only.argtypes = [vp, _dp]
-        L.or_vacf.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _i64p]
-        L.or_num_threads.restype = C.c_int
-        _lib = L
+        _lib = bind(_LIB)
     return _lib
 
 
@@ -190,16 +195,19 @@ def num_threads():
 class Sim:
     """Periodic LBM box with Langevin particles; one ``step`` = one time step."""
 
-    def __init__(self, nx, ny, nz, tau):
+    def __init__(self, nx, ny, nz, tau, library=None):
+        """``library``: another compiled copy of the oracle (``bind``), used by the
+        tests that check that a pin fails when a mistake is planted in a copy."""
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.tau = tau
         self.np = 0
-        self._h = lib().or_create(nx, ny, nz, float(tau))
+        self._L = library if library is not None else lib()
+        self._h = self._L.or_create(nx, ny, nz, float(tau))
 
     def close(self):
         if self._h:
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -209,63 +217,63 @@ class Sim:
             pass
 
     def set_fhat(self, fhat):
-        lib().or_set_fhat(self._h, _c(fhat).reshape(-1))
+        self._L.or_set_fhat(self._h, _c(fhat).reshape(-1))
 
     def fhat(self):
         out = np.empty((Q,) + self.shape)
-        lib().or_get_fhat(self._h, out.reshape(-1))
+        self._L.or_get_fhat(self._h, out.reshape(-1))
         return out
 
     def set_step(self, n):
-        lib().or_set_step(self._h, int(n))
+        self._L.or_set_step(self._h, int(n))
 
     @property
     def step_index(self):
-        return lib().or_get_step(self._h)
+        return self._L.or_get_step(self._h)
 
     def fields(self):
         rho = np.empty(self.N)
         u = np.empty(3 * self.N)
         p = np.empty(self.N)
-        lib().or_get_fields(self._h, rho, u, _ptr(p))
+        self._L.or_get_fields(self._h, rho, u, _ptr(p))
         return rho.reshape(self.shape), u.reshape((3,) + self.shape), p.reshape(self.shape)
 
     def add_particles(self, r, V, M, gamma, R):
         r, V = _c(r).reshape(-1, 3), _c(V).reshape(-1, 3)
         n = r.shape[0]
         M, gamma, R = (_c(np.broadcast_to(x, (n,))) for x in (M, gamma, R))
-        lib().or_add_particles(self._h, n, r.reshape(-1), V.reshape(-1), M, gamma, R)
+        self._L.or_add_particles(self._h, n, r.reshape(-1), V.reshape(-1), M, gamma, R)
         self.np += n
 
     def set_params(self, kT=0.0, seed=0, mode=STOKESLET, exclude_inside=False):
-        lib().or_set_params(self._h, float(kT), int(seed), int(mode), int(exclude_inside))
+        self._L.or_set_params(self._h, float(kT), int(seed), int(mode), int(exclude_inside))
 
     def set_external(self, Fext=None, pinned=None):
         F = None if Fext is None else _c(Fext).reshape(-1)
         P = None if pinned is None else _c(pinned, np.uint8)
-        lib().or_set_external(self._h, _ptr(F), _ptr(P))
+        self._L.or_set_external(self._h, _ptr(F), _ptr(P))
 
     def set_body_force(self, G):
         """Uniform external force density on every node (the F of Eq. 18)."""
-        lib().or_set_body_force(self._h, _c(G).reshape(3))
+        self._L.or_set_body_force(self._h, _c(G).reshape(3))
 
     def set_particles(self, r=None, V=None):
         rr = None if r is None else _c(r).reshape(-1)
         vv = None if V is None else _c(V).reshape(-1)
-        lib().or_set_particles(self._h, _ptr(rr), _ptr(vv))
+        self._L.or_set_particles(self._h, _ptr(rr), _ptr(vv))
 
     def particles(self):
         r = np.empty((self.np, 3))
         V = np.empty((self.np, 3))
         FH = np.empty((self.np, 3))
         FR = np.empty((self.np, 3))
-        lib().or_get_particles(self._h, _ptr(r), _ptr(V), _ptr(FH), _ptr(FR))
+        self._L.or_get_particles(self._h, _ptr(r), _ptr(V), _ptr(FH), _ptr(FR))
         return r, V, FH, FR
 
     def step(self, n=1):
-        lib().or_step(self._h, int(n))
+        self._L.or_step(self._h, int(n))
 
     def spread_only(self):
         F = np.empty(3 * self.N)
-        lib().or_spread_only(self._h, F)
+        self._L.or_spread_only(self._h, F)
         return F.reshape((3,) + self.shape)

@@ -461,3 +461,67 @@ def test_uniform_body_force_adds_its_momentum_every_step():
     assert np.allclose(mom, n * G[:, None, None, None], rtol=0, atol=1e-15)
     assert np.allclose(f.sum(0), 1.0, rtol=0, atol=1e-14)
     o.close()
+
+
+# ------------------------------------------------------------ point-wise friction (Eq. 7)
+def _linear_flow_populations(L, u0, A):
+    """Post-collision populations whose streamed (pulled) values at every node x
+    away from the periodic seam are f^eq(1, u0 + A x) (Eq. 17): fhat_a(y) =
+    f^eq_a(1, u0 + A (y + e_a)), so that f_a(x) = fhat_a(x - e_a)."""
+    f = np.empty((15, L, L, L))
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                for a in range(15):
+                    src = np.array([x, y, z], float) + E[a]
+                    f[a, z, y, x] = oracle.feq(1.0, u0 + A @ src)[a]
+    return f
+
+
+def _pointwise_first_step_force(library, r, V, gamma, u0, A, L=10):
+    s = oracle.Sim(L, L, L, 0.8, library=library)
+    s.set_fhat(_linear_flow_populations(L, u0, A))
+    s.add_particles([r], [V], [10.0], [gamma], [0.3])
+    s.set_params(mode=oracle.POINTWISE)
+    s.step(1)
+    FH = s.particles()[2][0]
+    s.close()
+    return FH
+
+
+_U0 = np.array([2e-3, -1e-3, 5e-4])
+_A = np.array([[3e-4, -2e-4, 1e-4], [1.5e-4, 2.5e-4, -3e-4], [-1e-4, 2e-4, 4e-4]])
+
+
+@pytest.mark.parametrize("r", [[4.3, 5.6, 3.7], [4.0, 5.0, 3.0], [4.9, 5.05, 3.45]])
+def test_pointwise_friction_uses_the_fluid_velocity_at_the_particle(r):
+    """Eq. 7, F_H = -gamma (V - u(r_i)), with u(r_i) interpolated from the eight
+    corners: in an affine velocity field u(x) = u0 + A x trilinear interpolation is
+    exact, so F_H must equal -gamma (V - u0 - A r_i) for any position in the cell
+    (a particle on a node sees that node's velocity).  The cell sits away from
+    the periodic seam, where the field is affine."""
+    r = np.array(r)
+    V, gamma = np.array([0.01, -0.004, 0.006]), 0.45
+    FH = _pointwise_first_step_force(None, r, V, gamma, _U0, _A)
+    expect = -gamma * (V - (_U0 + _A @ r))
+    assert np.allclose(FH, expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
+def test_pointwise_pin_catches_a_swapped_corner_weight(tmp_path):
+    """The pin above fails for an oracle copy whose Eq. 7 branch pairs each corner
+    velocity with its x-neighbour's weight (a planted mistake, in a copy built
+    here; the oracle itself is untouched)."""
+    src = open(oracle._SRC).read()
+    good = "for (int p = 0; p < 8; ++p) ur += Wp[p] * uN[3 * p + k];"
+    assert src.count(good) == 1
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(good, "for (int p = 0; p < 8; ++p) ur += Wp[p ^ 1] * uN[3 * p + k];"))
+    so = tmp_path / "libmutant.so"
+    import subprocess
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", str(mutant),
+                    "-o", str(so), "-lm"], check=True)
+    r = np.array([4.3, 5.6, 3.7])
+    V, gamma = np.array([0.01, -0.004, 0.006]), 0.45
+    FH = _pointwise_first_step_force(oracle.bind(str(so)), r, V, gamma, _U0, _A)
+    expect = -gamma * (V - (_U0 + _A @ r))
+    assert not np.allclose(FH, expect, rtol=0, atol=1e-13 * np.abs(expect).max())
