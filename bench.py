@@ -130,22 +130,26 @@ def recorded_traffic(precision, shape):
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 20 ms from before the warm-up to after the timed
+    passes; each sample carries nvidia-smi's own time stamp (host wall clock), so
+    the samples taken inside the timed region can be told apart from the rest."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=20):
         self.index = index
-        self.lines = []
+        self.period_ms = period_ms
+        self.lines = []  # csv lines
         self.proc = None
+        self.windows = []  # (t0, t1) host times of the timed regions
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -157,6 +161,10 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self, t0, t1):
+        """A timed region, in host wall-clock seconds (time.time())."""
+        self.windows.append((t0, t1))
+
     def __exit__(self, *exc):
         if self.proc:
             self.proc.terminate()
@@ -167,22 +175,48 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        """Median SM clock and throttle reasons of the samples taken while a timed
+        region ran (the nearest sample after each region's start counts too, so a
+        region shorter than the sampling period still has one); the same over the
+        whole sampled run (warm-up, timed passes, end-to-end run) for context."""
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for name, val in zip(names, parts[4:8]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        pick = set()
+        for a, b in self.windows:
+            pick.update(i for i, r in enumerate(rows) if a <= r[0] <= b)
+            after = [i for i, r in enumerate(rows) if r[0] >= a]
+            if after:
+                pick.add(after[0])
+
+        def stats(sel):
+            sm, mx, reasons = [], None, set()
+            for i, (t, mhz, mxv, flags) in enumerate(rows):
+                if not sel(i):
+                    continue
+                sm.append(mhz)
+                mx = mxv
+                for name, val in zip(names, flags):
+                    if val.lower() == "active":
+                        reasons.add(name)
+            return sm, mx, reasons
+
+        inside = lambda i: i in pick
+        sm, mx, reasons = stats(inside)
+        sm_all, mx_all, reasons_all = stats(lambda i: True)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx if mx else mx_all,
+                "reasons": sorted(reasons), "samples": len(sm), "period_ms": self.period_ms,
+                "run": {"sm_mhz": statistics.median(sm_all) if sm_all else None,
+                        "reasons": sorted(reasons_all), "samples": len(sm_all)}}
 
 
 # ---------------------------------------------------------------------------- CPU oracle
@@ -344,51 +378,97 @@ def run_gpu(args, w):
                    "ms_by_shape": {n: t for n, t in zip(SHAPE_NAMES, tms) if t > 0}}
         return h
 
-    def timed(h, steps, warmup, clocks=None):
-        """K steps between CUDA events on the caller's stream; the library's own
-        events around every stream-collide launch give that kernel's duration."""
+    def vacf_flush(h, out):
+        """Correlate the samples not yet in a VACF block (lbp_vacf_read flushes
+        them) into device buffers: queued on the stream, no host wait."""
+        if out["per_particle"]:
+            lbp.lbp_vacf_read_per_particle(h, out["csum"], out["counts"])
+        else:
+            lbp.lbp_vacf_read(h, out["csum"], out["counts"])
+
+    def vacf_out(h, wk):
+        pp = isinstance(wk, wl.Ensemble)
+        rows = wk.n_particles if pp else 1
+        return {"per_particle": pp,
+                "csum": torch.empty((rows, args.vacf_lag + 1), dtype=torch.float64, device="cuda"),
+                "counts": torch.empty(args.vacf_lag + 1, dtype=torch.int64, device="cuda")}
+
+    def timed(h, wk, steps, warmup, clocks=None):
+        """K steps between CUDA events on the caller's stream, on the path users
+        run (CUDA-graph replay, no per-launch events), with the VACF blocks of the
+        timed samples -- including the last, partial one, flushed before the end
+        event -- inside the region.  Then the same K steps once more with the
+        library's events around every stream-collide launch, for that kernel's
+        average duration (this pass takes the plain-launch path)."""
+        out = vacf_out(h, wk)
         lbp.lbp_step(h, warmup)
+        vacf_flush(h, out)  # nothing of the warm-up's VACF work is left pending
         lbp.lbp_check(h)
-        lbp.lbp_timing_enable(h, True)
         stream = torch.cuda.current_stream()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
-        with (clocks if clocks is not None else contextlib.nullcontext()):
-            start.record(stream)
-            lbp.lbp_step(h, steps)
-            end.record(stream)
-            barrier()
+        t0 = time.time()
+        start.record(stream)
+        lbp.lbp_step(h, steps)
+        vacf_flush(h, out)
+        end.record(stream)
+        barrier()
+        if clocks is not None:
+            clocks.mark(t0, time.time())
         ms = start.elapsed_time(end)
+        lbp.lbp_check(h)
+        # instrumented pass: the lattice kernel's own duration
+        lbp.lbp_timing_enable(h, True)
+        lbp.lbp_step(h, steps)
+        vacf_flush(h, out)
+        barrier()
         k3_ms, k3_n = lbp.lbp_timing_read(h)
         lbp.lbp_timing_enable(h, False)
         lbp.lbp_check(h)
         return ms, k3_ms / max(k3_n, 1), k3_n
 
+    def run_e2e(h, wk, clocks):
+        """End to end through the C ABI with host buffers: per step the external
+        forces go host->device and positions + velocities come back (one
+        lbp_step_exchange call per step), and at the end the VACF sums (with the
+        flush of the last partial block) are read into host memory."""
+        n = wk.n_particles
+        fext = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
+        r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        v_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        pp = isinstance(wk, wl.Ensemble)
+        cs_h = torch.empty((n if pp else 1, args.vacf_lag + 1), dtype=torch.float64).pin_memory().numpy()
+        cnt_h = torch.empty(args.vacf_lag + 1, dtype=torch.int64).pin_memory().numpy()
+        read = lbp.lbp_vacf_read_per_particle if pp else lbp.lbp_vacf_read
+        e2e_steps = max(3, min(args.steps, 200))
+        for _ in range(max(2, args.warmup)):  # warm-up: both buffer parities
+            lbp.lbp_step_exchange(h, fext, r_h, v_h)
+        read(h, cs_h, cnt_h)
+        barrier()
+        t0w = time.time()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            # one public call per step: forces in, one step, positions and velocities out
+            lbp.lbp_step_exchange(h, fext, r_h, v_h)
+        read(h, cs_h, cnt_h)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        clocks.mark(t0w, time.time())
+        e2e_max_s, = max_over_ranks([e2e_s], "cuda", dist)
+        value = aggregate_mlups(world, wk.nodes, e2e_steps, e2e_max_s * 1e3)
+        return value, e2e_steps, fext, r_h, v_h, (cs_h.nbytes + cnt_h.nbytes) / e2e_steps
+
     h = make(args.precision)
     tuned = h.tuned
     clk = ClockSampler(local)
-    ms, k3_one, k3_n = timed(h, args.steps, args.warmup, clk)
-    ms_max, k3_avg_ms = max_over_ranks([ms, k3_one], "cuda", dist)
-    value = aggregate_mlups(world, w.nodes, args.steps, ms_max)
-
-    # end to end through the C ABI with host buffers: per step the external
-    # forces go host->device and positions + velocities come back
-    n = w.n_particles
-    fext = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
-    r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-    v_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = max(3, min(args.steps, 200))
-    for _ in range(max(2, args.warmup)):  # warm-up: both buffer parities
-        lbp.lbp_step_exchange(h, fext, r_h, v_h)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        # one public call per step: forces in, one step, positions and velocities out
-        lbp.lbp_step_exchange(h, fext, r_h, v_h)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_max_s, = max_over_ranks([e2e_s], "cuda", dist)
-    e2e_value = aggregate_mlups(world, w.nodes, e2e_steps, e2e_max_s * 1e3)
+    clk.__enter__()
+    try:
+        ms, k3_one, k3_n = timed(h, w, args.steps, args.warmup, clk)
+        ms_max, k3_avg_ms = max_over_ranks([ms, k3_one], "cuda", dist)
+        value = aggregate_mlups(world, w.nodes, args.steps, ms_max)
+        e2e_value, e2e_steps, fext, r_h, v_h, e2e_d2h = run_e2e(h, w, clk)
+    finally:
+        clk.__exit__(None, None, None)
     lbp.lbp_check(h)
     lbp.lbp_destroy(h)
 
@@ -401,7 +481,7 @@ def run_gpu(args, w):
                 continue
             hv = make(prec)
             vsteps = max(1, min(args.steps, 500))
-            vms, vk3, _ = timed(hv, vsteps, args.warmup)
+            vms, vk3, _ = timed(hv, w, vsteps, args.warmup)
             vms, vk3 = max_over_ranks([vms, vk3], "cuda", dist)
             lbp.lbp_destroy(hv)
             vach = BYTES_PER_NODE[prec] * w.nodes / (vk3 * 1e-3) / 1e9
@@ -418,7 +498,7 @@ def run_gpu(args, w):
         hb = make(args.precision, e)
         bsteps = max(1, min(args.steps, 1000))
         btuned = hb.tuned
-        bms, bk3, _ = timed(hb, bsteps, args.warmup)
+        bms, bk3, _ = timed(hb, e, bsteps, args.warmup)
         bms, bk3 = max_over_ranks([bms, bk3], "cuda", dist)
         lbp.lbp_destroy(hb)
         bach = BYTES_PER_NODE[args.precision] * e.nodes / (bk3 * 1e-3) / 1e9
@@ -459,13 +539,20 @@ def run_gpu(args, w):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.precision] * w.nodes,
                      "avg_launch_ms": k3_avg_ms, "launches": k3_n},
-        "particle_updates_per_s": world * n * args.steps / (ms_max * 1e-3),
+        "particle_updates_per_s": world * w.n_particles * args.steps / (ms_max * 1e-3),
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": fext.nbytes,
-                "d2h_bytes_per_step": r_h.nbytes + v_h.nbytes, "steps": e2e_steps},
+                "d2h_bytes_per_step": r_h.nbytes + v_h.nbytes + e2e_d2h, "steps": e2e_steps,
+                "note": "one lbp_step_exchange per step (forces in, positions and velocities out, "
+                        "page-locked host buffers), then the VACF sums read to the host"},
         "autotune": tuned,
         "variants": variants,
+        # per step the particle kernel and the lattice kernel; per block of 64
+        # samples the VACF kernels (two, or one per-particle), and the same once
+        # more for the flush of the last, partial block at the end of the region
         "gpu_launches": LAUNCHES_PER_STEP * args.steps
-                        + (1 if isinstance(w, wl.Ensemble) else 2) * sum(1 for n in range(args.warmup, args.warmup + args.steps) if (n + 1) % 64 == 0),
+                        + (1 if isinstance(w, wl.Ensemble) else 2) * (args.steps // 64 + 1),
+        "timing": "headline on the graph-replay path without per-launch events; the lattice "
+                  "kernel's average from a second, instrumented pass of the same steps",
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline and not isinstance(w, wl.Ensemble):

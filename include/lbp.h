@@ -63,7 +63,7 @@ typedef enum {
     LBP_ENOMEM = 2,   /* device allocation failed */
     LBP_ECUDA = 3,    /* a CUDA call failed; the message names it */
     LBP_ETIMEOUT = 4, /* a bounded device wait ran out */
-    LBP_ENAN = 5,     /* a particle velocity or position became non-finite */
+    LBP_ENAN = 5,     /* a particle velocity or position, or a lattice population, became non-finite */
     LBP_ESTATE = 6,   /* call not valid in the current state */
     LBP_ERANGE = 7    /* a friction force exceeded the fixed-point range (|F_H| >= 32) */
 } lbp_status;
@@ -207,6 +207,24 @@ lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
  * stream-ordered copies and return after the whole step.                      */
 lbp_status lbp_step_exchange(lbp_sim *sim, const double *f_ext, double *r, double *v, int on_device);
 
+/* Bit-exact checkpoints (no counterpart in the paper; the Philox counter of
+ * Eqs. 4-5 is the step index, so a run continued from a checkpoint draws the
+ * same noise as the uninterrupted run).  A checkpoint holds the stored
+ * populations in their storage format (so nothing is rounded), the particle
+ * positions and velocities (FP64) and the step index; the handle's
+ * configuration -- boxes, storage, particles with their M, gamma, R, the
+ * coupling parameters, external forces, body forces -- is the caller's to
+ * recreate.  lbp_checkpoint_size gives the bytes of a checkpoint of this
+ * handle; lbp_checkpoint_save writes one into buf (host or device per
+ * on_device; synchronous); lbp_checkpoint_load restores one into a handle
+ * with the same boxes (sizes and tau), storage and particle count (LBP_EINVAL
+ * otherwise, with nothing changed).  Loading turns the VACF off, as
+ * lbp_set_step_index does.  Continuing a loaded handle gives results bitwise
+ * equal to continuing the handle that was saved.                             */
+lbp_status lbp_checkpoint_size(lbp_sim *sim, size_t *bytes);
+lbp_status lbp_checkpoint_save(lbp_sim *sim, void *buf, int on_device);
+lbp_status lbp_checkpoint_load(lbp_sim *sim, const void *buf, int on_device);
+
 /* The step index n that the next step uses as its Philox counter.            */
 lbp_status lbp_set_step_index(lbp_sim *sim, int64_t step);
 lbp_status lbp_get_step_index(lbp_sim *sim, int64_t *step);
@@ -233,8 +251,51 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *sim, int max_lag, int per_particle);
 lbp_status lbp_vacf_read_per_particle(lbp_sim *sim, double *csum, int64_t *counts, int on_device);
 
 /* Wait for the handle's queued work and report device-side errors: LBP_ENAN if
- * a particle state became non-finite, LBP_ERANGE on fixed-point overflow.     */
-lbp_status lbp_check(lbp_sim *sim);  /* also LBP_ETIMEOUT: a bounded device wait ran out */
+ * a particle state became non-finite or left the box, or if a collided
+ * population of the lattice became non-finite (every lattice kernel checks the
+ * collided rest population of each node, which every pulled population of the
+ * node enters through rho~ and u.u: a NaN or infinity anywhere in the node, or
+ * an overflow of u.u, is caught in the step it appears); LBP_ERANGE on
+ * fixed-point overflow; LBP_ETIMEOUT if a bounded device wait ran out.  The
+ * flags are cleared by the call.                                             */
+lbp_status lbp_check(lbp_sim *sim);
+
+/* Conservation budget.  Streaming and the BGK collision conserve mass and
+ * momentum (Eqs. 15, 17-20) and the fluid receives exactly -F_H (Eq. 9), so
+ * only the random and external forces on the particles (and a uniform body
+ * force) change the total momentum.  lbp_budget waits for the handle's work
+ * and writes out[10]:
+ *   out[0]    total mass, sum over all nodes and boxes of sum_a fhat_a;
+ *   out[1..3] fluid momentum, sum over nodes of sum_a e_a fhat_a;
+ *   out[4..6] particle momentum, sum_i M_i V_i;
+ *   out[7..9] momentum that F_R + F_ext put into the unpinned particles since
+ *             lbp_budget_track(sim, 1) (zero while not tracked).
+ * Lattice sums in FP64 from the stored populations, in a fixed order.  With
+ * no pinned particle and no body force, out[1..3] + out[4..6] - out[7..9]
+ * keeps its value from when tracking began, to rounding; a uniform body force
+ * g (lbp_set_body_force) adds N g per step, which the caller accounts for.
+ * Tracking adds one FP64 atomic per 32 particles and component to every step;
+ * lbp_budget_track(sim, 0) stops it.                                         */
+lbp_status lbp_budget_track(lbp_sim *sim, int enable);
+lbp_status lbp_budget(lbp_sim *sim, double *out);
+
+/* Bound of every device-side wait on an mbarrier (the bulk-copy staged
+ * lattice kernel, variant 2 of lbp_autotune), in SM clock cycles; 0 restores
+ * the default 2^30 (about half a second).  A wait that runs out leaves that
+ * step's lattice pass incomplete and makes lbp_check return LBP_ETIMEOUT; the
+ * kernel first waits (with the default bound) for the copies it has issued,
+ * so the device stays usable.  lbp_check then also resets the step's force
+ * records; the populations of that step are not valid, so restore a state
+ * (lbp_checkpoint_load, lbp_set_populations) before stepping on.             */
+lbp_status lbp_set_wait_bound(lbp_sim *sim, int64_t cycles);
+
+/* Failure probe for tests of the error path (no counterpart in the paper):
+ * while enabled, the staged lattice kernel's consumers first wait on a
+ * barrier that nothing completes, so that wait runs out after the bound of
+ * lbp_set_wait_bound, the step's lattice pass is skipped and lbp_check
+ * reports LBP_ETIMEOUT -- a device-side timeout made without a fault.  Other
+ * kernel shapes have no device-side waits and ignore it.                    */
+lbp_status lbp_set_wait_probe(lbp_sim *sim, int enable);
 
 /* Diagnostics of the last completed step (waits for the handle's work):
  * out[0] = reaction-force shares that did not fit their row segment's record
@@ -311,14 +372,18 @@ lbp_status lbp_philox4x64_10(const uint64_t *ctr, const uint64_t *key, uint64_t 
  * velocity components (any component order within a sample); outputs on the
  * device: csum[k] = sum over t0 <= T-1-k and all components of
  * samples[t0] * samples[t0 + k], counts[k] = npairs * (T - k) (0 if k >= T),
- * k = 0..max_lag -- the same estimator as lbp_vacf_read (products FP32, sums
- * FP64).  Scratch is a fixed 4 MiB array inside the library, so
- * ceil(ncomp / 1024) * (max_lag + 1) must not exceed 524288 (LBP_EINVAL
- * otherwise).  The first call on a device looks up that array's address; make
- * it before capturing this routine into a CUDA graph.  All calls on a device
- * share the array: calls that overlap on the GPU (different streams, host
- * threads) race and must be serialised by the caller.  Asynchronous on
- * `stream`; outputs are zeroed by the call.                                   */
+ * k = 0..max_lag -- the same estimator as lbp_vacf_read.  Products are FP32;
+ * the products of one component over one block of at most 64 samples are
+ * summed in FP32, every sum above that in FP64.  Scratch is a fixed 4 MiB
+ * array inside the library, so ceil(ncomp / 1024) * (max_lag + 1) must not
+ * exceed 524288, and ncomp must not exceed 65535 * 1024 (LBP_EINVAL
+ * otherwise, with nothing queued).  The first call on a device looks up that
+ * array's address and keeps it for the life of the process; make it before
+ * capturing this routine into a CUDA graph, and do not use this routine on a
+ * device after cudaDeviceReset (the kept address would be stale).  All calls
+ * on a device share the array: calls that overlap on the GPU (different
+ * streams, host threads) race and must be serialised by the caller.
+ * Asynchronous on `stream`; outputs are zeroed by the call.                   */
 lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp, int max_lag,
                                       int npairs, double *csum, int64_t *counts, void *stream);
 

@@ -77,6 +77,7 @@ def bind(path: str):
     L.or_step.argtypes = [vp, C.c_int64]
     L.or_spread_only.argtypes = [vp, _dp]
     L.or_vacf.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _i64p]
+    L.or_msd.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, _dp, _i64p]
     L.or_num_threads.restype = C.c_int
     return L
 
@@ -185,6 +186,17 @@ def vacf(Vtraj, K, stride=1):
     cnt = np.zeros(K + 1, np.int64)
     lib().or_vacf(V.reshape(-1), T, npart, K, stride, cs, cnt)
     return cs, cnt
+
+
+def msd(Xtraj, K):
+    """Mean squared displacement sums M(k) = sum_{i,t0} |X_i(t0+k) - X_i(t0)|^2
+    of unwrapped positions X [T, n, 3], and pair counts."""
+    X = _c(Xtraj)
+    T, npart, _ = X.shape
+    ms = np.zeros(K + 1)
+    cnt = np.zeros(K + 1, np.int64)
+    lib().or_msd(X.reshape(-1), T, npart, K, ms, cnt)
+    return ms, cnt
 
 
 def num_threads():

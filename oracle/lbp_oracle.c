@@ -525,6 +525,31 @@ void or_vacf(const double *V, int64_t T, int np, int K, int stride, double *csum
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Mean squared displacement of the particles (the dispersion that the */
+/* Brownian analysis of Section 3 accompanies the VACF with):          */
+/* M(k) = sum over particles i and origins t0 with t0 + k < T of       */
+/* |X_i(t0 + k) - X_i(t0)|^2, X [T][np][3] unwrapped positions (the    */
+/* sum of the displacements r^{n+1} - r^n = V^{n+1} of Eq. 2, without  */
+/* the periodic wrap).  Writes the sums and the numbers of pairs.      */
+/* ------------------------------------------------------------------ */
+void or_msd(const double *X, int64_t T, int np, int K, double *msum, int64_t *count)
+{
+    for (int k = 0; k <= K; ++k) {
+        double s = 0.0;
+        int64_t c = 0;
+        for (int64_t t0 = 0; t0 + k < T; ++t0)
+            for (int i = 0; i < np; ++i) {
+                const double *a = X + (t0 * np + i) * 3, *b = X + ((t0 + k) * np + i) * 3;
+                const double d0 = b[0] - a[0], d1 = b[1] - a[1], d2 = b[2] - a[2];
+                s += d0 * d0 + d1 * d1 + d2 * d2;
+                c += 1;
+            }
+        msum[k] = s;
+        count[k] = c;
+    }
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP

@@ -37,9 +37,10 @@ namespace lbp {
 // ---------------------------------------------------------------------------
 template <typename St>
 __device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
-                                              float omega, float F0, float F1, float F2) {
+                                              float omega, float F0, float F1, float F2, bool &bad) {
     float o[Q];
     collide_values(g, omega, F0, F1, F2, o);
+    bad |= nonfinite_node(o);
 #pragma unroll
     for (int a = 0; a < Q; ++a) St::store(pl.d[a] + d, a, o[a]);
 }
@@ -79,7 +80,7 @@ __device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int n
 // launch there, against 0.833 ms at the compiler's 72 registers).
 template <int BX, typename St, int R, int MAXR>
 __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide(Planes<St> pl, const RepTable<MAXR> rt,
-                                                       long long *bump) {
+                                                       long long *bump, int *err) {
     const int r = find_block_rep(rt, blockIdx.x);
     const Rep &rp = rt.rep[r];
     const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
@@ -103,9 +104,11 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide(Planes<St
             g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
                                           n[h].oz[ez(a) + 1]), a);
     }
+    bool bad = false;
 #pragma unroll
     for (int h = 0; h < R; ++h)
-        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, rp.gx, rp.gy, rp.gz);
+        if (grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, rp.gx, rp.gy, rp.gz, bad);
+    if (bad) atomicOr(err, ERR_LATTICE);
 }
 
 // Sum, exactly in 64-bit fixed point, the record entries whose x is this
@@ -145,7 +148,7 @@ __device__ __forceinline__ void record_sum(unsigned long long rw, int cnt, int x
 template <int BX, typename St, int R, int MAXR>
 __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
     Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
-    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err) {
     static_assert(BX == SEG, "one block per force-record segment");
     const int r = find_block_rep(rt, blockIdx.x);
     const Rep &rp = rt.rep[r];
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
     NodeIdx n[R];
     float g[R][Q];
     unsigned long long rw[R];
+    bool bad = false;
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
@@ -200,8 +204,9 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
             F1 = __fmaf_rn(inv, fix_to_float(a1), F1);
             F2 = __fmaf_rn(inv, fix_to_float(a2), F2);
         }
-        if (act && grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, F0, F1, F2);
+        if (act && grp * R + h < nrows) collide_store<St>(g[h], pl, n[h].d, rp.omega, F0, F1, F2, bad);
     }
+    if (bad) atomicOr(err, ERR_LATTICE);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,10 +253,23 @@ __device__ __forceinline__ unsigned pack2<StoreF16>(float lo, float hi, int a) {
 
 constexpr int PAIR_BX = SEG / 2;  // threads per block of the paired kernel
 
+// True if either 2-byte value of a packed pair is a NaN or an infinity (its
+// exponent field all ones: 0x7f80 for bfloat16, 0x7c00 for binary16).
+template <typename St>
+__device__ __forceinline__ bool packed_nonfinite(unsigned v);
+template <>
+__device__ __forceinline__ bool packed_nonfinite<StoreBF16>(unsigned v) {
+    return (v & 0x7f80u) == 0x7f80u || (v & 0x7f800000u) == 0x7f800000u;
+}
+template <>
+__device__ __forceinline__ bool packed_nonfinite<StoreF16>(unsigned v) {
+    return (v & 0x7c00u) == 0x7c00u || (v & 0x7c000000u) == 0x7c000000u;
+}
+
 template <typename St, int R, int MAXR, bool FORCED>
 __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
     Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
-    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err) {
     const int r = find_block_rep(rt, blockIdx.x);
     const Rep &rp = rt.rep[r];
     const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
@@ -334,6 +352,7 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
             float o0[Q], o1[Q];
             collide_values(g[h][0], rp.omega, F[0][0], F[0][1], F[0][2], o0);
             collide_values(g[h][1], rp.omega, F[1][0], F[1][1], F[1][2], o1);
+            if (nonfinite_node(o0) || nonfinite_node(o1)) atomicOr(err, ERR_LATTICE);
 #pragma unroll
             for (int a = 0; a < Q; ++a)
                 reinterpret_cast<unsigned *>(pl.d[a] + drow[h])[x >> 1] = pack2<St>(o0[a], o1[a], a);
@@ -392,7 +411,7 @@ __device__ __forceinline__ unsigned load_elem(const typename St::T *p) {
 template <typename St, int R, int MAXR, bool FORCED>
 __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_collide_quad(
     Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
-    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump) {
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     const unsigned item = blockIdx.x * QUAD_WARPS + (threadIdx.x >> 5);
     if (item >= rt.item_off[MAXR == 1 ? 1 : rt.nrep]) return;  // whole warp past the last segment
@@ -491,6 +510,9 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
             }
         }
         if (act && row_ok) {
+            // the packed collided rest populations of the four nodes: a NaN or an
+            // infinity (also one from the rounding to 2 bytes) has an all-ones exponent
+            if (packed_nonfinite<St>(p[h][0].x) || packed_nonfinite<St>(p[h][0].y)) atomicOr(err, ERR_LATTICE);
 #pragma unroll
             for (int a = 0; a < Q; ++a) *reinterpret_cast<uint2 *>(pl.d[a] + drow[h] + x) = p[h][a];
         }
@@ -619,9 +641,11 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
             using St = decltype(tag);
             if (s.nrep == 1)
                 return launch_staged_t<St, 1, FORCED>(planes_of<St>(s, src, dst), rep_table_staged<1>(s), rec_cur,
-                                                      rec_prev, s.fq, s.N, bump, s.d_err, s.num_sms, st);
+                                                      rec_prev, s.fq, s.N, bump, s.d_err, s.wait_cycles, s.wait_probe,
+                                                      s.num_sms, st);
             return launch_staged_t<St, MAX_BATCH, FORCED>(planes_of<St>(s, src, dst), rep_table_staged<MAX_BATCH>(s),
-                                                          rec_cur, rec_prev, s.fq, s.N, bump, s.d_err, s.num_sms, st);
+                                                          rec_cur, rec_prev, s.fq, s.N, bump, s.d_err,
+                                                          s.wait_cycles, s.wait_probe, s.num_sms, st);
         });
     }
     const bool use_pair = variant == 1, use_quad = variant == 3;
@@ -635,21 +659,22 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
                 if constexpr (!std::is_same<St, StoreF32>::value) {
                     if (use_pair) {
                         k_stream_collide_pair<St, R, MAXR, FORCED><<<grid, PAIR_BX, 0, st>>>(
-                            planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                            planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
                         return cudaGetLastError();
                     }
                     if (use_quad) {
                         k_stream_collide_quad<St, R, MAXR, FORCED>
                             <<<(grid + QUAD_WARPS - 1) / QUAD_WARPS, 32 * QUAD_WARPS, 0, st>>>(
-                                planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                                planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
                         return cudaGetLastError();
                     }
                 }
                 if constexpr (FORCED)
                     k_stream_collide_forced<BX, St, R, MAXR><<<grid, BX, 0, st>>>(
-                        planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump);
+                        planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
                 else
-                    k_stream_collide<BX, St, R, MAXR><<<grid, BX, 0, st>>>(planes_of<St>(s, src, dst), rt, bump);
+                    k_stream_collide<BX, St, R, MAXR><<<grid, BX, 0, st>>>(planes_of<St>(s, src, dst), rt, bump,
+                                                                           s.d_err);
                 return cudaGetLastError();
             });
         });
@@ -760,6 +785,58 @@ cudaError_t launch_to_f64(Sim &s, const void *src, double *f, cudaStream_t st) {
         using St = decltype(tag);
         k_to_f64<St><<<grid_for(Q * s.N, 256, s.num_sms), 256, 0, st>>>(
             static_cast<const typename St::T *>(src), f, s.N, s.P);
+        return cudaGetLastError();
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Totals of the stored populations for the conservation budget: per block, in
+// FP64, the sums over its nodes of sum_a g_a (mass minus the node count) and
+// sum_a e_a g_a (momentum; sum_a w_a e_a = 0), so out[4 b + k], k = 0..3.
+// Streaming permutes the populations, so these are also the totals of the
+// streamed f; the collision conserves the mass and adds exactly the body
+// force (Eqs. 15, 18-19).  A fixed grid and a fixed reduction order: the
+// result is the same on every call for the same state.
+// ---------------------------------------------------------------------------
+constexpr int BUDGET_THREADS = 256;
+
+template <typename St>
+__global__ void __launch_bounds__(BUDGET_THREADS) k_budget(const typename St::T *__restrict__ g, long long N,
+                                                           long long P, double *out) {
+    __shared__ double sh[4][BUDGET_THREADS];
+    double m = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    for (long long i = blockIdx.x * (long long)BUDGET_THREADS + threadIdx.x; i < N;
+         i += (long long)gridDim.x * BUDGET_THREADS) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double v = (double)St::load(g + (long long)a * P + i, a);
+            m += v;
+            if (ex(a)) p0 += ex(a) > 0 ? v : -v;
+            if (ey(a)) p1 += ey(a) > 0 ? v : -v;
+            if (ez(a)) p2 += ez(a) > 0 ? v : -v;
+        }
+    }
+    sh[0][threadIdx.x] = m;
+    sh[1][threadIdx.x] = p0;
+    sh[2][threadIdx.x] = p1;
+    sh[3][threadIdx.x] = p2;
+    __syncthreads();
+    for (int w = BUDGET_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+int budget_blocks(const Sim &s) { return 2 * s.num_sms; }
+
+cudaError_t launch_budget(Sim &s, const void *src, double *out, cudaStream_t st) {
+    return by_storage(s, [&](auto tag) {
+        using St = decltype(tag);
+        k_budget<St><<<budget_blocks(s), BUDGET_THREADS, 0, st>>>(static_cast<const typename St::T *>(src), s.N,
+                                                                 s.P, out);
         return cudaGetLastError();
     });
 }

@@ -22,9 +22,15 @@
 //
 // Requirements (checked on the host): every box has nx <= STAGED_NODES and
 // nx a multiple of 16 bytes of storage, so that every copy starts and ends on
-// a 16-byte boundary.  Every wait on an mbarrier is bounded: after
-// WAIT_CYCLES clock cycles the CTA sets ERR_TIMEOUT, waits (bounded again) for
-// the copies it issued, and leaves.
+// a 16-byte boundary.  Every wait on an mbarrier is bounded by `wait_cycles`
+// SM clock cycles (a kernel parameter).  A wait that runs out sets ERR_TIMEOUT
+// and a CTA-wide abort flag in shared memory; every other wait of the CTA
+// then gives up at its next poll and the producer stops issuing copies.
+// Before the producer thread leaves, in every case, it waits for the "full"
+// barrier of the last copy it issued into each stage, so that no bulk copy is
+// still writing into shared memory when the CTA exits.  Those last waits use
+// the fixed, long DRAIN_CYCLES bound (copies that were issued land within
+// microseconds).
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -35,9 +41,9 @@ namespace lbp {
 
 namespace {
 
-// bound of one mbarrier wait, in SM clock cycles (~0.5 s at 2 GHz); each
+// bound of the drain waits at exit, in SM clock cycles (~0.5 s at 2 GHz); each
 // try_wait poll may itself suspend the thread for a short, hardware-chosen time
-constexpr long long WAIT_CYCLES = 1ll << 30;
+constexpr long long DRAIN_CYCLES = 1ll << 30;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -68,11 +74,15 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     return ok != 0;
 }
 
-// bounded wait: true when the phase completed
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// bounded wait: true when the phase completed; false when `bound` cycles
+// passed or the CTA's abort flag (if given) is set
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long bound,
+                                          const volatile int *abort_flag) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+    while (!mbar_try_wait(bar, parity)) {
+        if (abort_flag && *abort_flag) return false;
+        if (clock64() - t0 > bound) return false;
+    }
     return true;
 }
 
@@ -100,7 +110,8 @@ struct StagedGeom {
     static constexpr int PLANE_BYTES = STAGED_NODES * E;
     static constexpr int REC_BYTES = STAGED_RECS * REC_WORDS * 8;  // records of an item's rows
     static constexpr int STAGE_BYTES = Q * PLANE_BYTES + REC_BYTES;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8;  // + full and empty barriers
+    // + full and empty barriers, and one barrier that nothing ever completes (the probe)
+    static constexpr int SMEM = STAGES * STAGE_BYTES + (2 * STAGES + 1) * 8;
 };
 
 // Item i -> (replica, z, first row y0, rows R) of the staged launch.
@@ -154,21 +165,26 @@ __device__ __forceinline__ void issue_item(const Planes<St> &pl, const RepTable<
 template <typename St, int MAXR, bool FORCED>
 __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
     Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
-    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err) {
+    unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err,
+    long long wait_cycles, int probe) {
     using G = StagedGeom<St>;
     constexpr int STAGES = G::STAGES;
     constexpr int NCW = STAGED_THREADS / 32;  // consumer warps; warp NCW is the producer
     extern __shared__ __align__(128) char smem[];
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + STAGES * G::STAGE_BYTES);
     unsigned long long *empty = full + STAGES;
+    unsigned long long *never = empty + STAGES;  // the probe: no arrival ever completes it
+    __shared__ volatile int s_abort;  // set by the first wait of the CTA that runs out
     const unsigned total = rt.item_off[rt.nrep];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (blockIdx.x == 0 && t == 0) *bump += 1;
     if (t == 0) {
+        s_abort = 0;
         for (int st = 0; st < STAGES; ++st) {
             mbar_init(smem_addr(full + st), 1);
             mbar_init(smem_addr(empty + st), NCW);
         }
+        mbar_init(smem_addr(never), 1);
         fence_barrier_init();
     }
     __syncthreads();  // the only CTA-wide barrier
@@ -176,31 +192,50 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
     if (warp == NCW) {
         // ---- producer: refill a stage as soon as the consumers release it
         if (lane == 0) {
-            unsigned k = 0;
+            unsigned k = 0;  // items issued
             for (unsigned item = blockIdx.x; item < total; item += gridDim.x, ++k) {
                 const int st = (int)(k % STAGES);
-                if (k >= (unsigned)STAGES && !mbar_wait(smem_addr(empty + st), ((k / STAGES) - 1) & 1u)) {
+                if (s_abort) break;
+                if (k >= (unsigned)STAGES &&
+                    !mbar_wait(smem_addr(empty + st), ((k / STAGES) - 1) & 1u, wait_cycles, &s_abort)) {
                     atomicOr(err, ERR_TIMEOUT);
+                    s_abort = 1;
                     break;
                 }
                 fence_proxy_async();
                 issue_item<St, MAXR, FORCED>(pl, rt, rec_cur, item, smem + st * G::STAGE_BYTES,
                                              smem_addr(full + st));
             }
+            // drain, whether or not a wait ran out: the last issue into each
+            // stage (at most STAGES items) has landed before the thread that
+            // issued it returns, so no copy is in flight once every thread of
+            // the CTA has left (a consumer may give up on a stage after this
+            // thread finished issuing)
+            const unsigned first = k > (unsigned)STAGES ? k - STAGES : 0u;
+            for (unsigned j = first; j < k; ++j)
+                mbar_wait(smem_addr(full + (j % STAGES)), (j / STAGES) & 1u, DRAIN_CYCLES, nullptr);
         }
         return;
     }
 
     // ---- consumers
     unsigned k = 0;
-    for (unsigned item = blockIdx.x; item < total; item += gridDim.x, ++k) {
+    bool bad = false;
+    if (probe && !mbar_wait(smem_addr(never), 0u, wait_cycles, &s_abort)) {
+        // the failure path on purpose: a bounded wait on a barrier that nothing
+        // completes runs out (lbp_set_wait_probe, for tests of the error path)
+        atomicOr(err, ERR_TIMEOUT);
+        s_abort = 1;
+        k = 0xffffffffu;  // skip every item
+    }
+    for (unsigned item = blockIdx.x; item < total && k != 0xffffffffu; item += gridDim.x, ++k) {
         const int st = (int)(k % STAGES);
         const unsigned parity = (k / STAGES) & 1u;
         char *stage = smem + st * G::STAGE_BYTES;
-        if (!mbar_wait(smem_addr(full + st), parity)) {
+        if (!mbar_wait(smem_addr(full + st), parity, wait_cycles, &s_abort)) {
+            // the producer drains the copies in flight before the CTA ends
             atomicOr(err, ERR_TIMEOUT);
-            // the copies into this stage may still land: wait once more (bounded)
-            mbar_wait(smem_addr(full + st), parity);
+            s_abort = 1;
             break;
         }
         int r, z, y0, R;
@@ -251,6 +286,7 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
             }
             float o[Q];
             collide_values(g, rp.omega, F0, F1, F2, o);
+            bad |= nonfinite_node(o);
 #pragma unroll
             for (int a = 0; a < Q; ++a) St::store(pl.d[a] + d, a, o[a]);
         }
@@ -258,13 +294,14 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(empty + st));
     }
+    if (bad) atomicOr(err, ERR_LATTICE);
 }
 
 // The launcher: one persistent CTA per free slot (occupancy of this kernel).
 template <typename St, int MAXR, bool FORCED>
 cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, const unsigned long long *rec_cur,
                             unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump,
-                            int *err, int num_sms, cudaStream_t st) {
+                            int *err, long long wait_cycles, int probe, int num_sms, cudaStream_t st) {
     using G = StagedGeom<St>;
     auto kern = k_stream_collide_staged<St, MAXR, FORCED>;
     static int per_sm = 0;  // per instantiation
@@ -279,7 +316,8 @@ cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, cons
     unsigned grid = (unsigned)(per_sm * num_sms);
     if (grid > total) grid = total;
     if (grid == 0) return cudaSuccess;
-    kern<<<grid, STAGED_THREADS + 32, G::SMEM, st>>>(pl, rt, rec_cur, rec_prev, fq, Ntot, bump, err);
+    kern<<<grid, STAGED_THREADS + 32, G::SMEM, st>>>(pl, rt, rec_cur, rec_prev, fq, Ntot, bump, err, wait_cycles,
+                                                     probe);
     return cudaGetLastError();
 }
 
@@ -297,7 +335,7 @@ int staged_rows(int nx, int ny) {
     template cudaError_t launch_staged_t<ST, MAXR, F>(const Planes<ST> &, const RepTable<MAXR> &,          \
                                                       const unsigned long long *, unsigned long long *,     \
                                                       unsigned long long *, long long, long long *, int *, \
-                                                      int, cudaStream_t);
+                                                      long long, int, int, cudaStream_t);
 LBP_STAGED_INST(StoreF32, 1, true)
 LBP_STAGED_INST(StoreF32, 1, false)
 LBP_STAGED_INST(StoreF32, MAX_BATCH, true)

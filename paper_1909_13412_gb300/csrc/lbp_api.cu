@@ -26,6 +26,7 @@ using namespace lbp;
 
 struct lbp_sim : public lbp::Sim {
     std::vector<double> h_gamma, h_radius;  // host copies for parameter updates
+    std::vector<double> h_mass;             // host copy for the momentum budget
     std::vector<int> h_prep;                // replica of each particle
 };
 
@@ -478,7 +479,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext, s->xbuf,
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
-                    s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage};
+                    s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage, s->inj, s->budget_part};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
@@ -713,6 +714,7 @@ lbp_status lbp_particles_add_to(lbp_sim *s, int replica, int n, const double *r,
     std::vector<int> hp(n, replica);
     CK(cudaMemcpy(s->prep + s->np, hp.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     s->h_gamma.insert(s->h_gamma.end(), hg.begin(), hg.end());
+    s->h_mass.insert(s->h_mass.end(), hm.begin(), hm.end());
     s->h_radius.insert(s->h_radius.end(), hR.begin(), hR.end());
     s->h_prep.insert(s->h_prep.end(), hp.begin(), hp.end());
     s->np = np_new;
@@ -1413,7 +1415,19 @@ lbp_status lbp_check(lbp_sim *s) {
     CK(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         CK(cudaMemset(s->d_err, 0, sizeof(int)));
-        if (err & ERR_TIMEOUT) return fail(LBP_ETIMEOUT, "lbp_check: a bounded wait on an mbarrier in the staged lattice kernel ran out");
+        if (err & ERR_TIMEOUT) {
+            // the lattice pass that gave up left some force-record counts and
+            // overflow entries of its step uncleared; between steps both are
+            // disposable, so start the next step from clean ones
+            if (s->fq) {
+                CK(cudaMemset(s->fq, 0, sizeof(unsigned long long) * 3 * (size_t)s->N));
+                for (int q = 0; q < 2; ++q)
+                    CK(cudaMemset(s->rec[q], 0, sizeof(unsigned long long) * (size_t)s->nseg * REC_WORDS));
+            }
+            return fail(LBP_ETIMEOUT, "lbp_check: a bounded wait on an mbarrier in the staged lattice kernel ran out "
+                                      "(that step's lattice pass is incomplete)");
+        }
+        if (err & ERR_LATTICE) return fail(LBP_ENAN, "lbp_check: a population of the lattice became non-finite");
         if (err & ERR_NAN) return fail(LBP_ENAN, "lbp_check: a particle velocity or position became non-finite or left the box");
         return fail(LBP_ERANGE, "lbp_check: a friction force exceeded the fixed-point range (|F_H| >= 32)");
     }
@@ -1437,6 +1451,177 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
     }
     for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
     return LBP_OK;
+}
+
+// ------------------------------------------------------------------ checkpoints
+// Layout: a header of 16 int64 words, then the populations in the storage
+// format (15 planes of N deviations, plane after plane), then the particle
+// positions and velocities (FP64, [3][np] each, SoA).
+namespace {
+constexpr int64_t CKPT_MAGIC = 0x4c42504b43503031ll;  // "LBPKCP01"
+constexpr int CKPT_HEADER = 16;
+
+size_t ckpt_bytes(const lbp_sim *s) {
+    return sizeof(int64_t) * CKPT_HEADER + (size_t)storage_bytes(s->precision) * Q * (size_t)s->N +
+           sizeof(double) * 6 * (size_t)s->np;
+}
+
+void ckpt_header(const lbp_sim *s, int64_t *h) {
+    for (int i = 0; i < CKPT_HEADER; ++i) h[i] = 0;
+    h[0] = CKPT_MAGIC;
+    h[1] = s->precision;
+    h[2] = s->nrep;
+    h[3] = s->N;
+    h[4] = s->np;
+    h[5] = s->step;
+    // a fingerprint of the box sizes and relaxation times
+    uint64_t fp = 1469598103934665603ull;
+    for (int r = 0; r < s->nrep; ++r) {
+        uint64_t tb;
+        std::memcpy(&tb, &s->taus[r], sizeof(tb));
+        const uint64_t v[4] = {(uint64_t)s->reps[r].nx, (uint64_t)s->reps[r].ny, (uint64_t)s->reps[r].nz, tb};
+        for (uint64_t x : v) fp = (fp ^ x) * 1099511628211ull;
+    }
+    h[6] = (int64_t)fp;
+}
+}  // namespace
+
+lbp_status lbp_checkpoint_size(lbp_sim *s, size_t *bytes) {
+    CHECK_SIM(s);
+    if (!bytes) return fail(LBP_EINVAL, "lbp_checkpoint_size: null bytes");
+    *bytes = ckpt_bytes(s);
+    return LBP_OK;
+}
+
+lbp_status lbp_checkpoint_save(lbp_sim *s, void *buf, int on_device) {
+    CHECK_SIM(s);
+    if (!buf) return fail(LBP_EINVAL, "lbp_checkpoint_save: null buffer");
+    TRY(enter(s));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    int64_t h[CKPT_HEADER];
+    ckpt_header(s, h);
+    char *out = static_cast<char *>(buf);
+    CK(cudaMemcpyAsync(out, h, sizeof(h), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s->s0));
+    out += sizeof(h);
+    const size_t plane = (size_t)storage_bytes(s->precision) * (size_t)s->N;
+    const size_t pstride = (size_t)storage_bytes(s->precision) * (size_t)s->P;
+    for (int a = 0; a < Q; ++a)
+        CK(cudaMemcpyAsync(out + a * plane, static_cast<const char *>(s->f[s->cur]) + a * pstride, plane, kind, s->s0));
+    out += Q * plane;
+    for (int k = 0; k < 3 && s->np > 0; ++k) {
+        CK(cudaMemcpyAsync(out + sizeof(double) * (size_t)k * s->np, s->r + (size_t)k * s->cap,
+                           sizeof(double) * s->np, kind, s->s0));
+        CK(cudaMemcpyAsync(out + sizeof(double) * (size_t)(3 + k) * s->np, s->v + (size_t)k * s->cap,
+                           sizeof(double) * s->np, kind, s->s0));
+    }
+    CK(cudaStreamSynchronize(s->s0));
+    return leave(s);
+}
+
+lbp_status lbp_checkpoint_load(lbp_sim *s, const void *buf, int on_device) {
+    CHECK_SIM(s);
+    if (!buf) return fail(LBP_EINVAL, "lbp_checkpoint_load: null buffer");
+    int64_t h[CKPT_HEADER], want[CKPT_HEADER];
+    CK(cudaMemcpy(h, buf, sizeof(h), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    ckpt_header(s, want);
+    if (h[0] != CKPT_MAGIC) return fail(LBP_EINVAL, "lbp_checkpoint_load: not a checkpoint of this library");
+    if (h[1] != want[1] || h[2] != want[2] || h[3] != want[3] || h[6] != want[6])
+        return fail(LBP_EINVAL, "lbp_checkpoint_load: the checkpoint holds other boxes (sizes, tau) or storage");
+    if (h[4] != want[4])
+        return fail(LBP_EINVAL, "lbp_checkpoint_load: the checkpoint holds %lld particles, the handle %d",
+                    (long long)h[4], s->np);
+    if (h[5] < 0) return fail(LBP_EINVAL, "lbp_checkpoint_load: bad step index");
+    s->edits += 1;  // invalidates an adjoint recording
+    TRY(enter(s));
+    TRY(join_vacf(s));
+    CK(cudaStreamSynchronize(s->s0));
+    CK(cudaStreamSynchronize(s->s1));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const char *in = static_cast<const char *>(buf) + sizeof(h);
+    const size_t plane = (size_t)storage_bytes(s->precision) * (size_t)s->N;
+    const size_t pstride = (size_t)storage_bytes(s->precision) * (size_t)s->P;
+    for (int a = 0; a < Q; ++a)
+        CK(cudaMemcpyAsync(static_cast<char *>(s->f[s->cur]) + a * pstride, in + a * plane, plane, kind, s->s0));
+    in += Q * plane;
+    for (int k = 0; k < 3 && s->np > 0; ++k) {
+        CK(cudaMemcpyAsync(s->r + (size_t)k * s->cap, in + sizeof(double) * (size_t)k * s->np,
+                           sizeof(double) * s->np, kind, s->s0));
+        CK(cudaMemcpyAsync(s->v + (size_t)k * s->cap, in + sizeof(double) * (size_t)(3 + k) * s->np,
+                           sizeof(double) * s->np, kind, s->s0));
+    }
+    long long st = h[5];
+    CK(cudaMemcpyAsync(s->d_step, &st, sizeof(long long), cudaMemcpyHostToDevice, s->s0));
+    CK(cudaStreamSynchronize(s->s0));
+    s->step = h[5];
+    s->vacf_lag = -1;  // as lbp_set_step_index: the VACF restarts from a new configure
+    drop_graphs(s);
+    return leave(s);
+}
+
+lbp_status lbp_set_wait_bound(lbp_sim *s, int64_t cycles) {
+    CHECK_SIM(s);
+    if (cycles < 0) return fail(LBP_EINVAL, "lbp_set_wait_bound: cycles < 0");
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    s->wait_cycles = cycles == 0 ? DEFAULT_WAIT_CYCLES : (long long)cycles;
+    drop_graphs(s);  // the graphs hold the bound as a kernel parameter
+    return leave(s);
+}
+
+lbp_status lbp_set_wait_probe(lbp_sim *s, int enable) {
+    CHECK_SIM(s);
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    s->wait_probe = enable ? 1 : 0;
+    drop_graphs(s);  // the graphs hold the probe flag as a kernel parameter
+    return leave(s);
+}
+
+lbp_status lbp_budget_track(lbp_sim *s, int enable) {
+    CHECK_SIM(s);
+    TRY(enter(s));
+    CK(cudaStreamSynchronize(s->s0));
+    CK(cudaStreamSynchronize(s->s1));
+    if (enable) {
+        if (!s->inj) TRY(dalloc(&s->inj, 3));
+        CK(cudaMemsetAsync(s->inj, 0, 3 * sizeof(double), s->s0));
+        CK(cudaStreamSynchronize(s->s0));
+    } else if (s->inj) {
+        cudaFree(s->inj);
+        s->inj = nullptr;
+    }
+    drop_graphs(s);  // the particle kernel's arguments change
+    return leave(s);
+}
+
+lbp_status lbp_budget(lbp_sim *s, double *out) {
+    CHECK_SIM(s);
+    if (!out) return fail(LBP_EINVAL, "lbp_budget: null out");
+    TRY(enter(s));
+    const int nb = budget_blocks(*s);
+    if (!s->budget_part) TRY(dalloc(&s->budget_part, 4 * (size_t)nb));
+    CK(launch_budget(*s, s->f[s->cur], s->budget_part, s->s0));
+    std::vector<double> part(4 * (size_t)nb), v(3 * (size_t)s->np);
+    double inj[3] = {0.0, 0.0, 0.0};
+    CK(cudaMemcpyAsync(part.data(), s->budget_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s->s0));
+    for (int k = 0; k < 3 && s->np > 0; ++k)
+        CK(cudaMemcpyAsync(v.data() + (size_t)k * s->np, s->v + (size_t)k * s->cap, sizeof(double) * s->np,
+                           cudaMemcpyDeviceToHost, s->s0));
+    if (s->inj) CK(cudaMemcpyAsync(inj, s->inj, sizeof(inj), cudaMemcpyDeviceToHost, s->s0));
+    CK(cudaStreamSynchronize(s->s0));
+    // fixed-order sums on the host
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 4; ++k) tot[k] += part[4 * (size_t)b + k];
+    out[0] = (double)s->N + tot[0];
+    for (int k = 0; k < 3; ++k) {
+        out[1 + k] = tot[1 + k];
+        double pk = 0.0;
+        for (int i = 0; i < s->np; ++i) pk += s->h_mass[i] * v[(size_t)k * s->np + i];
+        out[4 + k] = pk;
+        out[7 + k] = s->inj ? inj[k] : 0.0;
+    }
+    return leave(s);
 }
 
 lbp_status lbp_set_use_graphs(lbp_sim *s, int enable) {

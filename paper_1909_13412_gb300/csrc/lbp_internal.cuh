@@ -164,6 +164,13 @@ constexpr int REC_F0 = 5;
 constexpr int ERR_NAN = 1;
 constexpr int ERR_RANGE = 2;
 constexpr int ERR_TIMEOUT = 4;  // a bounded wait on an mbarrier ran out
+constexpr int ERR_LATTICE = 8;  // a collided population became non-finite
+
+// True when the collided rest population of a node is not finite.  Every
+// population of the node enters it through rho~ - 1 and u.u (collide_values),
+// so a NaN or an infinity anywhere among the node's pulled values, or an
+// overflow of u.u, shows here: one comparison per node.
+__device__ __forceinline__ bool nonfinite_node(const float o[Q]) { return !(fabsf(o[0]) <= 3.4028234663852886e38f); }
 
 // ------------------------------------------------------------------ Philox
 // Philox-4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -205,6 +212,10 @@ struct Rep {
 };
 
 constexpr int MAX_BATCH = 256;
+
+// default bound of a device-side wait on an mbarrier, in SM clock cycles
+// (~0.5 s at 2 GHz)
+constexpr long long DEFAULT_WAIT_CYCLES = 1ll << 30;
 
 template <int MAXR>
 struct RepTable {
@@ -265,6 +276,8 @@ struct Sim {
     int variant = 0;  // lattice kernel: 0 one node per thread, 1 two nodes, 2 bulk-copy staged
     int dev = 0;
     int num_sms = 0;
+    long long wait_cycles = DEFAULT_WAIT_CYCLES;  // bound of every device-side wait (SM cycles)
+    int wait_probe = 0;  // 1: the staged kernel's waits run out on purpose (tests of the error path)
 
     cudaStream_t user = nullptr;  // caller's stream
     cudaStream_t s0 = nullptr;    // library main stream (non-blocking)
@@ -316,6 +329,11 @@ struct Sim {
     Tape tape;
     uint64_t edits = 0;  // state-changing calls other than steps (set_*, add)
 
+    // conservation budget: momentum put into the unpinned particles by F_R and
+    // F_ext since tracking began (FP64, [3]; null: not tracked)
+    double *inj = nullptr;
+    double *budget_part = nullptr;  // [budget_blocks][4]
+
     double *xbuf = nullptr;  // [9][cap]: f_ext, r, V of lbp_step_exchange (array-of-structures)
     int xbuf_cap = 0;
 
@@ -365,6 +383,8 @@ cudaError_t launch_set_equilibrium(Sim &s, const double *rho, const double *u, v
                                    cudaStream_t st);
 cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, double *p,
                           cudaStream_t st);
+int budget_blocks(const Sim &s);
+cudaError_t launch_budget(Sim &s, const void *src, double *out, cudaStream_t st);  // [budget_blocks][4]
 // particle_kernels.cu
 cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
@@ -377,7 +397,7 @@ cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long lon
 template <typename St, int MAXR, bool FORCED>
 cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, const unsigned long long *rec_cur,
                             unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump,
-                            int *err, int num_sms, cudaStream_t st);
+                            int *err, long long wait_cycles, int probe, int num_sms, cudaStream_t st);
 bool staged_kernel_ok(const Sim &s);  // every box: nx a multiple of 16 bytes of storage, nx <= STAGED_NODES
 int staged_rows(int nx, int ny);      // rows per item of the staged kernel
 constexpr int STAGED_NODES = 512;     // nodes per item (whole rows) of the staged kernel

@@ -16,14 +16,12 @@
 // work divides its FP64 instruction count per particle by 32; with one
 // particle per warp the FP64 work of the fit dominated the whole time step.
 //
-// Precision split.  FP64: positions, velocities, the cell/fraction of r, the
-// least-squares solve U_inf = (sum w.a)/(sum |a|^2), F_H, the random force
-// and the Langevin update.  FP32: the gathered u^N (the lattice is FP32), the
-// corner geometry (d_p, 1/r_p, the basis a_p, e^N) and the eight-point sums of
-// the normal equations.  The relative velocity w_p = u_p - V is formed as
-// (u_p - V_hi) - V_lo with V = V_hi + V_lo split into two floats, so it keeps
-// FP32 relative accuracy even when the particle moves with the fluid and u_p
-// and V nearly cancel.
+// Precision split.  FP32: the gathered u^N (the lattice arithmetic is FP32).
+// FP64: everything after the gather -- positions, velocities, the cell and
+// fraction of r, the relative velocities w_p = u_p - V, e^N, the corner
+// geometry, the basis a_p and the eight-point sums of the normal equation
+// with its solve U_inf = (sum w.a)/(sum |a|^2), F_H, the random force and the
+// Langevin update.
 //
 // Reaction forces are 64-bit fixed-point integers (scale 2^56).  -F_H is
 // converted once and split over the eight corners by the trilinear fractions
@@ -62,6 +60,7 @@ struct ParticleArgs {
     int ring_cap;
     long long *d_vacf;  // [0] first sampled step, [2] samples written
     int *err;
+    double *inj;        // [3] momentum put in by F_R + F_ext (null: not tracked)
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -80,6 +79,11 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     __shared__ long long s_fix[PB][3];
     __shared__ long long s_frac[PB][3];
     __shared__ int s_spread[PB];
+    // state read only by the Langevin update, staged by warp 1 so that warp 0
+    // (the FP64 fit) carries fewer registers across the gather
+    __shared__ double s_fe[3][PB];
+    __shared__ double s_invM[PB], s_sg[PB];
+    __shared__ unsigned char s_pin[PB];
     const int t = threadIdx.x, lane = t & 31;
     const int i0 = blockIdx.x * PB;
     const long long step = *A.d_step;
@@ -94,9 +98,15 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     // loads overlap this step's other memory round trips.
     const int ip = i0 + lane;
     double r0 = 0.0, r1 = 0.0, r2 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
-    double V0 = 0.0, V1 = 0.0, V2 = 0.0, gam = 0.0, Rd = 0.0, sg = 0.0, invM = 0.0;
-    double fe0 = 0.0, fe1 = 0.0, fe2 = 0.0;
-    bool pin = false;
+    double V0 = 0.0, V1 = 0.0, V2 = 0.0, gam = 0.0, Rd = 0.0;
+    if (t >= 32 && t < 64 && ip < A.np) {
+        s_invM[lane] = A.inv_mass[ip];
+        s_sg[lane] = A.sig[ip];
+        s_fe[0][lane] = A.fext[ip];
+        s_fe[1][lane] = A.fext[cap + ip];
+        s_fe[2][lane] = A.fext[2 * cap + ip];
+        s_pin[lane] = A.pinned[ip];
+    }
     if (t < 32 && ip < A.np) {
         r0 = A.r[ip];
         r1 = A.r[cap + ip];
@@ -106,12 +116,6 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
         V2 = A.v[2 * cap + ip];
         gam = A.gamma[ip];
         Rd = A.radius[ip];
-        sg = A.sig[ip];
-        invM = A.inv_mass[ip];
-        fe0 = A.fext[ip];
-        fe1 = A.fext[cap + ip];
-        fe2 = A.fext[2 * cap + ip];
-        pin = A.pinned[ip] != 0;
         s_rep[lane] = MAXR == 1 ? 0 : A.prep[ip];
         const double b0 = floor(r0), b1 = floor(r1), b2 = floor(r2);
         q0 = r0 - b0;
@@ -159,72 +163,75 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
         double F0 = 0.0, F1 = 0.0, F2 = 0.0;
         bool spread = true;
         if (A.mode == LBP_STOKESLET) {
-            // w_p = u_p - V in FP32 with V split as V_hi + V_lo
-            const float Vh0 = (float)V0, Vh1 = (float)V1, Vh2 = (float)V2;
-            const float Vl0 = (float)(V0 - (double)Vh0), Vl1 = (float)(V1 - (double)Vh1),
-                        Vl2 = (float)(V2 - (double)Vh2);
-            float w0[8], w1[8], w2[8];
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+            // Eq. 8 in FP64 from the FP32 corner velocities: w_p = u_p - V,
+            // e^N = mean(w)/|mean(w)|, d_p = x_p - r_i (exact: corner minus
+            // cell fraction), basis a_p = (1 - 3R/(4 r_p)) e^N - 3R (e^N.d_p)/(4 r_p^3) d_p,
+            // and the normal equation U_inf sum|a_p|^2 = sum w_p.a_p.  w_p is
+            // formed again in the corner loop from the shared corner velocities
+            // (holding all 24 would spill).
+            double m0 = 0.0, m1 = 0.0, m2 = 0.0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                w0[c] = (s_u[lane][c][0] - Vh0) - Vl0;
-                w1[c] = (s_u[lane][c][1] - Vh1) - Vl1;
-                w2[c] = (s_u[lane][c][2] - Vh2) - Vl2;
-                m0 += w0[c];
-                m1 += w1[c];
-                m2 += w2[c];
+                m0 += (double)s_u[lane][c][0];
+                m1 += (double)s_u[lane][c][1];
+                m2 += (double)s_u[lane][c][2];
             }
-            // e^N: direction of the mean relative velocity (scaled before the
-            // norm so that tiny velocities do not underflow)
-            const float sc = fmaxf(fabsf(m0), fmaxf(fabsf(m1), fabsf(m2)));
-            if (sc > 0.f) {
-                const float is = 1.f / sc;
-                const float n0 = m0 * is, n1 = m1 * is, n2 = m2 * is;
-                const float inrm = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
-                const float e0 = n0 * inrm, e1 = n1 * inrm, e2 = n2 * inrm;
-                const float R = (float)Rd;
-                const float R2 = R * R, R34 = 0.75f * R;
-                // corner offsets d_p = c - q
-                const float dx[2] = {(float)(-q0), (float)(1.0 - q0)};
-                const float dy[2] = {(float)(-q1), (float)(1.0 - q1)};
-                const float dz[2] = {(float)(-q2), (float)(1.0 - q2)};
-                float num = 0.f, den = 0.f;
+            m0 -= 8.0 * V0;
+            m1 -= 8.0 * V1;
+            m2 -= 8.0 * V2;
+            if (m0 != 0.0 || m1 != 0.0 || m2 != 0.0) {
+                double mm = m0 * m0 + m1 * m1 + m2 * m2;
+                if (!(mm > 1e-280)) {
+                    // tiny mean: rescale before the norm so that it does not underflow
+                    const double sc = 1.0 / fmax(fabs(m0), fmax(fabs(m1), fabs(m2)));
+                    m0 *= sc;
+                    m1 *= sc;
+                    m2 *= sc;
+                    mm = m0 * m0 + m1 * m1 + m2 * m2;
+                }
+                const double inrm = rsqrt(mm);
+                const double e0 = m0 * inrm, e1 = m1 * inrm, e2 = m2 * inrm;
+                const double R34 = 0.75 * Rd, R2 = Rd * Rd;
+                const double dx[2] = {-q0, 1.0 - q0}, dy[2] = {-q1, 1.0 - q1}, dz[2] = {-q2, 1.0 - q2};
+                double num = 0.0, den = 0.0;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float d0 = dx[c & 1], d1 = dy[(c >> 1) & 1], d2 = dz[(c >> 2) & 1];
-                    const float rr = d0 * d0 + d1 * d1 + d2 * d2;
-                    if (rr < 1e-24f) continue;
+                    const double d0 = dx[c & 1], d1 = dy[(c >> 1) & 1], d2 = dz[(c >> 2) & 1];
+                    const double rr = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (rr < 1e-24) continue;
                     if (A.exclude_inside && rr < R2) continue;
-                    const float ir = rsqrtf(rr);
-                    const float x = e0 * d0 + e1 * d1 + e2 * d2;
-                    const float k1 = 1.f - R34 * ir;
-                    const float k2 = R34 * x * ir * ir * ir;
-                    const float a0 = k1 * e0 - k2 * d0, a1 = k1 * e1 - k2 * d1, a2 = k1 * e2 - k2 * d2;
-                    num += w0[c] * a0 + w1[c] * a1 + w2[c] * a2;
+                    const double ir = rsqrt(rr);
+                    const double x = e0 * d0 + e1 * d1 + e2 * d2;
+                    const double k1 = 1.0 - R34 * ir;
+                    const double k2 = R34 * x * (ir * ir * ir);
+                    const double a0 = k1 * e0 - k2 * d0, a1 = k1 * e1 - k2 * d1, a2 = k1 * e2 - k2 * d2;
+                    const double w0 = (double)s_u[lane][c][0] - V0;
+                    const double w1 = (double)s_u[lane][c][1] - V1;
+                    const double w2 = (double)s_u[lane][c][2] - V2;
+                    num += w0 * a0 + w1 * a1 + w2 * a2;
                     den += a0 * a0 + a1 * a1 + a2 * a2;
                 }
-                // one-parameter normal equation U sum|a|^2 = sum w.a, solved in FP64
-                const double U = den > 0.f ? (double)num / (double)den : 0.0;
+                const double U = den > 0.0 ? num / den : 0.0;
                 const double gU = gam * U;
-                F0 = gU * (double)e0;
-                F1 = gU * (double)e1;
-                F2 = gU * (double)e2;
+                F0 = gU * e0;
+                F1 = gU * e1;
+                F2 = gU * e2;
             }
         } else if (A.mode == LBP_POINTWISE) {
-            // Eq. 7 with u(r_i) = sum_p W_p u^N_p (trilinear)
-            const float fx = (float)q0, fy = (float)q1, fz = (float)q2;
-            const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
-            float ur0 = 0.f, ur1 = 0.f, ur2 = 0.f;
+            // Eq. 7 with u(r_i) = sum_p W_p u^N_p (trilinear weights of the cell
+            // fraction), in FP64
+            const double wx[2] = {1.0 - q0, q0}, wy[2] = {1.0 - q1, q1}, wz[2] = {1.0 - q2, q2};
+            double ur0 = 0.0, ur1 = 0.0, ur2 = 0.0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const float Wp = wx[c & 1] * wy[(c >> 1) & 1] * wz[(c >> 2) & 1];
-                ur0 += Wp * s_u[lane][c][0];
-                ur1 += Wp * s_u[lane][c][1];
-                ur2 += Wp * s_u[lane][c][2];
+                const double Wp = wx[c & 1] * wy[(c >> 1) & 1] * wz[(c >> 2) & 1];
+                ur0 += Wp * (double)s_u[lane][c][0];
+                ur1 += Wp * (double)s_u[lane][c][1];
+                ur2 += Wp * (double)s_u[lane][c][2];
             }
-            F0 = -gam * (V0 - (double)ur0);
-            F1 = -gam * (V1 - (double)ur1);
-            F2 = -gam * (V2 - (double)ur2);
+            F0 = -gam * (V0 - ur0);
+            F1 = -gam * (V1 - ur1);
+            F2 = -gam * (V2 - ur2);
         } else {
             // Eq. 6: friction against a fluid at rest; nothing is returned to the fluid
             F0 = -gam * V0;
@@ -260,12 +267,13 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double tt = __fma_rn(__ull2double_rn(2ull * (ctr[k] >> 11) + 1ull), 0x1.0p-53, -1.0);
-            R3[k] = __dmul_rn(sg, __dmul_rn(A.sqrt3, tt));
+            R3[k] = __dmul_rn(s_sg[lane], __dmul_rn(A.sqrt3, tt));
         }
         const double FH3[3] = {F0, F1, F2};
         const double Vo[3] = {V0, V1, V2};
         const double ro[3] = {r0, r1, r2};
-        const double fe[3] = {fe0, fe1, fe2};
+        const double invM = s_invM[lane];
+        const bool pin = s_pin[lane] != 0;
         const Rep &ri = rt.rep[MAXR == 1 ? 0 : s_rep[lane]];
         const int L[3] = {ri.nx, ri.ny, ri.nz};
         double Vn[3] = {V0, V1, V2};
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
             A.fr[k * cap + i] = R3[k];
             if (!pin) {
                 // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
-                Vn[k] = Vo[k] + (FH3[k] + R3[k] + fe[k]) * invM;
+                Vn[k] = Vo[k] + (FH3[k] + R3[k] + s_fe[k][lane]) * invM;
                 double rn = ro[k] + Vn[k];
                 if (rn < 0.0) rn += (double)L[k];
                 if (rn >= (double)L[k]) rn -= (double)L[k];
@@ -288,6 +296,9 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
             }
         }
         if (bad) atomicOr(A.err, ERR_NAN);
+        if (A.inj)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s_fe[k][lane] = pin ? 0.0 : R3[k] + s_fe[k][lane];
         if (A.ring) {
             const long long m = step - A.d_vacf[0];
             if (m >= 0) {
@@ -299,6 +310,19 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
         }
     }
     __syncthreads();
+
+    if (A.inj && t < 32) {
+        // conservation budget: the momentum F_R + F_ext put into the block's
+        // unpinned particles (left in s_fe by phase B), summed over the warp,
+        // one FP64 atomic per component
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double vk = ip < A.np ? s_fe[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vk += __shfl_xor_sync(0xffffffffu, vk, o);
+            if (lane == 0) atomicAdd(A.inj + k, vk);
+        }
+    }
 
     // ---- phase C: share of corner p of the fixed-point reaction force -F_H.
     // Per axis the far corner (c = 1) takes floor(v q) -- the signed high half
@@ -375,6 +399,7 @@ cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t s
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
+    A.inj = s.inj;
     const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
     if (s.nrep == 1) {
         RepTable<1> t;

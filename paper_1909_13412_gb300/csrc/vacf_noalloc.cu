@@ -13,9 +13,11 @@
 //
 // The correlation itself is the same blocked all-origin estimator as the
 // library's stateful VACF (vacf_kernels.cu): for every block of up to 64 new
-// samples t and every lag k <= max_lag it adds V(t).V(t - k), products in
-// FP32, sums in FP64.  Here the samples are the caller's whole trajectory
-// instead of the library's ring.
+// samples t and every lag k <= max_lag it adds V(t).V(t - k).  Products are
+// FP32; each lane sums the products of one component over one block (at most
+// 64 terms) in FP32 and adds that to an FP64 accumulator, and everything
+// above that (components, chunks, blocks) is summed in FP64.  Here the
+// samples are the caller's whole trajectory instead of the library's ring.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -50,9 +52,9 @@ __global__ void __launch_bounds__(256) k_corr_noalloc(const float *__restrict__ 
     const int k0 = blockIdx.x * NKT;
     const int jc0 = blockIdx.y * NJCH;
     const long long s_lo = tb - k0 - (NKT - 1);
-    float acc[NLW];
+    double dacc[NLW];
 #pragma unroll
-    for (int m = 0; m < NLW; ++m) acc[m] = 0.f;
+    for (int m = 0; m < NLW; ++m) dacc[m] = 0.0;
     for (int js = 0; js < NJCH; js += NJ) {
         const int jb = jc0 + js;
         if (jb >= ncomp) break;
@@ -72,6 +74,10 @@ __global__ void __launch_bounds__(256) k_corr_noalloc(const float *__restrict__ 
         // 16 samples at a time against the 31 window values they meet, in
         // registers with static indices
         const int base0 = NKT - 1 - NLW * warp;
+        // FP32 holds one component's products over this block only
+        float acc[NLW];
+#pragma unroll
+        for (int m = 0; m < NLW; ++m) acc[m] = 0.f;
 #pragma unroll 1
         for (int tc = 0; tc < NB; tc += NLW) {
             float a[NLW], w[2 * NLW - 1];
@@ -84,10 +90,12 @@ __global__ void __launch_bounds__(256) k_corr_noalloc(const float *__restrict__ 
 #pragma unroll
                 for (int m = 0; m < NLW; ++m) acc[m] = fmaf(a[i], w[i - m + NLW - 1], acc[m]);
         }
+#pragma unroll
+        for (int m = 0; m < NLW; ++m) dacc[m] += (double)acc[m];
     }
 #pragma unroll
     for (int m = 0; m < NLW; ++m) {
-        double v = (double)acc[m];
+        double v = dacc[m];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int k = k0 + NLW * warp + m;
@@ -115,7 +123,9 @@ lbp_status lbp_set_error_for_noalloc(lbp_status st, const char *msg);
 
 // One-time set-up per device happens inside the first call on that device
 // (cudaGetSymbolAddress with the device current): make that first call
-// before any CUDA graph capture that includes this routine.
+// before any CUDA graph capture that includes this routine.  The address is
+// kept for the life of the process, so the routine must not be used on a
+// device after cudaDeviceReset has torn down its context.
 extern "C" lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T, int ncomp,
                                                  int max_lag, int npairs, double *csum,
                                                  int64_t *counts, void *stream) {
@@ -124,11 +134,16 @@ extern "C" lbp_status lbp_vacf_correlate_noalloc(const float *samples, int64_t T
                                          "lbp_vacf_correlate_noalloc: need T >= 0, ncomp >= 1, max_lag >= 0, npairs >= 0");
     if (!csum || !counts || (T > 0 && !samples))
         return lbp_set_error_for_noalloc(LBP_EINVAL, "lbp_vacf_correlate_noalloc: null pointer");
-    const long long nchunks = (ncomp + NJCH - 1) / NJCH;
-    if (nchunks * (long long)(max_lag + 1) > SCRATCH_DOUBLES)
+    const long long nchunks = ((long long)ncomp + NJCH - 1) / NJCH;
+    // both factors are at least 1, so this also bounds max_lag (and with it the
+    // grid sizes below) by the scratch size
+    if (nchunks * ((long long)max_lag + 1) > SCRATCH_DOUBLES)
         return lbp_set_error_for_noalloc(
             LBP_EINVAL,
             "lbp_vacf_correlate_noalloc: ceil(ncomp / 1024) * (max_lag + 1) exceeds the 524288-entry scratch");
+    if (nchunks > 65535)
+        return lbp_set_error_for_noalloc(LBP_EINVAL,
+                                         "lbp_vacf_correlate_noalloc: ncomp > 65535 * 1024 (one grid row per chunk)");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return lbp_set_error_for_noalloc(LBP_ECUDA, cudaGetErrorString(e));

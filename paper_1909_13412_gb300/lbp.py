@@ -76,6 +76,13 @@ _SIGS = {
     "lbp_set_fluid": [_vp, _vp, _vp, C.c_int],
     "lbp_vacf_read_per_particle": [_vp, _vp, _vp, C.c_int],
     "lbp_check": [_vp],
+    "lbp_budget_track": [_vp, C.c_int],
+    "lbp_budget": [_vp, _vp],
+    "lbp_set_wait_bound": [_vp, C.c_int64],
+    "lbp_set_wait_probe": [_vp, C.c_int],
+    "lbp_checkpoint_size": [_vp, C.POINTER(C.c_size_t)],
+    "lbp_checkpoint_save": [_vp, _vp, C.c_int],
+    "lbp_checkpoint_load": [_vp, _vp, C.c_int],
     "lbp_set_use_graphs": [_vp, C.c_int],
     "lbp_diagnostics": [_vp, _vp, C.c_int],
     "lbp_timing_enable": [_vp, C.c_int],
@@ -479,3 +486,43 @@ def lbp_vacf_correlate_noalloc(samples, T, ncomp, max_lag, npairs, csum, counts,
     s = C.c_void_p(stream.cuda_stream if stream is not None else 0)
     _call("lbp_vacf_correlate_noalloc", a[0], int(T), int(ncomp), int(max_lag), int(npairs), b[0],
           c[0], s)
+
+
+def lbp_budget_track(h: Handle, enable=True):
+    _call("lbp_budget_track", h.ptr, int(bool(enable)))
+
+
+def lbp_budget(h: Handle):
+    """[mass, fluid momentum (3), particle momentum (3), injected momentum (3)]."""
+    out = np.zeros(10)
+    _call("lbp_budget", h.ptr, C.c_void_p(out.ctypes.data))
+    return out
+
+
+def lbp_set_wait_bound(h: Handle, cycles):
+    _call("lbp_set_wait_bound", h.ptr, int(cycles))
+
+
+def lbp_checkpoint_size(h: Handle) -> int:
+    n = C.c_size_t()
+    _call("lbp_checkpoint_size", h.ptr, C.byref(n))
+    return n.value
+
+
+def lbp_checkpoint_save(h: Handle, buf=None):
+    """Write a checkpoint into buf (a uint8 numpy array or CUDA tensor of
+    lbp_checkpoint_size bytes; None: a new numpy array) and return it."""
+    if buf is None:
+        buf = np.empty(lbp_checkpoint_size(h), np.uint8)
+    a = _ptr(buf, np.uint8, lbp_checkpoint_size(h), "buf", True)
+    _call("lbp_checkpoint_save", h.ptr, a[0], a[1])
+    return buf
+
+
+def lbp_checkpoint_load(h: Handle, buf):
+    a = _ptr(buf, np.uint8, None, "buf")
+    _call("lbp_checkpoint_load", h.ptr, a[0], a[1])
+
+
+def lbp_set_wait_probe(h: Handle, enable):
+    _call("lbp_set_wait_probe", h.ptr, int(bool(enable)))

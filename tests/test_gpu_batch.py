@@ -355,3 +355,58 @@ def test_adjoint_of_a_batch_equals_its_boxes_alone():
             assert ob["tau"][0] != 0.0
         p0 += nb
         node0 += Nb
+
+
+def test_batch_boxes_against_the_oracle():
+    """Three boxes of different sizes and relaxation times (tau = 0.6, 0.8, 1.0)
+    with particles in one handle, each compared with the FP64 oracle of that
+    box alone after 60 steps at the tolerances of the single-box coupled test
+    (V and F_H to 1e-5 relative, r to 1e-6, populations to 1e-5 of the deviation
+    scale).  kT = 0: a box's random force is keyed by the particle's index in
+    the whole handle, which the oracle of one box does not share."""
+    import oracle
+    boxes = [(20, 18, 16, 0.6), (33, 7, 12, 0.8), (24, 10, 6, 1.0)]
+    npart = [5, 3, 4]
+    states = []
+    for b, (nx, ny, nz, tau) in enumerate(boxes):
+        f = wl.perturbed_populations(W, (nz, ny, nx), 0.02, 200 + b)
+        ps = wl.uniform_particles(npart[b], (nz, ny, nx), 6.0, 0.5, 0.0, 0.0, 40 + b, 50 + b)
+        ps.R = np.full(ps.n, wl.stokes_radius(0.5, tau))
+        ps.V = np.random.default_rng(60 + b).normal(0.0, 0.01, (ps.n, 3))
+        states.append((f, ps))
+    h = lbp.lbp_create_batch(boxes)
+    lbp.lbp_set_populations(h, np.concatenate([f.reshape(Q, -1) for f, _ in states], axis=1))
+    for b, (_, ps) in enumerate(states):
+        lbp.lbp_particles_add_to(h, b, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=0.0, seed=3)
+    lbp.lbp_step(h, 60)
+    lbp.lbp_check(h)
+    N = sum(nx * ny * nz for nx, ny, nz, _ in boxes)
+    fall = np.empty((Q, N))
+    lbp.lbp_read_populations(h, fall)
+    n = sum(npart)
+    r, V, FH, FR = (np.empty((n, 3)) for _ in range(4))
+    lbp.lbp_particles_read(h, r, V, FH, FR)
+    lbp.lbp_destroy(h)
+    off, p0 = 0, 0
+    for b, (nx, ny, nz, tau) in enumerate(boxes):
+        f, ps = states[b]
+        o = oracle.Sim(nx, ny, nz, tau)
+        o.set_fhat(f)
+        o.add_particles(ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        o.set_params(kT=0.0, seed=3)
+        o.step(60)
+        ro, Vo, FHo, _ = o.particles()
+        fo = o.fhat()
+        o.close()
+        sl = slice(p0, p0 + ps.n)
+        assert np.max(np.abs(V[sl] - Vo)) <= 1e-5 * np.max(np.abs(Vo)), b
+        assert np.max(np.abs(FH[sl] - FHo)) <= 1e-5 * np.max(np.abs(FHo)), b
+        d = np.abs(r[sl] - ro)
+        d = np.minimum(d, np.array([nx, ny, nz], float) - d)
+        assert np.max(d) <= 1e-6, b
+        fb = fall[:, off:off + nx * ny * nz].reshape(Q, nz, ny, nx)
+        scale = np.max(np.abs(fo - W[:, None, None, None]))
+        assert np.max(np.abs(fb - fo)) <= 1e-5 * scale + 1e-14, b
+        off += nx * ny * nz
+        p0 += ps.n

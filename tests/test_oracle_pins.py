@@ -525,3 +525,61 @@ def test_pointwise_pin_catches_a_swapped_corner_weight(tmp_path):
     FH = _pointwise_first_step_force(oracle.bind(str(so)), r, V, gamma, _U0, _A)
     expect = -gamma * (V - (_U0 + _A @ r))
     assert not np.allclose(FH, expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
+# ------------------------------------------------------------ MSD (Section 3 dispersion)
+def test_msd_equals_the_double_sum_of_velocity_products():
+    """With X(t) the running sum of the velocities (Eq. 2 without the wrap), the
+    displacement over k steps is the sum of the k velocities after the origin,
+    so M(k) = sum_{i,t0} sum_{a,b=1..k} V_i(t0+a).V_i(t0+b) (brute force)."""
+    g = np.random.default_rng(7)
+    T, n, K = 23, 3, 9
+    V = g.standard_normal((T, n, 3))
+    X = np.cumsum(V, axis=0) + g.uniform(0, 50, (1, n, 3))
+    ms, cnt = oracle.msd(X, K)
+    for k in range(K + 1):
+        ref = 0.0
+        for t0 in range(T - k):
+            w = V[t0 + 1:t0 + k + 1]  # [k, n, 3]
+            ref += np.einsum("anc,bnc->", w, w)
+        assert ms[k] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+        assert cnt[k] == n * (T - k)
+
+
+def test_msd_of_uniform_motion_is_ballistic():
+    T, K = 40, 12
+    V = np.array([[0.01, -0.02, 0.005], [0.0, 0.003, 0.0]])
+    X = np.arange(T)[:, None, None] * V[None] + 3.0
+    ms, cnt = oracle.msd(X, K)
+    k = np.arange(K + 1)
+    assert np.allclose(ms, (T - k) * k ** 2 * (V ** 2).sum(), rtol=1e-12, atol=1e-20)
+
+
+def test_msd_of_the_ornstein_uhlenbeck_process():
+    """Eq. 6 mode: the discrete OU process with C(m) = 3 s2 a^m (s2 the stationary
+    variance per component, a = 1 - gamma/M) has
+    E|X(t0+k) - X(t0)|^2 = 3 s2 [k + 2 sum_{m<k} (k - m) a^m], which tends to
+    6 D k with D = kT/gamma (Einstein): oracle trajectory vs closed form."""
+    M, gamma, kT = 4.0, 1.0, 1e-4
+    a = 1 - gamma / M
+    n, T, K = 300, 1200, 60
+    s = oracle.Sim(2, 2, 2, 0.8)
+    g = np.random.default_rng(1)
+    s.add_particles(g.uniform(0, 2, (n, 3)), g.standard_normal((n, 3)) * math.sqrt(kT / M),
+                    np.full(n, M), np.full(n, gamma), np.full(n, 0.2))
+    s.set_params(kT=kT, seed=4, mode=oracle.BROWNIAN)
+    Vt = []
+    for _ in range(T):
+        s.step(1)
+        Vt.append(s.particles()[1])
+    Vt = np.array(Vt)[100:]
+    X = np.cumsum(Vt, axis=0)
+    ms, cnt = oracle.msd(X, K)
+    s2 = (2 * gamma * kT / M ** 2) / (1 - a * a)
+    k = np.arange(K + 1)
+    expect = np.array([3 * s2 * (kk + 2 * sum((kk - m) * a ** m for m in range(1, kk))) for kk in k])
+    assert np.allclose(ms[1:] / cnt[1:], expect[1:], rtol=0.06)
+    # long lags: 6 D k with D = kT / gamma, up to the finite-k correction
+    D = kT / gamma
+    corr = 1 - 2 * a * (1 - a ** K) / (K * (1 - a) * (1 + a))
+    assert ms[K] / cnt[K] / (6 * D * K) == pytest.approx(corr, rel=0.06)

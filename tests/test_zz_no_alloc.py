@@ -12,6 +12,7 @@ in the shared scratch.  The file is named so that pytest collects it last.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1909_13412_gb300 import lbp
 from paper_1909_13412_gb300 import workloads as wl
 
@@ -59,6 +60,35 @@ def test_noalloc_vacf_matches_regular_vacf_twice():
         assert np.max(np.abs(got - ref)) <= 1e-6 * ref[0], call
 
 
+def _noalloc(samples, T, ncomp, K, npairs):
+    cs = torch.full((K + 1,), np.nan, dtype=torch.float64, device="cuda")
+    cnt = torch.full((K + 1,), -1, dtype=torch.int64, device="cuda")
+    lbp.lbp_vacf_correlate_noalloc(samples, T, ncomp, K, npairs, cs, cnt)
+    torch.cuda.synchronize()
+    return cs.cpu().numpy(), cnt.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,K,T", [(400, 300, 420), (700, 333, 701)])
+def test_noalloc_vacf_matches_the_oracle_over_several_tiles_and_chunks(n, K, T):
+    """Several ragged lag tiles (128 lags per CTA) and component chunks (1024 per
+    CTA): 400 particles = 1200 components (2 chunks), 700 = 2100 (3 chunks).
+    Compared with the oracle's FP64 correlation (Section 3 estimator) of the same
+    FP32 samples, twice in a row through the shared scratch."""
+    g = np.random.default_rng(n)
+    # velocities with a slowly decaying correlation, like a Brownian trajectory
+    V = np.empty((T, n, 3))
+    V[0] = g.standard_normal((n, 3)) * 0.005
+    for t in range(1, T):
+        V[t] = 0.97 * V[t - 1] + 0.0012 * g.standard_normal((n, 3))
+    V32 = V.astype(np.float32)
+    ref, ref_cnt = oracle.vacf(V32.astype(np.float64), K)
+    samples = torch.from_numpy(np.ascontiguousarray(V32.reshape(T, 3 * n))).cuda()
+    for call in range(2):
+        got, got_cnt = _noalloc(samples, T, 3 * n, K, n)
+        assert np.array_equal(got_cnt, ref_cnt), call
+        assert np.max(np.abs(got - ref)) <= 1e-6 * ref[0], call
+
+
 def test_noalloc_vacf_rejects_sizes_beyond_its_scratch():
     samples = torch.zeros((4, 3000), dtype=torch.float32, device="cuda")
     K = 524288 // 3  # 3 chunks of 1024 components x (K + 1) lags > 524288
@@ -67,4 +97,12 @@ def test_noalloc_vacf_rejects_sizes_beyond_its_scratch():
     with pytest.raises(lbp.LbpError) as ei:
         lbp.lbp_vacf_correlate_noalloc(samples, 4, 3000, K, 1000, cs, cnt)
     assert ei.value.status == lbp.LBP_EINVAL
+    assert "scratch" in lbp.lbp_last_error()
+    # a lag count whose + 1 would overflow a 32-bit int is rejected, not wrapped
+    # (straight through the C ABI: the binding would refuse the short outputs)
+    import ctypes
+    st = lbp.load().lbp_vacf_correlate_noalloc(ctypes.c_void_p(samples.data_ptr()), 4, 3000, 2 ** 31 - 1,
+                                               1000, ctypes.c_void_p(cs.data_ptr()),
+                                               ctypes.c_void_p(cnt.data_ptr()), ctypes.c_void_p(0))
+    assert st == lbp.LBP_EINVAL
     assert "scratch" in lbp.lbp_last_error()
