@@ -55,7 +55,8 @@ VACF_LAG = 5000
 SHAPE_NAMES = [{0: "1node", 1: "2nodes", 3: "4nodes"}[v] + ("_1row" if r == 1 else f"_{r}rows")
                if v != 2 else "bulk_staged" for v, r in AUTOTUNE_SHAPES]
 SHAPES = dict(zip(SHAPE_NAMES, AUTOTUNE_SHAPES))
-LAUNCHES_PER_STEP = 2  # particles, stream-collide (+2 VACF kernels every 64 steps)
+LAUNCHES_PER_STEP = 2  # particles, stream-collide
+VACF_LAUNCHES = 5      # per block of 64 samples: correlator, chunk sum, MSD scan, MSD diagonals, sums
 
 
 def workload(name):
@@ -547,10 +548,11 @@ def run_gpu(args, w):
         "autotune": tuned,
         "variants": variants,
         # per step the particle kernel and the lattice kernel; per block of 64
-        # samples the VACF kernels (two, or one per-particle), and the same once
-        # more for the flush of the last, partial block at the end of the region
+        # samples the VACF and MSD kernels (five, or one per-particle VACF
+        # kernel), and the same once more for the flush of the last, partial
+        # block at the end of the region
         "gpu_launches": LAUNCHES_PER_STEP * args.steps
-                        + (1 if isinstance(w, wl.Ensemble) else 2) * (args.steps // 64 + 1),
+                        + (1 if isinstance(w, wl.Ensemble) else VACF_LAUNCHES) * (args.steps // 64 + 1),
         "timing": "headline on the graph-replay path without per-launch events; the lattice "
                   "kernel's average from a second, instrumented pass of the same steps",
         "clocks": clk.summary(),

@@ -238,6 +238,19 @@ lbp_status lbp_get_step_index(lbp_sim *sim, int64_t *step);
 lbp_status lbp_vacf_configure(lbp_sim *sim, int max_lag);
 lbp_status lbp_vacf_read(lbp_sim *sim, double *csum, int64_t *counts, int on_device);
 
+/* Mean squared displacement of the particles over the same samples and lags
+ * (the dispersion that accompanies the VACF of Section 3): msum[k] = sum over
+ * particles i and origins t0 with t0 + k <= last sample of
+ * |X_i(t0 + k) - X_i(t0)|^2, X the unwrapped position (X(t) - X(t - 1) = V(t),
+ * the update of Eq. 2 before the periodic wrap), counts[k] as for
+ * lbp_vacf_read.  Kept alongside the VACF of lbp_vacf_configure (not with
+ * per_particle = 1); computed from the same per-sample products
+ * G(t, m) = sum_i V_i(t).V_i(t - m) through the exact recurrence
+ * W(e, k) = W(e - 1, k - 1) + G(e, 0) + 2 sum_{m=1}^{k-1} G(e, m) of the
+ * squared window sums W, in FP64 (products FP32).  Reading flushes the
+ * samples not yet correlated, as lbp_vacf_read does.                         */
+lbp_status lbp_msd_read(lbp_sim *sim, double *msum, int64_t *counts, int on_device);
+
 /* The same estimator kept per particle, for ensembles whose particles are not
  * alike (a batch of boxes of different sizes or viscosities, Section 3's
  * dependence of the VACF on L and nu): per_particle = 0 is lbp_vacf_configure;

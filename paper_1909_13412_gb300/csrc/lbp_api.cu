@@ -451,14 +451,14 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     }
     if (st == LBP_OK) st = dalloc(&s->d_step, 1);
     if (st == LBP_OK) st = dalloc(&s->d_err, 1);
-    if (st == LBP_OK) st = dalloc(&s->d_vacf, 4);
+    if (st == LBP_OK) st = dalloc(&s->d_vacf, 8);
 
     if (st != LBP_OK) return bail(st);
     e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = launch_fill_rest(*s, s->f[i], s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_step, 0, sizeof(long long), s->s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->s0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_vacf, 0, 4 * sizeof(long long), s->s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_vacf, 0, 8 * sizeof(long long), s->s0);
 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->s0);
     if (e != cudaSuccess) {
@@ -479,7 +479,8 @@ lbp_status lbp_destroy(lbp_sim *s) {
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext, s->xbuf,
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
-                    s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage, s->inj, s->budget_part};
+                    s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage, s->inj, s->budget_part,
+                    s->corr_g, s->corr_h, s->corr_w, s->msd_state, s->msd_sum};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
@@ -962,8 +963,9 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     CK(cudaStreamSynchronize(s->s0));
     drop_graphs(s);
     s->vacf_lag = -1;
-    void **bufs[] = {(void **)&s->ring, (void **)&s->vacf_sum, (void **)&s->vacf_cnt,
-                     (void **)&s->vacf_part};
+    void **bufs[] = {(void **)&s->ring,   (void **)&s->vacf_sum, (void **)&s->vacf_cnt,
+                     (void **)&s->vacf_part, (void **)&s->corr_g, (void **)&s->corr_h,
+                     (void **)&s->corr_w, (void **)&s->msd_state, (void **)&s->msd_sum};
     for (void **b : bufs)
         if (*b) {
             cudaFree(*b);
@@ -983,12 +985,23 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     if (per_particle && (nsum > ((size_t)1 << 28) || s->np > 65535))
         return fail(LBP_EINVAL,
                     "lbp_vacf_configure_ex: per particle needs n_particles <= 65535 and n_particles * (max_lag + 1) <= 2^28");
+    const size_t K1 = (size_t)max_lag + 1;
     TRY(dalloc(&s->vacf_sum, nsum));
-    TRY(dalloc(&s->vacf_cnt, (size_t)max_lag + 1));
-    TRY(dalloc(&s->vacf_part, (size_t)s->vacf_nchunks * (max_lag + 1)));
+    TRY(dalloc(&s->vacf_cnt, K1));
     CK(cudaMemsetAsync(s->vacf_sum, 0, sizeof(double) * nsum, s->s0));
-    CK(cudaMemsetAsync(s->vacf_cnt, 0, sizeof(long long) * (max_lag + 1), s->s0));
-    long long hv[4] = {s->step, 0, 0, 0};
+    CK(cudaMemsetAsync(s->vacf_cnt, 0, sizeof(long long) * K1, s->s0));
+    if (!per_particle) {
+        const int B = vacf_block_samples();
+        TRY(dalloc(&s->vacf_part, (size_t)s->vacf_nchunks * B * K1));
+        TRY(dalloc(&s->corr_g, (size_t)B * K1));
+        TRY(dalloc(&s->corr_h, (size_t)B * K1));
+        TRY(dalloc(&s->corr_w, (size_t)B * K1));
+        TRY(dalloc(&s->msd_state, 2 * K1));
+        TRY(dalloc(&s->msd_sum, K1));
+        CK(cudaMemsetAsync(s->msd_state, 0, sizeof(double) * 2 * K1, s->s0));
+        CK(cudaMemsetAsync(s->msd_sum, 0, sizeof(double) * K1, s->s0));
+    }
+    long long hv[8] = {s->step, 0, 0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(s->d_vacf, hv, sizeof(hv), cudaMemcpyHostToDevice, s->s0));
     CK(cudaStreamSynchronize(s->s0));
     s->vacf_lag = max_lag;
@@ -1017,6 +1030,22 @@ lbp_status lbp_vacf_read(lbp_sim *s, double *csum, int64_t *counts, int on_devic
     if (s->vacf_lag < 0) return fail(LBP_ESTATE, "lbp_vacf_read: VACF not configured");
     if (s->vacf_pp) return fail(LBP_ESTATE, "lbp_vacf_read: configured per particle; use lbp_vacf_read_per_particle");
     return vacf_read_impl(s, csum, counts, on_device, 1);
+}
+
+lbp_status lbp_msd_read(lbp_sim *s, double *msum, int64_t *counts, int on_device) {
+    CHECK_SIM(s);
+    if (s->vacf_lag < 0) return fail(LBP_ESTATE, "lbp_msd_read: VACF not configured (lbp_vacf_configure)");
+    if (s->vacf_pp) return fail(LBP_ESTATE, "lbp_msd_read: not kept when the VACF is configured per particle");
+    TRY(enter(s));
+    TRY(join_vacf(s));
+    CK(launch_vacf_block(*s, true, s->s0));
+    s->vacf_done_host = s->step - s->vacf_t0;
+    const size_t K1 = (size_t)s->vacf_lag + 1;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (msum) CK(cudaMemcpyAsync(msum, s->msd_sum, sizeof(double) * K1, kind, s->s0));
+    if (counts) CK(cudaMemcpyAsync(counts, s->vacf_cnt, sizeof(long long) * K1, kind, s->s0));
+    if (!on_device) CK(cudaStreamSynchronize(s->s0));
+    return leave(s);
 }
 
 lbp_status lbp_vacf_read_per_particle(lbp_sim *s, double *csum, int64_t *counts, int on_device) {

@@ -323,8 +323,14 @@ struct Sim {
     long long vacf_t0 = 0;        // step index of sample 0
     double *vacf_sum = nullptr;   // [K + 1]
     long long *vacf_cnt = nullptr;
-    double *vacf_part = nullptr;  // [nchunks][K + 1]
+    float *vacf_part = nullptr;   // [nchunks][64][K + 1] per-chunk G(t, k) of a block
     int vacf_nchunks = 0;
+    // mean squared displacement (with the ensemble VACF, not per particle)
+    double *corr_g = nullptr;     // [64][K + 1] G(t, k) of the block
+    double *corr_h = nullptr;     // [64][K + 1] H(t, k)
+    double *corr_w = nullptr;     // [64][K + 1] W(e, k)
+    double *msd_state = nullptr;  // [2][K + 1] W(last sample, k), by parity
+    double *msd_sum = nullptr;    // [K + 1]
 
     Tape tape;
     uint64_t edits = 0;  // state-changing calls other than steps (set_*, add)

@@ -1,17 +1,34 @@
-// vacf_kernels.cu -- velocity autocorrelation accumulator of liblbp (sm_103a).
+// vacf_kernels.cu -- velocity autocorrelation and mean squared displacement
+// accumulators of liblbp (sm_103a).
 //
 // C(k) = sum_i sum_{t0} V_i(t0).V_i(t0 + k) over all time origins (the VACF of
-// Section 3 / Fig. 2).  The particle kernel writes every step's velocities
-// (FP32) into a ring of K + B samples.  Every B = 64 samples the correlator
-// adds, for the B new samples t and every lag k <= K, the products
-// V(t).V(t - k): a dense contraction over the 3 n_p velocity components.
+// Section 3 / Fig. 2) and M(k) = sum_i sum_{t0} |X_i(t0 + k) - X_i(t0)|^2,
+// the mean squared displacement of the same particles (X the unwrapped
+// position, X(t) - X(t - 1) = V(t) by Eq. 2).  The particle kernel writes
+// every step's velocities (FP32) into a ring of K + 2B samples.  Every B = 64
+// samples the correlator forms, for the B new samples t and every lag k <= K,
+//     G(t, k) = sum_j V_j(t) V_j(t - k)          (j over the 3 n_p components)
+// -- a dense contraction -- and both observables follow from G exactly:
+//   C(k) += sum_t G(t, k);
+//   the squared displacement over the window (e - k, e], summed over the
+//   particles, W(e, k) = sum_i |sum_{s=e-k+1}^{e} V_i(s)|^2, obeys
+//     W(e, k) = W(e - 1, k - 1) + H(e, k),
+//     H(e, k) = G(e, 0) + 2 sum_{m=1}^{k-1} G(e, m),
+//   (|w + v|^2 = |w|^2 + 2 v.w + |v|^2 with w the window sum up to e - 1), and
+//   M(k) += W(e, k) for every new sample e >= k (an origin t0 = e - k >= 0).
+// So the MSD needs no positions and no per-particle state: between blocks
+// only W(last sample, k), k <= K, is kept (FP64).
 //
-// k_vacf_mma  : CTA = 128 lags x 256 components: the products of the 64 new
-//               samples with the 191 window samples as a matrix product on the
-//               tensor cores (TF32 in three terms, FP32 accuracy), the lag sums
-//               of its band in FP64 into one partial per (chunk, k).
-// k_vacf_reduce : adds the chunk partials in chunk order (FP64) to the
-//               running sums and pair counts, then marks the samples done.
+// k_vacf_mma    : CTA = 128 lags x 256 components: the products of the 64 new
+//                 samples with the 191 window samples as a matrix product on
+//                 the tensor cores (TF32 in three terms, FP32 accuracy); its
+//                 band is G restricted to the CTA's components, written as FP32
+//                 partials part[chunk][t][k].
+// k_corr_gsum   : G(t, k) = sum over chunks of the partials, in chunk order, FP64.
+// k_msd_scan    : H(t, k), a prefix sum over k of each G row (FP64).
+// k_msd_diag    : W along the diagonals e - k = const through the block.
+// k_corr_acc    : C(k) += sum_t G(t, k), M(k) += sum_e W(e, k), pair counts;
+//                 the last block marks the samples done.
 #include <cuda_runtime.h>
 
 #include "lbp_internal.cuh"
@@ -31,13 +48,18 @@ struct VacfArgs {
     int cap;     // ring samples
     int ncomp;   // 3 n_p
     int K;
-    long long *d_vacf;  // [0] t0, [1] samples done, [2] samples written, [3] block counter
+    long long *d_vacf;  // [0] t0, [1] samples done, [2] samples written, [3] block counter,
+                        // [4] parity of the MSD state
     int flush;
-    double *part;       // [nchunks][K+1]
-    double *sum;        // [K+1]
+    float *part;        // [nchunks][VB][K+1] partial G of each component chunk
+    int nchunks;
+    double *G, *H, *W;  // [VB][K+1] each
+    double *wstate;     // [2][K+1] W(last sample, k), by parity
+    double *sum;        // [K+1] VACF sums
+    double *msd;        // [K+1] MSD sums
     long long *cnt;     // [K+1]
     int np;
-    unsigned int *done; // block counter of the reduce kernel
+    unsigned int *done; // block counter of the last kernel of the chain
 };
 
 __device__ __forceinline__ bool vacf_range(const VacfArgs &A, long long &tb, long long &te) {
@@ -222,11 +244,13 @@ __global__ void __launch_bounds__(256) k_vacf_mma(const VacfArgs A) {
         sP[(t + 8) * MPLD + sr + 1] = acc[q][3];
     }
     __syncthreads();
-    if (threadIdx.x < VKT) {
-        const int kk = threadIdx.x, k = k0 + kk;
-        double v = 0.0;
-        for (int t = 0; t < nb; ++t) v += (double)sP[t * MPLD + t + (VKT - 1) - kk];
-        if (k <= A.K) A.part[(long long)blockIdx.y * (A.K + 1) + k] = v;
+    // the band: G restricted to this chunk, G(t, k0 + kk) = P[t][t + 127 - kk],
+    // written for the block's samples (coalesced along the lags)
+    const int K1 = A.K + 1;
+    float *out = A.part + (long long)blockIdx.y * VB * K1;
+    for (int e = threadIdx.x; e < nb * VKT; e += blockDim.x) {
+        const int t = e / VKT, kk = e - t * VKT, k = k0 + kk;
+        if (k < K1) out[(long long)t * K1 + k] = sP[t * MPLD + t + (VKT - 1) - kk];
     }
 }
 
@@ -234,22 +258,112 @@ cudaError_t prepare_vacf_kernels() {
     return cudaFuncSetAttribute(k_vacf_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
 }
 
-__global__ void __launch_bounds__(256) k_vacf_reduce(const VacfArgs A, int nchunks) {
+// G(t, k) for the block's samples: the chunk partials summed in chunk order
+// (FP64), one thread per (t, k).
+__global__ void __launch_bounds__(256) k_corr_gsum(const VacfArgs A) {
     long long tb, te;
     if (!vacf_range(A, tb, te)) return;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= A.K; k += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += A.part[(long long)c * (A.K + 1) + k];
-        A.sum[k] += s;
+    const int t = blockIdx.y;
+    if (t >= (int)(te - tb)) return;
+    const int K1 = A.K + 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K1) return;
+    const long long stride = (long long)VB * K1;
+    const float *p = A.part + (long long)t * K1 + k;
+    double g = 0.0;
+    for (int c = 0; c < A.nchunks; ++c) g += (double)p[c * stride];
+    A.G[(long long)t * K1 + k] = g;
+}
+
+// H(t, k) = G(t, 0) + 2 sum_{m=1}^{k-1} G(t, m) for k = 1..K, one CTA per sample
+// row: a block-wide inclusive scan of 2 G(t, m) over m = 1..K-1 in tiles of
+// 1024, in a fixed order (FP64).  H(t, 0) = 0.
+constexpr int SCAN_T = 1024;
+__global__ void __launch_bounds__(SCAN_T) k_msd_scan(const VacfArgs A) {
+    long long tb, te;
+    if (!vacf_range(A, tb, te)) return;
+    const int t = blockIdx.x;
+    if (t >= (int)(te - tb)) return;
+    const int K1 = A.K + 1;
+    const double *g = A.G + (long long)t * K1;
+    double *h = A.H + (long long)t * K1;
+    __shared__ double sh[SCAN_T];
+    const double g0 = g[0];
+    double carry = 0.0;  // 2 sum of G(t, m) over the tiles before
+    if (threadIdx.x == 0) h[0] = 0.0;
+    // H(t, k) for k = 1 + m0 + i uses the scan of m = 1 .. k - 1
+    for (int m0 = 0; m0 < A.K; m0 += SCAN_T) {
+        const int i = threadIdx.x;
+        const int m = m0 + i;  // H index k = m + 1 takes G(t, 1..m)
+        double v = (m >= 1 && m < K1) ? 2.0 * g[m] : 0.0;
+        sh[i] = v;
+        __syncthreads();
+        for (int off = 1; off < SCAN_T; off <<= 1) {
+            const double add = i >= off ? sh[i - off] : 0.0;
+            __syncthreads();
+            sh[i] += add;
+            __syncthreads();
+        }
+        const double incl = carry + sh[i];
+        if (m + 1 < K1) h[m + 1] = g0 + incl;
+        carry += sh[SCAN_T - 1];
+        __syncthreads();
+    }
+}
+
+// W(e, k) along the diagonals: thread d walks the block's samples e = tb + j
+// with k = d - (nb - 1) + j, W(e, k) = W(e - 1, k - 1) + H(e, k) (W(., 0) = 0),
+// starting from the kept W(tb - 1, .) and leaving W(te - 1, d) for the next
+// block.  Writes W[j][k] for 1 <= k <= K.
+__global__ void __launch_bounds__(256) k_msd_diag(const VacfArgs A) {
+    long long tb, te;
+    if (!vacf_range(A, tb, te)) return;
+    const int nb = (int)(te - tb);
+    const int K1 = A.K + 1;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;  // k at the block's last sample
+    if (d < 1 || d > A.K + nb - 1) return;
+    const int par = (int)(A.d_vacf[4] & 1);
+    const double *prev = A.wstate + (long long)par * K1;
+    double *next = A.wstate + (long long)(par ^ 1) * K1;
+    int k = d - nb;  // k at sample tb - 1
+    double w = k >= 1 ? prev[k] : 0.0;
+    for (int j = 0; j < nb; ++j) {
+        ++k;
+        if (k >= 1 && k < K1) {
+            w += A.H[(long long)j * K1 + k];
+            A.W[(long long)j * K1 + k] = w;
+        }
+    }
+    if (d < K1) next[d] = w;
+}
+
+// C(k) += sum_t G(t, k); M(k) += sum_{e >= k} W(e, k); pair counts (the same
+// origins for both).  The last block marks the samples done and flips the
+// parity of the kept W.
+__global__ void __launch_bounds__(256) k_corr_acc(const VacfArgs A) {
+    long long tb, te;
+    if (!vacf_range(A, tb, te)) return;
+    const int nb = (int)(te - tb);
+    const int K1 = A.K + 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K1) {
+        double c = 0.0, m = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            c += A.G[(long long)j * K1 + k];
+            if (k >= 1 && tb + j >= k) m += A.W[(long long)j * K1 + k];
+        }
+        A.sum[k] += c;
+        A.msd[k] += m;
         const long long first = tb > k ? tb : (long long)k;
         if (te > first) A.cnt[k] += (long long)A.np * (te - first);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned int d = atomicAdd(A.done, 1u);
-        if (d == gridDim.x - 1) {
+        const unsigned int dn = atomicAdd(A.done, 1u);
+        if (dn == gridDim.x - 1) {
             A.d_vacf[1] = te;
+            A.d_vacf[4] += 1;
             *A.done = 0u;
             __threadfence();
         }
@@ -321,16 +435,23 @@ cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st) {
     A.d_vacf = s.d_vacf;
     A.flush = flush ? 1 : 0;
     A.part = s.vacf_part;
+    A.nchunks = s.vacf_nchunks;
+    A.G = s.corr_g;
+    A.H = s.corr_h;
+    A.W = s.corr_w;
+    A.wstate = s.msd_state;
     A.sum = s.vacf_sum;
+    A.msd = s.msd_sum;
     A.cnt = s.vacf_cnt;
     A.np = s.np;
     A.done = reinterpret_cast<unsigned int *>(s.d_vacf + 3);
+    const int K1 = s.vacf_lag + 1;
     dim3 g1((s.vacf_lag + VKT) / VKT, s.vacf_nchunks);
     k_vacf_mma<<<g1, 256, MMA_SMEM, st>>>(A);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int g2 = (s.vacf_lag + 1 + 255) / 256;
-    k_vacf_reduce<<<g2, 256, 0, st>>>(A, s.vacf_nchunks);
+    k_corr_gsum<<<dim3((K1 + 255) / 256, VB), 256, 0, st>>>(A);
+    k_msd_scan<<<VB, SCAN_T, 0, st>>>(A);
+    k_msd_diag<<<(K1 + VB + 255) / 256, 256, 0, st>>>(A);
+    k_corr_acc<<<(K1 + 255) / 256, 256, 0, st>>>(A);
     return cudaGetLastError();
 }
 

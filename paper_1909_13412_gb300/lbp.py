@@ -65,6 +65,7 @@ _SIGS = {
     "lbp_get_step_index": [_vp, C.POINTER(C.c_int64)],
     "lbp_vacf_configure": [_vp, C.c_int],
     "lbp_vacf_read": [_vp, _vp, _vp, C.c_int],
+    "lbp_msd_read": [_vp, _vp, _vp, C.c_int],
     "lbp_vacf_configure_ex": [_vp, C.c_int, C.c_int],
     "lbp_autotune": [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "lbp_set_block_shape": [_vp, C.c_int, C.c_int],
@@ -357,6 +358,14 @@ def lbp_vacf_read(h: Handle, csum, counts):
     b = _ptr(counts, np.int64, None, "counts", True)
     d = _same_side(a, b)
     _call("lbp_vacf_read", h.ptr, a[0], b[0], d)
+
+
+def lbp_msd_read(h: Handle, msum, counts):
+    """Mean squared displacement sums [max_lag + 1] (FP64) and pair counts."""
+    a = _ptr(msum, np.float64, None, "msum", True)
+    b = _ptr(counts, np.int64, None, "counts", True)
+    d = _same_side(a, b)
+    _call("lbp_msd_read", h.ptr, a[0], b[0], d)
 
 
 def lbp_vacf_configure_ex(h: Handle, max_lag, per_particle):

@@ -514,7 +514,9 @@ def test_vacf_matches_oracle_on_the_same_trajectory():
     ref, refc = oracle.vacf(np.array(traj, np.float32).astype(np.float64), K)
     assert np.array_equal(cnt, refc)
     assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
-    # reading again after more steps continues the same sums
+    check_msd(h, traj, K)
+    # reading again after more steps continues the same sums (the flush above
+    # left the next blocks starting at sample 150, not at a multiple of 64)
     for _ in range(70):
         lbp.lbp_step(h, 1)
         traj.append(gpu_particles(h)[1])
@@ -522,6 +524,29 @@ def test_vacf_matches_oracle_on_the_same_trajectory():
     ref, refc = oracle.vacf(np.array(traj, np.float32).astype(np.float64), K)
     assert np.array_equal(cnt, refc)
     assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
+    check_msd(h, traj, K)
+
+
+# FP32 products summed over components by the tensor cores, then FP64: the MSD
+# of the GPU's own (FP32) velocity samples within this relative error
+MSD_REL = 2e-6
+
+
+def check_msd(h, traj, K, rel=MSD_REL):
+    """The library's mean squared displacement against the oracle's, evaluated on
+    positions X(t) = sum_{s <= t} V(s) of the same FP32 velocity samples (the
+    displacement X(t0 + k) - X(t0) is the sum of the k velocities after t0, Eq. 2)."""
+    ms = np.empty(K + 1)
+    mc = np.empty(K + 1, np.int64)
+    lbp.lbp_msd_read(h, ms, mc)
+    V = np.array(traj, np.float32).astype(np.float64)
+    ref, refc = oracle.msd(np.cumsum(V, axis=0), K)
+    assert np.array_equal(mc, refc)
+    assert ms[0] == 0.0
+    T = min(len(traj), K + 1)  # lags with at least one origin
+    assert np.all(ms[T:] == 0.0)
+    err = np.abs(ms[1:T] - ref[1:T]) / ref[1:T]
+    assert np.max(err) <= rel, (np.max(err), int(np.argmax(err)) + 1)
 
 
 def test_vacf_spans_lag_tiles_and_component_chunks_with_ragged_tails():
@@ -542,10 +567,22 @@ def test_vacf_spans_lag_tiles_and_component_chunks_with_ragged_tails():
     cs = np.empty(K + 1)
     cnt = np.empty(K + 1, np.int64)
     lbp.lbp_vacf_read(h, cs, cnt)
-    lbp.lbp_destroy(h)
     ref, refc = oracle.vacf(np.array(traj, np.float32).astype(np.float64), K)
     assert np.array_equal(cnt, refc)
     assert np.max(np.abs(cs - ref)) <= 1e-6 * ref[0]
+    check_msd(h, traj, K)
+    lbp.lbp_destroy(h)
+
+
+def test_msd_is_not_kept_per_particle():
+    shape = (8, 8, 8)
+    ps = wl.uniform_particles(5, shape, 6.0, 0.5, 0.2, 1e-4, 1, 2)
+    h = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=2)
+    lbp.lbp_vacf_configure_ex(h, 20, 1)
+    lbp.lbp_step(h, 5)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_msd_read(h, np.empty(21), np.empty(21, np.int64))
+    assert ei.value.status == lbp.LBP_ESTATE
 
 
 def test_vacf_requires_particles():
@@ -717,6 +754,9 @@ def test_full_size_vacf_run_against_its_own_trajectory():
     cs = np.empty(K + 1)
     cnt = np.empty(K + 1, np.int64)
     lbp.lbp_vacf_read(h, cs, cnt)
+    ms = np.empty(K + 1)
+    mc = np.empty(K + 1, np.int64)
+    lbp.lbp_msd_read(h, ms, mc)
     lbp.lbp_check(h)
     lbp.lbp_destroy(h)
     x = traj.reshape(T, 3 * n).astype(np.float64)
@@ -725,6 +765,19 @@ def test_full_size_vacf_run_against_its_own_trajectory():
     ref = np.fft.irfft((F * np.conj(F)).sum(axis=1), n=L)[:K + 1]
     assert np.array_equal(cnt, n * (T - np.arange(K + 1)))
     assert np.max(np.abs(cs - ref)) <= 1e-5 * ref[0]
+    # MSD of the positions X(t) = sum_{s <= t} V(s): sum_t0 |X(t0+k)|^2 + |X(t0)|^2
+    # - 2 X(t0+k).X(t0), the cross term by FFT (FP64)
+    X = np.cumsum(x, axis=0)
+    X -= X[T // 2]  # centre the positions to keep the FFT's cancellation small
+    s2 = (X * X).sum(axis=1)
+    c2 = np.concatenate([[0.0], np.cumsum(s2)])
+    FX = np.fft.rfft(X, n=L, axis=0)
+    cross = np.fft.irfft((FX * np.conj(FX)).sum(axis=1), n=L)[:K + 1]
+    k = np.arange(K + 1)
+    mref = (c2[T] - c2[k]) + c2[T - k] - 2.0 * cross
+    assert np.array_equal(mc, cnt)
+    rel = np.abs(ms[1:] - mref[1:]) / mref[1:]
+    assert np.max(rel) <= 1e-4, (np.max(rel), int(np.argmax(rel)) + 1)
 
 
 def test_full_size_ensemble_equals_its_boxes_alone():
