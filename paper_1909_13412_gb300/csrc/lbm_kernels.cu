@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
     const unsigned grp = item / (unsigned)nchunks;
     const int chunk = (int)(item - grp * (unsigned)nchunks);
     const size_t seg0 = (size_t)rp.seg_off;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+    // the previous step's records (this step's particle kernel writes the others)
     if (threadIdx.x < R && grp * R + threadIdx.x < nrows)
         rec_prev[(seg0 + (size_t)(grp * R + threadIdx.x) * nchunks + chunk) * REC_WORDS] = 0ull;
     const int xw = chunk * BX + (threadIdx.x & ~31);
@@ -181,6 +181,14 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
         for (int a = 0; a < Q; ++a)
             g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
                                           n[h].oz[ez(a) + 1]), a);
+    }
+    // the loads above do not depend on this step's particle kernel; what follows does
+    // (a no-op unless launched as its programmatic dependent)
+    grid_dependency_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
         rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
     }
 #pragma unroll
@@ -279,9 +287,9 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
     const unsigned grp = item / (unsigned)nchunks;
     const int chunk = (int)(item - grp * (unsigned)nchunks);
     const size_t seg0 = (size_t)rp.seg_off;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     if (FORCED && threadIdx.x < R && grp * R + threadIdx.x < nrows)
         rec_prev[(seg0 + (size_t)(grp * R + threadIdx.x) * nchunks + chunk) * REC_WORDS] = 0ull;
+    if (!FORCED && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     const int xw = chunk * SEG + 2 * (threadIdx.x & ~31);  // first node of the warp
     if (xw >= nx) return;
     const int x0 = xw + 2 * lane;
@@ -319,7 +327,15 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
             }
             unpack2<St>(w, a, g[h][0][a], g[h][1][a]);
         }
-        if (FORCED) rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
+    }
+    if (FORCED) {
+        grid_dependency_wait();  // the records come from this step's particle kernel
+        if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+#pragma unroll
+        for (int h = 0; h < R; ++h) {
+            const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
+            rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
+        }
     }
 #pragma unroll
     for (int h = 0; h < R; ++h) {
@@ -412,7 +428,7 @@ template <typename St, int R, int MAXR, bool FORCED>
 __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_collide_quad(
     Planes<St> pl, const RepTable<MAXR> rt, const unsigned long long *__restrict__ rec_cur,
     unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump, int *err) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+    if (!FORCED && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
     const unsigned item = blockIdx.x * QUAD_WARPS + (threadIdx.x >> 5);
     if (item >= rt.item_off[MAXR == 1 ? 1 : rt.nrep]) return;  // whole warp past the last segment
     const int r = find_block_rep(rt, item);
@@ -462,7 +478,15 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
                 p[h][a] = v;
             }
         }
-        if (FORCED) rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
+    }
+    if (FORCED) {
+        grid_dependency_wait();  // the records come from this step's particle kernel
+        if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
+#pragma unroll
+        for (int h = 0; h < R; ++h) {
+            const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
+            rw[h] = __ldg(rec_cur + (seg0 + (size_t)row * nchunks + chunk) * REC_WORDS + lane);
+        }
     }
 #pragma unroll
     for (int h = 0; h < R; ++h) {
@@ -627,13 +651,33 @@ bool variant_ok(const Sim &s, int variant) {
            (variant == 3 && quad_kernel_ok(s));
 }
 
+// Launch `kern` on `st`; with `pdl` as the programmatic dependent of the
+// kernel launched before it on that stream (see grid_dependency_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                            bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // variant 0: one node per thread; 1: two nodes per thread (2-byte storage,
 // even nx); 2: bulk-copy staged persistent kernel (lbm_staged.cu); 3: four
-// nodes per thread, one warp per row segment (2-byte storage, nx % 4 == 0)
+// nodes per thread, one warp per row segment (2-byte storage, nx % 4 == 0).
+// pdl: launched right after the step's particle kernel, as its programmatic
+// dependent (forced passes only).
 template <bool FORCED>
 static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned long long *rec_cur,
                              unsigned long long *rec_prev, long long *bump, int rows, int variant,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool pdl = false) {
     constexpr int BX = SC_BX;
     if (!variant_ok(s, variant)) variant = 0;
     if (variant == 2) {
@@ -642,10 +686,10 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
             if (s.nrep == 1)
                 return launch_staged_t<St, 1, FORCED>(planes_of<St>(s, src, dst), rep_table_staged<1>(s), rec_cur,
                                                       rec_prev, s.fq, s.N, bump, s.d_err, s.wait_cycles, s.wait_probe,
-                                                      s.num_sms, st);
+                                                      s.num_sms, st, pdl);
             return launch_staged_t<St, MAX_BATCH, FORCED>(planes_of<St>(s, src, dst), rep_table_staged<MAX_BATCH>(s),
                                                           rec_cur, rec_prev, s.fq, s.N, bump, s.d_err,
-                                                          s.wait_cycles, s.wait_probe, s.num_sms, st);
+                                                          s.wait_cycles, s.wait_probe, s.num_sms, st, pdl);
         });
     }
     const bool use_pair = variant == 1, use_quad = variant == 3;
@@ -657,21 +701,17 @@ static cudaError_t launch_sc(Sim &s, const void *src, void *dst, const unsigned 
                 constexpr int MAXR = sizeof(rt.rep) / sizeof(Rep);
                 const unsigned grid = rt.item_off[rt.nrep];
                 if constexpr (!std::is_same<St, StoreF32>::value) {
-                    if (use_pair) {
-                        k_stream_collide_pair<St, R, MAXR, FORCED><<<grid, PAIR_BX, 0, st>>>(
-                            planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
-                        return cudaGetLastError();
-                    }
-                    if (use_quad) {
-                        k_stream_collide_quad<St, R, MAXR, FORCED>
-                            <<<(grid + QUAD_WARPS - 1) / QUAD_WARPS, 32 * QUAD_WARPS, 0, st>>>(
-                                planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
-                        return cudaGetLastError();
-                    }
+                    if (use_pair)
+                        return launch_k(k_stream_collide_pair<St, R, MAXR, FORCED>, grid, PAIR_BX, 0, st, pdl,
+                                        planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
+                    if (use_quad)
+                        return launch_k(k_stream_collide_quad<St, R, MAXR, FORCED>, (grid + QUAD_WARPS - 1) / QUAD_WARPS,
+                                        32 * QUAD_WARPS, 0, st, pdl, planes_of<St>(s, src, dst), rt, rec_cur, rec_prev,
+                                        s.fq, s.N, bump, s.d_err);
                 }
                 if constexpr (FORCED)
-                    k_stream_collide_forced<BX, St, R, MAXR><<<grid, BX, 0, st>>>(
-                        planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
+                    return launch_k(k_stream_collide_forced<BX, St, R, MAXR>, grid, BX, 0, st, pdl,
+                                    planes_of<St>(s, src, dst), rt, rec_cur, rec_prev, s.fq, s.N, bump, s.d_err);
                 else
                     k_stream_collide<BX, St, R, MAXR><<<grid, BX, 0, st>>>(planes_of<St>(s, src, dst), rt, bump,
                                                                            s.d_err);
@@ -698,9 +738,8 @@ cudaError_t launch_stream_collide(Sim &s, const void *src, void *dst, cudaStream
 }
 
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
-                                         cudaStream_t st) {
-    return launch_stream_collide_forced_cfg(s, src, dst, s.rec[parity], s.rec[parity ^ 1], s.d_step,
-                                            s.rows, s.variant, st);
+                                         cudaStream_t st, bool pdl) {
+    return launch_sc<true>(s, src, dst, s.rec[parity], s.rec[parity ^ 1], s.d_step, s.rows, s.variant, st, pdl);
 }
 
 // ---------------------------------------------------------------------------

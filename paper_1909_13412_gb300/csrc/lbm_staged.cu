@@ -35,73 +35,12 @@
 
 #include <type_traits>
 
+#include "lbp_async.cuh"
 #include "lbp_internal.cuh"
 
 namespace lbp {
 
-namespace {
-
-// bound of the drain waits at exit, in SM clock cycles (~0.5 s at 2 GHz); each
-// try_wait poll may itself suspend the thread for a short, hardware-chosen time
-constexpr long long DRAIN_CYCLES = 1ll << 30;
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait: true when the phase completed; false when `bound` cycles
-// passed or the CTA's abort flag (if given) is set
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long bound,
-                                          const volatile int *abort_flag) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (abort_flag && *abort_flag) return false;
-        if (clock64() - t0 > bound) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-}  // namespace
+using namespace async;
 
 template <typename St>
 struct StagedGeom {
@@ -177,6 +116,7 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
     __shared__ volatile int s_abort;  // set by the first wait of the CTA that runs out
     const unsigned total = rt.item_off[rt.nrep];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (FORCED) grid_dependency_wait();  // everything below may read this step's particle kernel's output
     if (blockIdx.x == 0 && t == 0) *bump += 1;
     if (t == 0) {
         s_abort = 0;
@@ -301,7 +241,7 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
 template <typename St, int MAXR, bool FORCED>
 cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, const unsigned long long *rec_cur,
                             unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump,
-                            int *err, long long wait_cycles, int probe, int num_sms, cudaStream_t st) {
+                            int *err, long long wait_cycles, int probe, int num_sms, cudaStream_t st, bool pdl) {
     using G = StagedGeom<St>;
     auto kern = k_stream_collide_staged<St, MAXR, FORCED>;
     static int per_sm = 0;  // per instantiation
@@ -316,9 +256,17 @@ cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, cons
     unsigned grid = (unsigned)(per_sm * num_sms);
     if (grid > total) grid = total;
     if (grid == 0) return cudaSuccess;
-    kern<<<grid, STAGED_THREADS + 32, G::SMEM, st>>>(pl, rt, rec_cur, rec_prev, fq, Ntot, bump, err, wait_cycles,
-                                                     probe);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(STAGED_THREADS + 32);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, pl, rt, rec_cur, rec_prev, fq, Ntot, bump, err, wait_cycles, probe);
 }
 
 // rows per item of a box: as many whole rows as fit STAGED_NODES nodes and
@@ -335,7 +283,7 @@ int staged_rows(int nx, int ny) {
     template cudaError_t launch_staged_t<ST, MAXR, F>(const Planes<ST> &, const RepTable<MAXR> &,          \
                                                       const unsigned long long *, unsigned long long *,     \
                                                       unsigned long long *, long long, long long *, int *, \
-                                                      long long, int, int, cudaStream_t);
+                                                      long long, int, int, cudaStream_t, bool);
 LBP_STAGED_INST(StoreF32, 1, true)
 LBP_STAGED_INST(StoreF32, 1, false)
 LBP_STAGED_INST(StoreF32, MAX_BATCH, true)

@@ -145,8 +145,11 @@ lbp_status enqueue_step(lbp_sim *s, bool timed, const Readback *readback = nullp
         CK(cudaEventRecord(s->ev_xjoin, s->s2));
     }
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
+    // the lattice pass as the programmatic dependent of the particle kernel
+    // (its population loads overlap the particle kernel's tail); not when
+    // events around it time the lattice kernel alone
     if (s->np > 0)
-        CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
+        CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0, !timed && !readback));
     else
         CK(launch_stream_collide(*s, src, dst, s->s0));
     if (readback) CK(cudaStreamWaitEvent(s->s0, s->ev_xjoin, 0));
@@ -480,7 +483,7 @@ lbp_status lbp_destroy(lbp_sim *s) {
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage, s->inj, s->budget_part,
-                    s->corr_g, s->corr_h, s->corr_w, s->msd_state, s->msd_sum};
+                    s->corr_g, s->corr_h, s->corr_w, s->msd_state, s->msd_sum, s->ring16};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
@@ -963,7 +966,7 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     CK(cudaStreamSynchronize(s->s0));
     drop_graphs(s);
     s->vacf_lag = -1;
-    void **bufs[] = {(void **)&s->ring,   (void **)&s->vacf_sum, (void **)&s->vacf_cnt,
+    void **bufs[] = {(void **)&s->ring,   (void **)&s->ring16,   (void **)&s->vacf_sum, (void **)&s->vacf_cnt,
                      (void **)&s->vacf_part, (void **)&s->corr_g, (void **)&s->corr_h,
                      (void **)&s->corr_w, (void **)&s->msd_state, (void **)&s->msd_sum};
     for (void **b : bufs)
@@ -975,12 +978,27 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     if (s->np == 0) return fail(LBP_ESTATE, "lbp_vacf_configure: add particles first");
     const int B = vacf_block_samples();
     const long long ncomp = 3ll * s->np;
-    const size_t ring_bytes = sizeof(float) * (size_t)(max_lag + 2 * B) * (size_t)ncomp;
+    // per particle: FP32 ring of max_lag + 2 blocks (one block more than the
+    // window, see join_vacf); ensemble: fp16 hi/lo ring of max_lag + 320
+    // samples plus the duplicated first rows (see vacf_kernels.cu)
+    const int ld = (int)((ncomp + 7) / 8 * 8);
+    const long long cap = per_particle ? (long long)max_lag + 2 * B : (long long)max_lag + 320;
+    const size_t ring_bytes = per_particle ? sizeof(float) * (size_t)cap * (size_t)ncomp
+                                           : 4 * (size_t)(cap + vacf_ring_dup_rows()) * (size_t)ld;
     if (ring_bytes > ((size_t)64 << 30))
         return fail(LBP_EINVAL, "lbp_vacf_configure: ring of %zu bytes exceeds 64 GiB", ring_bytes);
-    s->vacf_cap = max_lag + 2 * B;  // one block more than the window: see join_vacf
+    if (!per_particle && cap + vacf_ring_dup_rows() > 2147483647ll)
+        return fail(LBP_EINVAL, "lbp_vacf_configure: max_lag too large");
+    s->vacf_cap = (int)cap;
+    s->ring_ld = ld;
     s->vacf_nchunks = (int)((ncomp + vacf_chunk_components() - 1) / vacf_chunk_components());
-    TRY(dalloc(&s->ring, (size_t)s->vacf_cap * ncomp));
+    if (per_particle) {
+        TRY(dalloc(&s->ring, (size_t)s->vacf_cap * ncomp));
+    } else {
+        TRY(dalloc(reinterpret_cast<char **>(&s->ring16), ring_bytes));
+        CK(cudaMemsetAsync(s->ring16, 0, ring_bytes, s->s0));
+        CK(encode_vacf_tensor_maps(*s));
+    }
     const size_t nsum = (per_particle ? (size_t)s->np : 1) * ((size_t)max_lag + 1);
     if (per_particle && (nsum > ((size_t)1 << 28) || s->np > 65535))
         return fail(LBP_EINVAL,
@@ -1349,7 +1367,7 @@ lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r
             void *dst = state(j + 1);
             if (np > 0) {
                 ADJ_CK(launch_particles(*s, src, parity, s->s0));
-                ADJ_CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0));
+                ADJ_CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0, false));
             } else {
                 ADJ_CK(launch_stream_collide(*s, src, dst, s->s0));
             }

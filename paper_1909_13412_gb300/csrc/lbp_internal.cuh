@@ -131,6 +131,15 @@ __device__ __forceinline__ void collide_values(const float g[Q], float omega, fl
 #undef LBP_PAIR
 }
 
+// Programmatic dependent launch.  A step's lattice pass is launched as the
+// programmatic dependent of the step's particle kernel: the particle kernel
+// lets it start early, and the lattice kernel issues its population loads
+// (which do not depend on the particle kernel) before it waits for the
+// particle kernel to complete and its writes (force records, overflow
+// accumulator) to be visible.  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // The float nearest (within one unit in the last place) to a 64-bit integer,
 // from its two 32-bit halves: the direct 64-bit conversion runs on the FP64
 // pipe, which is narrow on this GPU.  Every lattice kernel converts its
@@ -165,6 +174,7 @@ constexpr int ERR_NAN = 1;
 constexpr int ERR_RANGE = 2;
 constexpr int ERR_TIMEOUT = 4;  // a bounded wait on an mbarrier ran out
 constexpr int ERR_LATTICE = 8;  // a collided population became non-finite
+constexpr float VACF_RING_SCALE = 4096.f;  // the fp16 ring holds hi/lo of 4096 V; |V| < 16 fits
 
 // True when the collided rest population of a node is not finite.  Every
 // population of the node enters it through rho~ - 1 and u.u (collide_values),
@@ -316,7 +326,11 @@ struct Sim {
     int vacf_lag = -1;
     int vacf_pp = 0;              // 1: sums per particle ([np][K + 1])
     int vacf_cap = 0;             // ring length in samples
-    float *ring = nullptr;        // [vacf_cap][3 * cap]
+    float *ring = nullptr;        // per-particle VACF: FP32 [vacf_cap][3 n_p]
+    // ensemble VACF and MSD: fp16 hi/lo of 4096 V, [vacf_cap + dup rows][2][ring_ld]
+    void *ring16 = nullptr;
+    int ring_ld = 0;
+    alignas(64) unsigned char tmaps[2][128];  // TMA tensor maps of ring16 (window, new samples)
     long long *d_vacf = nullptr;  // [0] t0 step, [1] samples correlated, [2] samples written,
                                   // [3] block counter of the reduce kernel
     long long vacf_done_host = 0; // host mirror of d_vacf[1]
@@ -380,8 +394,10 @@ cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
 int default_rows_per_block(int precision);
 bool pair_kernel_ok(const Sim &s);  // 2-byte storage and every box with even nx
 bool variant_ok(const Sim &s, int variant);
+// pdl: launched right after the step's particle kernel on `st`, as its
+// programmatic dependent
 cudaError_t launch_stream_collide_forced(Sim &s, const void *src, void *dst, int parity,
-                                         cudaStream_t st);
+                                         cudaStream_t st, bool pdl);
 cudaError_t launch_fill_rest(Sim &s, void *dst, cudaStream_t st);
 cudaError_t launch_from_f64(Sim &s, const double *f, void *dst, cudaStream_t st);
 cudaError_t launch_to_f64(Sim &s, const void *src, double *f, cudaStream_t st);
@@ -403,7 +419,8 @@ cudaError_t launch_philox(const unsigned long long *ctr, const unsigned long lon
 template <typename St, int MAXR, bool FORCED>
 cudaError_t launch_staged_t(const Planes<St> &pl, const RepTable<MAXR> &rt, const unsigned long long *rec_cur,
                             unsigned long long *rec_prev, unsigned long long *fq, long long Ntot, long long *bump,
-                            int *err, long long wait_cycles, int probe, int num_sms, cudaStream_t st);
+                            int *err, long long wait_cycles, int probe, int num_sms, cudaStream_t st,
+                            bool pdl = false);
 bool staged_kernel_ok(const Sim &s);  // every box: nx a multiple of 16 bytes of storage, nx <= STAGED_NODES
 int staged_rows(int nx, int ny);      // rows per item of the staged kernel
 constexpr int STAGED_NODES = 512;     // nodes per item (whole rows) of the staged kernel
@@ -423,6 +440,8 @@ cudaError_t launch_f32_to_f64(Sim &s, const float *src, double *dst, cudaStream_
 int vacf_block_samples();
 cudaError_t prepare_vacf_kernels();  // opt-in shared memory of the tensor-core correlator
 int vacf_chunk_components();
+int vacf_ring_dup_rows();                  // rows of ring16 kept twice (its first rows again after cap)
+cudaError_t encode_vacf_tensor_maps(Sim &s);
 cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st);
 
 }  // namespace lbp

@@ -56,7 +56,9 @@ struct ParticleArgs {
     int mode, exclude_inside;
     unsigned long long *rec; // force records of this step's parity
     unsigned long long *fq;  // [3][N] fixed-point overflow accumulator
-    float *ring;
+    float *ring;        // per-particle VACF ring (FP32), or null
+    __half *ring16;     // ensemble VACF/MSD ring (fp16 hi/lo planes), or null
+    int ring_ld, ring_dup;
     int ring_cap;
     long long *d_vacf;  // [0] first sampled step, [2] samples written
     int *err;
@@ -87,8 +89,11 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     const int t = threadIdx.x, lane = t & 31;
     const int i0 = blockIdx.x * PB;
     const long long step = *A.d_step;
+    // the step's lattice pass may launch now: it waits for this grid's
+    // completion before it reads anything this kernel writes (or bumps the step)
+    grid_dependents_launch();
     const int cap = A.cap;
-    if (A.ring && blockIdx.x == 0 && t == 0) {
+    if ((A.ring || A.ring16) && blockIdx.x == 0 && t == 0) {
         const long long m = step - A.d_vacf[0];
         if (m >= 0) A.d_vacf[2] = m + 1;
     }
@@ -308,6 +313,33 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
                 dst[2 * A.np + i] = (float)Vn[2];
             }
         }
+        if (A.ring16) {
+            // the sample as fp16 hi/lo of 4096 V (the tensor-core correlator's
+            // operands), at its ring row and, for the first rows, once more
+            // after the end of the ring
+            const long long m = step - A.d_vacf[0];
+            if (m >= 0) {
+                const int row = (int)(m % A.ring_cap);
+                bool big = false;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double a = Vn[k] * (double)VACF_RING_SCALE;
+                    big |= !(fabs(a) < 65504.0);
+                    const __half hi = __double2half(a);
+                    const __half lo = __double2half(a - (double)__half2float(hi));
+                    const long long j = (long long)k * A.np + i;
+                    __half *p = A.ring16 + (long long)row * 2 * A.ring_ld + j;
+                    p[0] = hi;
+                    p[A.ring_ld] = lo;
+                    if (row < A.ring_dup) {
+                        __half *p2 = p + (long long)A.ring_cap * 2 * A.ring_ld;
+                        p2[0] = hi;
+                        p2[A.ring_ld] = lo;
+                    }
+                }
+                if (big) atomicOr(A.err, ERR_RANGE);
+            }
+        }
     }
     __syncthreads();
 
@@ -395,7 +427,10 @@ cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t s
     A.exclude_inside = s.exclude_inside;
     A.fq = s.fq;
     A.rec = s.rec[parity];
-    A.ring = s.vacf_lag >= 0 ? s.ring : nullptr;
+    A.ring = s.vacf_lag >= 0 && s.vacf_pp ? s.ring : nullptr;
+    A.ring16 = s.vacf_lag >= 0 && !s.vacf_pp ? static_cast<__half *>(s.ring16) : nullptr;
+    A.ring_ld = s.ring_ld;
+    A.ring_dup = vacf_ring_dup_rows();
     A.ring_cap = s.vacf_cap;
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;

@@ -29,22 +29,78 @@
 // k_msd_diag    : W along the diagonals e - k = const through the block.
 // k_corr_acc    : C(k) += sum_t G(t, k), M(k) += sum_e W(e, k), pair counts;
 //                 the last block marks the samples done.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "lbp_async.cuh"
 #include "lbp_internal.cuh"
 
 namespace lbp {
 
-constexpr int VB = 64;        // samples per correlation block
-constexpr int VKT = 128;      // lags per CTA
-constexpr int VJCH = 256;     // components per CTA (short CTAs interleave with the lattice pass)
-constexpr int VWIN = VB + VKT - 1;
+using namespace async;
+
+constexpr int VB = 64;  // samples per correlation block
+
+// ---------------------------------------------------------------------------
+// k_vacf_tc: the block correlation on the 5th-generation tensor cores.
+//
+// The ring keeps every sample as two fp16 planes, hi = fp16(4096 V) and
+// lo = fp16(4096 V - hi): 22 significant bits (the scale keeps the tail lo in
+// fp16's normal range for |V| >= 2^-12, and |V| < 16 is checked by the
+// particle kernel).  The product of two samples is formed in three terms,
+// a.b = a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo is below
+// 2^-22 of it), so kind::f16 MMAs give FP32-level accuracy at twice the TF32
+// rate and half its operand bytes.
+//
+// A CTA covers TC_LT = 192 lags [k0, k0 + 192) and TC_JCH = 1024 components.
+// With the window rows s = s_lo + r, s_lo = tb - k0 - 191, r in [0, 256) (255
+// used) as the MMA's A operand (two M = 128 tiles) and the block's 64 new
+// samples as B (N = 64), the accumulator D[r][t] = sum_j V_j(s) V_j(tb + t)
+// holds G(t, k0 + kk) on the band kk = t + 191 - r in [0, 192).  Per
+// sub-chunk of 64 components (one 128-byte row of fp16, the width of the
+// 128-byte swizzle):
+//   warp 8 (one thread) loads the four operand tiles (window hi/lo, new
+//          hi/lo) with TMA straight into the swizzled K-major layout the MMA
+//          reads, two stages deep;
+//   warp 9 (one thread) issues 2 M tiles x 4 K steps x 3 terms = 24
+//          tcgen05.mma (M 128, N 64, K 16) into a fresh TMEM accumulator set
+//          (two sets of 128 columns, alternating), then commits them to the
+//          stage's "empty" barrier and the set's "full" barrier;
+//   warps 0-7 move the set from TMEM to registers (tcgen05.ld, one row per
+//          thread: warp w reads lanes 32 (w % 4).. of M tile w / 4) and add it,
+//          rounded to nearest, to FP32 running sums, then release the set.
+// A fresh accumulator per sub-chunk keeps the tensor core's own FP32
+// accumulation to 12 products per entry.  At the end each thread writes its
+// row's band entries as FP32 partials part[chunk][t][k] (scaled back by
+// 2^-24), coalesced along the lags.  Every mbarrier wait is bounded; a wait
+// that runs out sets ERR_TIMEOUT and a CTA abort flag, the producer then
+// waits for the copies it issued and the MMA thread for the MMAs it issued,
+// and TMEM is freed before the CTA leaves.
+//
+// Ring rows: sample m is kept at row m % cap and, for the first TC_ROWS rows,
+// again at row cap + m % cap, so every window of TC_ROWS rows is contiguous
+// for TMA.  With cap >= K + 320 a window that starts before sample 0 (read at
+// negative row coordinates, which TMA fills with zeros) has not wrapped yet.
+// ---------------------------------------------------------------------------
+constexpr int TC_LT = 192;                 // lags per CTA
+constexpr int TC_ROWS = 256;               // window rows: TC_LT + VB - 1 = 255, one spare
+constexpr int TC_KC = 64;                  // components per sub-chunk (128 bytes of fp16)
+constexpr int TC_JCH = 1024;               // components per CTA
+constexpr int TC_STAGES = 2;
+constexpr int TC_A_BYTES = TC_ROWS * 128;  // one plane of window rows
+constexpr int TC_B_BYTES = VB * 128;       // one plane of new-sample rows
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 80 KB
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;        // + 1024-byte alignment slack
+constexpr int TC_TMEM_COLS = 256;          // two accumulator sets of 2 x 64 columns
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 2);  // + TMA warp + MMA warp
 
 int vacf_block_samples() { return VB; }
-int vacf_chunk_components() { return VJCH; }
+int vacf_chunk_components() { return TC_JCH; }
+int vacf_ring_dup_rows() { return TC_ROWS; }
 
 struct VacfArgs {
-    const float *ring;
+    const float *ring;  // FP32 ring of the per-particle VACF, [cap][3 n_p]
     int cap;     // ring samples
     int ncomp;   // 3 n_p
     int K;
@@ -60,6 +116,8 @@ struct VacfArgs {
     long long *cnt;     // [K+1]
     int np;
     unsigned int *done; // block counter of the last kernel of the chain
+    int *err;
+    long long wait_cycles;
 };
 
 __device__ __forceinline__ bool vacf_range(const VacfArgs &A, long long &tb, long long &te) {
@@ -70,192 +128,234 @@ __device__ __forceinline__ bool vacf_range(const VacfArgs &A, long long &tb, lon
     return te - tb == VB;
 }
 
-// ---------------------------------------------------------------------------
-// k_vacf_mma: the block correlation on the tensor cores.  For the CTA's 128
-// lags and 256 components the products of the B = 64 new samples t with
-// the 191 window samples s form a matrix product
-//     P[t][s] = sum_j V_j(t) V_j(s)       (64 x 192, inner dimension 256),
-// and lag k0 + kk collects the band s = t + 127 - kk:  C(k) = sum_t P[t][.].
-// The product runs as mma.sync m16n8k8 with TF32 operands in three terms,
-// a.b = a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = a rounded to TF32, a_lo =
-// the rest rounded to TF32), which keeps FP32 accuracy (the dropped a_lo b_lo
-// is below 2^-22 of the product); accumulation is FP32 in the tensor core.
-// Eight warps: warp w takes the 16 samples of M tile w/2 and 9 of the 18 N
-// tiles of 8 window rows that meet its band (the rest of the 24 are zero
-// contributions).  The band of P goes through shared memory and each of 128
-// threads sums its lag over t in FP64, in sample order, into the chunk's
-// partial (the reduce kernel adds the chunks in chunk order): the result does
-// not depend on scheduling.
-// ---------------------------------------------------------------------------
-constexpr int MJ = 32;           // components per staged sub-chunk
-constexpr int MLD = MJ + 4;      // staged row stride (floats): conflict-free fragment loads
-constexpr int MWR = 192;         // window rows staged (VWIN = 191, one zero row)
-constexpr int MWRA = MWR + 8;    // rows allocated: the fragment loads of a warp's last
-                                 // N tile pair read one 8-row tile past the staged rows
-constexpr int MPLD = MWR + 4;    // row stride of the P tile in the epilogue
-constexpr int MMA_SMEM = 2 * (VB + MWRA) * MLD * 4;  // hi and lo copies: 76,032 bytes
-static_assert(VB * MPLD * 4 <= MMA_SMEM, "the P tile reuses the staging space");
-
-__device__ __forceinline__ unsigned tf32_rna(float x) {
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+// shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart
+__device__ __forceinline__ unsigned long long umma_desc(unsigned saddr) {
+    return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((unsigned long long)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
 
-__device__ __forceinline__ void mma_tf32(float d[4], const unsigned a[4], const unsigned b[2]) {
+// D[tmem] (+)= A * B^T, fp16 operands from shared memory, FP32 accumulator
+__device__ __forceinline__ void umma_f16(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                         unsigned accumulate) {
     asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
-// value v split into its TF32 head and tail, stored at index i of hi / lo
-__device__ __forceinline__ void stage_split(unsigned *hi, unsigned *lo, int i, float v) {
-    const unsigned h = tf32_rna(v);
-    hi[i] = h;
-    lo[i] = tf32_rna(v - __uint_as_float(h));
+// arrive on an mbarrier once every MMA issued so far by this thread completes
+__device__ __forceinline__ void umma_commit(unsigned bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
 }
 
-// four 8 x 4 blocks of 32-bit values (8 x 8 of 16-bit) from shared memory,
-// one register each; thread i gives the address of row i % 8 of block i / 8
-__device__ __forceinline__ void ldsm_x4(unsigned r[4], const unsigned *p) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane, waited for
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_vacf_mma(const VacfArgs A) {
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_vacf_tc(const VacfArgs A, const __grid_constant__ CUtensorMap tm_win, const __grid_constant__ CUtensorMap tm_new) {
     long long tb, te;
     if (!vacf_range(A, tb, te)) return;
     const int nb = (int)(te - tb);
-    extern __shared__ float vsm[];
-    unsigned *hA = reinterpret_cast<unsigned *>(vsm);
-    unsigned *lA = hA + VB * MLD;
-    unsigned *hW = lA + VB * MLD;
-    unsigned *lW = hW + MWRA * MLD;
-    __shared__ long long s_row[VB + MWR];  // ring offset of each staged row, -1: zero row
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k0 = blockIdx.x * VKT;
-    const int jc0 = blockIdx.y * VJCH;
-    const long long s_lo = tb - k0 - (VKT - 1);  // sample of window row 0
-    const int mt = warp >> 1;                   // M tile: samples 16 mt .. 16 mt + 15
-    const int nt0 = 2 * mt + 9 * (warp & 1);    // first of the warp's 9 N tiles
-    const int cap = A.cap;
+    extern __shared__ unsigned char tc_smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    __shared__ __align__(8) unsigned long long bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_accf[2],
+        bar_acce[2];
+    __shared__ unsigned s_tmem;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int k0 = blockIdx.x * TC_LT;
+    const int j0 = blockIdx.y * TC_JCH;
+    const int nj = A.ncomp - j0 < TC_JCH ? A.ncomp - j0 : TC_JCH;
+    const int nsub = (nj + TC_KC - 1) / TC_KC;
+    const long long s_lo = tb - k0 - (TC_LT - 1);  // sample of window row 0
 
-    // ring rows of the 64 new samples and the 192 window rows, once per CTA
-    for (int rr = threadIdx.x; rr < VB + MWR; rr += blockDim.x) {
-        long long off = -1;
-        if (rr < VB) {
-            if (rr < nb) off = (long long)((tb + rr) % cap) * A.ncomp;
-        } else {
-            const int sr = rr - VB;
-            const long long smp = s_lo + sr;
-            // rows older than te - cap were overwritten; they only meet lags > K
-            if (sr < VWIN && smp >= 0 && smp >= te - cap && smp < te) off = (long long)(smp % cap) * A.ncomp;
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(smem_addr(&bar_full[i]), 1);
+            mbar_init(smem_addr(&bar_empty[i]), 1);
         }
-        s_row[rr] = off;
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_addr(&bar_accf[i]), 1);
+            mbar_init(smem_addr(&bar_acce[i]), TC_EPI_WARPS);
+        }
+        s_abort = 0;
+        fence_barrier_init();
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = s_tmem;
 
-    float acc[9][4];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-
-    // ldmatrix row addresses: A fragment of M tile mt (rows g and g + 8, columns
-    // c and c + 4 of the 8-column step) and B fragments of N tile pairs
-    const int mrow = lane & 7, mblk = lane >> 3;
-    const int a_off = (16 * mt + mrow + 8 * (mblk & 1)) * MLD + 4 * (mblk >> 1);
-    const int b_off = (8 * (nt0 + (mblk >> 1)) + mrow) * MLD + 4 * (mblk & 1);
-
-    // staging: warp w holds rows w, w + 8, ..., w + 248 of a sub-chunk (lane =
-    // component) in registers; the next sub-chunk's loads are issued before
-    // the current one's products, so they are in flight during them
-    float v[32];
-    auto load_rows = [&](int jb) {
-        const bool colok = jb + lane < A.ncomp;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const long long off = s_row[warp + 8 * i];
-            v[i] = (off >= 0 && colok) ? __ldg(A.ring + off + jb + lane) : 0.f;
-        }
-    };
-    __syncthreads();  // s_row
-    load_rows(jc0);
-    for (int js = 0; js < VJCH; js += MJ) {
-        const int jb = jc0 + js;
-        if (jb >= A.ncomp) break;
-        __syncthreads();  // the previous products are done with the staged tiles
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int rr = warp + 8 * i;  // rows 0..63: new samples (i < 8); then the window
-            if (i < 8)
-                stage_split(hA, lA, rr * MLD + lane, v[i]);
-            else
-                stage_split(hW, lW, (rr - VB) * MLD + lane, v[i]);
-        }
-        __syncthreads();
-        if (js + MJ < VJCH && jb + MJ < A.ncomp) load_rows(jb + MJ);
-        // the tensor core adds into its FP32 accumulator with truncation, which
-        // biases long chains of additions; each sub-chunk's 12 products per
-        // entry go to a fresh accumulator that is then added, rounded to
-        // nearest, to the running sum
-        float pacc[9][4];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) pacc[q][0] = pacc[q][1] = pacc[q][2] = pacc[q][3] = 0.f;
-#pragma unroll
-        for (int k8 = 0; k8 < MJ; k8 += 8) {
-            unsigned ah[4], al[4];
-            ldsm_x4(ah, hA + a_off + k8);
-            ldsm_x4(al, lA + a_off + k8);
-#pragma unroll
-            for (int q = 0; q < 9; q += 2) {
-                // N tiles nt0 + q and nt0 + q + 1 (the last pair also loads the tile
-                // after the warp's nine -- rows up to 199, inside the allocation --
-                // and does not use it)
-                unsigned bh[4], bl[4];
-                ldsm_x4(bh, hW + b_off + 8 * q * MLD + k8);
-                ldsm_x4(bl, lW + b_off + 8 * q * MLD + k8);
-                mma_tf32(pacc[q], al, bh);
-                mma_tf32(pacc[q], ah, bl);
-                mma_tf32(pacc[q], ah, bh);
-                if (q + 1 < 9) {
-                    mma_tf32(pacc[q + 1], al, bh + 2);
-                    mma_tf32(pacc[q + 1], ah, bl + 2);
-                    mma_tf32(pacc[q + 1], ah, bh + 2);
+    if (warp == TC_EPI_WARPS) {
+        // ---- TMA producer
+        if (lane == 0) {
+            const int zw = s_lo < 0 ? (int)s_lo : (int)(s_lo % A.cap);
+            const int zn = (int)(tb % A.cap);
+            int c = 0;
+            for (; c < nsub; ++c) {
+                const int st = c % TC_STAGES;
+                if (s_abort) break;
+                if (c >= TC_STAGES &&
+                    !mbar_wait(smem_addr(&bar_empty[st]), ((c / TC_STAGES) - 1) & 1, A.wait_cycles, &s_abort)) {
+                    atomicOr(A.err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
                 }
+                unsigned char *base = sm + st * TC_STAGE_BYTES;
+                const unsigned bar = smem_addr(&bar_full[st]);
+                mbar_expect_tx(bar, TC_STAGE_BYTES);
+                const int x = j0 + c * TC_KC;
+                tma_load_3d(smem_addr(base), &tm_win, x, 0, zw, bar);
+                tma_load_3d(smem_addr(base + TC_A_BYTES), &tm_win, x, 1, zw, bar);
+                tma_load_3d(smem_addr(base + 2 * TC_A_BYTES), &tm_new, x, 0, zn, bar);
+                tma_load_3d(smem_addr(base + 2 * TC_A_BYTES + TC_B_BYTES), &tm_new, x, 1, zn, bar);
+            }
+            // the last copies into each stage have landed before this thread leaves
+            for (int j = c > TC_STAGES ? c - TC_STAGES : 0; j < c; ++j)
+                mbar_wait(smem_addr(&bar_full[j % TC_STAGES]), (j / TC_STAGES) & 1, DRAIN_CYCLES, nullptr);
+        }
+    } else if (warp == TC_EPI_WARPS + 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            // kind::f16 instruction descriptor: FP32 D, fp16 A and B, both
+            // K-major, N = 64, M = 128
+            const unsigned idesc = (1u << 4) | ((unsigned)(VB >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+            int c = 0;
+            for (; c < nsub; ++c) {
+                const int st = c % TC_STAGES, set = c & 1;
+                if (!mbar_wait(smem_addr(&bar_full[st]), (c / TC_STAGES) & 1, A.wait_cycles, &s_abort) ||
+                    (c >= 2 && !mbar_wait(smem_addr(&bar_acce[set]), ((c >> 1) - 1) & 1, A.wait_cycles, &s_abort))) {
+                    atomicOr(A.err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned base = smem_addr(sm + st * TC_STAGE_BYTES);
+                const unsigned a_hi = base, a_lo = base + TC_A_BYTES;
+                const unsigned b_hi = base + 2 * TC_A_BYTES, b_lo = b_hi + TC_B_BYTES;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const unsigned d = tmem + (unsigned)(set * 128 + m * 64);
+#pragma unroll
+                    for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                        const unsigned ao = (unsigned)(m * (TC_A_BYTES / 2) + ks * 32), bo = (unsigned)(ks * 32);
+                        umma_f16(d, umma_desc(a_hi + ao), umma_desc(b_hi + bo), idesc, ks > 0 ? 1u : 0u);
+                        umma_f16(d, umma_desc(a_hi + ao), umma_desc(b_lo + bo), idesc, 1u);
+                        umma_f16(d, umma_desc(a_lo + ao), umma_desc(b_hi + bo), idesc, 1u);
+                    }
+                }
+                umma_commit(smem_addr(&bar_empty[st]));
+                umma_commit(smem_addr(&bar_accf[set]));
+            }
+            // every MMA issued has completed before TMEM is freed
+            if (c > 0)
+                mbar_wait(smem_addr(&bar_accf[(c - 1) & 1]), ((c - 1) >> 1) & 1, DRAIN_CYCLES, nullptr);
+        }
+    } else {
+        // ---- epilogue: window row r of M tile mt
+        const int mt = warp >> 2, q = warp & 3;
+        const int r = 128 * mt + 32 * q + lane;
+        float acc[VB];
+#pragma unroll
+        for (int i = 0; i < VB; ++i) acc[i] = 0.f;
+        for (int c = 0; c < nsub; ++c) {
+            const int set = c & 1;
+            if (!mbar_wait(smem_addr(&bar_accf[set]), (c >> 1) & 1, A.wait_cycles, &s_abort)) {
+                atomicOr(A.err, ERR_TIMEOUT);
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const unsigned taddr = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(set * 128 + mt * 64);
+#pragma unroll
+            for (int g = 0; g < VB / 16; ++g) {
+                unsigned v[16];
+                tmem_ld16(taddr + 16 * g, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[16 * g + i] = __fadd_rn(acc[16 * g + i], __uint_as_float(v[i]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&bar_acce[set]));
+        }
+        if (!s_abort) {
+            // band entries of this row: G(t, k0 + kk) with kk = t + 191 - r,
+            // back in V^2 units (the ring holds 4096 V)
+            const int K1 = A.K + 1;
+            float *out = A.part + (long long)blockIdx.y * VB * K1 + k0;
+#pragma unroll
+            for (int t = 0; t < VB; ++t) {
+                const int kk = t + TC_LT - 1 - r;
+                if (t < nb && kk >= 0 && kk < TC_LT && k0 + kk < K1)
+                    out[(long long)t * K1 + kk] = acc[t] * 5.9604644775390625e-08f;  // 2^-24
             }
         }
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[q][r] = __fadd_rn(acc[q][r], pacc[q][r]);
     }
+    tc_fence_before();
     __syncthreads();
-    // the tile P[t][s] (only the band is read back) and the lag sums over t
-    float *sP = vsm;
-    const int g = lane >> 2, c = lane & 3;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const int t = 16 * mt + g, sr = 8 * (nt0 + q) + 2 * c;
-        sP[t * MPLD + sr] = acc[q][0];
-        sP[t * MPLD + sr + 1] = acc[q][1];
-        sP[(t + 8) * MPLD + sr] = acc[q][2];
-        sP[(t + 8) * MPLD + sr + 1] = acc[q][3];
-    }
-    __syncthreads();
-    // the band: G restricted to this chunk, G(t, k0 + kk) = P[t][t + 127 - kk],
-    // written for the block's samples (coalesced along the lags)
-    const int K1 = A.K + 1;
-    float *out = A.part + (long long)blockIdx.y * VB * K1;
-    for (int e = threadIdx.x; e < nb * VKT; e += blockDim.x) {
-        const int t = e / VKT, kk = e - t * VKT, k = k0 + kk;
-        if (k < K1) out[(long long)t * K1 + k] = sP[t * MPLD + t + (VKT - 1) - kk];
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
     }
 }
 
 cudaError_t prepare_vacf_kernels() {
-    return cudaFuncSetAttribute(k_vacf_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
+    return cudaFuncSetAttribute(k_vacf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+}
+
+// Tensor maps of the fp16 hi/lo ring ([rows][2][ld] halves, rows = cap +
+// TC_ROWS): window boxes of 64 components x 1 plane x TC_ROWS samples and
+// new-sample boxes of 64 x 1 x VB, in the 128-byte swizzle.  Encoded once per
+// ring by the driver's cuTensorMapEncodeTiled (found through the runtime).
+cudaError_t encode_vacf_tensor_maps(Sim &s) {
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)(3ll * s.np), 2, (cuuint64_t)(s.vacf_cap + TC_ROWS)};
+    const cuuint64_t strides[2] = {(cuuint64_t)s.ring_ld * 2, (cuuint64_t)s.ring_ld * 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t box_w[3] = {TC_KC, 1, TC_ROWS}, box_n[3] = {TC_KC, 1, VB};
+    CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(s.tmaps);
+    for (int i = 0; i < 2; ++i) {
+        const CUresult r = encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, s.ring16, dims, strides,
+                                  i == 0 ? box_w : box_n, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 // G(t, k) for the block's samples: the chunk partials summed in chunk order
@@ -445,9 +545,12 @@ cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st) {
     A.cnt = s.vacf_cnt;
     A.np = s.np;
     A.done = reinterpret_cast<unsigned int *>(s.d_vacf + 3);
+    A.err = s.d_err;
+    A.wait_cycles = s.wait_cycles;
     const int K1 = s.vacf_lag + 1;
-    dim3 g1((s.vacf_lag + VKT) / VKT, s.vacf_nchunks);
-    k_vacf_mma<<<g1, 256, MMA_SMEM, st>>>(A);
+    const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(s.tmaps);
+    dim3 g1((s.vacf_lag + TC_LT) / TC_LT, s.vacf_nchunks);
+    k_vacf_tc<<<g1, TC_THREADS, TC_SMEM, st>>>(A, maps[0], maps[1]);
     k_corr_gsum<<<dim3((K1 + 255) / 256, VB), 256, 0, st>>>(A);
     k_msd_scan<<<VB, SCAN_T, 0, st>>>(A);
     k_msd_diag<<<(K1 + VB + 255) / 256, 256, 0, st>>>(A);
