@@ -498,8 +498,14 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
             F[k][1] = rp.gy;
             F[k][2] = rp.gz;
         }
+        // no force anywhere in this warp's row segment (no record entry, no body
+        // force): the collision with literal zero forces, whose force terms the
+        // compiler folds away -- the same operations on the same values as with
+        // F = 0 passed in, so the results are the same bits
+        bool unforced = rp.gx == 0.f && rp.gy == 0.f && rp.gz == 0.f;
         if (FORCED) {
             const int cnt = (int)(unsigned)(__shfl_sync(0xffffffffu, rw[h], 0) & 0xffffffffull);
+            unforced = unforced && cnt == 0;
             if (cnt > 0 && row_ok) {
                 long long sum[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
                 record_sum4(rw[h], cnt, x, sum);
@@ -525,8 +531,13 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
             float g0[Q], g1[Q], o0[Q], o1[Q];
 #pragma unroll
             for (int a = 0; a < Q; ++a) unpack2<St>(j ? p[h][a].y : p[h][a].x, a, g0[a], g1[a]);
-            collide_values(g0, rp.omega, F[2 * j][0], F[2 * j][1], F[2 * j][2], o0);
-            collide_values(g1, rp.omega, F[2 * j + 1][0], F[2 * j + 1][1], F[2 * j + 1][2], o1);
+            if (unforced) {
+                collide_values(g0, rp.omega, 0.f, 0.f, 0.f, o0);
+                collide_values(g1, rp.omega, 0.f, 0.f, 0.f, o1);
+            } else {
+                collide_values(g0, rp.omega, F[2 * j][0], F[2 * j][1], F[2 * j][2], o0);
+                collide_values(g1, rp.omega, F[2 * j + 1][0], F[2 * j + 1][1], F[2 * j + 1][2], o1);
+            }
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const unsigned w = pack2<St>(o0[a], o1[a], a);

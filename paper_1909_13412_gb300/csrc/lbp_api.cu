@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbp_internal.cuh"
 
 using namespace lbp;
@@ -31,6 +33,16 @@ struct lbp_sim : public lbp::Sim {
 };
 
 namespace {
+
+// NVTX range for profilers and tracers (a no-op unless a tool is attached):
+// every ABI entry point that queues GPU work, and the step's launches, are
+// named on the host timeline
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 thread_local std::string g_err;
 
@@ -130,6 +142,7 @@ struct Readback {
     double *r, *v;  // device-accessible addresses of page-locked host buffers
 };
 lbp_status enqueue_step(lbp_sim *s, bool timed, const Readback *readback = nullptr) {
+    Range range("lbp step: particles + lattice pass");
     const void *src = s->f[s->cur];
     void *dst = s->f[s->cur ^ 1];
     const int parity = s->cur;
@@ -173,6 +186,7 @@ lbp_status join_vacf(lbp_sim *s) {
 }
 
 lbp_status fork_vacf(lbp_sim *s) {
+    Range range("lbp VACF/MSD block");
     TRY(join_vacf(s));
     CK(cudaEventRecord(s->ev_fork, s->s0));
     CK(cudaStreamWaitEvent(s->s1, s->ev_fork, 0));
@@ -888,6 +902,7 @@ lbp_status lbp_particles_read_cells(lbp_sim *s, int32_t *base, double *frac, int
 }
 
 lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
+    Range range("lbp_step");
     CHECK_SIM(s);
     if (nsteps < 0) return fail(LBP_EINVAL, "lbp_step: nsteps < 0");
     if (nsteps == 0) return LBP_OK;
@@ -898,6 +913,7 @@ lbp_status lbp_step(lbp_sim *s, int64_t nsteps) {
 
 
 lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double *v, int on_device) {
+    Range range("lbp_step_exchange");
     CHECK_SIM(s);
     TRY(enter(s));
     const int n = s->np;
@@ -1031,6 +1047,7 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
 
 static lbp_status vacf_read_impl(lbp_sim *s, double *csum, int64_t *counts, int on_device,
                                  int nsets) {
+    Range range("lbp_vacf_read (flush)");
     TRY(enter(s));
     TRY(join_vacf(s));
     CK(launch_vacf_block(*s, true, s->s0));
@@ -1051,6 +1068,7 @@ lbp_status lbp_vacf_read(lbp_sim *s, double *csum, int64_t *counts, int on_devic
 }
 
 lbp_status lbp_msd_read(lbp_sim *s, double *msum, int64_t *counts, int on_device) {
+    Range range("lbp_msd_read (flush)");
     CHECK_SIM(s);
     if (s->vacf_lag < 0) return fail(LBP_ESTATE, "lbp_msd_read: VACF not configured (lbp_vacf_configure)");
     if (s->vacf_pp) return fail(LBP_ESTATE, "lbp_msd_read: not kept when the VACF is configured per particle");
@@ -1115,6 +1133,7 @@ lbp_status lbp_set_block_rows(lbp_sim *s, int rows) {
 }
 
 lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *variant, double *ms) {
+    Range range("lbp_autotune");
     CHECK_SIM(s);
     if (launches < 1 || launches > 1000) return fail(LBP_EINVAL, "lbp_autotune: launches must be in [1, 1000]");
     TRY(enter(s));
@@ -1190,6 +1209,7 @@ lbp_status lbp_autotune(lbp_sim *s, int launches, int *rows, int *variant, doubl
 
 lbp_status lbp_adjoint_record(lbp_sim *s, int64_t nsteps, int checkpoint_every, double *v_traj,
                               double *r_traj, int on_device) {
+    Range range("lbp_adjoint_record");
     CHECK_SIM(s);
     if (nsteps < 1 || checkpoint_every < 1)
         return fail(LBP_EINVAL, "lbp_adjoint_record: need nsteps >= 1 and checkpoint_every >= 1");
@@ -1243,6 +1263,7 @@ lbp_status lbp_adjoint_record(lbp_sim *s, int64_t nsteps, int checkpoint_every, 
 
 lbp_status lbp_adjoint_backward(lbp_sim *s, const double *g_v, const double *g_r, int on_device,
                                 const lbp_gradients *out) {
+    Range range("lbp_adjoint_backward");
     CHECK_SIM(s);
     if (!out) return fail(LBP_EINVAL, "lbp_adjoint_backward: null grads");
     const lbp::Tape &tp = s->tape;
@@ -1541,6 +1562,7 @@ lbp_status lbp_checkpoint_size(lbp_sim *s, size_t *bytes) {
 }
 
 lbp_status lbp_checkpoint_save(lbp_sim *s, void *buf, int on_device) {
+    Range range("lbp_checkpoint_save");
     CHECK_SIM(s);
     if (!buf) return fail(LBP_EINVAL, "lbp_checkpoint_save: null buffer");
     TRY(enter(s));
@@ -1566,6 +1588,7 @@ lbp_status lbp_checkpoint_save(lbp_sim *s, void *buf, int on_device) {
 }
 
 lbp_status lbp_checkpoint_load(lbp_sim *s, const void *buf, int on_device) {
+    Range range("lbp_checkpoint_load");
     CHECK_SIM(s);
     if (!buf) return fail(LBP_EINVAL, "lbp_checkpoint_load: null buffer");
     int64_t h[CKPT_HEADER], want[CKPT_HEADER];
@@ -1642,6 +1665,7 @@ lbp_status lbp_budget_track(lbp_sim *s, int enable) {
 }
 
 lbp_status lbp_budget(lbp_sim *s, double *out) {
+    Range range("lbp_budget");
     CHECK_SIM(s);
     if (!out) return fail(LBP_EINVAL, "lbp_budget: null out");
     TRY(enter(s));

@@ -371,14 +371,16 @@ __global__ void __launch_bounds__(256) k_corr_gsum(const VacfArgs A) {
     const long long stride = (long long)VB * K1;
     const float *p = A.part + (long long)t * K1 + k;
     double g = 0.0;
+#pragma unroll 8
     for (int c = 0; c < A.nchunks; ++c) g += (double)p[c * stride];
     A.G[(long long)t * K1 + k] = g;
 }
 
 // H(t, k) = G(t, 0) + 2 sum_{m=1}^{k-1} G(t, m) for k = 1..K, one CTA per sample
-// row: a block-wide inclusive scan of 2 G(t, m) over m = 1..K-1 in tiles of
-// 1024, in a fixed order (FP64).  H(t, 0) = 0.
-constexpr int SCAN_T = 1024;
+// row: each thread sums a run of consecutive m, the runs' totals are scanned
+// across the CTA (warp shuffles, then the warps' totals in order), and each
+// thread writes its run's prefix sums -- a fixed order (FP64).  H(t, 0) = 0.
+constexpr int SCAN_T = 256;
 __global__ void __launch_bounds__(SCAN_T) k_msd_scan(const VacfArgs A) {
     long long tb, te;
     if (!vacf_range(A, tb, te)) return;
@@ -387,27 +389,35 @@ __global__ void __launch_bounds__(SCAN_T) k_msd_scan(const VacfArgs A) {
     const int K1 = A.K + 1;
     const double *g = A.G + (long long)t * K1;
     double *h = A.H + (long long)t * K1;
-    __shared__ double sh[SCAN_T];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nm = A.K - 1;  // terms m = 1 .. K - 1
+    const int per = nm > 0 ? (nm + SCAN_T - 1) / SCAN_T : 0;
+    const int m0 = 1 + threadIdx.x * per;
+    double run = 0.0;
+    for (int i = 0; i < per; ++i)
+        if (m0 + i <= nm) run += 2.0 * g[m0 + i];
+    double x = run;  // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __shared__ double wsum[SCAN_T / 32];
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    double pre = x - run;  // the terms before this thread's run
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
     const double g0 = g[0];
-    double carry = 0.0;  // 2 sum of G(t, m) over the tiles before
-    if (threadIdx.x == 0) h[0] = 0.0;
-    // H(t, k) for k = 1 + m0 + i uses the scan of m = 1 .. k - 1
-    for (int m0 = 0; m0 < A.K; m0 += SCAN_T) {
-        const int i = threadIdx.x;
-        const int m = m0 + i;  // H index k = m + 1 takes G(t, 1..m)
-        double v = (m >= 1 && m < K1) ? 2.0 * g[m] : 0.0;
-        sh[i] = v;
-        __syncthreads();
-        for (int off = 1; off < SCAN_T; off <<= 1) {
-            const double add = i >= off ? sh[i - off] : 0.0;
-            __syncthreads();
-            sh[i] += add;
-            __syncthreads();
+    if (threadIdx.x == 0) {
+        h[0] = 0.0;
+        if (A.K >= 1) h[1] = g0;
+    }
+    for (int i = 0; i < per; ++i) {
+        const int m = m0 + i;
+        if (m <= nm) {
+            pre += 2.0 * g[m];
+            h[m + 1] = g0 + pre;
         }
-        const double incl = carry + sh[i];
-        if (m + 1 < K1) h[m + 1] = g0 + incl;
-        carry += sh[SCAN_T - 1];
-        __syncthreads();
     }
 }
 
@@ -415,7 +425,8 @@ __global__ void __launch_bounds__(SCAN_T) k_msd_scan(const VacfArgs A) {
 // with k = d - (nb - 1) + j, W(e, k) = W(e - 1, k - 1) + H(e, k) (W(., 0) = 0),
 // starting from the kept W(tb - 1, .) and leaving W(te - 1, d) for the next
 // block.  Writes W[j][k] for 1 <= k <= K.
-__global__ void __launch_bounds__(256) k_msd_diag(const VacfArgs A) {
+constexpr int DIAG_T = 64;  // small blocks: the walk is latency-bound, so spread it over SMs
+__global__ void __launch_bounds__(DIAG_T) k_msd_diag(const VacfArgs A) {
     long long tb, te;
     if (!vacf_range(A, tb, te)) return;
     const int nb = (int)(te - tb);
@@ -425,13 +436,23 @@ __global__ void __launch_bounds__(256) k_msd_diag(const VacfArgs A) {
     const int par = (int)(A.d_vacf[4] & 1);
     const double *prev = A.wstate + (long long)par * K1;
     double *next = A.wstate + (long long)(par ^ 1) * K1;
-    int k = d - nb;  // k at sample tb - 1
-    double w = k >= 1 ? prev[k] : 0.0;
-    for (int j = 0; j < nb; ++j) {
-        ++k;
-        if (k >= 1 && k < K1) {
-            w += A.H[(long long)j * K1 + k];
-            A.W[(long long)j * K1 + k] = w;
+    const int k0 = d - nb;  // k at sample tb - 1
+    double w = k0 >= 1 ? prev[k0] : 0.0;
+    // the walk's loads are independent of one another: 16 at a time in flight
+    for (int j0 = 0; j0 < nb; j0 += 16) {
+        double hv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = j0 + i, k = k0 + 1 + j;
+            hv[i] = (j < nb && k >= 1 && k < K1) ? A.H[(long long)j * K1 + k] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int j = j0 + i, k = k0 + 1 + j;
+            if (j < nb && k >= 1 && k < K1) {
+                w += hv[i];
+                A.W[(long long)j * K1 + k] = w;
+            }
         }
     }
     if (d < K1) next[d] = w;
@@ -440,7 +461,8 @@ __global__ void __launch_bounds__(256) k_msd_diag(const VacfArgs A) {
 // C(k) += sum_t G(t, k); M(k) += sum_{e >= k} W(e, k); pair counts (the same
 // origins for both).  The last block marks the samples done and flips the
 // parity of the kept W.
-__global__ void __launch_bounds__(256) k_corr_acc(const VacfArgs A) {
+constexpr int ACC_T = 64;
+__global__ void __launch_bounds__(ACC_T) k_corr_acc(const VacfArgs A) {
     long long tb, te;
     if (!vacf_range(A, tb, te)) return;
     const int nb = (int)(te - tb);
@@ -448,9 +470,19 @@ __global__ void __launch_bounds__(256) k_corr_acc(const VacfArgs A) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < K1) {
         double c = 0.0, m = 0.0;
-        for (int j = 0; j < nb; ++j) {
-            c += A.G[(long long)j * K1 + k];
-            if (k >= 1 && tb + j >= k) m += A.W[(long long)j * K1 + k];
+        for (int j0 = 0; j0 < nb; j0 += 16) {
+            double gv[16], wv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = j0 + i;
+                gv[i] = j < nb ? A.G[(long long)j * K1 + k] : 0.0;
+                wv[i] = (j < nb && k >= 1 && tb + j >= k) ? A.W[(long long)j * K1 + k] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                c += gv[i];
+                m += wv[i];
+            }
         }
         A.sum[k] += c;
         A.msd[k] += m;
@@ -553,8 +585,8 @@ cudaError_t launch_vacf_block(Sim &s, bool flush, cudaStream_t st) {
     k_vacf_tc<<<g1, TC_THREADS, TC_SMEM, st>>>(A, maps[0], maps[1]);
     k_corr_gsum<<<dim3((K1 + 255) / 256, VB), 256, 0, st>>>(A);
     k_msd_scan<<<VB, SCAN_T, 0, st>>>(A);
-    k_msd_diag<<<(K1 + VB + 255) / 256, 256, 0, st>>>(A);
-    k_corr_acc<<<(K1 + 255) / 256, 256, 0, st>>>(A);
+    k_msd_diag<<<(K1 + VB + DIAG_T - 1) / DIAG_T, DIAG_T, 0, st>>>(A);
+    k_corr_acc<<<(K1 + ACC_T - 1) / ACC_T, ACC_T, 0, st>>>(A);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,12 @@
     of Brownian particles (the library's all-origins estimator).
   * ``tail_amplitude`` -- the long-time tail C_v(t)/C_v(0) ~ B t^(-3/2),
     B = M / [12 rho0 (pi nu)^(3/2)], measured on the kicked particle.
+  * ``brownian_run`` / ``config2`` -- the Brownian suspension at its stated
+    size and length (128^3, 2000 particles, kT = 1e-4, 2 x 10^4 steps, VACF
+    and MSD to lag 5000), in independent realisations: particle updates per
+    second, the log-log slope and amplitude of the VACF tail over a window
+    with their spread over the realisations, and the diffusion coefficient
+    from the MSD against the Green-Kubo integral of the VACF.
 
 Every step of every run is the library's CUDA path; this module only sets up
 inputs, reads results and does the bookkeeping of each experiment.  Run as
@@ -161,9 +167,71 @@ def tail_amplitude(L, tau, M, gamma, T, window, V0=0.01):
     return B, M / (12.0 * (math.pi * nu_of(tau)) ** 1.5), slope
 
 
+def brownian_run(L, tau, n, M, gamma, kT, steps, max_lag, seed):
+    """One realisation of a Brownian suspension: n particles at uniform random
+    positions with Maxwellian velocities, `steps` steps, VACF and MSD to
+    `max_lag`.  Returns (C(k)/C(0), MSD(k) per pair, C(0) per pair, seconds of
+    stepping, measured on the device)."""
+    import time
+    from . import workloads as wl
+    ps = wl.uniform_particles(n, (L, L, L), M, gamma, wl.stokes_radius(gamma, tau), kT, seed, seed + 1)
+    h = lbp.lbp_create(L, L, L, tau)
+    try:
+        lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        lbp.lbp_particles_set_params(h, kT=kT, seed=seed + 2)
+        lbp.lbp_step(h, 2)
+        lbp.lbp_autotune(h, 5)
+        lbp.lbp_vacf_configure(h, max_lag)
+        cs = np.empty(max_lag + 1)
+        cnt = np.empty(max_lag + 1, np.int64)
+        ms = np.empty(max_lag + 1)
+        lbp.lbp_vacf_read(h, cs, cnt)  # waits for the set-up
+        t0 = time.perf_counter()
+        lbp.lbp_step(h, steps)
+        lbp.lbp_vacf_read(h, cs, cnt)  # host read: waits for every step and block
+        secs = time.perf_counter() - t0
+        lbp.lbp_msd_read(h, ms, cnt)
+        lbp.lbp_check(h)
+    finally:
+        lbp.lbp_destroy(h)
+    C = cs / cnt
+    return C / C[0], ms / cnt, float(C[0]), secs
+
+
+def config2_statistics(runs, window, M, tau):
+    """Tail statistics of independent realisations (lists of C/C(0) and MSD
+    arrays): per realisation the log-log slope of C/C(0) over `window` and the
+    amplitude B = mean over the window of C/C(0) t^(3/2); reported as the
+    mean and the standard error over realisations.  D from the MSD's slope
+    over the last half of the lags (per component: MSD / 6 per step) against
+    the Green-Kubo integral of the VACF over the same lags."""
+    t0, t1 = window
+    t = np.arange(t0, t1 + 1)
+    slopes, amps, d_msd, d_gk = [], [], [], []
+    for C, msd, c0 in runs:
+        y = C[t0:t1 + 1]
+        slopes.append(float(np.polyfit(np.log(t), np.log(np.abs(y)), 1)[0]))
+        amps.append(float(np.mean(y * t ** 1.5)))
+        K = len(msd) - 1
+        k = np.arange(K // 2, K + 1)
+        d_msd.append(float(np.polyfit(k, msd[K // 2:], 1)[0] / 6.0))
+        # discrete Green-Kubo: MSD(k)/k -> C(0) + 2 sum_{m>=1} C(m) (per pair), over 6
+        d_gk.append(float(c0 * (1.0 + 2.0 * C[1:K // 2].sum()) / 6.0))
+    n = len(runs)
+    se = lambda v: float(np.std(v, ddof=1) / math.sqrt(n)) if n > 1 else float("nan")
+    return {"window": [t0, t1], "realisations": n,
+            "slope": float(np.mean(slopes)), "slope_se": se(slopes),
+            "B": float(np.mean(amps)), "B_se": se(amps),
+            "B_paper": M / (12.0 * (math.pi * nu_of(tau)) ** 1.5),
+            "D_msd": float(np.mean(d_msd)), "D_msd_se": se(d_msd),
+            "D_green_kubo": float(np.mean(d_gk)), "D_green_kubo_se": se(d_gk)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("experiment", choices=["fig1", "fig3", "tail"])
+    ap.add_argument("experiment", choices=["fig1", "fig3", "tail", "config2"])
+    ap.add_argument("--realisations", type=int, default=4)
+    ap.add_argument("--window", type=int, nargs=2, default=[100, 400])
     ap.add_argument("--paper", action="store_true",
                     help="fig1 at the paper's parameters (100^3 box, nu = 0.0178, U = 1e-4)")
     a = ap.parse_args(argv)
@@ -188,6 +256,22 @@ def main(argv=None):
                           "V_R": [float(kick[t - 1] / kick[0]) for t in (1, 5, 10, 20, 50, 100, 200, 400)],
                           "A_R": [float(A_R[t - 1] / A_R[0]) for t in (1, 5, 10, 20, 50, 100, 200, 400)],
                           "C_v": [float(C[t - 1] / C[0]) for t in (1, 5, 10, 20, 50, 100, 200, 400)]}))
+    elif a.experiment == "config2":
+        from . import workloads as wl
+        w = wl.BROWNIAN_128
+        L, tau, n, kT = w.shape_zyx[0], w.tau, w.n_particles, w.kT
+        runs, secs = [], []
+        for r in range(a.realisations):
+            C, msd, c0, sec = brownian_run(L, tau, n, w.M, w.gamma, kT, w.steps, w.vacf_lag, 100 + 10 * r)
+            runs.append((C, msd, c0))
+            secs.append(sec)
+        out = config2_statistics(runs, tuple(a.window), w.M, tau)
+        out.update({"workload": w.name, "steps": w.steps, "max_lag": w.vacf_lag,
+                    "particle_updates_per_s": n * w.steps / float(np.mean(secs)),
+                    "mlups": L ** 3 * w.steps / float(np.mean(secs)) / 1e6,
+                    "C_over_C0": {str(t): float(np.mean([c[0][t] for c in runs])) for t in
+                                  (1, 10, 50, 100, 200, 400, 1000)}})
+        print(json.dumps(out))
     else:
         B, B_th, slope = tail_amplitude(128, 0.8, 10.0, 0.5, 3000, (600, 2000))
         print(json.dumps({"B_measured": B, "B_theory": B_th, "slope": slope}))
