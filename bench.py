@@ -55,6 +55,9 @@ VACF_LAG = 5000
 SHAPE_NAMES = [{0: "1node", 1: "2nodes", 3: "4nodes"}[v] + ("_1row" if r == 1 else f"_{r}rows")
                if v != 2 else "bulk_staged" for v, r in AUTOTUNE_SHAPES]
 SHAPES = dict(zip(SHAPE_NAMES, AUTOTUNE_SHAPES))
+# the lattice kernel each variant launches when the box holds particles
+LATTICE_KERNEL = {0: "k_stream_collide_forced", 1: "k_stream_collide_pair", 2: "k_stream_collide_staged",
+                  3: "k_stream_collide_quad"}
 LAUNCHES_PER_STEP = 2  # particles, stream-collide
 VACF_LAUNCHES = 5      # per block of 64 samples: correlator, chunk sum, MSD scan, MSD diagonals, sums
 
@@ -488,6 +491,7 @@ def run_gpu(args, w):
             vach = BYTES_PER_NODE[prec] * w.nodes / (vk3 * 1e-3) / 1e9
             variants[prec] = {"value": aggregate_mlups(world, w.nodes, vsteps, vms), "unit": "MLUPS",
                               "steps": vsteps, "ms_per_step": vms / vsteps,
+                              "kernel": LATTICE_KERNEL[SHAPES[hv.tuned["variant"]][0]],
                               "stream_collide_ms": vk3, "achieved_gbs": vach,
                               "frac": vach / measured_peaks()[0],
                               "traffic": recorded_traffic(prec, hv.tuned["variant"]) if w is wl.BROWNIAN_256
@@ -535,7 +539,7 @@ def run_gpu(args, w):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(w, world, args.vacf_lag, args.precision),
-        "roofline": {"bound": "hbm", "kernel": "k_stream_collide_forced", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": LATTICE_KERNEL[SHAPES[tuned["variant"]][0]], "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE[args.precision] * w.nodes,

@@ -54,6 +54,8 @@ def bind(path: str):
     L.or_moments.argtypes = [_dp, _dp, _dp, C.c_int64]
     L.or_feq.argtypes = [C.c_double, _dp, _dp]
     L.or_collide.argtypes = [_dp, _dp, _dp, vp, C.c_double, C.c_int64, _dp]
+    L.or_collide_dev.argtypes = [_dp, _dp, _dp, vp, C.c_double, C.c_int64, _dp]
+    L.or_set_deviation.argtypes = [vp, C.c_int]
     L.or_set_body_force.argtypes = [vp, _dp]
     L.or_corners.argtypes = [_dp, _i32p, _dp, _dp]
     L.or_stokeslet_fit.argtypes = [_dp, _dp, _dp, C.c_double, C.c_int, _dp]
@@ -207,15 +209,19 @@ def num_threads():
 class Sim:
     """Periodic LBM box with Langevin particles; one ``step`` = one time step."""
 
-    def __init__(self, nx, ny, nz, tau, library=None):
+    def __init__(self, nx, ny, nz, tau, library=None, deviation=False):
         """``library``: another compiled copy of the oracle (``bind``), used by the
-        tests that check that a pin fails when a mistake is planted in a copy."""
+        tests that check that a pin fails when a mistake is planted in a copy.
+        ``deviation``: keep and step the state as g = fhat - w_a (the same
+        method, a self-check of the deviation algebra); fhat in and out stays
+        the full population."""
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.tau = tau
         self.np = 0
         self._L = library if library is not None else lib()
         self._h = self._L.or_create(nx, ny, nz, float(tau))
+        self._L.or_set_deviation(self._h, int(bool(deviation)))
 
     def close(self):
         if self._h:

@@ -22,7 +22,10 @@
  *        trilinear weights of r_i^n
  *     6. Langevin update (Eqs. 1-2), semi-implicit Euler, dt = 1
  *     7. BGK collision with body force (Eqs. 14, 15, 17, 18, 19)
- *   The state kept between steps is the post-collision fhat.
+ *   The state kept between steps is the post-collision fhat.  The same step
+ *   also runs in deviation form (or_set_deviation): the state is then
+ *   g = fhat - w_a, streamed the same way, with the moments rho~ - 1 and u
+ *   and the collision of or_collide_dev -- a self-check of that algebra.
  *
  * Readings where the paper is silent:
  *   D3Q15 table: e_0 = 0 (w 2/9), 6 faces (w 1/9), 8 corners (w 1/72).
@@ -153,6 +156,28 @@ void or_collide(const double *f, const double *rho, const double *u, const doubl
             if (F) G = 3.0 * (F[i] * E[a][0] + F[N + i] * E[a][1] + F[2 * N + i] * E[a][2]);
             double Qa = (feq[a] - f[a * N + i]) / tau;
             fhat[a * N + i] = f[a * N + i] + Qa + W[a] * G;
+        }
+    }
+}
+
+/* The same collision in deviation form, g = f - w_a (a self-check of the
+ * algebra the storage of the GPU path relies on).  With sum_a w_a = 1 and
+ * sum_a w_a e_a = 0, the moments of g are rho~ - 1 (drho) and u, and
+ * f^eq_a - w_a = w_a [(rho~ - 1) + 3 u.e_a + 9/2 (u.e_a)^2 - 3/2 u.u], so
+ * ghat_a = g_a + (g^eq_a - g_a)/tau + w_a G_a is fhat_a - w_a exactly.   */
+void or_collide_dev(const double *g, const double *drho, const double *u, const double *F,
+                    double tau, int64_t N, double *ghat)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double ux = u[i], uy = u[N + i], uz = u[2 * N + i];
+        double uu = ux * ux + uy * uy + uz * uz;
+        for (int a = 0; a < Q; ++a) {
+            double eu = E[a][0] * ux + E[a][1] * uy + E[a][2] * uz;
+            double geq = W[a] * (drho[i] + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+            double G = 0.0;
+            if (F) G = 3.0 * (F[i] * E[a][0] + F[N + i] * E[a][1] + F[2 * N + i] * E[a][2]);
+            ghat[a * N + i] = g[a * N + i] + (geq - g[a * N + i]) / tau + W[a] * G;
         }
     }
 }
@@ -298,6 +323,7 @@ typedef struct {
     int mode, exclude_inside;
     int64_t step;
     double G[3]; /* uniform body force density on every node (Eq. 18) */
+    int deviation; /* fhat, f hold g = f - w_a, and rho holds rho~ - 1 */
 } or_sim;
 
 or_sim *or_create(int nx, int ny, int nz, double tau)
@@ -326,8 +352,29 @@ void or_destroy(or_sim *s)
     free(s);
 }
 
-void or_set_fhat(or_sim *s, const double *fhat) { memcpy(s->fhat, fhat, sizeof(double) * Q * s->N); }
-void or_get_fhat(const or_sim *s, double *fhat) { memcpy(fhat, s->fhat, sizeof(double) * Q * s->N); }
+/* fhat in and out is always the full population; in deviation form the
+ * state keeps fhat - w_a.                                                */
+void or_set_fhat(or_sim *s, const double *fhat)
+{
+    for (int a = 0; a < Q; ++a)
+        for (int64_t i = 0; i < s->N; ++i)
+            s->fhat[a * s->N + i] = s->deviation ? fhat[a * s->N + i] - W[a] : fhat[a * s->N + i];
+}
+void or_get_fhat(const or_sim *s, double *fhat)
+{
+    for (int a = 0; a < Q; ++a)
+        for (int64_t i = 0; i < s->N; ++i)
+            fhat[a * s->N + i] = s->deviation ? s->fhat[a * s->N + i] + W[a] : s->fhat[a * s->N + i];
+}
+/* Switch the stored state between full and deviation form. */
+void or_set_deviation(or_sim *s, int on)
+{
+    on = on != 0;
+    if (on == s->deviation) return;
+    for (int a = 0; a < Q; ++a)
+        for (int64_t i = 0; i < s->N; ++i) s->fhat[a * s->N + i] += on ? -W[a] : W[a];
+    s->deviation = on;
+}
 void or_set_step(or_sim *s, int64_t step) { s->step = step; }
 int64_t or_get_step(const or_sim *s) { return s->step; }
 
@@ -337,6 +384,8 @@ void or_get_fields(or_sim *s, double *rho, double *u, double *p)
 {
     or_stream(s->fhat, s->f, s->nx, s->ny, s->nz);
     or_moments(s->f, rho, u, s->N);
+    if (s->deviation)
+        for (int64_t i = 0; i < s->N; ++i) rho[i] += 1.0;
     if (p)
         for (int64_t i = 0; i < s->N; ++i) p[i] = rho[i] / 3.0;
 }
@@ -475,7 +524,10 @@ static void one_step(or_sim *s)
         }
     }
     /* 7: collision with the body force */
-    or_collide(s->f, s->rho, s->u, s->F, s->tau, N, s->fhat);
+    if (s->deviation)
+        or_collide_dev(s->f, s->rho, s->u, s->F, s->tau, N, s->fhat);
+    else
+        or_collide(s->f, s->rho, s->u, s->F, s->tau, N, s->fhat);
     s->step += 1;
 }
 

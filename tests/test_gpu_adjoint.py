@@ -164,6 +164,63 @@ def test_adjoint_of_a_vacf_loss():
     assert_close(got, want, 1e-4)
 
 
+BATCH = [((14, 12, 10), 0.6, 4), ((9, 8, 12), 0.8, 0), ((16, 6, 5), 1.0, 3)]  # (nx, ny, nz), tau, particles
+
+
+def _box_leaves(b, shape, tau, n):
+    nx, ny, nz = shape
+    g = np.random.default_rng(70 + b)
+    fhat = W[:, None, None, None] * (1.0 + 0.02 * g.uniform(-1, 1, (15, nz, ny, nx)))
+    r = np.floor(g.uniform(0, 1, (n, 3)) * [nx, ny, nz]) + g.uniform(0.3, 0.7, (n, 3))
+    t = lambda a: torch.tensor(np.asarray(a, dtype=np.float64), requires_grad=True)
+    return dict(tau=t(tau), gamma=t(g.uniform(0.3, 0.7, n)), radius=t(g.uniform(0.15, 0.4, n)),
+                mass=t(g.uniform(4.0, 8.0, n)), v0=t(g.normal(0, 0.01, (n, 3))), r0=t(r), f0=t(fhat))
+
+
+def test_batched_autograd_run_equals_its_boxes():
+    """batch_trajectory over three boxes of different sizes and relaxation times
+    (one without particles) under a loss that mixes them -- the ensemble VACF
+    of Section 3 over all particles plus a linear functional: the trajectories
+    and every gradient (tau per box, gamma, R, M, V0, r0, f0) equal, bit for bit,
+    those of each box run alone through trajectory() and driven back with its
+    slice of the same upstream gradient; the particle-free box gets zero."""
+    steps, C, K = 25, 10, 8
+    per = [_box_leaves(b, *bx) for b, bx in enumerate(BATCH)]
+    counts = tuple(n for _, _, n in BATCH)
+    cat = lambda k: torch.cat([p[k].detach() for p in per if p[k].numel()], 0)
+    bl = {k: cat(k).clone().requires_grad_(True) for k in ("gamma", "radius", "mass", "v0", "r0")}
+    bl["tau"] = torch.tensor([tau for _, tau, _ in BATCH], dtype=torch.float64, requires_grad=True)
+    bl["f0"] = torch.cat([p["f0"].detach().reshape(15, -1) for p in per], 1).requires_grad_(True)
+    spec = adjoint.BatchSpec(tuple(s for s, _, _ in BATCH), counts, steps, C)
+    Vt, rt = adjoint.batch_trajectory(bl["tau"], bl["gamma"], bl["radius"], bl["mass"], bl["v0"],
+                                      bl["r0"], spec, f0=bl["f0"])
+    n = sum(counts)
+    Vd, rd = Vt.detach().requires_grad_(True), rt.detach().requires_grad_(True)
+    C_k = adjoint.vacf(Vd, K)
+    loss = ((C_k / C_k[0].detach() - 0.5) ** 2).sum() + linear_loss(steps, n, seed=4)(Vd, rd)
+    gV, gR = torch.autograd.grad(loss, (Vd, rd))
+    torch.autograd.backward((Vt, rt), (gV, gR))
+    p0, node0 = 0, 0
+    for b, ((nx, ny, nz), tau, nb) in enumerate(BATCH):
+        Nb = nx * ny * nz
+        x = per[b]
+        if nb == 0:
+            assert bl["tau"].grad[b].item() == 0.0
+            assert not torch.any(bl["f0"].grad[:, node0:node0 + Nb])
+        else:
+            sl = slice(p0, p0 + nb)
+            Vb, rb = adjoint.trajectory(x["tau"], x["gamma"], x["radius"], x["mass"], x["v0"], x["r0"],
+                                        adjoint.RunSpec(nx, ny, nz, steps, C), f0=x["f0"])
+            assert torch.equal(Vb, Vt[:, sl].detach()) and torch.equal(rb, rt[:, sl].detach()), b
+            torch.autograd.backward((Vb, rb), (gV[:, sl].contiguous(), gR[:, sl].contiguous()))
+            assert x["tau"].grad.item() == bl["tau"].grad[b].item() != 0.0, b
+            for k in ("gamma", "radius", "mass", "v0", "r0"):
+                assert torch.equal(x[k].grad, bl[k].grad[sl]), (b, k)
+            assert torch.equal(x["f0"].grad.reshape(15, -1), bl["f0"].grad[:, node0:node0 + Nb]), b
+        p0 += nb
+        node0 += Nb
+
+
 def test_checkpoint_interval_and_repeat_are_bitwise_invariant():
     c = case(seed=5)
     steps = 30

@@ -583,3 +583,39 @@ def test_msd_of_the_ornstein_uhlenbeck_process():
     D = kT / gamma
     corr = 1 - 2 * a * (1 - a ** K) / (K * (1 - a) * (1 + a))
     assert ms[K] / cnt[K] / (6 * D * K) == pytest.approx(corr, rel=0.06)
+
+
+@pytest.mark.parametrize("amp", [1e-7, 0.02])
+def test_deviation_form_self_check(amp):
+    """The oracle run in deviation form (state g = fhat - w_a, moments rho~ - 1
+    and u, g^eq = w_a[(rho~ - 1) + 3 u.e + 9/2 (u.e)^2 - 3/2 u.u]; the algebra
+    the GPU storage relies on, Eqs. 12-13 and 17 with sum w = 1, sum w e = 0)
+    agrees with the full form over 40 coupled steps with noise and an external
+    force, to the full form's own FP64 rounding: populations within 8 units in
+    the last place of max fhat per step, V within 1e-12 of max |V|, r within
+    16 units in the last place of the box size."""
+    shape = (9, 10, 12)
+    g = np.random.default_rng(1)
+    fh = W[:, None, None, None] * (1 + amp * g.uniform(-1, 1, (15,) + shape))
+    n, steps = 6, 40
+    r = g.uniform(0, 1, (n, 3)) * [12, 10, 9]
+    V = g.normal(0, 0.01, (n, 3))
+    res = []
+    for dev in (False, True):
+        s = oracle.Sim(12, 10, 9, 0.7, deviation=dev)
+        s.set_fhat(fh)
+        s.add_particles(r, V, 6.0, 0.5, 0.2)
+        s.set_params(kT=1e-4, seed=3)
+        s.set_external(np.full((n, 3), 1e-5))
+        s.step(steps)
+        rho = s.fields()[0]
+        res.append((s.fhat(), *s.particles()[:2], rho))
+        s.close()
+    (fa, ra, va, rhoa), (fb, rb, vb, rhob) = res
+    ulp = 2.0 ** -53
+    assert np.abs(fa - fb).max() <= 8 * steps * ulp * np.abs(fa).max()
+    assert np.abs(rhoa - rhob).max() <= 16 * steps * ulp * np.abs(rhoa).max()
+    assert np.abs(va - vb).max() <= 1e-12 * np.abs(va).max()
+    assert np.abs(ra - rb).max() <= 16 * ulp * 12
+    # the particles moved the fluid well away from rest: the check is not vacuous
+    assert np.abs(fa - W[:, None, None, None]).max() > 1e-4
