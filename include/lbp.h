@@ -233,8 +233,13 @@ lbp_status lbp_get_step_index(lbp_sim *sim, int64_t *step);
  * step's post-update velocities are samples t = 0, 1, ...; lbp_vacf_read gives
  * csum[k] = sum over particles i and origins t0 with t0 + k <= last sample of
  * V_i(t0).V_i(t0+k), and counts[k] = the number of (i, t0) pairs, k = 0..max_lag.
- * Products are formed in FP32, sums accumulated in FP64.  max_lag = -1 turns
- * it off.                                                                       */
+ * Each sample component is kept to 22 significant bits (an fp16 pair hi + lo
+ * of 4096 V; |V| >= 16 is reported by lbp_check as LBP_ERANGE), the products of
+ * a 64-sample block are accumulated in FP32 on the tensor cores and the sums
+ * across blocks in FP64.  max_lag = -1 turns it off.  LBP_EINVAL, with nothing
+ * allocated and the VACF off, if the ring, sums and correlation buffers
+ * would take more than 64 GiB (about 3 * n_particles * 4 bytes per lag for the
+ * ring, plus (ceil(3 n_particles / 1024) + 3) * 512 bytes per lag).           */
 lbp_status lbp_vacf_configure(lbp_sim *sim, int max_lag);
 lbp_status lbp_vacf_read(lbp_sim *sim, double *csum, int64_t *counts, int on_device);
 

@@ -999,15 +999,25 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
     // samples plus the duplicated first rows (see vacf_kernels.cu)
     const int ld = (int)((ncomp + 7) / 8 * 8);
     const long long cap = per_particle ? (long long)max_lag + 2 * B : (long long)max_lag + 320;
-    const size_t ring_bytes = per_particle ? sizeof(float) * (size_t)cap * (size_t)ncomp
-                                           : 4 * (size_t)(cap + vacf_ring_dup_rows()) * (size_t)ld;
-    if (ring_bytes > ((size_t)64 << 30))
-        return fail(LBP_EINVAL, "lbp_vacf_configure: ring of %zu bytes exceeds 64 GiB", ring_bytes);
+    const size_t K1 = (size_t)max_lag + 1;
+    const size_t nsum = (per_particle ? (size_t)s->np : 1) * K1;
+    const int nchunks = (int)((ncomp + vacf_chunk_components() - 1) / vacf_chunk_components());
+    // every size check before the first allocation: a refused call allocates nothing
+    if (per_particle && (nsum > ((size_t)1 << 28) || s->np > 65535))
+        return fail(LBP_EINVAL,
+                    "lbp_vacf_configure_ex: per particle needs n_particles <= 65535 and n_particles * (max_lag + 1) <= 2^28");
     if (!per_particle && cap + vacf_ring_dup_rows() > 2147483647ll)
         return fail(LBP_EINVAL, "lbp_vacf_configure: max_lag too large");
+    const size_t ring_bytes = per_particle ? sizeof(float) * (size_t)cap * (size_t)ncomp
+                                           : 4 * (size_t)(cap + vacf_ring_dup_rows()) * (size_t)ld;
+    // sums and counts; the ensemble's block partials, G, H, W and MSD state and sums
+    size_t total = ring_bytes + sizeof(double) * nsum + sizeof(long long) * K1;
+    if (!per_particle) total += sizeof(double) * K1 * ((size_t)nchunks * B + 3 * (size_t)B + 3);
+    if (total > ((size_t)64 << 30))
+        return fail(LBP_EINVAL, "lbp_vacf_configure: %zu bytes of VACF buffers exceed 64 GiB", total);
     s->vacf_cap = (int)cap;
     s->ring_ld = ld;
-    s->vacf_nchunks = (int)((ncomp + vacf_chunk_components() - 1) / vacf_chunk_components());
+    s->vacf_nchunks = nchunks;
     if (per_particle) {
         TRY(dalloc(&s->ring, (size_t)s->vacf_cap * ncomp));
     } else {
@@ -1015,11 +1025,6 @@ lbp_status lbp_vacf_configure_ex(lbp_sim *s, int max_lag, int per_particle) {
         CK(cudaMemsetAsync(s->ring16, 0, ring_bytes, s->s0));
         CK(encode_vacf_tensor_maps(*s));
     }
-    const size_t nsum = (per_particle ? (size_t)s->np : 1) * ((size_t)max_lag + 1);
-    if (per_particle && (nsum > ((size_t)1 << 28) || s->np > 65535))
-        return fail(LBP_EINVAL,
-                    "lbp_vacf_configure_ex: per particle needs n_particles <= 65535 and n_particles * (max_lag + 1) <= 2^28");
-    const size_t K1 = (size_t)max_lag + 1;
     TRY(dalloc(&s->vacf_sum, nsum));
     TRY(dalloc(&s->vacf_cnt, K1));
     CK(cudaMemsetAsync(s->vacf_sum, 0, sizeof(double) * nsum, s->s0));

@@ -410,3 +410,60 @@ def test_batch_boxes_against_the_oracle():
         assert np.max(np.abs(fb - fo)) <= 1e-5 * scale + 1e-14, b
         off += nx * ny * nz
         p0 += ps.n
+
+
+def test_largest_batch_of_256_boxes():
+    """A batch of MAX_BATCH = 256 boxes of ragged sizes and four relaxation
+    times in one handle (the replica table's search at both ends, the node and
+    segment offsets of the last boxes): after 8 steps with graphs, boxes 0, 1,
+    127, 128, 254, 255 and every box holding particles are bitwise equal to the
+    same box run alone.  A 257th box is refused."""
+    sizes = [(4, 4, 4), (8, 3, 5), (12, 6, 2), (20, 4, 3), (36, 2, 2), (132, 2, 1), (130, 3, 2), (9, 7, 3)]
+    boxes = [(*sizes[b % len(sizes)], (0.6, 0.75, 0.9, 1.1)[b % 4]) for b in range(256)]
+    npart = [3 if b % 37 == 0 or b == 255 else 0 for b in range(256)]
+
+    def state(b):
+        nx, ny, nz, tau = boxes[b]
+        f = wl.perturbed_populations(W, (nz, ny, nx), 0.02, 500 + b)
+        ps = wl.uniform_particles(npart[b], (nz, ny, nx), 6.0, 0.5, wl.stokes_radius(0.5, tau), 0.0,
+                                  600 + b, 700 + b)
+        return f, ps
+
+    h = lbp.lbp_create_batch(boxes)
+    assert lbp.lbp_replica_count(h) == 256
+    lbp.lbp_set_populations(h, np.concatenate([state(b)[0].reshape(Q, -1) for b in range(256)], axis=1))
+    for b in range(256):
+        if npart[b]:
+            _, ps = state(b)
+            lbp.lbp_particles_add_to(h, b, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=0.0, seed=5)
+    lbp.lbp_set_use_graphs(h, True)
+    lbp.lbp_step(h, 8)
+    lbp.lbp_check(h)
+    f_all, parts = read_batch(h)
+    lbp.lbp_destroy(h)
+    node0 = np.cumsum([0] + [nx * ny * nz for nx, ny, nz, _ in boxes])
+    p0 = np.cumsum([0] + npart)
+    check = sorted({0, 1, 127, 128, 254, 255} | {b for b in range(256) if npart[b]})
+    for b in check:
+        nx, ny, nz, tau = boxes[b]
+        f, ps = state(b)
+        hb = lbp.lbp_create(nx, ny, nz, tau)
+        lbp.lbp_set_populations(hb, f)
+        if npart[b]:
+            lbp.lbp_particles_add(hb, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+            lbp.lbp_particles_set_params(hb, kT=0.0, seed=5)
+        lbp.lbp_step(hb, 8)
+        lbp.lbp_check(hb)
+        fb = np.empty((Q, nz * ny * nx))
+        lbp.lbp_read_populations(hb, fb)
+        assert np.array_equal(fb, f_all[:, node0[b]:node0[b + 1]]), b
+        if npart[b]:
+            pb = [np.empty((npart[b], 3)) for _ in range(4)]
+            lbp.lbp_particles_read(hb, *pb)
+            for a, c in zip(pb, parts):
+                assert np.array_equal(a, c[p0[b]:p0[b + 1]]), b
+        lbp.lbp_destroy(hb)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_create_batch(boxes + [(4, 4, 4, 0.8)])
+    assert ei.value.status == lbp.LBP_EINVAL

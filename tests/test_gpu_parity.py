@@ -585,6 +585,44 @@ def test_msd_is_not_kept_per_particle():
     assert ei.value.status == lbp.LBP_ESTATE
 
 
+def test_vacf_configure_refuses_oversized_buffers_without_allocating():
+    """A VACF whose buffers would pass 64 GiB (lbp_vacf_configure), or a
+    per-particle VACF past its limits, is refused before anything is
+    allocated: LBP_EINVAL, the VACF off, device memory unchanged, and the
+    handle steps on.  A large accepted configuration then correlates the few
+    samples taken (pair counts exact, lags beyond the samples zero)."""
+    shape = (16, 16, 16)
+    h = lbp.lbp_create(16, 16, 16, 0.8)
+    ps = wl.uniform_particles(3000, shape, 6.0, 0.5, 0.2, 1e-4, 1, 2)
+    lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+    lbp.lbp_particles_set_params(h, kT=1e-4, seed=3)
+    lbp.lbp_vacf_configure(h, 16)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    # ~36 KB of ring and ~6 KB of sums and correlation buffers per lag
+    for call in (lambda: lbp.lbp_vacf_configure(h, 2_000_000),
+                 lambda: lbp.lbp_vacf_configure_ex(h, 100_000, True)):
+        with pytest.raises(lbp.LbpError) as ei:
+            call()
+        assert ei.value.status == lbp.LBP_EINVAL
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_vacf_read(h, np.empty(17), np.empty(17, np.int64))
+    assert ei.value.status == lbp.LBP_ESTATE
+    lbp.lbp_step(h, 2)
+    lbp.lbp_check(h)
+    K = 200_000  # ~8.4 GB of buffers
+    lbp.lbp_vacf_configure(h, K)
+    lbp.lbp_step(h, 3)
+    cs, ct = np.empty(K + 1), np.empty(K + 1, np.int64)
+    lbp.lbp_vacf_read(h, cs, ct)
+    lbp.lbp_check(h)
+    assert list(ct[:4]) == [9000, 6000, 3000, 0] and not np.any(ct[4:]) and not np.any(cs[3:])
+    assert cs[0] > 0
+    lbp.lbp_destroy(h)
+
+
 def test_vacf_requires_particles():
     h = gpu_sim((4, 4, 4), 0.8)
     with pytest.raises(lbp.LbpError) as ei:
