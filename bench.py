@@ -63,6 +63,8 @@ VACF_LAUNCHES = 5      # per block of 64 samples: correlator, chunk sum, MSD sca
 
 
 def workload(name):
+    if name.endswith(".json"):
+        return wl.load(name)
     return {"brownian_256": wl.BROWNIAN_256, "brownian_128": wl.BROWNIAN_128,
             "brownian_64": wl.BROWNIAN_64, "profile_128": wl.PROFILE_128, "profile_192": wl.PROFILE_192,
             "ensemble_68": wl.ENSEMBLE_68}[name]
@@ -494,7 +496,7 @@ def run_gpu(args, w):
                               "kernel": LATTICE_KERNEL[SHAPES[hv.tuned["variant"]][0]],
                               "stream_collide_ms": vk3, "achieved_gbs": vach,
                               "frac": vach / measured_peaks()[0],
-                              "traffic": recorded_traffic(prec, hv.tuned["variant"]) if w is wl.BROWNIAN_256
+                              "traffic": recorded_traffic(prec, hv.tuned["variant"]) if w == wl.BROWNIAN_256
                               else None,
                               "bytes_per_node": BYTES_PER_NODE[prec], "autotune": hv.tuned}
     if not args.no_variants and not isinstance(w, wl.Ensemble) and want("batched"):
@@ -524,7 +526,7 @@ def run_gpu(args, w):
                                                  wa.extra["checkpoint_every"], 0.0, 0)
     if not args.no_variants and not isinstance(w, wl.Ensemble) and want("adjoint"):
         # the reverse sweep on the bench workload itself (population copies larger than L2)
-        key = "adjoint_256" if w is wl.BROWNIAN_256 else "adjoint_" + w.name
+        key = "adjoint_256" if w == wl.BROWNIAN_256 else "adjoint_" + w.name
         variants[key] = adjoint_variant(lbp, torch, w, w.particles(), 100, 20, w.kT, w.seed_noise)
 
     if rank != 0:
@@ -533,7 +535,7 @@ def run_gpu(args, w):
         return 0
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_NODE[args.precision] * w.nodes / (k3_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(args.precision, tuned["variant"]) if w is wl.BROWNIAN_256 else None
+    traffic = recorded_traffic(args.precision, tuned["variant"]) if w == wl.BROWNIAN_256 else None
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -575,7 +577,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["lbp", "reference"], default="lbp")
-    ap.add_argument("--workload", default="brownian_256")
+    ap.add_argument("--workload", default="brownian_256",
+                    help="brownian_256, brownian_128, brownian_64, profile_128, profile_192, ensemble_68, "
+                         "or a workload JSON file (paper_1909_13412_gb300/configs/)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vacf-lag", type=int, default=VACF_LAG)
     ap.add_argument("--precision", choices=["f32", "bf16", "f16"], default="f32")

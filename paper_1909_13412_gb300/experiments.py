@@ -25,7 +25,8 @@
 
 Every step of every run is the library's CUDA path; this module only sets up
 inputs, reads results and does the bookkeeping of each experiment.  Run as
-``python -m paper_1909_13412_gb300.experiments fig1|fig3|tail`` for the tables.
+``python -m paper_1909_13412_gb300.experiments fig1|fig3|tail|config2`` for the
+tables (``config2 --config FILE.json`` for another workload file).
 """
 from __future__ import annotations
 
@@ -232,6 +233,9 @@ def main(argv=None):
     ap.add_argument("experiment", choices=["fig1", "fig3", "tail", "config2"])
     ap.add_argument("--realisations", type=int, default=4)
     ap.add_argument("--window", type=int, nargs=2, default=[100, 400])
+    ap.add_argument("--config", default=None,
+                    help="config2: a workload JSON file (cubic box, vacf_lag > 0) instead of "
+                         "configs/config2_brownian_128.json")
     ap.add_argument("--paper", action="store_true",
                     help="fig1 at the paper's parameters (100^3 box, nu = 0.0178, U = 1e-4)")
     a = ap.parse_args(argv)
@@ -258,7 +262,9 @@ def main(argv=None):
                           "C_v": [float(C[t - 1] / C[0]) for t in (1, 5, 10, 20, 50, 100, 200, 400)]}))
     elif a.experiment == "config2":
         from . import workloads as wl
-        w = wl.BROWNIAN_128
+        w = wl.load(a.config) if a.config else wl.BROWNIAN_128
+        if len(set(w.shape_zyx)) != 1 or w.vacf_lag <= 0:
+            raise SystemExit("config2 needs a cubic box and vacf_lag > 0")
         L, tau, n, kT = w.shape_zyx[0], w.tau, w.n_particles, w.kT
         runs, secs = [], []
         for r in range(a.realisations):

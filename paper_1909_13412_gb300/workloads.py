@@ -13,8 +13,10 @@ configurations.  All quantities are in lattice units dx = dt = rho0 = 1.
 """
 from __future__ import annotations
 
+import json
 import math
-from dataclasses import dataclass, field
+import os
+from dataclasses import asdict, dataclass, field
 
 import numpy as np
 
@@ -191,3 +193,42 @@ def relaxation_particle(w: Workload, offset=(0.5, 0.5, 0.5), V0=(0.01, 0.0, 0.0)
     r = np.array([[nx // 2 + offset[0], ny // 2 + offset[1], nz // 2 + offset[2]]], dtype=np.float64)
     V = np.array([V0], dtype=np.float64)
     return ParticleSet(r, V, np.array([w.M]), np.array([w.gamma]), np.array([w.R]))
+
+
+# ---------------------------------------------------------------- JSON configs
+# A workload as a JSON object: {"kind": "box", "name", "shape_zyx", "tau",
+# "n_particles", "M", "gamma", "kT", "steps", "seed_pos", "seed_vel",
+# "seed_noise", "vacf_lag", "extra"} or {"kind": "ensemble", "name", "boxes"
+# ([nx, ny, nz, tau] each), "n_per_box", "M", "gamma", "kT", seeds}.  The
+# files under configs/ hold the five benchmark configurations.
+
+CONFIG_DIR = os.path.join(os.path.dirname(__file__), "configs")
+
+
+def to_dict(w) -> dict:
+    d = asdict(w)
+    if isinstance(w, Ensemble):
+        d["kind"] = "ensemble"
+        d["boxes"] = [list(b) for b in w.boxes]
+    else:
+        d["kind"] = "box"
+        d["shape_zyx"] = list(w.shape_zyx)
+    return d
+
+
+def from_dict(d: dict):
+    d = dict(d)
+    kind = d.pop("kind", "box")
+    if kind == "ensemble":
+        d["boxes"] = [tuple(b) for b in d["boxes"]]
+        return Ensemble(**d)
+    if kind != "box":
+        raise ValueError(f"unknown workload kind {kind!r}")
+    d["shape_zyx"] = tuple(int(v) for v in d["shape_zyx"])
+    return Workload(**d)
+
+
+def load(path: str):
+    """The workload described by a JSON file (see to_dict)."""
+    with open(path) as fh:
+        return from_dict(json.load(fh))

@@ -623,6 +623,44 @@ def test_vacf_configure_refuses_oversized_buffers_without_allocating():
     lbp.lbp_destroy(h)
 
 
+def test_kernel_timing_counts_launches_and_changes_no_result():
+    """lbp_timing_enable / lbp_timing_read: one timed stream-collide launch per
+    step (plain launches with events instead of the graph), a positive total
+    duration, the counter restarted by a new enable; the populations and
+    particles equal, bit for bit, those of the same run with timing off."""
+    shape = (12, 10, 24)
+
+    def make():
+        h = lbp.lbp_create(24, 10, 12, 0.7)
+        lbp.lbp_set_populations(h, wl.perturbed_populations(W, shape, 0.02, 4))
+        ps = wl.uniform_particles(7, shape, 6.0, 0.5, 0.2, 1e-4, 5, 6)
+        lbp.lbp_particles_add(h, ps.r, ps.V, ps.M, ps.gamma, ps.R)
+        lbp.lbp_particles_set_params(h, kT=1e-4, seed=2)
+        return h
+    ha, hb = make(), make()
+    lbp.lbp_timing_enable(ha, True)
+    lbp.lbp_step(ha, 11)
+    ms, n = lbp.lbp_timing_read(ha)
+    assert n == 11 and 0.0 < ms < 1e4
+    lbp.lbp_timing_enable(ha, True)
+    lbp.lbp_step(ha, 4)
+    assert lbp.lbp_timing_read(ha)[1] == 4
+    lbp.lbp_timing_enable(ha, False)
+    lbp.lbp_step(ha, 5)
+    lbp.lbp_step(hb, 20)
+    outs = []
+    for h in (ha, hb):
+        lbp.lbp_check(h)
+        f = np.empty((15,) + shape)
+        lbp.lbp_read_populations(h, f)
+        r, v = np.empty((7, 3)), np.empty((7, 3))
+        lbp.lbp_particles_read(h, r, v)
+        outs.append((f, r, v))
+        lbp.lbp_destroy(h)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 def test_vacf_requires_particles():
     h = gpu_sim((4, 4, 4), 0.8)
     with pytest.raises(lbp.LbpError) as ei:
