@@ -320,8 +320,10 @@ lbp_status lbp_set_wait_probe(lbp_sim *sim, int enable);
  * and took the overflow path (both counts are implementation details of the
  * force accumulation; the results do not depend on them), out[1] = capacity of
  * a record in shares, out[2] = number of row segments, out[3] = rows of 128
- * nodes per lattice-kernel block, out[4] = its variant (see lbp_autotune).
- * n = entries of out.                                                        */
+ * nodes per lattice-kernel block, out[4] = its variant (see lbp_autotune),
+ * out[5] = 1 if the particle kernel fits Eq. 8 with one lane per cell corner
+ * (fewer than 48 particles per SM), 0 if with one thread per particle; both
+ * layouts give the same bits.  n = entries of out (up to 6).                 */
 lbp_status lbp_diagnostics(lbp_sim *sim, int64_t *out, int n);
 
 /* Uniform body force density g = (gx, gy, gz) added on every node of box

@@ -1511,7 +1511,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
     CHECK_SIM(s);
     if (n < 0 || (n > 0 && !out)) return fail(LBP_EINVAL, "lbp_diagnostics: bad output");
     CK(cudaStreamSynchronize(s->s0));
-    int64_t v[5] = {0, REC_SLOTS, s->nseg, s->rows, (int64_t)s->variant};
+    int64_t v[6] = {0, REC_SLOTS, s->nseg, s->rows, (int64_t)s->variant, particles_fit_per_corner(*s) ? 1 : 0};
     if (s->rec[0]) {
         // shares beyond the slots of the records of the last completed step
         std::vector<unsigned long long> words((size_t)s->nseg * REC_WORDS);
@@ -1522,7 +1522,7 @@ lbp_status lbp_diagnostics(lbp_sim *s, int64_t *out, int n) {
             if (c > REC_SLOTS) v[0] += c - REC_SLOTS;
         }
     }
-    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
+    for (int i = 0; i < n && i < 6; ++i) out[i] = v[i];
     return LBP_OK;
 }
 

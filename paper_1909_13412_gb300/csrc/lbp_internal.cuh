@@ -409,6 +409,7 @@ int budget_blocks(const Sim &s);
 cudaError_t launch_budget(Sim &s, const void *src, double *out, cudaStream_t st);  // [budget_blocks][4]
 // particle_kernels.cu
 cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st);
+bool particles_fit_per_corner(const Sim &s);  // the fit of Eq. 8 one lane per corner (few particles)
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *soa, double *aos, int n, int ld, cudaStream_t st);

@@ -67,13 +67,79 @@ struct ParticleArgs {
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-constexpr int PB = 32;  // particles per block of k_particles
+// Eq. 8 in FP64, shared by both layouts of the fit below.  Every operation is
+// rounded explicitly (no contraction left to the compiler), and the eight
+// corners' terms are summed as the tree ((0 + 1) + (2 + 3)) + ((4 + 5) + (6 + 7)),
+// which is also the order of a butterfly over eight lanes: one thread per
+// particle and one lane per corner give the same bits.
+//
+// e^N = m/|m| of the mean relative velocity m (times 8); false if m = 0.
+__device__ __forceinline__ bool fit_direction(double m0, double m1, double m2, double &e0, double &e1,
+                                              double &e2) {
+    if (m0 == 0.0 && m1 == 0.0 && m2 == 0.0) return false;
+    double mm = __fma_rn(m2, m2, __fma_rn(m1, m1, __dmul_rn(m0, m0)));
+    if (!(mm > 1e-280)) {
+        // tiny mean: rescale before the norm so that it does not underflow
+        const double sc = 1.0 / fmax(fabs(m0), fmax(fabs(m1), fabs(m2)));
+        m0 = __dmul_rn(m0, sc);
+        m1 = __dmul_rn(m1, sc);
+        m2 = __dmul_rn(m2, sc);
+        mm = __fma_rn(m2, m2, __fma_rn(m1, m1, __dmul_rn(m0, m0)));
+    }
+    const double inrm = rsqrt(mm);
+    e0 = __dmul_rn(m0, inrm);
+    e1 = __dmul_rn(m1, inrm);
+    e2 = __dmul_rn(m2, inrm);
+    return true;
+}
+
+// The terms of one corner: t_n = w.a and t_d = |a|^2 with d = x_p - r_i (the
+// corner minus the cell fraction, exact), w = u_p - V and the basis
+// a = (1 - 3R/(4 r)) e^N - 3R (e^N.d)/(4 r^3) d; zero for a corner the fit
+// skips (r < 1e-12, or r < R with exclude).
+__device__ __forceinline__ void fit_corner(double d0, double d1, double d2, double e0, double e1, double e2,
+                                           double R34, double R2, int exclude, double w0, double w1, double w2,
+                                           double &tn, double &td) {
+    tn = 0.0;
+    td = 0.0;
+    const double rr = __fma_rn(d2, d2, __fma_rn(d1, d1, __dmul_rn(d0, d0)));
+    if (rr < 1e-24 || (exclude && rr < R2)) return;
+    const double ir = rsqrt(rr);
+    const double x = __fma_rn(e2, d2, __fma_rn(e1, d1, __dmul_rn(e0, d0)));
+    const double k1 = __fma_rn(-R34, ir, 1.0);
+    const double k2 = __dmul_rn(__dmul_rn(R34, x), __dmul_rn(__dmul_rn(ir, ir), ir));
+    const double a0 = __fma_rn(k1, e0, -__dmul_rn(k2, d0));
+    const double a1 = __fma_rn(k1, e1, -__dmul_rn(k2, d1));
+    const double a2 = __fma_rn(k1, e2, -__dmul_rn(k2, d2));
+    tn = __fma_rn(w2, a2, __fma_rn(w1, a1, __dmul_rn(w0, a0)));
+    td = __fma_rn(a2, a2, __fma_rn(a1, a1, __dmul_rn(a0, a0)));
+}
+
+// Sum of v over the eight lanes of a particle (lanes 8j .. 8j + 7), in the
+// tree order above; every lane of the group gets the same sum.
+__device__ __forceinline__ double sum8(double v) {
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Particles per block: 32 (256 threads) with the fit one thread per particle
+// (FIT8 = false); 8 (64 threads) with the fit one lane per corner (FIT8 =
+// true).  An FP64 warp instruction occupies the SM's narrow FP64 pipe for 16
+// cycles whatever its active lanes, and the fit is ~480 of them per particle.
+// With many particles the pipe is the limit and one thread per particle uses
+// every lane of each instruction.  With few particles (a warp or two per SM)
+// the fit is one warp's chain of dependent FP64 instructions; spreading the
+// eight corners over eight lanes, and the particles over more blocks, cuts
+// that chain about fourfold.
+constexpr int PB_WIDE = 32, PB_NARROW = 8;
 
 // 64 registers (four blocks of 256 threads per SM) keep the 16384-particle
 // grid of the 256^3 workload (512 blocks) in a single wave on 152 SMs (at 80
 // registers, three blocks per SM, it took two).
-template <typename St, int MAXR>
-__global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, const RepTable<MAXR> rt) {
+template <typename St, int MAXR, int PB, bool FIT8>
+__global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(const ParticleArgs A,
+                                                                            const RepTable<MAXR> rt) {
     const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[PB][3];
     __shared__ int s_rep[PB];
@@ -86,6 +152,10 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     __shared__ double s_fe[3][PB];
     __shared__ double s_invM[PB], s_sg[PB];
     __shared__ unsigned char s_pin[PB];
+    // one lane per corner: the particle state the corner lanes read, and the fit
+    __shared__ double s_q[FIT8 ? PB : 1][4], s_V[FIT8 ? PB : 1][3];
+    __shared__ double s_e[FIT8 ? PB : 1][3], s_nd[FIT8 ? PB : 1][2];
+    __shared__ int s_eok[FIT8 ? PB : 1];
     const int t = threadIdx.x, lane = t & 31;
     const int i0 = blockIdx.x * PB;
     const long long step = *A.d_step;
@@ -104,7 +174,7 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     const int ip = i0 + lane;
     double r0 = 0.0, r1 = 0.0, r2 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
     double V0 = 0.0, V1 = 0.0, V2 = 0.0, gam = 0.0, Rd = 0.0;
-    if (t >= 32 && t < 64 && ip < A.np) {
+    if (t >= 32 && t < 32 + PB && ip < A.np) {
         s_invM[lane] = A.inv_mass[ip];
         s_sg[lane] = A.sig[ip];
         s_fe[0][lane] = A.fext[ip];
@@ -112,7 +182,7 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
         s_fe[2][lane] = A.fext[2 * cap + ip];
         s_pin[lane] = A.pinned[ip];
     }
-    if (t < 32 && ip < A.np) {
+    if (t < PB && ip < A.np) {
         r0 = A.r[ip];
         r1 = A.r[cap + ip];
         r2 = A.r[2 * cap + ip];
@@ -129,6 +199,15 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
         s_base[lane][0] = (int)b0;
         s_base[lane][1] = (int)b1;
         s_base[lane][2] = (int)b2;
+        if (FIT8) {
+            s_q[lane][0] = q0;
+            s_q[lane][1] = q1;
+            s_q[lane][2] = q2;
+            s_q[lane][3] = Rd;
+            s_V[lane][0] = V0;
+            s_V[lane][1] = V1;
+            s_V[lane][2] = V2;
+        }
     }
     __syncthreads();
 
@@ -162,8 +241,44 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     }
     __syncthreads();
 
+    // ---- the fit of Eq. 8 with one lane per corner (all threads): the mean
+    // relative velocity and e^N in every lane of the particle (sum8 gives all
+    // eight the same sum), the corner's terms, their sums to s_nd
+    if (FIT8 && A.mode == LBP_STOKESLET) {
+        const bool live = ij < A.np;
+        double V[3] = {0.0, 0.0, 0.0}, m[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (live) V[k] = s_V[j][k];
+            m[k] = __fma_rn(-8.0, V[k], sum8(live ? (double)s_u[j][p][k] : 0.0));
+        }
+        double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+        const bool eok = live && fit_direction(m[0], m[1], m[2], e0, e1, e2);
+        double tn = 0.0, td = 0.0;
+        if (eok) {
+            const double q0p = s_q[j][0], q1p = s_q[j][1], q2p = s_q[j][2], Rp = s_q[j][3];
+            const double d0 = c0 ? __dsub_rn(1.0, q0p) : -q0p;
+            const double d1 = c1 ? __dsub_rn(1.0, q1p) : -q1p;
+            const double d2 = c2 ? __dsub_rn(1.0, q2p) : -q2p;
+            fit_corner(d0, d1, d2, e0, e1, e2, 0.75 * Rp, Rp * Rp, A.exclude_inside,
+                       __dsub_rn((double)s_u[j][p][0], V[0]), __dsub_rn((double)s_u[j][p][1], V[1]),
+                       __dsub_rn((double)s_u[j][p][2], V[2]), tn, td);
+        }
+        tn = sum8(tn);
+        td = sum8(td);
+        if (live && p == 0) {
+            s_eok[j] = eok;
+            s_e[j][0] = e0;
+            s_e[j][1] = e1;
+            s_e[j][2] = e2;
+            s_nd[j][0] = tn;
+            s_nd[j][1] = td;
+        }
+        __syncthreads();
+    }
+
     // ---- phase B (warp 0): fit, random force, Langevin update
-    if (t < 32 && ip < A.np) {
+    if (t < PB && ip < A.np) {
         const int i = ip;
         double F0 = 0.0, F1 = 0.0, F2 = 0.0;
         bool spread = true;
@@ -171,51 +286,55 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
             // Eq. 8 in FP64 from the FP32 corner velocities: w_p = u_p - V,
             // e^N = mean(w)/|mean(w)|, d_p = x_p - r_i (exact: corner minus
             // cell fraction), basis a_p = (1 - 3R/(4 r_p)) e^N - 3R (e^N.d_p)/(4 r_p^3) d_p,
-            // and the normal equation U_inf sum|a_p|^2 = sum w_p.a_p.  w_p is
-            // formed again in the corner loop from the shared corner velocities
-            // (holding all 24 would spill).
-            double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+            // and the normal equation U_inf sum|a_p|^2 = sum w_p.a_p, solved
+            // for U_inf; F_H = gamma U_inf e^N (Eq. 7 with u_inf = U_inf e^N + V).
+            double num = 0.0, den = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
+            bool eok;
+            if (FIT8) {
+                eok = s_eok[lane];
+                e0 = s_e[lane][0];
+                e1 = s_e[lane][1];
+                e2 = s_e[lane][2];
+                num = s_nd[lane][0];
+                den = s_nd[lane][1];
+            } else {
+                // the same operations as the lane-per-corner layout, in one
+                // thread: w_p is formed again in the corner loop from the shared
+                // corner velocities (holding all 24 would spill)
+                double m[3];
+                const double Vk[3] = {V0, V1, V2};
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                m0 += (double)s_u[lane][c][0];
-                m1 += (double)s_u[lane][c][1];
-                m2 += (double)s_u[lane][c][2];
+                for (int k = 0; k < 3; ++k) {
+                    double h[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2)
+                        h[c >> 1] = __dadd_rn((double)s_u[lane][c][k], (double)s_u[lane][c + 1][k]);
+                    m[k] = __fma_rn(-8.0, Vk[k], __dadd_rn(__dadd_rn(h[0], h[1]), __dadd_rn(h[2], h[3])));
+                }
+                eok = fit_direction(m[0], m[1], m[2], e0, e1, e2);
+                if (eok) {
+                    const double R34 = 0.75 * Rd, R2 = Rd * Rd;
+                    const double dx[2] = {-q0, __dsub_rn(1.0, q0)}, dy[2] = {-q1, __dsub_rn(1.0, q1)},
+                                 dz[2] = {-q2, __dsub_rn(1.0, q2)};
+                    double hn[4], hd[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        double tn0, td0, tn1, td1;
+                        fit_corner(dx[0], dy[(c >> 1) & 1], dz[(c >> 2) & 1], e0, e1, e2, R34, R2, A.exclude_inside,
+                                   __dsub_rn((double)s_u[lane][c][0], V0), __dsub_rn((double)s_u[lane][c][1], V1),
+                                   __dsub_rn((double)s_u[lane][c][2], V2), tn0, td0);
+                        fit_corner(dx[1], dy[(c >> 1) & 1], dz[(c >> 2) & 1], e0, e1, e2, R34, R2, A.exclude_inside,
+                                   __dsub_rn((double)s_u[lane][c + 1][0], V0),
+                                   __dsub_rn((double)s_u[lane][c + 1][1], V1),
+                                   __dsub_rn((double)s_u[lane][c + 1][2], V2), tn1, td1);
+                        hn[c >> 1] = __dadd_rn(tn0, tn1);
+                        hd[c >> 1] = __dadd_rn(td0, td1);
+                    }
+                    num = __dadd_rn(__dadd_rn(hn[0], hn[1]), __dadd_rn(hn[2], hn[3]));
+                    den = __dadd_rn(__dadd_rn(hd[0], hd[1]), __dadd_rn(hd[2], hd[3]));
+                }
             }
-            m0 -= 8.0 * V0;
-            m1 -= 8.0 * V1;
-            m2 -= 8.0 * V2;
-            if (m0 != 0.0 || m1 != 0.0 || m2 != 0.0) {
-                double mm = m0 * m0 + m1 * m1 + m2 * m2;
-                if (!(mm > 1e-280)) {
-                    // tiny mean: rescale before the norm so that it does not underflow
-                    const double sc = 1.0 / fmax(fabs(m0), fmax(fabs(m1), fabs(m2)));
-                    m0 *= sc;
-                    m1 *= sc;
-                    m2 *= sc;
-                    mm = m0 * m0 + m1 * m1 + m2 * m2;
-                }
-                const double inrm = rsqrt(mm);
-                const double e0 = m0 * inrm, e1 = m1 * inrm, e2 = m2 * inrm;
-                const double R34 = 0.75 * Rd, R2 = Rd * Rd;
-                const double dx[2] = {-q0, 1.0 - q0}, dy[2] = {-q1, 1.0 - q1}, dz[2] = {-q2, 1.0 - q2};
-                double num = 0.0, den = 0.0;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const double d0 = dx[c & 1], d1 = dy[(c >> 1) & 1], d2 = dz[(c >> 2) & 1];
-                    const double rr = d0 * d0 + d1 * d1 + d2 * d2;
-                    if (rr < 1e-24) continue;
-                    if (A.exclude_inside && rr < R2) continue;
-                    const double ir = rsqrt(rr);
-                    const double x = e0 * d0 + e1 * d1 + e2 * d2;
-                    const double k1 = 1.0 - R34 * ir;
-                    const double k2 = R34 * x * (ir * ir * ir);
-                    const double a0 = k1 * e0 - k2 * d0, a1 = k1 * e1 - k2 * d1, a2 = k1 * e2 - k2 * d2;
-                    const double w0 = (double)s_u[lane][c][0] - V0;
-                    const double w1 = (double)s_u[lane][c][1] - V1;
-                    const double w2 = (double)s_u[lane][c][2] - V2;
-                    num += w0 * a0 + w1 * a1 + w2 * a2;
-                    den += a0 * a0 + a1 * a1 + a2 * a2;
-                }
+            if (eok) {
                 const double U = den > 0.0 ? num / den : 0.0;
                 const double gU = gam * U;
                 F0 = gU * e0;
@@ -349,7 +468,7 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
         // one FP64 atomic per component
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double vk = ip < A.np ? s_fe[k][lane] : 0.0;
+            double vk = lane < PB && ip < A.np ? s_fe[k][lane] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) vk += __shfl_xor_sync(0xffffffffu, vk, o);
             if (lane == 0) atomicAdd(A.inj + k, vk);
@@ -391,14 +510,27 @@ __global__ void __launch_bounds__(256, 4) k_particles(const ParticleArgs A, cons
     }
 }
 
-template <int MAXR>
-static void launch_particles_t(const Sim &s, const ParticleArgs &A, const RepTable<MAXR> &t,
-                               unsigned grid, cudaStream_t st) {
+template <int MAXR, int PB, bool FIT8>
+static void launch_particles_pb(const Sim &s, const ParticleArgs &A, const RepTable<MAXR> &t, cudaStream_t st) {
+    const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
     switch (s.precision) {
-        case LBP_BF16: k_particles<StoreBF16, MAXR><<<grid, 8 * PB, 0, st>>>(A, t); break;
-        case LBP_F16: k_particles<StoreF16, MAXR><<<grid, 8 * PB, 0, st>>>(A, t); break;
-        default: k_particles<StoreF32, MAXR><<<grid, 8 * PB, 0, st>>>(A, t); break;
+        case LBP_BF16: k_particles<StoreBF16, MAXR, PB, FIT8><<<grid, 8 * PB, 0, st>>>(A, t); break;
+        case LBP_F16: k_particles<StoreF16, MAXR, PB, FIT8><<<grid, 8 * PB, 0, st>>>(A, t); break;
+        default: k_particles<StoreF32, MAXR, PB, FIT8><<<grid, 8 * PB, 0, st>>>(A, t); break;
     }
+}
+
+// The fit one lane per corner while the one-thread-per-particle layout would
+// leave the FP64 pipe mostly idle (fewer than ~50 particles per SM: its
+// dependent chain, not the pipe, sets the time); both give the same bits.
+bool particles_fit_per_corner(const Sim &s) { return s.np < 48 * (s.num_sms > 0 ? s.num_sms : 1); }
+
+template <int MAXR>
+static void launch_particles_t(const Sim &s, const ParticleArgs &A, const RepTable<MAXR> &t, cudaStream_t st) {
+    if (particles_fit_per_corner(s))
+        launch_particles_pb<MAXR, PB_NARROW, true>(s, A, t, st);
+    else
+        launch_particles_pb<MAXR, PB_WIDE, false>(s, A, t, st);
 }
 
 cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st) {
@@ -435,20 +567,19 @@ cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t s
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
     A.inj = s.inj;
-    const unsigned grid = (unsigned)((s.np + PB - 1) / PB);
     if (s.nrep == 1) {
         RepTable<1> t;
         t.nrep = 1;
         t.item_off[0] = 0;
         t.item_off[1] = 0;
         t.rep[0] = s.reps[0];
-        launch_particles_t(s, A, t, grid, st);
+        launch_particles_t(s, A, t, st);
     } else {
         RepTable<MAX_BATCH> t;  // kernel parameter
         t.nrep = s.nrep;
         for (int r = 0; r <= s.nrep; ++r) t.item_off[r] = 0;
         for (int r = 0; r < s.nrep; ++r) t.rep[r] = s.reps[r];
-        launch_particles_t(s, A, t, grid, st);
+        launch_particles_t(s, A, t, st);
     }
     return cudaGetLastError();
 }

@@ -426,10 +426,10 @@ def lbp_check(h: Handle):
 
 
 def lbp_diagnostics(h: Handle):
-    out = np.zeros(5, np.int64)
-    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 5)
+    out = np.zeros(6, np.int64)
+    _call("lbp_diagnostics", h.ptr, C.c_void_p(out.ctypes.data), 6)
     return {"overflow_shares": int(out[0]), "record_slots": int(out[1]), "segments": int(out[2]),
-            "rows_per_block": int(out[3]), "variant": int(out[4])}
+            "rows_per_block": int(out[3]), "variant": int(out[4]), "fit_per_corner": bool(out[5])}
 
 
 def lbp_set_body_force(h: Handle, g, replica=-1):

@@ -467,3 +467,46 @@ def test_largest_batch_of_256_boxes():
     with pytest.raises(lbp.LbpError) as ei:
         lbp.lbp_create_batch(boxes + [(4, 4, 4, 0.8)])
     assert ei.value.status == lbp.LBP_EINVAL
+
+
+@pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16])
+def test_fit_layouts_give_the_same_bits(prec):
+    """The particle kernel fits Eq. 8 one lane per cell corner when there are
+    few particles and one thread per particle when there are many; both sum
+    the corners in the same tree order.  A small box inside a batch holding
+    enough particles for the thread-per-particle layout evolves bit for bit
+    like the same box alone, which takes the lane-per-corner layout."""
+    steps = 20
+    small = (16, 16, 16, 0.8)
+    big = (128, 64, 64, 0.7)
+    ps0 = wl.uniform_particles(20, (16, 16, 16), 6.0, 0.5, wl.stokes_radius(0.5, 0.8), 1e-4, 41, 42)
+    ps1 = wl.uniform_particles(12000, (64, 64, 128), 6.0, 0.5, wl.stokes_radius(0.5, 0.7), 1e-4, 43, 44)
+    f0 = wl.perturbed_populations(W, (16, 16, 16), 0.02, 45)
+    f1 = wl.perturbed_populations(W, (64, 64, 128), 0.02, 46)
+
+    hb = lbp.lbp_create_batch([small, big], precision=prec)
+    lbp.lbp_set_populations(hb, np.concatenate([f0.reshape(Q, -1), f1.reshape(Q, -1)], axis=1))
+    lbp.lbp_particles_add_to(hb, 0, ps0.r, ps0.V, ps0.M, ps0.gamma, ps0.R)
+    lbp.lbp_particles_add_to(hb, 1, ps1.r, ps1.V, ps1.M, ps1.gamma, ps1.R)
+    lbp.lbp_particles_set_params(hb, kT=1e-4, seed=9)
+    assert not lbp.lbp_diagnostics(hb)["fit_per_corner"]
+    lbp.lbp_step(hb, steps)
+    lbp.lbp_check(hb)
+    fb, pb = read_batch(hb)
+    lbp.lbp_destroy(hb)
+
+    hs = lbp.lbp_create(16, 16, 16, 0.8, precision=prec)
+    lbp.lbp_set_populations(hs, f0)
+    lbp.lbp_particles_add(hs, ps0.r, ps0.V, ps0.M, ps0.gamma, ps0.R)
+    lbp.lbp_particles_set_params(hs, kT=1e-4, seed=9)
+    assert lbp.lbp_diagnostics(hs)["fit_per_corner"]
+    lbp.lbp_step(hs, steps)
+    lbp.lbp_check(hs)
+    fs, psl = read_batch(hs)
+    lbp.lbp_destroy(hs)
+
+    n = 16 ** 3
+    assert np.array_equal(fb[:, :n], fs)
+    for k in range(4):
+        assert np.array_equal(pb[k][:20], psl[k]), k
+    assert np.any(pb[2][:20] != 0.0)  # the fit ran (F_H non-zero)
