@@ -58,6 +58,7 @@ SHAPES = dict(zip(SHAPE_NAMES, AUTOTUNE_SHAPES))
 # the lattice kernel each variant launches when the box holds particles
 LATTICE_KERNEL = {0: "k_stream_collide_forced", 1: "k_stream_collide_pair", 2: "k_stream_collide_staged",
                   3: "k_stream_collide_quad"}
+L2_BYTES = 129e6  # GB300 L2
 LAUNCHES_PER_STEP = 2  # particles, stream-collide
 VACF_LAUNCHES = 5      # per block of 64 samples: correlator, chunk sum, MSD scan, MSD diagonals, sums
 
@@ -287,6 +288,14 @@ def run_reference(args, w):
     return 0
 
 
+def l2_note(nodes, precision):
+    """Whether the step's population traffic needs an L2 flush between steps."""
+    buf = 15 * nodes * (4 if precision == "f32" else 2)
+    if 2 * buf > L2_BYTES:
+        return f"no flush: 2 x {buf / 1e6:.0f} MB population buffers per step exceed the 129 MB L2"
+    return f"population buffers (2 x {buf / 1e6:.0f} MB) fit in the 129 MB L2: not an HBM-bound case"
+
+
 def config_of(w, world, vacf_lag=VACF_LAG, precision="f32"):
     if isinstance(w, wl.Ensemble):
         return {"workload": w.name, "boxes": [list(b) for b in w.boxes], "nodes_per_rank": w.nodes,
@@ -294,13 +303,13 @@ def config_of(w, world, vacf_lag=VACF_LAG, precision="f32"):
                 "coupling": "stokeslet", "storage": f"{precision} deviation",
                 "vacf_max_lag": vacf_lag, "vacf": "per particle (= per replica)",
                 "parallelism": f"replicas{world}",
-                "l2": "no flush: 2 x 2.6 GB population buffers per step exceed the 129 MB L2"}
+                "l2": l2_note(w.nodes, precision)}
     nz, ny, nx = w.shape_zyx
     return {"workload": w.name, "lattice": [nx, ny, nz], "nodes_per_rank": w.nodes,
             "particles_per_rank": w.n_particles, "tau": w.tau, "kT": w.kT, "M": w.M,
             "gamma": w.gamma, "coupling": "stokeslet", "storage": f"{precision} deviation",
             "vacf_max_lag": vacf_lag, "parallelism": f"replicas{world}",
-            "l2": "no flush: 2 x 1.0 GB population buffers per step exceed the 129 MB L2"}
+            "l2": l2_note(w.nodes, precision)}
 
 
 # ---------------------------------------------------------------------------- adjoint
