@@ -158,8 +158,12 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.first = threading.Event()
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi's start-up (NVML initialisation) can stall the GPU's
+            # work for about a second: let it finish before anything is timed
+            self.first.wait(timeout=10.0)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -167,6 +171,8 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
+        self.first.set()
 
     def mark(self, t0, t1):
         """A timed region, in host wall-clock seconds (time.time())."""

@@ -143,7 +143,9 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
     const typename St::T *G = static_cast<const typename St::T *>(A.g);
     __shared__ int s_base[PB][3];
     __shared__ int s_rep[PB];
-    __shared__ float s_u[PB][8][3];
+    // u^N of each corner: summed in FP32 by its gather thread, which also
+    // converts it to FP64 (exact), while the FP64 pipe is otherwise idle
+    __shared__ double s_u[PB][8][3];
     __shared__ long long s_fix[PB][3];
     __shared__ long long s_frac[PB][3];
     __shared__ int s_spread[PB];
@@ -235,9 +237,9 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
             if (ey(a)) sy += ey(a) > 0 ? gv : -gv;
             if (ez(a)) sz += ez(a) > 0 ? gv : -gv;
         }
-        s_u[j][p][0] = sx;
-        s_u[j][p][1] = sy;
-        s_u[j][p][2] = sz;
+        s_u[j][p][0] = (double)sx;
+        s_u[j][p][1] = (double)sy;
+        s_u[j][p][2] = (double)sz;
     }
     __syncthreads();
 
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             if (live) V[k] = s_V[j][k];
-            m[k] = __fma_rn(-8.0, V[k], sum8(live ? (double)s_u[j][p][k] : 0.0));
+            m[k] = __fma_rn(-8.0, V[k], sum8(live ? s_u[j][p][k] : 0.0));
         }
         double e0 = 0.0, e1 = 0.0, e2 = 0.0;
         const bool eok = live && fit_direction(m[0], m[1], m[2], e0, e1, e2);
@@ -261,8 +263,8 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
             const double d1 = c1 ? __dsub_rn(1.0, q1p) : -q1p;
             const double d2 = c2 ? __dsub_rn(1.0, q2p) : -q2p;
             fit_corner(d0, d1, d2, e0, e1, e2, 0.75 * Rp, Rp * Rp, A.exclude_inside,
-                       __dsub_rn((double)s_u[j][p][0], V[0]), __dsub_rn((double)s_u[j][p][1], V[1]),
-                       __dsub_rn((double)s_u[j][p][2], V[2]), tn, td);
+                       __dsub_rn(s_u[j][p][0], V[0]), __dsub_rn(s_u[j][p][1], V[1]),
+                       __dsub_rn(s_u[j][p][2], V[2]), tn, td);
         }
         tn = sum8(tn);
         td = sum8(td);
@@ -305,10 +307,11 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
                 const double Vk[3] = {V0, V1, V2};
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
+                    asm volatile("" ::: "memory");
                     double h[4];
 #pragma unroll
                     for (int c = 0; c < 8; c += 2)
-                        h[c >> 1] = __dadd_rn((double)s_u[lane][c][k], (double)s_u[lane][c + 1][k]);
+                        h[c >> 1] = __dadd_rn(s_u[lane][c][k], s_u[lane][c + 1][k]);
                     m[k] = __fma_rn(-8.0, Vk[k], __dadd_rn(__dadd_rn(h[0], h[1]), __dadd_rn(h[2], h[3])));
                 }
                 eok = fit_direction(m[0], m[1], m[2], e0, e1, e2);
@@ -319,14 +322,17 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
                     double hn[4], hd[4];
 #pragma unroll
                     for (int c = 0; c < 8; c += 2) {
+                        // load each pair's corner velocities where they are used
+                        // (hoisting all 24 doubles would spill)
+                        asm volatile("" ::: "memory");
                         double tn0, td0, tn1, td1;
                         fit_corner(dx[0], dy[(c >> 1) & 1], dz[(c >> 2) & 1], e0, e1, e2, R34, R2, A.exclude_inside,
-                                   __dsub_rn((double)s_u[lane][c][0], V0), __dsub_rn((double)s_u[lane][c][1], V1),
-                                   __dsub_rn((double)s_u[lane][c][2], V2), tn0, td0);
+                                   __dsub_rn(s_u[lane][c][0], V0), __dsub_rn(s_u[lane][c][1], V1),
+                                   __dsub_rn(s_u[lane][c][2], V2), tn0, td0);
                         fit_corner(dx[1], dy[(c >> 1) & 1], dz[(c >> 2) & 1], e0, e1, e2, R34, R2, A.exclude_inside,
-                                   __dsub_rn((double)s_u[lane][c + 1][0], V0),
-                                   __dsub_rn((double)s_u[lane][c + 1][1], V1),
-                                   __dsub_rn((double)s_u[lane][c + 1][2], V2), tn1, td1);
+                                   __dsub_rn(s_u[lane][c + 1][0], V0),
+                                   __dsub_rn(s_u[lane][c + 1][1], V1),
+                                   __dsub_rn(s_u[lane][c + 1][2], V2), tn1, td1);
                         hn[c >> 1] = __dadd_rn(tn0, tn1);
                         hd[c >> 1] = __dadd_rn(td0, td1);
                     }
@@ -349,9 +355,9 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const double Wp = wx[c & 1] * wy[(c >> 1) & 1] * wz[(c >> 2) & 1];
-                ur0 += Wp * (double)s_u[lane][c][0];
-                ur1 += Wp * (double)s_u[lane][c][1];
-                ur2 += Wp * (double)s_u[lane][c][2];
+                ur0 += Wp * s_u[lane][c][0];
+                ur1 += Wp * s_u[lane][c][1];
+                ur2 += Wp * s_u[lane][c][2];
             }
             F0 = -gam * (V0 - ur0);
             F1 = -gam * (V1 - ur1);
