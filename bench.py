@@ -178,7 +178,26 @@ class ClockSampler:
         """A timed region, in host wall-clock seconds (time.time())."""
         self.windows.append((t0, t1))
 
+    @staticmethod
+    def _stamp(line):
+        import datetime
+        try:
+            return datetime.datetime.strptime(line.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def __exit__(self, *exc):
+        if self.proc and self.windows:
+            # nvidia-smi's output reaches the pipe in blocks: wait (bounded) until a
+            # sample taken after the last timed region has arrived, so that the
+            # samples of the regions are not lost when the process is stopped
+            end = max(b for _, b in self.windows)
+            deadline = time.time() + 3.0
+            while time.time() < deadline:
+                t = self._stamp(self.lines[-1]) if self.lines else None
+                if t is not None and t >= end:
+                    break
+                time.sleep(0.05)
         if self.proc:
             self.proc.terminate()
             try:
@@ -420,8 +439,15 @@ def run_gpu(args, w):
         timed samples -- including the last, partial one, flushed before the end
         event -- inside the region.  Then the same K steps once more with the
         library's events around every stream-collide launch, for that kernel's
-        average duration (this pass takes the plain-launch path)."""
+        average duration (this pass takes the plain-launch path).  Before the W
+        warm-up steps, untimed steps for about a second: a GPU that was idle can
+        stall for about a second while its clocks and memory state come up, which
+        a timed region of a few milliseconds (small K) must not contain."""
         out = vacf_out(h, wk)
+        t_spin = time.time()
+        while time.time() - t_spin < 1.0:
+            lbp.lbp_step(h, 16)
+            torch.cuda.synchronize()
         lbp.lbp_step(h, warmup)
         vacf_flush(h, out)  # nothing of the warm-up's VACF work is left pending
         lbp.lbp_check(h)
