@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
     const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
     const float omega = rp.omega;
     const unsigned item = blockIdx.x - rt.item_off[rb];
-    const unsigned row = item / (unsigned)nchunks;
+    const unsigned row = divide(item, rp.dchunks);
     const int chunk = (int)(item - row * (unsigned)nchunks);
     const size_t seg = (size_t)rp.seg_off + (size_t)row * nchunks + chunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(SEG, 6) k_adj_lattice(const typename St::T *__
     const bool act = x0 < nx;
     const int x = act ? x0 : nx - 1;
     // node index and the offsets of x - e (index e + 1), periodic
-    const int z = (int)(row / (unsigned)ny), y = (int)(row - (unsigned)z * ny);
+    const int z = (int)divide(row, rp.dny), y = (int)(row - (unsigned)z * ny);
     const int slab = nx * ny;
     const int d = (int)rp.node_off + (int)row * nx + x;
     const int ox[3] = {x == nx - 1 ? 1 - nx : 1, 0, x == 0 ? nx - 1 : -1};

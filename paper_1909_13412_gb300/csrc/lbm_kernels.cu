@@ -52,9 +52,10 @@ struct NodeIdx {
     int ox[3], oy[3], oz[3];
 };
 
-__device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int ny, int nz) {
+template <bool MUL_DIV = true>
+__device__ __forceinline__ NodeIdx node_index(int x, unsigned row, int nx, int ny, int nz, Divisor dny) {
     NodeIdx n;
-    const int z = (int)(row / (unsigned)ny);
+    const int z = MUL_DIV ? (int)divide(row, dny) : (int)(row / (unsigned)ny);
     const int y = (int)(row - (unsigned)z * ny);
     const int slab = nx * ny;
     n.d = (int)row * nx + x;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide(Planes<St
     const int nx = rp.nx, ny = rp.ny, nz = rp.nz, nchunks = rp.nchunks;
     const unsigned nrows = (unsigned)ny * (unsigned)nz;
     const unsigned item = blockIdx.x - rt.item_off[r];
-    const unsigned grp = item / (unsigned)nchunks;
+    const unsigned grp = divide(item, rp.dchunks);
     const int chunk = (int)(item - grp * (unsigned)nchunks);
     const int x = chunk * BX + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) *bump += 1;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide(Planes<St
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
-        n[h] = node_index(x, row, nx, ny, nz);
+        n[h] = node_index(x, row, nx, ny, nz, rp.dny);
         n[h].d += base;
 #pragma unroll
         for (int a = 0; a < Q; ++a)
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
     const unsigned nrows = (unsigned)ny * (unsigned)nz;
     const int lane = threadIdx.x & 31;
     const unsigned item = blockIdx.x - rt.item_off[r];
-    const unsigned grp = item / (unsigned)nchunks;
+    const unsigned grp = divide(item, rp.dchunks);
     const int chunk = (int)(item - grp * (unsigned)nchunks);
     const size_t seg0 = (size_t)rp.seg_off;
     // the previous step's records (this step's particle kernel writes the others)
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
-        n[h] = node_index(x, row, nx, ny, nz);
+        n[h] = node_index(x, row, nx, ny, nz, rp.dny);
         n[h].d += base;
 #pragma unroll
         for (int a = 0; a < Q; ++a)
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
     const unsigned nrows = (unsigned)ny * (unsigned)nz;
     const int lane = threadIdx.x & 31;
     const unsigned item = blockIdx.x - rt.item_off[r];
-    const unsigned grp = item / (unsigned)nchunks;
+    const unsigned grp = divide(item, rp.dchunks);
     const int chunk = (int)(item - grp * (unsigned)nchunks);
     const size_t seg0 = (size_t)rp.seg_off;
     if (FORCED && threadIdx.x < R && grp * R + threadIdx.x < nrows)
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
-        const NodeIdx n = node_index(0, row, nx, ny, nz);
+        const NodeIdx n = node_index(0, row, nx, ny, nz, rp.dny);
         drow[h] = base + n.d;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
@@ -437,7 +438,11 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
     const unsigned nrows = (unsigned)ny * (unsigned)nz;
     const int lane = threadIdx.x & 31;
     const unsigned it = item - rt.item_off[r];
-    const unsigned grp = it / (unsigned)nchunks;
+    // the row segment by one multiplication (Divisor); the FP16 instantiation
+    // keeps the hardware division, measured faster there (0.1798 vs 0.1861 ms
+    // at 256^3), while BF16 gains (0.1740 -> 0.1707 ms)
+    constexpr bool MUL_DIV = !std::is_same<St, StoreF16>::value;
+    const unsigned grp = MUL_DIV ? divide(it, rp.dchunks) : it / (unsigned)nchunks;
     const int chunk = (int)(it - grp * (unsigned)nchunks);
     const size_t seg0 = (size_t)rp.seg_off;
     if (FORCED && lane < R && grp * R + lane < nrows)
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
 #pragma unroll
     for (int h = 0; h < R; ++h) {
         const unsigned row = grp * R + h < nrows ? grp * R + h : nrows - 1;
-        const NodeIdx n = node_index(0, row, nx, ny, nz);
+        const NodeIdx n = node_index<MUL_DIV>(0, row, nx, ny, nz, rp.dny);
         drow[h] = base + n.d;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {

@@ -413,6 +413,22 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
         rp.omega = (float)(1.0 / d.tau);
         rp.gx = rp.gy = rp.gz = 0.f;
         rp.pad = 0;
+        rp.dchunks = make_divisor((unsigned)rp.nchunks);
+        rp.dny = make_divisor((unsigned)d.ny);
+        // the lattice kernels divide row-segment and row indices by these; check
+        // the one-multiplication division on the edges of both ranges
+        const unsigned rows = (unsigned)d.ny * (unsigned)d.nz, items = rows * (unsigned)rp.nchunks;
+        const unsigned dv[2] = {(unsigned)rp.nchunks, (unsigned)d.ny}, top[2] = {items, rows};
+        const Divisor dd[2] = {rp.dchunks, rp.dny};
+        for (int k = 0; k < 2; ++k) {
+            const unsigned probe[] = {0u, 1u, dv[k] - 1, dv[k], dv[k] + 1, 2 * dv[k] - 1, top[k] - 1, top[k],
+                                      0x7fffffffu};
+            for (unsigned n : probe)
+                if (divide(n, dd[k]) != n / dv[k]) {
+                    delete s;
+                    return fail(LBP_EINVAL, "lbp_create: internal check of the index division failed");
+                }
+        }
         s->taus[r] = d.tau;
         noff += (long long)d.nx * d.ny * d.nz;
         soff += (long long)d.ny * d.nz * rp.nchunks;

@@ -212,6 +212,24 @@ __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned 
 // batched ensemble).  Their populations are concatenated node-wise in the same
 // 15 planes; every kernel gets the replica table by value (a kernel parameter,
 // so the per-block lookup reads the constant bank, not global memory).
+// Division by a divisor fixed per box, for numerators below 2^31, by one
+// multiplication (Granlund & Montgomery, PLDI 1994, Theorem 4.2 with N = 31):
+// with l = ceil(log2 d) and m = ceil(2^(31 + l) / d) (m < 2^32),
+// floor(n / d) = floor(n m / 2^(31 + l)) for 0 <= n < 2^31.
+struct Divisor {
+    unsigned m;
+    int l;
+};
+__host__ __device__ __forceinline__ unsigned divide(unsigned n, Divisor d) {
+    return (unsigned)(((unsigned long long)n * d.m) >> (31 + d.l));
+}
+inline Divisor make_divisor(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long p = 1ull << (31 + l);
+    return Divisor{(unsigned)((p + d - 1) / d), l};
+}
+
 struct Rep {
     int nx, ny, nz, nchunks;  // box and SEG-node segments per row
     long long node_off;       // first global node of the box
@@ -219,6 +237,7 @@ struct Rep {
     float omega;              // 1 / tau
     float gx, gy, gz;         // uniform body force density on every node of the box (Eq. 18)
     int pad;                  // rows per item of the staged lattice kernel (set per launch)
+    Divisor dchunks, dny;     // division by nchunks and by ny (row -> z) in the lattice kernels
 };
 
 constexpr int MAX_BATCH = 256;
