@@ -197,12 +197,13 @@ lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
  * work queued on the handle's stream.
  * With page-locked host buffers mapped into the device's address space
  * (cudaHostAlloc / cudaHostRegister with unified addressing) and graphs on,
- * the layout conversions read f_ext from and write r and v to the host
- * buffers directly, and they replay with the step as one CUDA graph per
- * buffer parity, cached on the three buffer addresses; positions and
- * velocities are final after the step's particle kernel (Eqs. 1-2), so they
- * go out while the lattice pass of the same step still runs, and the call
- * may return before that pass ends.  Every later call on the handle is ordered after it,
+ * the step's particle kernel itself reads f_ext from and writes r and v to
+ * the host buffers, and the step replays as one CUDA graph per buffer parity,
+ * cached on the three buffer addresses; positions and velocities are final
+ * after the particle kernel (Eqs. 1-2), whose last block then sets a
+ * completion flag in page-locked memory, so the call returns (after a bounded
+ * poll of that flag: LBP_ECUDA or LBP_ETIMEOUT if the stream fails or the flag
+ * does not come) while the lattice pass of the same step still runs.  Every later call on the handle is ordered after it,
  * and the handle's user stream waits for it.  Pageable buffers take plain
  * stream-ordered copies and return after the whole step.                      */
 lbp_status lbp_step_exchange(lbp_sim *sim, const double *f_ext, double *r, double *v, int on_device);

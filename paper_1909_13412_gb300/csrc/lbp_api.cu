@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -134,38 +135,24 @@ bool radius_ok(double R, int exclude) {
 
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
-// one time step (see the sequence at the top of this file).  With `readback`
-// (r, v host buffers, either may be NULL) the positions and velocities the
-// particle kernel has just written go to the host on s2 while s0 runs the
-// lattice pass; ev_xdone marks the end of that branch.
-struct Readback {
-    double *r, *v;  // device-accessible addresses of page-locked host buffers
-};
-lbp_status enqueue_step(lbp_sim *s, bool timed, const Readback *readback = nullptr) {
+// one time step (see the sequence at the top of this file).  With `io` (the
+// page-locked host buffers of lbp_step_exchange, device views) the particle
+// kernel reads the external forces from the host and writes the positions and
+// velocities back itself, then raises the step's completion flag.
+lbp_status enqueue_step(lbp_sim *s, bool timed, const ParticleIO *io = nullptr) {
     Range range("lbp step: particles + lattice pass");
     const void *src = s->f[s->cur];
     void *dst = s->f[s->cur ^ 1];
     const int parity = s->cur;
-    if (s->np > 0) CK(launch_particles(*s, src, parity, s->s0));
-    if (readback) {
-        // the layout conversion writes the host buffers directly (over the
-        // CPU-GPU link), so the branch is two small kernels and no copies
-        CK(cudaEventRecord(s->ev_xmid, s->s0));
-        CK(cudaStreamWaitEvent(s->s2, s->ev_xmid, 0));
-        if (readback->r) CK(launch_soa_to_aos(s->r, readback->r, s->np, s->cap, s->s2));
-        if (readback->v) CK(launch_soa_to_aos(s->v, readback->v, s->np, s->cap, s->s2));
-        CK(cudaEventRecordWithFlags(s->ev_xdone, s->s2, cudaEventRecordExternal));
-        CK(cudaEventRecord(s->ev_xjoin, s->s2));
-    }
+    if (s->np > 0) CK(launch_particles(*s, src, parity, s->s0, io));
     if (timed) CK(cudaEventRecord(s->tev[2 * s->ntimed], s->s0));
     // the lattice pass as the programmatic dependent of the particle kernel
     // (its population loads overlap the particle kernel's tail); not when
     // events around it time the lattice kernel alone
     if (s->np > 0)
-        CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0, !timed && !readback));
+        CK(launch_stream_collide_forced(*s, src, dst, parity, s->s0, !timed));
     else
         CK(launch_stream_collide(*s, src, dst, s->s0));
-    if (readback) CK(cudaStreamWaitEvent(s->s0, s->ev_xjoin, 0));
     if (timed) {
         CK(cudaEventRecord(s->tev[2 * s->ntimed + 1], s->s0));
         s->ntimed += 1;
@@ -291,10 +278,10 @@ lbp_status device_view(double *&p) {
     return LBP_OK;
 }
 
-// [forces in, step with the read-back branch] from and to page-locked host
+// [forces in, step, positions and velocities out] from and to page-locked host
 // buffers as one graph for the current buffer parity, kept while the same
-// buffers come back: the layout conversions read and write the host buffers
-// directly, so the graph holds kernels only
+// buffers come back: the particle kernel reads and writes the host buffers
+// directly, so the graph holds the step's two kernels only
 lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v, cudaGraphExec_t *out) {
     const int par = s->cur;
     const void *key[3] = {f_ext, r, v};
@@ -305,19 +292,21 @@ lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v,
             cudaGraphExecDestroy(s->xgraph[par]);
             s->xgraph[par] = nullptr;
         }
+        if (!s->d_xticket) {
+            TRY(dalloc(&s->d_xticket, 1));
+            CK(cudaMemset(s->d_xticket, 0, sizeof(unsigned)));
+            CK(cudaHostAlloc((void **)&s->h_xflag, sizeof(long long), cudaHostAllocMapped));
+            *s->h_xflag = -1;
+            CK(cudaHostGetDevicePointer((void **)&s->h_xflag_dev, s->h_xflag, 0));
+        }
         double *f_dev = const_cast<double *>(f_ext), *r_dev = r, *v_dev = v;
         TRY(device_view(f_dev));
         TRY(device_view(r_dev));
         TRY(device_view(v_dev));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
-        const Readback rb{r_dev, v_dev};
-        lbp_status st = LBP_OK;
-        if (f_dev) {
-            cudaError_t e0 = launch_aos_to_soa(f_dev, s->fext, s->np, s->cap, 0, s->s0);
-            if (e0 != cudaSuccess) st = fail(LBP_ECUDA, "lbp_step_exchange: %s", cudaGetErrorString(e0));
-        }
-        if (st == LBP_OK) st = enqueue_step(s, false, &rb);
+        const ParticleIO io{f_dev, r_dev, v_dev};
+        lbp_status st = enqueue_step(s, false, &io);
         cudaError_t e = cudaStreamEndCapture(s->s0, &g);
         if (st != LBP_OK) {
             if (g) cudaGraphDestroy(g);
@@ -332,6 +321,27 @@ lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v,
     }
     *out = s->xgraph[par];
     return LBP_OK;
+}
+
+// Wait until the particle kernel of step `step` has written the positions and
+// velocities to the host buffers (its completion flag in page-locked memory),
+// without waiting for the step's lattice pass.  Bounded: if the stream fails,
+// or is idle without the flag, or nothing happens for a minute, give up with
+// an error instead of spinning on.
+lbp_status wait_exchange_flag(lbp_sim *s, long long step) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long long spin = 1;; ++spin) {
+        if (__atomic_load_n(s->h_xflag, __ATOMIC_ACQUIRE) == step) return LBP_OK;
+        if (spin % 4096 == 0) {
+            const cudaError_t q = cudaStreamQuery(s->s0);
+            if (q != cudaSuccess && q != cudaErrorNotReady)
+                return fail(LBP_ECUDA, "lbp_step_exchange: %s", cudaGetErrorString(q));
+            if (q == cudaSuccess && __atomic_load_n(s->h_xflag, __ATOMIC_ACQUIRE) != step)
+                return fail(LBP_ECUDA, "lbp_step_exchange: the step finished without its completion flag");
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+                return fail(LBP_ETIMEOUT, "lbp_step_exchange: no completion flag within 60 s");
+        }
+    }
 }
 
 // page-locked (or registered) host memory mapped into the device's address
@@ -464,14 +474,10 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s0, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s1, cudaStreamNonBlocking, prio_low);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->s2, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_xmid, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_xjoin, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_xdone, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fail(LBP_ECUDA, "lbp_create: %s", cudaGetErrorString(e));
         return bail(LBP_ECUDA);
@@ -506,24 +512,23 @@ lbp_status lbp_destroy(lbp_sim *s) {
     if (!s) return LBP_OK;
     if (s->s0) cudaStreamSynchronize(s->s0);
     if (s->s1) cudaStreamSynchronize(s->s1);
-    if (s->s2) cudaStreamSynchronize(s->s2);
     drop_graphs(s);
     free_tape(s);
     void *bufs[] = {s->f[0], s->f[1], s->d_step, s->d_err, s->r, s->v, s->fh, s->fr, s->fext, s->xbuf,
                     s->mass, s->inv_mass, s->gamma, s->radius, s->sig, s->pinned, s->prep, s->fq, s->rec[0],
                     s->rec[1], s->ring,
                     s->d_vacf, s->vacf_sum, s->vacf_cnt, s->vacf_part, s->stage, s->inj, s->budget_part,
-                    s->corr_g, s->corr_h, s->corr_w, s->msd_state, s->msd_sum, s->ring16};
+                    s->corr_g, s->corr_h, s->corr_w, s->msd_state, s->msd_sum, s->ring16, s->d_xticket};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    if (s->h_xflag) cudaFreeHost(s->h_xflag);
     for (int i = 0; i < 2 * lbp::Sim::MAX_TIMED; ++i)
         if (s->tev[i]) cudaEventDestroy(s->tev[i]);
-    cudaEvent_t evs[] = {s->ev_in, s->ev_out, s->ev_fork, s->ev_join, s->ev_xmid, s->ev_xjoin, s->ev_xdone};
+    cudaEvent_t evs[] = {s->ev_in, s->ev_out, s->ev_fork, s->ev_join};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
     if (s->s0) cudaStreamDestroy(s->s0);
     if (s->s1) cudaStreamDestroy(s->s1);
-    if (s->s2) cudaStreamDestroy(s->s2);
     delete s;
     return LBP_OK;
 }
@@ -952,8 +957,9 @@ lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double 
         // step's lattice pass may still run, and later work on s0 follows it
         cudaGraphExec_t whole = nullptr;
         TRY(exchange_graph(s, f_ext, r, v, &whole));
+        const long long step = s->step;
         TRY(step_once(s, whole));
-        CK(cudaEventSynchronize(s->ev_xdone));
+        TRY(wait_exchange_flag(s, step));
         return leave(s);
     }
     const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

@@ -312,10 +312,6 @@ struct Sim {
     cudaStream_t s0 = nullptr;    // library main stream (non-blocking)
     cudaStream_t s1 = nullptr;    // library side stream (particles, VACF)
     cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
-    // lbp_step_exchange: the read-back branch (positions and velocities after
-    // the particle kernel, alongside the lattice pass) and its events
-    cudaStream_t s2 = nullptr;
-    cudaEvent_t ev_xmid = nullptr, ev_xjoin = nullptr, ev_xdone = nullptr;
 
     void *f[2] = {nullptr, nullptr};   // deviation populations, 15 planes of P (storage type)
     int cur = 0;                       // f[cur] holds fhat^n
@@ -374,6 +370,12 @@ struct Sim {
     double *budget_part = nullptr;  // [budget_blocks][4]
 
     double *xbuf = nullptr;  // [9][cap]: f_ext, r, V of lbp_step_exchange (array-of-structures)
+    // lbp_step_exchange with page-locked buffers: a block counter and a flag in
+    // page-locked host memory that the particle kernel sets to the step index
+    // once r and V are in the host buffers
+    unsigned *d_xticket = nullptr;
+    long long *h_xflag = nullptr;      // host address
+    long long *h_xflag_dev = nullptr;  // its device view
     int xbuf_cap = 0;
 
     // scratch for host <-> device conversions
@@ -427,7 +429,13 @@ cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, doubl
 int budget_blocks(const Sim &s);
 cudaError_t launch_budget(Sim &s, const void *src, double *out, cudaStream_t st);  // [budget_blocks][4]
 // particle_kernels.cu
-cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st);
+// host I/O of one lbp_step_exchange step, done by the particle kernel itself
+// ([n][3] FP64 device views of page-locked host buffers; null: none)
+struct ParticleIO {
+    const double *fext_in;
+    double *r_out, *v_out;
+};
+cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st, const ParticleIO *io = nullptr);
 bool particles_fit_per_corner(const Sim &s);  // the fit of Eq. 8 one lane per corner (few particles)
 cudaError_t launch_aos_to_soa(const double *aos, double *soa, int n, int ld, int offset,
                               cudaStream_t st);

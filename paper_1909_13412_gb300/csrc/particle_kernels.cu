@@ -47,7 +47,8 @@ struct ParticleArgs {
     long long P;
     long long N;
     double *r, *v, *fh, *fr;
-    const double *fext, *inv_mass, *gamma, *radius, *sig;
+    double *fext;  // written only when fext_in is given (lbp_step_exchange)
+    const double *inv_mass, *gamma, *radius, *sig;
     const unsigned char *pinned;
     int cap, np;
     const long long *d_step;
@@ -63,6 +64,14 @@ struct ParticleArgs {
     long long *d_vacf;  // [0] first sampled step, [2] samples written
     int *err;
     double *inj;        // [3] momentum put in by F_R + F_ext (null: not tracked)
+    // lbp_step_exchange with page-locked host buffers ([n][3] FP64, device views
+    // of host memory; null: none): the external forces to use (and keep), and
+    // the positions and velocities after the update; done_flag (host memory) is
+    // set to the step index once every block has written them
+    const double *fext_in;
+    double *r_out, *v_out;
+    unsigned *done_ticket;
+    long long *done_flag;
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -179,9 +188,18 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
     if (t >= 32 && t < 32 + PB && ip < A.np) {
         s_invM[lane] = A.inv_mass[ip];
         s_sg[lane] = A.sig[ip];
-        s_fe[0][lane] = A.fext[ip];
-        s_fe[1][lane] = A.fext[cap + ip];
-        s_fe[2][lane] = A.fext[2 * cap + ip];
+        if (A.fext_in) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double f = A.fext_in[3 * (size_t)ip + k];
+                s_fe[k][lane] = f;
+                A.fext[k * cap + ip] = f;  // kept for the steps that follow
+            }
+        } else {
+            s_fe[0][lane] = A.fext[ip];
+            s_fe[1][lane] = A.fext[cap + ip];
+            s_fe[2][lane] = A.fext[2 * cap + ip];
+        }
         s_pin[lane] = A.pinned[ip];
     }
     if (t < PB && ip < A.np) {
@@ -412,6 +430,7 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
         for (int k = 0; k < 3; ++k) {
             A.fh[k * cap + i] = FH3[k];
             A.fr[k * cap + i] = R3[k];
+            double rw = ro[k];
             if (!pin) {
                 // Eqs. 1-2, dt = 1: V += (F_H + F_R + F_ext)/M; r += V; periodic wrap
                 Vn[k] = Vo[k] + (FH3[k] + R3[k] + s_fe[k][lane]) * invM;
@@ -423,8 +442,12 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
                 bad |= b;
                 A.v[k * cap + i] = Vn[k];
                 A.r[k * cap + i] = rn;
+                rw = rn;
             }
+            if (A.r_out) A.r_out[3 * (size_t)i + k] = rw;
+            if (A.v_out) A.v_out[3 * (size_t)i + k] = Vn[k];
         }
+        if (A.done_flag) __threadfence_system();  // the host copies before the flag
         if (bad) atomicOr(A.err, ERR_NAN);
         if (A.inj)
 #pragma unroll
@@ -514,6 +537,20 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
             atomicAdd(A.fq + 2 * A.N + node, (unsigned long long)sh[2]);
         }
     }
+
+    // the last block to finish tells the host that every position and velocity
+    // is in its buffers (the lattice pass may still run)
+    if (A.done_flag) {
+        __syncthreads();
+        if (t == 0) {
+            const unsigned ticket = atomicAdd(A.done_ticket, 1u);
+            if (ticket == gridDim.x - 1) {
+                *A.done_ticket = 0u;
+                __threadfence_system();
+                *reinterpret_cast<volatile long long *>(A.done_flag) = step;
+            }
+        }
+    }
 }
 
 template <int MAXR, int PB, bool FIT8>
@@ -539,7 +576,7 @@ static void launch_particles_t(const Sim &s, const ParticleArgs &A, const RepTab
         launch_particles_pb<MAXR, PB_WIDE, false>(s, A, t, st);
 }
 
-cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st) {
+cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st, const ParticleIO *io) {
     if (s.np == 0) return cudaSuccess;
     ParticleArgs A;
     A.g = src;
@@ -573,6 +610,11 @@ cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t s
     A.d_vacf = s.d_vacf;
     A.err = s.d_err;
     A.inj = s.inj;
+    A.fext_in = io ? io->fext_in : nullptr;
+    A.r_out = io ? io->r_out : nullptr;
+    A.v_out = io ? io->v_out : nullptr;
+    A.done_ticket = io ? s.d_xticket : nullptr;
+    A.done_flag = io ? s.h_xflag_dev : nullptr;
     if (s.nrep == 1) {
         RepTable<1> t;
         t.nrep = 1;

@@ -365,6 +365,33 @@ def test_step_exchange_with_page_locked_buffers_equals_the_separate_calls():
         lbp.lbp_destroy(h)
 
 
+def test_step_exchange_with_one_output_buffer():
+    """Page-locked exchange asking for positions only, then velocities only: the
+    particle kernel writes just the requested host buffer, and the run stays
+    bitwise equal to the separate calls."""
+    shape = (10, 9, 8)
+    ps = wl.uniform_particles(5, shape, 8.0, 0.5, wl.stokes_radius(0.5, 0.8), 1e-4, 7, 8)
+    ha = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=6)
+    hb = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=6)
+    n = ps.n
+    rb = torch.full((n, 3), np.nan, dtype=torch.float64, pin_memory=True).numpy()
+    vb = torch.full((n, 3), np.nan, dtype=torch.float64, pin_memory=True).numpy()
+    for k in range(12):
+        lbp.lbp_step(ha, 1)
+        ra, va = np.empty((n, 3)), np.empty((n, 3))
+        lbp.lbp_particles_read(ha, r=ra, v=va)
+        if k < 6:
+            lbp.lbp_step_exchange(hb, None, rb, None)
+            assert np.array_equal(ra, rb), k
+            assert np.all(np.isnan(vb)), k
+        else:
+            lbp.lbp_step_exchange(hb, None, None, vb)
+            assert np.array_equal(va, vb), k
+    assert np.array_equal(gpu_pops(ha), gpu_pops(hb))
+    for h in (ha, hb):
+        lbp.lbp_destroy(h)
+
+
 def test_set_fluid_is_the_equilibrium_of_eq17():
     """lbp_set_fluid(rho, u) sets f = f^eq(rho~, u) at every node (oracle's Eq. 17)."""
     shape = (5, 6, 7)
