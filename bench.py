@@ -271,11 +271,26 @@ def cpu_baseline(w, ps, target_s=10.0):
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
+    cores = oracle.num_threads()
+    # the same on one core (a shorter sample: about a fifth of the time budget)
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        o.step(1)
+        t1s = time.perf_counter() - t0
+        steps1 = int(min(10, max(1, 0.2 * target_s / max(t1s, 1e-3))))
+        t0 = time.perf_counter()
+        o.step(steps1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
     o.close()
-    return {"value": w.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+    return {"value": w.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": cores,
             "kind": "oracle",
+            "single_core": w.nodes * steps1 / dt1 / 1e6,
             "sample": f"{steps} FP64 oracle steps (after 1 warm-up step) of the {w.name} workload "
-                      f"({w.nodes} nodes, {w.n_particles} particles; VACF accumulation not included)"}
+                      f"({w.nodes} nodes, {w.n_particles} particles; VACF accumulation not included) "
+                      f"on {cores} threads; single_core: {steps1} further steps on one thread"}
 
 
 def run_reference(args, w):

@@ -81,6 +81,8 @@ def bind(path: str):
     L.or_vacf.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, C.c_int, _dp, _i64p]
     L.or_msd.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, _dp, _i64p]
     L.or_num_threads.restype = C.c_int
+    L.or_set_num_threads.argtypes = [C.c_int]
+    L.or_set_num_threads.restype = None
     return L
 
 
@@ -203,6 +205,11 @@ def msd(Xtraj, K):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    """OpenMP threads of the oracle's loops over z-planes (timing only)."""
+    lib().or_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- whole system

@@ -611,3 +611,15 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops over z-planes (timing only; the results do not
+ * depend on it: every node and particle is computed by one thread). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}

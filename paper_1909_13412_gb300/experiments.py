@@ -228,9 +228,76 @@ def config2_statistics(runs, window, M, tau):
             "D_green_kubo": float(np.mean(d_gk)), "D_green_kubo_se": se(d_gk)}
 
 
+def ensemble_groups(boxes):
+    """Box indices of each (L, tau) group of a replica ensemble ((nx, ny, nz, tau)
+    per box, cubic), in order of first appearance: the VACF is averaged within a
+    group, since averaging across tau would mix viscosities (Section 3 takes the
+    VACF over replicas of one suspension)."""
+    groups = {}
+    for b, (nx, ny, nz, tau) in enumerate(boxes):
+        groups.setdefault((nx, tau), []).append(b)
+    return groups
+
+
+def ensemble_run(w, steps, max_lag, seed, mode=lbp.LBP_STOKESLET):
+    """The batched ensemble `w` (one handle, one particle launch and one lattice
+    launch per step over all boxes) for `steps` steps with the per-particle VACF
+    to `max_lag`.  Returns the per-particle sums [n, K + 1], the pair counts
+    per lag [K + 1] and the seconds of stepping (device-waited).  `mode`: the
+    coupling (Eq. 8 by default; Eq. 6 leaves the fluid out)."""
+    import time
+    h = lbp.lbp_create_batch(w.boxes)
+    try:
+        for b in range(len(w.boxes)):
+            pb = w.particles(b)
+            lbp.lbp_particles_add_to(h, b, pb.r, pb.V, pb.M, pb.gamma, pb.R)
+        lbp.lbp_particles_set_params(h, kT=w.kT, seed=seed, mode=mode)
+        lbp.lbp_step(h, 2)
+        lbp.lbp_autotune(h, 5)
+        lbp.lbp_vacf_configure_ex(h, max_lag, 1)
+        cs = np.empty((w.n_particles, max_lag + 1))
+        cnt = np.empty(max_lag + 1, np.int64)
+        lbp.lbp_vacf_read_per_particle(h, cs, cnt)  # waits for the set-up
+        t0 = time.perf_counter()
+        lbp.lbp_step(h, steps)
+        lbp.lbp_vacf_read_per_particle(h, cs, cnt)  # host read: waits for every step and block
+        secs = time.perf_counter() - t0
+        lbp.lbp_check(h)
+    finally:
+        lbp.lbp_destroy(h)
+    return cs, cnt, secs
+
+
+def ensemble_statistics(w, cs, cnt, window, lags=(1, 10, 50, 100, 200, 400, 1000)):
+    """Per (L, tau) group: the group's VACF C(k) = sum over its particles of the
+    per-particle sums / (particles x pairs per lag), C(k)/C(0) at `lags`, C(0)
+    per pair (not 3 kT/M with the athermal fluid: the particle drags it along),
+    and the tail amplitude B = mean over `window`
+    of C/C(0) t^(3/2) with the standard error over the group's particles (each
+    particle's own C_i/C_i(0)), beside M/[12 rho (pi nu)^(3/2)] at the group's tau."""
+    t0, t1 = window
+    t = np.arange(t0, t1 + 1)
+    K = cs.shape[1] - 1
+    per = w.n_per_box
+    out = []
+    for (L, tau), boxes in ensemble_groups(w.boxes).items():
+        rows = [b * per + q for b in boxes for q in range(per)]
+        C = cs[rows].sum(axis=0) / (len(rows) * cnt)
+        Ci = cs[rows] / cnt
+        amps = [float(np.mean(c[t0:t1 + 1] / c[0] * t ** 1.5)) for c in Ci]
+        n = len(amps)
+        out.append({"L": int(L), "tau": float(tau), "boxes": len(boxes), "particles": n,
+                    "C0": float(C[0]),
+                    "C_over_C0": {str(k): float(C[k] / C[0]) for k in lags if k <= K},
+                    "B": float(np.mean(C[t0:t1 + 1] / C[0] * t ** 1.5)),
+                    "B_se": float(np.std(amps, ddof=1) / math.sqrt(n)) if n > 1 else float("nan"),
+                    "B_paper": w.M / (12.0 * (math.pi * nu_of(tau)) ** 1.5)})
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("experiment", choices=["fig1", "fig3", "tail", "config2"])
+    ap.add_argument("experiment", choices=["fig1", "fig3", "tail", "config2", "config4"])
     ap.add_argument("--realisations", type=int, default=4)
     ap.add_argument("--window", type=int, nargs=2, default=[100, 400])
     ap.add_argument("--config", default=None,
@@ -278,6 +345,16 @@ def main(argv=None):
                     "C_over_C0": {str(t): float(np.mean([c[0][t] for c in runs])) for t in
                                   (1, 10, 50, 100, 200, 400, 1000)}})
         print(json.dumps(out))
+    elif a.experiment == "config4":
+        from . import workloads as wl
+        w = wl.load(a.config) if a.config else wl.ENSEMBLE_68
+        steps, max_lag = 10000, 5000
+        cs, cnt, secs = ensemble_run(w, steps, max_lag, w.seed_noise)
+        print(json.dumps({"workload": w.name, "steps": steps, "max_lag": max_lag,
+                          "mlups": w.nodes * steps / secs / 1e6,
+                          "particle_updates_per_s": w.n_particles * steps / secs,
+                          "window": list(a.window),
+                          "groups": ensemble_statistics(w, cs, cnt, tuple(a.window))}))
     else:
         B, B_th, slope = tail_amplitude(128, 0.8, 10.0, 0.5, 3000, (600, 2000))
         print(json.dumps({"B_measured": B, "B_theory": B_th, "slope": slope}))

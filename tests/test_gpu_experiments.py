@@ -122,3 +122,25 @@ def test_brownian_suspension_at_its_stated_size_and_length():
     assert st["D_msd"] == pytest.approx(st["D_green_kubo"], rel=0.03), st
     # Einstein's D = kT / gamma of the bare friction sets the scale
     assert 0.5 * w.kT / w.gamma < st["D_msd"] < 1.5 * w.kT / w.gamma, st
+
+
+def test_ensemble_vacf_per_group_on_the_gpu():
+    """A small uneven replica ensemble run as one batch with the per-particle
+    VACF, in Eq. 6 mode (fluid not coupled), where each particle is a discrete
+    Ornstein-Uhlenbeck process: per (L, tau) group C(0) per pair is
+    3 (kT/M) 2/(2 - g) and C(k)/C(0) = (1 - g)^k with g = gamma/M, within the
+    statistical error of ~10^4 decorrelated samples; the groups' sums add up to
+    the whole ensemble's."""
+    from paper_1909_13412_gb300 import workloads as wl
+    boxes = [(16, 16, 16, 0.6), (16, 16, 16, 0.8), (20, 20, 20, 0.6), (16, 16, 16, 0.6), (20, 20, 20, 0.6)]
+    w = wl.Ensemble("ens_test", boxes, n_per_box=12)
+    cs, cnt, _ = ex.ensemble_run(w, 4000, 200, 7, mode=lbp.LBP_BROWNIAN)
+    out = ex.ensemble_statistics(w, cs, cnt, (20, 60), lags=(1, 10, 50))
+    assert [(g["L"], g["tau"], g["particles"]) for g in out] == [(16, 0.6, 24), (16, 0.8, 12), (20, 0.6, 24)]
+    gm = w.gamma / w.M
+    for g in out:
+        assert abs(g["C0"] / (3.0 * w.kT / w.M * 2.0 / (2.0 - gm)) - 1.0) < 0.1, g
+        assert abs(g["C_over_C0"]["1"] - (1.0 - gm)) < 0.01, g
+        assert abs(g["C_over_C0"]["10"] - (1.0 - gm) ** 10) < 0.06, g
+    total = sum(g["C0"] * g["particles"] for g in out)
+    assert math.isclose(total, cs[:, 0].sum() / cnt[0], rel_tol=1e-12)
