@@ -358,7 +358,9 @@ lbp_status lbp_set_body_force(lbp_sim *sim, int replica, const double *g);
  * steps first for timings that include the particle coupling) and bump a
  * scratch step counter.
  * Synchronous; LBP_ETIMEOUT if a bounded device wait ran out.  Default before
- * any call: variant 0 with 1 row (LBP_F32) or 2 rows (the 2-byte types).     */
+ * any call (the picks measured at 256^3): variant 0 with 2 rows for LBP_F32;
+ * variant 3 with 1 row for the 2-byte types when every box's nx is a multiple
+ * of 4, else variant 0 with 2 rows.                                          */
 #define LBP_AUTOTUNE_CANDIDATES 10
 lbp_status lbp_autotune(lbp_sim *sim, int launches, int *rows, int *variant, double *ms);
 

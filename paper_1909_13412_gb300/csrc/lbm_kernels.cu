@@ -585,10 +585,24 @@ static cudaError_t by_storage(const Sim &s, F &&f) {
     }
 }
 
-// Rows of SEG nodes per block: the default is 1 for FP32 storage and 2 for
-// the 2-byte types (more independent loads in flight per thread where each
-// load is half as wide); lbp_autotune picks among 1, 2 and 4 by timing.
-int default_rows_per_block(int precision) { return precision == LBP_F32 ? 1 : 2; }
+bool quad_kernel_ok(const Sim &s);
+
+// The lattice kernel's shape before any lbp_autotune: the autotuner's pick on
+// GB300 at 256^3 and for the 68-box ensemble -- one node per thread with two
+// rows of SEG nodes per block for FP32 (0.302 ms against 0.315-0.322 with one
+// row at 256^3; 0.769 against 0.957 ms for the ensemble), four nodes per
+// thread with one row for the 2-byte types (0.172 ms against 0.245 ms for one
+// node per thread with two rows) where every box's nx is a multiple of 4, else
+// one node per thread with two rows.
+void default_shape(const Sim &s, int &rows, int &variant) {
+    if (s.precision != LBP_F32 && quad_kernel_ok(s)) {
+        variant = 3;
+        rows = 1;
+    } else {
+        variant = 0;
+        rows = 2;
+    }
+}
 
 template <typename F>
 static cudaError_t by_rows(int R, F &&f) {

@@ -452,8 +452,7 @@ lbp_status lbp_create_batch(const lbp_lattice_desc *descs, int nrep, void *strea
     s->tau = descs[0].tau;
     s->precision = descs[0].precision;
     // the measured best on GB300 without tuning (lbp_autotune measures the rest)
-    s->variant = 0;
-    s->rows = default_rows_per_block(s->precision);
+    default_shape(*s, s->rows, s->variant);
     s->user = (cudaStream_t)stream;
     s->sqrt3 = std::sqrt(3.0);
     auto bail = [&](lbp_status st) {

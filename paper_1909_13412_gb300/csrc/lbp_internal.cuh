@@ -412,7 +412,7 @@ cudaError_t launch_stream_collide_forced_cfg(Sim &s, const void *src, void *dst,
                                              const unsigned long long *rec_cur,
                                              unsigned long long *rec_prev, long long *bump, int rows,
                                              int variant, cudaStream_t st);
-int default_rows_per_block(int precision);
+void default_shape(const Sim &s, int &rows, int &variant);  // before lbp_autotune
 bool pair_kernel_ok(const Sim &s);  // 2-byte storage and every box with even nx
 bool variant_ok(const Sim &s, int variant);
 // pdl: launched right after the step's particle kernel on `st`, as its

@@ -295,6 +295,23 @@ def test_kernel_shapes_and_autotune_leave_results_unchanged(prec, where):
             lbp.lbp_destroy(h)
 
 
+@pytest.mark.parametrize("prec", [lbp.LBP_F32, lbp.LBP_BF16, lbp.LBP_F16])
+def test_default_kernel_shape(prec):
+    """Before any lbp_autotune a handle runs the shape the autotuner picks at
+    256^3: two rows of one node per thread for FP32, four nodes per thread for
+    the 2-byte types where every nx is a multiple of 4 (else two rows of one)."""
+    for box, quad in ((SHAPE_BOXES["20x18x16"], True), (SHAPE_BOXES["22x6x5"], False)):
+        h = make_box(prec, 0.0, box)
+        d = lbp.lbp_diagnostics(h)
+        want = (1, 3) if prec != lbp.LBP_F32 and quad else (2, 0)
+        assert (d["rows_per_block"], d["variant"]) == want, box
+        lbp.lbp_destroy(h)
+    h = make_batch(prec, 0.0, True)  # nx = 33 in one box: no four-node kernel
+    d = lbp.lbp_diagnostics(h)
+    assert (d["rows_per_block"], d["variant"]) == (2, 0)
+    lbp.lbp_destroy(h)
+
+
 def test_block_rows_validation():
     h = make_batch(lbp.LBP_F32, 0.0, True)
     with pytest.raises(lbp.LbpError):
