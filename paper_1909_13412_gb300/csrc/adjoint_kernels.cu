@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
     for (int k = 0; k < 3; ++k) d[k] = (double)((c >> k) & 1) - q[k];
     // forward re-evaluation of F_H
     double FH[3] = {0.0, 0.0, 0.0}, e[3] = {0.0, 0.0, 0.0};
-    double U = 0.0, num = 0.0, den = 0.0, nw = 0.0;
+    double U = 0.0, num = 0.0, den = 0.0, nw = 0.0, inw = 0.0, iden = 0.0;
     double ur[3] = {0.0, 0.0, 0.0};
     bool fit = false;
     // this corner's fit geometry (used by the forward and the adjoint fit)
@@ -196,16 +196,21 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
         double m[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) m[k] = grp8_sum(u[k] - V[k]) * 0.125;
-        nw = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
-        if (nw > 0.0) {
+        // reciprocal square roots instead of square roots and divisions (the
+        // FP64 pipe is narrow and divisions are long sequences on it)
+        const double mm = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+        if (mm > 0.0) {
+            inw = rsqrt(mm);
+            nw = mm * inw;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) e[k] = m[k] / nw;
+            for (int k = 0; k < 3; ++k) e[k] = m[k] * inw;
         }
-        rp = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double rr = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        ir = rr > 0.0 ? rsqrt(rr) : 0.0;
+        rp = rr * ir;
         use = nw > 0.0 && !(rp < 1e-12 || (A.exclude_inside && rp < R));
         double pn = 0.0, pd = 0.0;
         if (use) {
-            ir = 1.0 / rp;
             ir3 = ir * ir * ir;
             x = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
             k1 = 1.0 - cR * ir;
@@ -220,7 +225,8 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
         num = grp8_sum(pn);
         den = grp8_sum(pd);
         if (nw > 0.0 && den != 0.0) {
-            U = num / den;
+            iden = 1.0 / den;
+            U = num * iden;
             fit = true;
         }
 #pragma unroll
@@ -262,8 +268,9 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
         gM = -lF_tot * invM * invM;
         // F_R = sigma xi, sigma = sqrt(2 gamma kT)
         if (sg > 0.0) {
-            gG += lFR_xi * (A.kT / sg);
-            gK += lFR_xi * (gam / sg);
+            const double isg = 1.0 / sg;
+            gG += lFR_xi * (A.kT * isg);
+            gK += lFR_xi * (gam * isg);
         }
     }
     const bool spread = A.mode != LBP_BROWNIAN;
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
         const double lU = fit ? gam * eF : 0.0;
         if (fit) gG += U * eF;
         double le[3] = {gam * U * lFH[0], gam * U * lFH[1], gam * U * lFH[2]};
-        const double lnum = fit ? lU / den : 0.0, lden = fit ? -lU * num / (den * den) : 0.0;
+        const double lnum = fit ? lU * iden : 0.0, lden = fit ? -lU * num * iden * iden : 0.0;
         double ple[3] = {0.0, 0.0, 0.0}, pq[3] = {0.0, 0.0, 0.0}, plc = 0.0;
         if (use && fit) {
             const double ir5 = ir3 * ir * ir;
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(64) k_adj_fp64(const AdjPArgs A, const RepTabl
             // e = m/|m| with m the mean of the w_p
             const double ee = e[0] * le[0] + e[1] * le[1] + e[2] * le[2];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) lu[k] += (le[k] - e[k] * ee) / nw * 0.125;
+            for (int k = 0; k < 3; ++k) lu[k] += (le[k] - e[k] * ee) * inw * 0.125;
         }
         // w_p = u_p - V
 #pragma unroll
