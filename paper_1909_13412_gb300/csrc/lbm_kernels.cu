@@ -39,10 +39,10 @@ template <typename St>
 __device__ __forceinline__ void collide_store(const float g[Q], const Planes<St> &pl, int d,
                                               float omega, float F0, float F1, float F2, bool &bad) {
     float o[Q];
-    collide_values(g, omega, F0, F1, F2, o);
+    collide_st<St>(g, omega, F0, F1, F2, o);
     bad |= nonfinite_node(o);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) St::store(pl.d[a] + d, a, o[a]);
+    for (int a = 0; a < Q; ++a) St::cstore(pl.d[a] + d, a, o[a]);
 }
 
 // Index arithmetic shared by both variants: node d of (x, row) and the
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide(Planes<St
         n[h].d += base;
 #pragma unroll
         for (int a = 0; a < Q; ++a)
-            g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
+            g[h][a] = St::cload(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
                                           n[h].oz[ez(a) + 1]), a);
     }
     bool bad = false;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
         n[h].d += base;
 #pragma unroll
         for (int a = 0; a < Q; ++a)
-            g[h][a] = St::load(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
+            g[h][a] = St::cload(pl.s[a] + (n[h].d + n[h].ox[ex(a) + 1] + n[h].oy[ey(a) + 1] +
                                           n[h].oz[ez(a) + 1]), a);
     }
     // the loads above do not depend on this step's particle kernel; what follows does
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(BX, R == 2 ? 8 : 1) k_stream_collide_forced(
 // end load the neighbouring pair themselves (periodic in x).  This halves the
 // load and store instructions per node and leaves the conversions packed, so
 // the kernel is no longer bound by instruction issue.  Per node the
-// arithmetic is that of collide_values: results equal the one-node kernels'
+// arithmetic is that of collide_st: results equal the one-node kernels'
 // bit for bit.
 // ---------------------------------------------------------------------------
 template <typename St>
@@ -240,11 +240,11 @@ __device__ __forceinline__ void unpack2<StoreBF16>(unsigned v, int, float &lo, f
     lo = __uint_as_float(v << 16);
     hi = __uint_as_float(v & 0xffff0000u);
 }
+// FP16: the collision-space values h (StoreF16::cload), not scaled
 template <>
-__device__ __forceinline__ void unpack2<StoreF16>(unsigned v, int a, float &lo, float &hi) {
-    const float sc = wgtf(a) * (1.f / F16_SCALE);
-    lo = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))) * sc;
-    hi = __half2float(__ushort_as_half((unsigned short)(v >> 16))) * sc;
+__device__ __forceinline__ void unpack2<StoreF16>(unsigned v, int, float &lo, float &hi) {
+    lo = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+    hi = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
 }
 template <typename St>
 __device__ __forceinline__ unsigned pack2(float lo, float hi, int a);
@@ -254,9 +254,8 @@ __device__ __forceinline__ unsigned pack2<StoreBF16>(float lo, float hi, int) {
     return *reinterpret_cast<const unsigned *>(&p);
 }
 template <>
-__device__ __forceinline__ unsigned pack2<StoreF16>(float lo, float hi, int a) {
-    const float sc = F16_SCALE / wgtf(a);
-    const __half2 p = __floats2half2_rn(lo * sc, hi * sc);
+__device__ __forceinline__ unsigned pack2<StoreF16>(float lo, float hi, int) {
+    const __half2 p = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const unsigned *>(&p);
 }
 
@@ -367,8 +366,8 @@ __global__ void __launch_bounds__(PAIR_BX) k_stream_collide_pair(
         }
         if (act && grp * R + h < nrows) {
             float o0[Q], o1[Q];
-            collide_values(g[h][0], rp.omega, F[0][0], F[0][1], F[0][2], o0);
-            collide_values(g[h][1], rp.omega, F[1][0], F[1][1], F[1][2], o1);
+            collide_st<St>(g[h][0], rp.omega, F[0][0], F[0][1], F[0][2], o0);
+            collide_st<St>(g[h][1], rp.omega, F[1][0], F[1][1], F[1][2], o1);
             if (nonfinite_node(o0) || nonfinite_node(o1)) atomicOr(err, ERR_LATTICE);
 #pragma unroll
             for (int a = 0; a < Q; ++a)
@@ -410,7 +409,7 @@ __device__ __forceinline__ void record_sum4(unsigned long long rw, int cnt, int 
 // x).  A thread keeps 15 R 8-byte loads in flight in 30 R registers, twice the
 // bytes per register of the paired kernel, and collides the pairs (x, x + 1)
 // and (x + 2, x + 3) in turn, packing the results over the pulled values.
-// Per node the arithmetic is that of collide_values, and the force sums are
+// Per node the arithmetic is that of collide_st, and the force sums are
 // the same exact integer sums: results equal the other kernels' bit for bit.
 // ---------------------------------------------------------------------------
 constexpr int QUAD_WARPS = 4;  // row segments (warps) per block
@@ -537,11 +536,11 @@ __global__ void __launch_bounds__(32 * QUAD_WARPS, R == 1 ? 6 : 1) k_stream_coll
 #pragma unroll
             for (int a = 0; a < Q; ++a) unpack2<St>(j ? p[h][a].y : p[h][a].x, a, g0[a], g1[a]);
             if (unforced) {
-                collide_values(g0, rp.omega, 0.f, 0.f, 0.f, o0);
-                collide_values(g1, rp.omega, 0.f, 0.f, 0.f, o1);
+                collide_st<St>(g0, rp.omega, 0.f, 0.f, 0.f, o0);
+                collide_st<St>(g1, rp.omega, 0.f, 0.f, 0.f, o1);
             } else {
-                collide_values(g0, rp.omega, F[2 * j][0], F[2 * j][1], F[2 * j][2], o0);
-                collide_values(g1, rp.omega, F[2 * j + 1][0], F[2 * j + 1][1], F[2 * j + 1][2], o1);
+                collide_st<St>(g0, rp.omega, F[2 * j][0], F[2 * j][1], F[2 * j][2], o0);
+                collide_st<St>(g1, rp.omega, F[2 * j + 1][0], F[2 * j + 1][1], F[2 * j + 1][2], o1);
             }
 #pragma unroll
             for (int a = 0; a < Q; ++a) {

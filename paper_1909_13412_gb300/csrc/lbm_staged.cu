@@ -4,7 +4,7 @@
 //
 // Same update as lbm_kernels.cu (pull streaming of Eq. 20, moments of
 // Eqs. 12-13, BGK collision with the force term of Eqs. 15, 17-19, per node
-// the arithmetic of collide_values, so results are identical bit for bit), but
+// the arithmetic of collide_st, so results are identical bit for bit), but
 // the loads no longer come from registers.  A persistent CTA walks the items
 // of the lattice -- an item is R whole x-rows of one z-plane (R nx <= STAGED_NODES)
 // -- through a pipeline of shared-memory stages.  A producer warp refills a
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const typename St::T *p = reinterpret_cast<const typename St::T *>(stage + a * G::PLANE_BYTES);
-                g[a] = St::load_shared(p + rb + (ex(a) > 0 ? xm : (ex(a) < 0 ? xp : x)), a);
+                g[a] = St::cload_shared(p + rb + (ex(a) > 0 ? xm : (ex(a) < 0 ? xp : x)), a);
             }
             float F0 = rp.gx, F1 = rp.gy, F2 = rp.gz;
             const long long d = rp.node_off + (row0 + yy) * nx + x;
@@ -225,10 +225,10 @@ __global__ void __launch_bounds__(STAGED_THREADS + 32) k_stream_collide_staged(
                 }
             }
             float o[Q];
-            collide_values(g, rp.omega, F0, F1, F2, o);
+            collide_st<St>(g, rp.omega, F0, F1, F2, o);
             bad |= nonfinite_node(o);
 #pragma unroll
-            for (int a = 0; a < Q; ++a) St::store(pl.d[a] + d, a, o[a]);
+            for (int a = 0; a < Q; ++a) St::cstore(pl.d[a] + d, a, o[a]);
         }
         // this warp is done with the stage
         __syncwarp();

@@ -47,20 +47,34 @@ __host__ __device__ constexpr float wgtf(int a) {
 //          |g/w| up to 64 still fits.
 constexpr float F16_SCALE = 1024.f;
 
+// load/store: the deviation g.  cload/cstore (and cload_shared): the values
+// the lattice kernels' collision works on (collide_st): g itself for F32 and
+// BF16; for F16 the stored variable h = g F16_SCALE / w_a, on which the
+// collision is written directly (collide_values_scaled), so the lattice pass
+// does not scale its 15 loads and 15 stores per node.
 struct StoreF32 {
     using T = float;
+    static constexpr bool SCALED = false;
     static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
     static __device__ __forceinline__ float load_shared(const T *p, int) { return *p; }
     static __device__ __forceinline__ void store(T *p, int, float v) { *p = v; }
+    static __device__ __forceinline__ float cload(const T *p, int a) { return load(p, a); }
+    static __device__ __forceinline__ float cload_shared(const T *p, int a) { return load_shared(p, a); }
+    static __device__ __forceinline__ void cstore(T *p, int a, float v) { store(p, a, v); }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
+    static constexpr bool SCALED = false;
     static __device__ __forceinline__ float load(const T *p, int) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float load_shared(const T *p, int) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void store(T *p, int, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float cload(const T *p, int a) { return load(p, a); }
+    static __device__ __forceinline__ float cload_shared(const T *p, int a) { return load_shared(p, a); }
+    static __device__ __forceinline__ void cstore(T *p, int a, float v) { store(p, a, v); }
 };
 struct StoreF16 {
     using T = __half;
+    static constexpr bool SCALED = true;
     static __device__ __forceinline__ float load(const T *p, int a) {
         return __half2float(__ldg(p)) * (wgtf(a) * (1.f / F16_SCALE));
     }
@@ -70,6 +84,9 @@ struct StoreF16 {
     static __device__ __forceinline__ void store(T *p, int a, float v) {
         *p = __float2half_rn(v * (F16_SCALE / wgtf(a)));
     }
+    static __device__ __forceinline__ float cload(const T *p, int) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float cload_shared(const T *p, int) { return __half2float(*p); }
+    static __device__ __forceinline__ void cstore(T *p, int, float v) { *p = __float2half_rn(v); }
 };
 
 __host__ __device__ constexpr int storage_bytes(int precision) { return precision == LBP_F32 ? 4 : 2; }
@@ -129,6 +146,65 @@ __device__ __forceinline__ void collide_values(const float g[Q], float omega, fl
     LBP_PAIR(11, 1.f / 72.f, wo_c, s_c, __fadd_rn(__fsub_rn(ux, uy), uz), __fadd_rn(__fsub_rn(F0, F1), F2))
     LBP_PAIR(13, 1.f / 72.f, wo_c, s_c, __fadd_rn(__fsub_rn(uy, ux), uz), __fadd_rn(__fsub_rn(F1, F0), F2))
 #undef LBP_PAIR
+}
+
+// The same collision on the scaled variables h_a = g_a F16_SCALE / w_a of the
+// FP16 storage (in and out).  The moments take the weights back, per class:
+//     rho~ - 1 = (2/9 h_0 + 1/9 sum_faces h + 1/72 sum_corners h) / F16_SCALE,
+//     u = (1/9 sum_faces e h + 1/72 sum_corners e h) / F16_SCALE;
+// in the outputs the weights cancel against the scale:
+//     h'_0 = (1 - omega) h_0 + F16_SCALE omega base,
+//     h'_A, h'_{A+1} = (1 - omega) h + S' +- X',
+//     S' = F16_SCALE omega (base + 9/2 (e.u)^2),  X' = 3 F16_SCALE (omega e.u + e.F),
+// the same for every velocity class.  Every operation is rounded explicitly, so
+// every FP16 lattice kernel gives the same bits.
+__device__ __forceinline__ void collide_values_scaled(const float h[Q], float omega, float F0, float F1,
+                                                      float F2, float o[Q]) {
+    constexpr float kr = (2.f / 9.f) / F16_SCALE, kf = (1.f / 9.f) / F16_SCALE, kc = (1.f / 72.f) / F16_SCALE;
+    const float sf = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(h[1], h[2]), h[3]), h[4]), h[5]), h[6]);
+    float sc = h[7];
+#pragma unroll
+    for (int a = 8; a < Q; ++a) sc = __fadd_rn(sc, h[a]);
+    const float drho = __fmaf_rn(kc, sc, __fmaf_rn(kf, sf, __fmul_rn(kr, h[0])));
+    const float c78 = __fsub_rn(h[7], h[8]), c910 = __fsub_rn(h[9], h[10]),
+                c1112 = __fsub_rn(h[11], h[12]), c1314 = __fsub_rn(h[13], h[14]);
+    const float a78 = __fadd_rn(c78, c910), b78 = __fsub_rn(c78, c910);
+    const float ux = __fmaf_rn(kc, __fsub_rn(__fadd_rn(a78, c1112), c1314), __fmul_rn(kf, __fsub_rn(h[1], h[2])));
+    const float uy = __fmaf_rn(kc, __fadd_rn(__fsub_rn(a78, c1112), c1314), __fmul_rn(kf, __fsub_rn(h[3], h[4])));
+    const float uz = __fmaf_rn(kc, __fadd_rn(__fadd_rn(b78, c1112), c1314), __fmul_rn(kf, __fsub_rn(h[5], h[6])));
+    const float uu = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+    const float base = __fmaf_rn(-1.5f, uu, drho);
+    const float om1 = __fsub_rn(1.f, omega);
+    const float so = __fmul_rn(F16_SCALE, omega);   // F16_SCALE omega
+    const float sb = __fmul_rn(so, base);
+    const float s45 = __fmul_rn(4.5f, so), s3 = __fmul_rn(3.f, so);
+    o[0] = __fmaf_rn(om1, h[0], sb);
+#define LBP_PAIR_S(A, EU, FE)                                                              \
+    {                                                                                      \
+        const float eu = (EU);                                                             \
+        const float S = __fmaf_rn(s45, __fmul_rn(eu, eu), sb);                             \
+        const float X = __fmaf_rn(s3, eu, __fmul_rn(3.f * F16_SCALE, (FE)));               \
+        o[A] = __fmaf_rn(om1, h[A], __fadd_rn(S, X));                                      \
+        o[A + 1] = __fmaf_rn(om1, h[A + 1], __fsub_rn(S, X));                              \
+    }
+    LBP_PAIR_S(1, ux, F0)
+    LBP_PAIR_S(3, uy, F1)
+    LBP_PAIR_S(5, uz, F2)
+    LBP_PAIR_S(7, __fadd_rn(__fadd_rn(ux, uy), uz), __fadd_rn(__fadd_rn(F0, F1), F2))
+    LBP_PAIR_S(9, __fsub_rn(__fadd_rn(ux, uy), uz), __fsub_rn(__fadd_rn(F0, F1), F2))
+    LBP_PAIR_S(11, __fadd_rn(__fsub_rn(ux, uy), uz), __fadd_rn(__fsub_rn(F0, F1), F2))
+    LBP_PAIR_S(13, __fadd_rn(__fsub_rn(uy, ux), uz), __fadd_rn(__fsub_rn(F1, F0), F2))
+#undef LBP_PAIR_S
+}
+
+// The collision of the lattice kernels on their collision-space values (cload).
+template <typename St>
+__device__ __forceinline__ void collide_st(const float g[Q], float omega, float F0, float F1, float F2,
+                                           float o[Q]) {
+    if constexpr (St::SCALED)
+        collide_values_scaled(g, omega, F0, F1, F2, o);
+    else
+        collide_values(g, omega, F0, F1, F2, o);
 }
 
 // Programmatic dependent launch.  A step's lattice pass is launched as the
