@@ -957,6 +957,9 @@ lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double 
         cudaGraphExec_t whole = nullptr;
         TRY(exchange_graph(s, f_ext, r, v, &whole));
         const long long step = s->step;
+        // the flag may hold this step index from before a lbp_set_step_index or a
+        // checkpoint load; the previous call's kernel has finished writing it
+        __atomic_store_n(s->h_xflag, -1ll, __ATOMIC_RELEASE);
         TRY(step_once(s, whole));
         TRY(wait_exchange_flag(s, step));
         return leave(s);

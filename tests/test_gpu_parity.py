@@ -388,6 +388,17 @@ def test_step_exchange_with_one_output_buffer():
             lbp.lbp_step_exchange(hb, None, None, vb)
             assert np.array_equal(va, vb), k
     assert np.array_equal(gpu_pops(ha), gpu_pops(hb))
+    # the step index set back to the last exchanged step, whose index the
+    # completion flag still holds: the call must still wait for the new step
+    back = lbp.lbp_get_step_index(hb) - 1
+    for h in (ha, hb):
+        lbp.lbp_set_step_index(h, back)
+    for k in range(3):
+        lbp.lbp_step(ha, 1)
+        ra = np.empty((n, 3))
+        lbp.lbp_particles_read(ha, r=ra)
+        lbp.lbp_step_exchange(hb, None, rb, None)
+        assert np.array_equal(ra, rb), k
     for h in (ha, hb):
         lbp.lbp_destroy(h)
 
