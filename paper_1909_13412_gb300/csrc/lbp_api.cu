@@ -216,7 +216,7 @@ lbp_status capture(lbp_sim *s, int parity) {
 }
 
 // one time step on s0 (graph replay, timed or plain launches); `whole`, when
-// given, is a graph that holds this step with copies around it and replaces
+// given, is a graph that holds this step with its host exchange and replaces
 // the step graph of this parity
 lbp_status step_once(lbp_sim *s, cudaGraphExec_t whole = nullptr) {
     // the VACF correlator runs when the step completes a block of B samples
@@ -247,6 +247,7 @@ lbp_status step_once(lbp_sim *s, cudaGraphExec_t whole = nullptr) {
 }
 
 // the exchange's copies and conversions before and after one step, on s0
+// (pageable or device buffers; page-locked ones take exchange_graph)
 lbp_status exchange_in(lbp_sim *s, const double *f_ext, cudaMemcpyKind kind) {
     const int n = s->np;
     if (n > 0 && f_ext) {

@@ -1,11 +1,13 @@
 // particle_kernels.cu -- two-way coupling kernel of liblbp (sm_103a).
 //
-// k_particles: a block of 256 threads serves 32 particles in three phases.
+// k_particles: a block of 8 PB threads serves PB particles in three phases.
 //   A. eight threads per particle (one per corner) gather u^N at the corners
 //      of the particle's cell from the stored populations (a pull, i.e. the
 //      streamed f^n of Eq. 20): 14 independent loads per thread;
-//   B. one thread per particle fits the Stokeslet flow of Eq. 8, draws the
-//      Philox random force (Eqs. 4-5) and advances V and r (Eqs. 1-2);
+//   B. the Stokeslet flow of Eq. 8 is fitted -- by one thread per particle
+//      (PB = 32), or with few particles by its eight corner lanes (PB = 8) --
+//      and one thread per particle draws the Philox random force (Eqs. 4-5)
+//      and advances V and r (Eqs. 1-2);
 //   C. eight threads per particle append the shares of the reaction force
 //      -F_H (Eq. 9) at the corner nodes to the force records of the row
 //      segments holding those nodes; the stream-collide kernel applies them.
@@ -15,6 +17,9 @@
 // or 32 lanes need it.  Packing 32 particles into the warp that does the FP64
 // work divides its FP64 instruction count per particle by 32; with one
 // particle per warp the FP64 work of the fit dominated the whole time step.
+// That holds while the FP64 pipe is the limit; with a warp or two of
+// particles per SM the fit's dependent chain is, and the lane-per-corner
+// layout shortens it (see PB_WIDE / PB_NARROW below).
 //
 // Precision split.  FP32: the gathered u^N (the lattice arithmetic is FP32).
 // FP64: everything after the gather -- positions, velocities, the cell and
