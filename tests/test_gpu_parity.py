@@ -776,8 +776,8 @@ def test_reduced_precision_one_step(prec, tol):
 def test_reduced_precision_subrun_error(prec, tol_v, tol_u):
     """The 64^3 subrun of the 256^3 storage comparison (256 particles, same number
     density, kT = 1e-4), 300 steps against the FP64 oracle.  Measured on GB300 after
-    1000 steps (max relative error): particle V 3.7e-6 (F32), 2.2e-5 (F16), 2.7e-4
-    (BF16); fluid u 4.8e-6, 2.1e-4, 1.8e-3."""
+    1000 steps (max relative error): particle V 5.7e-6 (F32), 3.8e-5 (F16), 1.9e-4
+    (BF16); fluid u 7.3e-6, 2.9e-4, 1.8e-3."""
     w = wl.BROWNIAN_64
     ps = w.particles()
     nz, ny, nx = w.shape_zyx
@@ -808,8 +808,8 @@ def test_full_size_bench_workload_against_the_oracle(prec, tol_v, tol_f):
     perturbed state, against the FP64 oracle: every particle's F_R bit for bit,
     F_H, V and r within the stated tolerance, and populations on 200000
     sampled nodes.  Tolerances per storage type: FP32 as the small-box tests;
-    BF16 and FP16 at their measured one-step storage errors (BF16 4.7e-3,
-    FP16 5.0e-4 of the deviation scale on the 64^3 subrun)."""
+    BF16 and FP16 at their measured one-step storage errors (BF16 3.9e-3,
+    FP16 4.8e-4 of the deviation scale on the 64^3 subrun)."""
     w = wl.BROWNIAN_256
     nz, ny, nx = w.shape_zyx
     ps = w.particles()
