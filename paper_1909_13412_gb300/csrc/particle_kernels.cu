@@ -449,10 +449,12 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
                 A.r[k * cap + i] = rn;
                 rw = rn;
             }
-            if (A.r_out) A.r_out[3 * (size_t)i + k] = rw;
-            if (A.v_out) A.v_out[3 * (size_t)i + k] = Vn[k];
+            if (FIT8) {  // few particles: straight from the update's registers
+                if (A.r_out) A.r_out[3 * (size_t)i + k] = rw;
+                if (A.v_out) A.v_out[3 * (size_t)i + k] = Vn[k];
+            }
         }
-        if (A.done_flag) __threadfence_system();  // the host copies before the flag
+        if (FIT8 && A.done_flag) __threadfence_system();  // the host copies before the flag
         if (bad) atomicOr(A.err, ERR_NAN);
         if (A.inj)
 #pragma unroll
@@ -495,6 +497,20 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
         }
     }
     __syncthreads();
+
+    // With many particles (one thread per particle), positions and velocities
+    // go to the caller's buffers ([n][3], host memory seen through its device
+    // mapping) as one contiguous span per block, read back from the state
+    // arrays the update above wrote (a pinned particle's entries there are its
+    // unchanged ones), before phase C so that their round trip overlaps it.
+    // (With one lane per corner the update's threads write them directly: the
+    // 64-register budget of that layout has no room for this step beside
+    // phase C's live values.)
+    if (!FIT8 && (A.r_out || A.v_out) && t < 3 * PB && 3LL * i0 + t < 3LL * A.np) {
+        const int pi = i0 + t / 3, k = t - 3 * (t / 3);
+        if (A.r_out) A.r_out[3LL * i0 + t] = A.r[k * cap + pi];
+        if (A.v_out) A.v_out[3LL * i0 + t] = A.v[k * cap + pi];
+    }
 
     if (A.inj && t < 32) {
         // conservation budget: the momentum F_R + F_ext put into the block's
@@ -546,6 +562,8 @@ __global__ void __launch_bounds__(8 * PB, PB == PB_WIDE ? 4 : 16) k_particles(co
     // the last block to finish tells the host that every position and velocity
     // is in its buffers (the lattice pass may still run)
     if (A.done_flag) {
+        // the writes to the host buffers, made visible before the block's ticket
+        if (!FIT8 && t < 3 * PB) __threadfence_system();
         __syncthreads();
         if (t == 0) {
             const unsigned ticket = atomicAdd(A.done_ticket, 1u);

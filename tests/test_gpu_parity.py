@@ -403,6 +403,43 @@ def test_step_exchange_with_one_output_buffer():
         lbp.lbp_destroy(h)
 
 
+def test_step_exchange_with_page_locked_buffers_and_many_particles():
+    """Enough particles for the thread-per-particle layout of the fit (48 or
+    more per SM), with a partial last block and some pinned particles: the
+    blocks write positions and velocities to the page-locked buffers as
+    contiguous spans read back from the particle state, and the run stays
+    bitwise equal to the separate calls, with both outputs and with one."""
+    n = 48 * torch.cuda.get_device_properties(0).multi_processor_count + 35
+    shape = (64, 64, 64)
+    ps = wl.uniform_particles(n, shape, 8.0, 0.5, wl.stokes_radius(0.5, 0.8), 1e-4, 11, 12)
+    pinned = np.zeros(n, np.uint8)
+    pinned[::97] = 1
+    pinned[-1] = 1
+    ha = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=8)
+    hb = gpu_sim(shape, 0.8, ps, kT=1e-4, seed=8)
+    f = np.random.default_rng(3).normal(0, 1e-5, (n, 3))
+    for h in (ha, hb):
+        lbp.lbp_particles_set_external_force(h, f, pinned)
+    assert not lbp.lbp_diagnostics(hb)["fit_per_corner"]
+    pin = lambda: torch.full((n, 3), np.nan, dtype=torch.float64, pin_memory=True).numpy()
+    rb, vb = pin(), pin()
+    for k in range(8):
+        lbp.lbp_step(ha, 1)
+        ra, va = np.empty((n, 3)), np.empty((n, 3))
+        lbp.lbp_particles_read(ha, r=ra, v=va)
+        if k < 6:
+            lbp.lbp_step_exchange(hb, None, rb, vb)
+            assert np.array_equal(va, vb), k
+        else:
+            lbp.lbp_step_exchange(hb, None, rb, None)
+        assert np.array_equal(ra, rb), k
+    assert np.array_equal(rb[pinned == 1], ps.r[pinned == 1])
+    assert np.array_equal(gpu_pops(ha), gpu_pops(hb))
+    for h in (ha, hb):
+        lbp.lbp_check(h)
+        lbp.lbp_destroy(h)
+
+
 def test_set_fluid_is_the_equilibrium_of_eq17():
     """lbp_set_fluid(rho, u) sets f = f^eq(rho~, u) at every node (oracle's Eq. 17)."""
     shape = (5, 6, 7)
