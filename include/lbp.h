@@ -195,17 +195,20 @@ lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
  * and velocities after it (as lbp_particles_read).  The call returns when the
  * host outputs are written (on_device = 0) or, for device pointers, with the
  * work queued on the handle's stream.
- * With page-locked host buffers mapped into the device's address space
- * (cudaHostAlloc / cudaHostRegister with unified addressing) and graphs on,
- * the step's particle kernel itself reads f_ext from and writes r and v to
- * the host buffers, and the step replays as one CUDA graph per buffer parity,
- * cached on the three buffer addresses; positions and velocities are final
- * after the particle kernel (Eqs. 1-2), whose last block then sets a
- * completion flag in page-locked memory, so the call returns (after a bounded
- * poll of that flag: LBP_ECUDA or LBP_ETIMEOUT if the stream fails or the flag
- * does not come) while the lattice pass of the same step still runs.  Every later call on the handle is ordered after it,
- * and the handle's user stream waits for it.  Pageable buffers take plain
- * stream-ordered copies and return after the whole step.                      */
+ * With graphs on and 8-byte aligned buffers that the device can address --
+ * memory of the current device (on_device = 1), or page-locked host memory
+ * mapped into the device's address space (cudaHostAlloc / cudaHostRegister
+ * with unified addressing) -- the step's particle kernel itself reads f_ext
+ * and writes r and v, and the step replays as one CUDA graph per buffer
+ * parity, cached on the three buffer addresses.  For host buffers, positions
+ * and velocities are final after the particle kernel (Eqs. 1-2), whose last
+ * block then sets a completion flag in page-locked memory, so the call
+ * returns (after a bounded poll of that flag: LBP_ECUDA or LBP_ETIMEOUT if
+ * the stream fails or the flag does not come) while the lattice pass of the
+ * same step still runs.  Every later call on the handle is ordered after it,
+ * and the handle's user stream waits for it.  Other buffers (pageable, or
+ * not 8-byte aligned) take plain stream-ordered copies; with host buffers
+ * the call then returns after the whole step.                                 */
 lbp_status lbp_step_exchange(lbp_sim *sim, const double *f_ext, double *r, double *v, int on_device);
 
 /* Bit-exact checkpoints (no counterpart in the paper; the Philox counter of

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <chrono>
@@ -136,9 +137,10 @@ bool radius_ok(double R, int exclude) {
 double nu_of(double tau) { return (tau - 0.5) / 3.0; }
 
 // one time step (see the sequence at the top of this file).  With `io` (the
-// page-locked host buffers of lbp_step_exchange, device views) the particle
-// kernel reads the external forces from the host and writes the positions and
-// velocities back itself, then raises the step's completion flag.
+// buffers of lbp_step_exchange: device buffers, or the device views of
+// page-locked host buffers) the particle kernel reads the external forces and
+// writes the positions and velocities itself, and for host buffers raises the
+// step's completion flag.
 lbp_status enqueue_step(lbp_sim *s, bool timed, const ParticleIO *io = nullptr) {
     Range range("lbp step: particles + lattice pass");
     const void *src = s->f[s->cur];
@@ -280,20 +282,21 @@ lbp_status device_view(double *&p) {
 }
 
 // [forces in, step, positions and velocities out] from and to page-locked host
-// buffers as one graph for the current buffer parity, kept while the same
-// buffers come back: the particle kernel reads and writes the host buffers
-// directly, so the graph holds the step's two kernels only
-lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v, cudaGraphExec_t *out) {
+// buffers or device buffers as one graph for the current buffer parity, kept
+// while the same buffers come back: the particle kernel reads and writes the
+// buffers directly, so the graph holds the step's two kernels only
+lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v, int on_device,
+                          cudaGraphExec_t *out) {
     const int par = s->cur;
     const void *key[3] = {f_ext, r, v};
-    bool same = s->xgraph[par] && s->xkey_np[par] == s->np;
+    bool same = s->xgraph[par] && s->xkey_np[par] == s->np && s->xkey_dev[par] == on_device;
     for (int k = 0; k < 3 && same; ++k) same = s->xkey[par][k] == key[k];
     if (!same) {
         if (s->xgraph[par]) {
             cudaGraphExecDestroy(s->xgraph[par]);
             s->xgraph[par] = nullptr;
         }
-        if (!s->d_xticket) {
+        if (!on_device && !s->d_xticket) {
             TRY(dalloc(&s->d_xticket, 1));
             CK(cudaMemset(s->d_xticket, 0, sizeof(unsigned)));
             CK(cudaHostAlloc((void **)&s->h_xflag, sizeof(long long), cudaHostAllocMapped));
@@ -301,12 +304,14 @@ lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v,
             CK(cudaHostGetDevicePointer((void **)&s->h_xflag_dev, s->h_xflag, 0));
         }
         double *f_dev = const_cast<double *>(f_ext), *r_dev = r, *v_dev = v;
-        TRY(device_view(f_dev));
-        TRY(device_view(r_dev));
-        TRY(device_view(v_dev));
+        if (!on_device) {
+            TRY(device_view(f_dev));
+            TRY(device_view(r_dev));
+            TRY(device_view(v_dev));
+        }
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
-        const ParticleIO io{f_dev, r_dev, v_dev};
+        const ParticleIO io{f_dev, r_dev, v_dev, !on_device};
         lbp_status st = enqueue_step(s, false, &io);
         cudaError_t e = cudaStreamEndCapture(s->s0, &g);
         if (st != LBP_OK) {
@@ -319,6 +324,7 @@ lbp_status exchange_graph(lbp_sim *s, const double *f_ext, double *r, double *v,
         CK(e);
         for (int k = 0; k < 3; ++k) s->xkey[par][k] = key[k];
         s->xkey_np[par] = s->np;
+        s->xkey_dev[par] = on_device;
     }
     *out = s->xgraph[par];
     return LBP_OK;
@@ -346,15 +352,31 @@ lbp_status wait_exchange_flag(lbp_sim *s, long long step) {
 }
 
 // page-locked (or registered) host memory mapped into the device's address
-// space, which kernels can read and write directly
+// space, which kernels can read and write directly (FP64 elements: 8-byte
+// aligned; anything else takes the copies, which accept any alignment)
 bool host_pinned(const void *p) {
     if (!p) return true;
+    if (reinterpret_cast<uintptr_t>(p) % sizeof(double) != 0) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return at.type == cudaMemoryTypeHost && at.devicePointer != nullptr;
+}
+
+// memory of the current device that its kernels can read and write directly
+// (8-byte aligned, as host_pinned)
+bool device_memory(const void *p) {
+    if (!p) return true;
+    if (reinterpret_cast<uintptr_t>(p) % sizeof(double) != 0) return false;
+    int dev = 0;
+    cudaPointerAttributes at;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 
@@ -950,13 +972,22 @@ lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double 
         }
     }
     if (n > 0 && f_ext) s->edits += 1;  // as lbp_particles_set_external_force
-    const bool as_graph = !on_device && n > 0 && s->use_graphs && !s->timing && host_pinned(f_ext) &&
-                          host_pinned(r) && host_pinned(v);
+    const bool as_graph = n > 0 && s->use_graphs && !s->timing &&
+                          (on_device ? device_memory(f_ext) && device_memory(r) && device_memory(v)
+                                     : host_pinned(f_ext) && host_pinned(r) && host_pinned(v));
+    if (as_graph && on_device) {
+        // the particle kernel reads f_ext and writes r, v in device memory;
+        // stream-ordered like any other step
+        cudaGraphExec_t whole = nullptr;
+        TRY(exchange_graph(s, f_ext, r, v, 1, &whole));
+        TRY(step_once(s, whole));
+        return leave(s);
+    }
     if (as_graph) {
         // returns once f_ext has been consumed and r, v are on the host; the
         // step's lattice pass may still run, and later work on s0 follows it
         cudaGraphExec_t whole = nullptr;
-        TRY(exchange_graph(s, f_ext, r, v, &whole));
+        TRY(exchange_graph(s, f_ext, r, v, 0, &whole));
         const long long step = s->step;
         // the flag may hold this step index from before a lbp_set_step_index or a
         // checkpoint load; the previous call's kernel has finished writing it

@@ -461,11 +461,13 @@ struct Sim {
     // graphs
     int use_graphs = 1;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step, by buffer parity
-    // lbp_step_exchange with page-locked host buffers: copies + step, by parity,
-    // with the buffer addresses and particle count it was captured for
+    // lbp_step_exchange with page-locked host or device buffers: the step whose
+    // particle kernel does the I/O, by parity, with the buffer addresses, their
+    // side and the particle count it was captured for
     cudaGraphExec_t xgraph[2] = {nullptr, nullptr};
     const void *xkey[2][3] = {};
     int xkey_np[2] = {0, 0};
+    int xkey_dev[2] = {0, 0};
     int vacf_pending = 0;  // a VACF block runs on s1 (ev_join marks its end)
 
     // kernel timing
@@ -505,11 +507,14 @@ cudaError_t launch_fields(Sim &s, const void *src, double *rho, double *u, doubl
 int budget_blocks(const Sim &s);
 cudaError_t launch_budget(Sim &s, const void *src, double *out, cudaStream_t st);  // [budget_blocks][4]
 // particle_kernels.cu
-// host I/O of one lbp_step_exchange step, done by the particle kernel itself
-// ([n][3] FP64 device views of page-locked host buffers; null: none)
+// the I/O of one lbp_step_exchange step, done by the particle kernel itself
+// ([n][3] FP64: device buffers, or the device views of page-locked host
+// buffers; null: none); `signal`: raise the completion flag for a host
+// waiting on page-locked buffers
 struct ParticleIO {
     const double *fext_in;
     double *r_out, *v_out;
+    bool signal;
 };
 cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t st, const ParticleIO *io = nullptr);
 bool particles_fit_per_corner(const Sim &s);  // the fit of Eq. 8 one lane per corner (few particles)

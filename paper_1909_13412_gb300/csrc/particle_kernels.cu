@@ -636,8 +636,8 @@ cudaError_t launch_particles(Sim &s, const void *src, int parity, cudaStream_t s
     A.fext_in = io ? io->fext_in : nullptr;
     A.r_out = io ? io->r_out : nullptr;
     A.v_out = io ? io->v_out : nullptr;
-    A.done_ticket = io ? s.d_xticket : nullptr;
-    A.done_flag = io ? s.h_xflag_dev : nullptr;
+    A.done_ticket = io && io->signal ? s.d_xticket : nullptr;
+    A.done_flag = io && io->signal ? s.h_xflag_dev : nullptr;
     if (s.nrep == 1) {
         RepTable<1> t;
         t.nrep = 1;

@@ -403,12 +403,15 @@ def test_step_exchange_with_one_output_buffer():
         lbp.lbp_destroy(h)
 
 
-def test_step_exchange_with_page_locked_buffers_and_many_particles():
+@pytest.mark.parametrize("device", [False, True])
+def test_step_exchange_with_many_particles(device):
     """Enough particles for the thread-per-particle layout of the fit (48 or
     more per SM), with a partial last block and some pinned particles: the
-    blocks write positions and velocities to the page-locked buffers as
-    contiguous spans read back from the particle state, and the run stays
-    bitwise equal to the separate calls, with both outputs and with one."""
+    blocks write positions and velocities to the page-locked (or device)
+    buffers as contiguous spans read back from the particle state, and the run
+    stays bitwise equal to the separate calls, with both outputs and with one,
+    with new external forces in some steps and the previous ones kept in
+    others."""
     n = 48 * torch.cuda.get_device_properties(0).multi_processor_count + 35
     shape = (64, 64, 64)
     ps = wl.uniform_particles(n, shape, 8.0, 0.5, wl.stokes_radius(0.5, 0.8), 1e-4, 11, 12)
@@ -421,19 +424,31 @@ def test_step_exchange_with_page_locked_buffers_and_many_particles():
     for h in (ha, hb):
         lbp.lbp_particles_set_external_force(h, f, pinned)
     assert not lbp.lbp_diagnostics(hb)["fit_per_corner"]
-    pin = lambda: torch.full((n, 3), np.nan, dtype=torch.float64, pin_memory=True).numpy()
-    rb, vb = pin(), pin()
+    if device:
+        buf = lambda: torch.full((n, 3), np.nan, dtype=torch.float64, device="cuda")
+        host = lambda x: (torch.cuda.synchronize(), x.cpu().numpy())[1]
+        fb = buf()
+    else:
+        buf = lambda: torch.full((n, 3), np.nan, dtype=torch.float64, pin_memory=True).numpy()
+        host = lambda x: x
+        fb = buf()
+    rb, vb = buf(), buf()
+    g = np.random.default_rng(4)
     for k in range(8):
+        fk = None if k % 3 == 2 else g.normal(0, 1e-5, (n, 3))
+        if fk is not None:
+            lbp.lbp_particles_set_external_force(ha, fk, pinned)  # NULL pinned would unpin
+            fb[:] = torch.tensor(fk, device="cuda") if device else fk
         lbp.lbp_step(ha, 1)
         ra, va = np.empty((n, 3)), np.empty((n, 3))
         lbp.lbp_particles_read(ha, r=ra, v=va)
         if k < 6:
-            lbp.lbp_step_exchange(hb, None, rb, vb)
-            assert np.array_equal(va, vb), k
+            lbp.lbp_step_exchange(hb, None if fk is None else fb, rb, vb)
+            assert np.array_equal(va, host(vb)), k
         else:
-            lbp.lbp_step_exchange(hb, None, rb, None)
-        assert np.array_equal(ra, rb), k
-    assert np.array_equal(rb[pinned == 1], ps.r[pinned == 1])
+            lbp.lbp_step_exchange(hb, None if fk is None else fb, rb, None)
+        assert np.array_equal(ra, host(rb)), k
+    assert np.array_equal(host(rb)[pinned == 1], ps.r[pinned == 1])
     assert np.array_equal(gpu_pops(ha), gpu_pops(hb))
     for h in (ha, hb):
         lbp.lbp_check(h)
