@@ -248,8 +248,9 @@ lbp_status step_once(lbp_sim *s, cudaGraphExec_t whole = nullptr) {
     return LBP_OK;
 }
 
-// the exchange's copies and conversions before and after one step, on s0
-// (pageable or device buffers; page-locked ones take exchange_graph)
+// the exchange's copies and conversions before and after one step, on s0, for
+// buffers the particle kernel cannot address directly (pageable, another
+// device's, not 8-byte aligned); the others take exchange_graph
 lbp_status exchange_in(lbp_sim *s, const double *f_ext, cudaMemcpyKind kind) {
     const int n = s->np;
     if (n > 0 && f_ext) {
@@ -966,7 +967,7 @@ lbp_status lbp_step_exchange(lbp_sim *s, const double *f_ext, double *r, double 
             if (s->xbuf) cudaFree(s->xbuf);
             s->xbuf = nullptr;
             s->xbuf_cap = 0;
-            drop_graphs(s);  // the exchange graphs hold the old buffer
+            drop_graphs(s);  // the particle capacity grew: captured anew
             TRY(dalloc(&s->xbuf, (size_t)9 * s->cap));
             s->xbuf_cap = s->cap;
         }
