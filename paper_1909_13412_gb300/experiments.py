@@ -44,6 +44,21 @@ def nu_of(tau):
     return (tau - 0.5) / 3.0
 
 
+# The physical setting of Figs. 1-2 (Section 3, the figure captions), SI units:
+# box edge, grid interval, time step, kinematic viscosity and density of the
+# fluid, the flow speed of Fig. 1, and the particles of Fig. 2.
+PAPER_SI = {"box": 500e-9, "dx": 5e-9, "dt": 0.5e-12, "nu": 0.89e-6, "rho0": 1.0e3, "U": 1.0,
+            "n_particles": 500, "R": 5e-9, "M": 2e-21}
+
+
+def lattice_units(box, dx, dt, nu, rho0, U, R, M, **_):
+    """The setting in lattice units (dx = dt = rho0 = 1): box edge L in nodes,
+    tau from nu = (tau - 1/2)/3 (Eq. 16), flow speed, radius and mass."""
+    nu_l = nu * dt / dx ** 2
+    return {"L": box / dx, "nu": nu_l, "tau": 0.5 + 3.0 * nu_l, "U": U * dt / dx, "R": R / dx,
+            "M": M / (rho0 * dx ** 3)}
+
+
 def hasimoto_factor(R, L):
     """K(c) of Hasimoto (1959) for a simple cubic array of spheres of radius R
     and period L: the drag is 6 pi eta R U / K."""
@@ -310,7 +325,8 @@ def main(argv=None):
         if a.paper:
             # Section 3 / Fig. 1: box 500 nm, dx = 5 nm, dt = 0.5 ps, nu = 0.89e-6 m^2/s,
             # U = 1 m/s -> L = 100, nu = 0.0178 (tau = 0.5534), U = 1e-4 (lattice units)
-            L, tau, U, steps = 100, 0.5 + 3 * 0.89e-6 * 0.5e-12 / (5e-9) ** 2, 1e-4, 120000
+            lu = lattice_units(**PAPER_SI)
+            L, tau, U, steps = int(round(lu["L"])), lu["tau"], lu["U"], 120000
         else:
             L, tau, U, steps = 40, 0.8, 1e-4, 8000
         rows = []
