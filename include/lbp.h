@@ -185,6 +185,14 @@ lbp_status lbp_particles_read_cells(lbp_sim *sim, int32_t *base, double *frac, i
 /* Number of particles.                                                       */
 lbp_status lbp_particles_count(lbp_sim *sim, int *n);
 
+/* Volume fraction of the particles of box `replica` (-1: the largest over the
+ * boxes): the sum of 4/3 pi R^3 over the box's particles divided by its
+ * nx ny nz nodes.  The method was checked for volume fractions below 0.1
+ * (Section 2.2, closing remarks); lbp_particles_add does not refuse a denser
+ * suspension, and the Python binding warns when one is added.  Host
+ * bookkeeping only: no GPU work.                                              */
+lbp_status lbp_volume_fraction(lbp_sim *sim, int replica, double *phi);
+
 /* Advance nsteps >= 0 time steps (asynchronous on the handle's stream).       */
 lbp_status lbp_step(lbp_sim *sim, int64_t nsteps);
 

@@ -815,6 +815,28 @@ lbp_status lbp_particles_count(lbp_sim *s, int *n) {
     return LBP_OK;
 }
 
+lbp_status lbp_volume_fraction(lbp_sim *s, int replica, double *phi) {
+    CHECK_SIM(s);
+    if (!phi) return fail(LBP_EINVAL, "lbp_volume_fraction: null phi");
+    if (replica < -1 || replica >= s->nrep)
+        return fail(LBP_EINVAL, "lbp_volume_fraction: replica %d outside [-1, %d)", replica, s->nrep);
+    // sphere volumes per box, from the host copies of the radii
+    std::vector<double> vol(s->nrep, 0.0);
+    for (size_t i = 0; i < s->h_radius.size(); ++i) {
+        const double R = s->h_radius[i];
+        vol[s->h_prep[i]] += 4.0 / 3.0 * M_PI * R * R * R;
+    }
+    double best = 0.0;
+    for (int r = 0; r < s->nrep; ++r) {
+        const Rep &rp = s->reps[r];
+        const double f = vol[r] / ((double)rp.nx * rp.ny * rp.nz);
+        if (r == replica) best = f;
+        if (replica < 0) best = std::max(best, f);
+    }
+    *phi = best;
+    return LBP_OK;
+}
+
 lbp_status lbp_particles_set_params(lbp_sim *s, const lbp_particle_params *prm) {
     CHECK_SIM(s);
     s->edits += 1;  // invalidates an adjoint recording

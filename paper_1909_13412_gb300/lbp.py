@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import warnings
 
 import numpy as np
 
@@ -60,6 +61,7 @@ _SIGS = {
     "lbp_particles_read": [_vp, _vp, _vp, _vp, _vp, C.c_int],
     "lbp_particles_read_cells": [_vp, _vp, _vp, C.c_int],
     "lbp_particles_count": [_vp, C.POINTER(C.c_int)],
+    "lbp_volume_fraction": [_vp, C.c_int, C.POINTER(C.c_double)],
     "lbp_step": [_vp, C.c_int64],
     "lbp_set_step_index": [_vp, C.c_int64],
     "lbp_get_step_index": [_vp, C.POINTER(C.c_int64)],
@@ -240,6 +242,7 @@ def lbp_particles_add_to(h: Handle, replica, r, v, mass, gamma, radius=None):
             _ptr(radius, np.float64, n, "radius")]
     d = _same_side(*args)
     _call("lbp_particles_add_to", h.ptr, int(replica), n, *[a[0] for a in args], d)
+    _warn_if_dense(h)
 
 
 def lbp_destroy(h: Handle):
@@ -282,6 +285,24 @@ def lbp_particles_add(h: Handle, r, v, mass, gamma, radius=None):
             _ptr(radius, np.float64, n, "radius")]
     d = _same_side(*args)
     _call("lbp_particles_add", h.ptr, n, *[a[0] for a in args], d)
+    _warn_if_dense(h)
+
+
+# the volume fraction below which the method was checked (Section 2.2)
+PHI_CHECKED = 0.1
+
+
+def lbp_volume_fraction(h: Handle, replica=-1) -> float:
+    phi = C.c_double()
+    _call("lbp_volume_fraction", h.ptr, int(replica), C.byref(phi))
+    return phi.value
+
+
+def _warn_if_dense(h: Handle):
+    phi = lbp_volume_fraction(h)
+    if phi > PHI_CHECKED:
+        warnings.warn(f"particle volume fraction {phi:.3f} exceeds {PHI_CHECKED}, the range the "
+                      "method was checked for (Section 2.2)", RuntimeWarning, stacklevel=3)
 
 
 def lbp_particles_set_params(h: Handle, kT=0.0, seed=0, mode=LBP_STOKESLET, fit_exclude_inside=0):

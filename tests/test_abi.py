@@ -62,6 +62,25 @@ def test_null_handle_is_rejected(lib):
     st = lib.lbp_step(C.c_void_p(0), 1)
     assert st == lbp.LBP_EINVAL
     assert lib.lbp_destroy(C.c_void_p(0)) == lbp.LBP_OK
+    phi = C.c_double(-1.0)
+    assert lib.lbp_volume_fraction(C.c_void_p(0), -1, C.byref(phi)) == lbp.LBP_EINVAL
+    assert phi.value == -1.0
+
+
+def test_binding_warns_when_a_dense_suspension_is_added(monkeypatch):
+    """Section 2.2: the method was checked below a volume fraction of 0.1; the
+    binding warns after an add that takes a box beyond it (host logic only: the
+    fraction itself comes from lbp_volume_fraction)."""
+    import warnings
+    monkeypatch.setattr(lbp, "lbp_volume_fraction", lambda h, replica=-1: 0.125)
+    with pytest.warns(RuntimeWarning, match="volume fraction 0.125 exceeds 0.1"):
+        lbp._warn_if_dense(None)
+    for phi in (0.0, 0.05, 0.1):
+        monkeypatch.setattr(lbp, "lbp_volume_fraction", lambda h, replica=-1, p=phi: p)
+        with warnings.catch_warnings(record=True) as seen:
+            warnings.simplefilter("always")
+            lbp._warn_if_dense(None)
+        assert not seen, phi
 
 
 @pytest.mark.parametrize("boxes,prec", [

@@ -8,6 +8,7 @@ Tolerances (written in each test):
   * particle velocity after 10^3 steps (single kicked particle): 1e-4 relative.
 """
 import math
+import warnings
 
 import numpy as np
 import pytest
@@ -778,6 +779,39 @@ def test_particle_validation():
         lbp.lbp_particles_set_params(h, fit_exclude_inside=1)  # R = 1 > sqrt(3)/2
     with pytest.raises(lbp.LbpError):
         lbp.lbp_particles_set_params(h, kT=-1.0)
+
+
+def test_volume_fraction_and_the_dense_suspension_warning():
+    """Section 2.2: the method was checked below a volume fraction of 0.1.
+    lbp_volume_fraction gives sum(4/3 pi R^3) / nodes per box (-1: the largest),
+    R from Stokes' law where no radius is given; a denser suspension is
+    accepted, with a warning from the binding."""
+    sphere = 4.0 / 3.0 * math.pi
+    h = lbp.lbp_create_batch([(16, 16, 16, 0.8), (8, 8, 8, 0.8)])
+    g = np.random.default_rng(5)
+    with warnings.catch_warnings(record=True) as seen:
+        warnings.simplefilter("always")
+        lbp.lbp_particles_add_to(h, 0, g.random((10, 3)) * 16, np.zeros((10, 3)), np.full(10, 10.0),
+                                 np.full(10, 0.5), np.full(10, 1.0))
+    assert not [w for w in seen if "volume fraction" in str(w.message)]  # below 0.1: none
+    assert lbp.lbp_volume_fraction(h, 0) == pytest.approx(10 * sphere / 4096, rel=1e-12)
+    assert lbp.lbp_volume_fraction(h, 1) == 0.0
+    with pytest.warns(RuntimeWarning, match="volume fraction"):
+        lbp.lbp_particles_add_to(h, 1, g.random((13, 3)) * 8, np.zeros((13, 3)), np.full(13, 10.0),
+                                 np.full(13, 0.5), np.full(13, 1.0))
+    assert h.np == 23
+    assert lbp.lbp_volume_fraction(h, 1) == pytest.approx(13 * sphere / 512, rel=1e-12)
+    assert lbp.lbp_volume_fraction(h, -1) == pytest.approx(13 * sphere / 512, rel=1e-12)
+    for bad in (2, -2):
+        with pytest.raises(lbp.LbpError) as ei:
+            lbp.lbp_volume_fraction(h, bad)
+        assert ei.value.status == lbp.LBP_EINVAL
+    lbp.lbp_destroy(h)
+    h = gpu_sim((16, 16, 16), 0.8)
+    lbp.lbp_particles_add(h, g.random((5, 3)) * 16, np.zeros((5, 3)), np.full(5, 10.0), np.full(5, 0.5))
+    R = 0.5 / (6 * math.pi * 0.1)
+    assert lbp.lbp_volume_fraction(h) == pytest.approx(5 * sphere * R ** 3 / 4096, rel=1e-12)
+    lbp.lbp_destroy(h)
 
 
 def test_stokes_radius_default():
