@@ -21,6 +21,16 @@
 // particles per SM the fit's dependent chain is, and the lane-per-corner
 // layout shortens it (see PB_WIDE / PB_NARROW below).
 //
+// Exchange I/O (lbp_step_exchange with device buffers or page-locked host
+// buffers, seen through their device views): warp 1 reads the block's
+// external forces from the caller's [n][3] buffer and keeps them; the new
+// positions and velocities go to the caller's buffers after phase B, as one
+// contiguous span per block read back from the state arrays (PB = 32) or
+// straight from the update's registers (PB = 8).  For host buffers the last
+// block to finish then sets a completion flag in page-locked memory after a
+// system-scope fence, and the host returns without waiting for the lattice
+// pass.
+//
 // Precision split.  FP32: the gathered u^N (the lattice arithmetic is FP32).
 // FP64: everything after the gather -- positions, velocities, the cell and
 // fraction of r, the relative velocities w_p = u_p - V, e^N, the corner
